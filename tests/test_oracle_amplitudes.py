@@ -1,0 +1,184 @@
+"""Pins for the oracle's |M|^2 (oracle.feynman, oracle.berends_giele, oracle.processes).
+
+* diagram counts of the enumerator: 3 / 16 / 123 (gg -> t tbar + 0/1/2 g);
+* closed forms: gg -> t tbar (Combridge 1979; Ellis-Stirling-Webber Table 7.1),
+  u ubar -> t tbar, e+ e- -> mu+ mu- (photon exchange), per event;
+* gauge invariance: eps_j -> k_j makes the amplitude vanish (Gamma_t = 0);
+* Lorentz invariance under random boosts and rotations;
+* Bose symmetry of identical gluons;
+* two independent algorithms agree: Feynman diagrams with explicit colour vs
+  colour-ordered recursion with the trace-basis colour matrix;
+* massless limit: the helicity configurations that must vanish do, and the
+  MHV partial amplitudes follow the Parke-Taylor form |<f- j>^3 <f+ j>|^2 / prod|s|;
+* |M|^2 scales as g_s^(2 (n_ext - 2)).
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import phase_space as ps
+from oracle.berends_giele import QQbarGluons
+from oracle.feynman import DiagramSet
+from oracle.processes import Process, outgoing_flavours
+
+
+def mdot(a, b):
+    return a[..., 0] * b[..., 0] - np.sum(a[..., 1:] * b[..., 1:], axis=-1)
+
+
+def points(nfin, N, rs=1500.0, masses=None, seed=0):
+    rng = np.random.default_rng(seed)
+    masses = masses if masses is not None else [173.0, 173.0] + [0.0] * (nfin - 2)
+    p = np.zeros((N, nfin + 2, 4))
+    p[:, 0] = [rs / 2, 0, 0, rs / 2]
+    p[:, 1] = [rs / 2, 0, 0, -rs / 2]
+    pm, _ = ps.rambo_diet(rs, rng.random((3 * nfin - 4, N)), nfin)
+    p[:, 2:], _ = ps.massive(pm, masses, rs)
+    return p
+
+
+@pytest.mark.parametrize("name,count", [("gg_ttx", 3), ("gg_ttxg", 16), ("gg_ttxgg", 123),
+                                        ("uux_ttx", 1), ("epem_mupmum", 1)])
+def test_diagram_counts(name, count):
+    assert len(DiagramSet(outgoing_flavours(name)).diagrams) == count
+
+
+def test_gg_ttx_closed_form():
+    mt, rs = 173.0, 1000.0
+    p = points(2, 40, rs, seed=1)
+    proc = Process("gg_ttx", mt=mt)
+    s = rs * rs
+    t1, t2, rho = 2 * mdot(p[:, 0], p[:, 2]) / s, 2 * mdot(p[:, 1], p[:, 2]) / s, 4 * mt * mt / s
+    ref = proc.gs ** 4 * (1 / (6 * t1 * t2) - 3 / 8) * (t1 ** 2 + t2 ** 2 + rho - rho ** 2 / (4 * t1 * t2))
+    np.testing.assert_allclose(proc.me2(p), ref, rtol=1e-13)
+
+
+def test_uux_ttx_closed_form():
+    mt, rs = 173.0, 800.0
+    p = points(2, 40, rs, seed=2)
+    proc = Process("uux_ttx", mt=mt)
+    s = rs * rs
+    t1, t2, rho = 2 * mdot(p[:, 0], p[:, 2]) / s, 2 * mdot(p[:, 1], p[:, 2]) / s, 4 * mt * mt / s
+    ref = proc.gs ** 4 * (4 / 9) * (t1 ** 2 + t2 ** 2 + rho / 2)
+    np.testing.assert_allclose(proc.me2(p), ref, rtol=1e-13)
+
+
+def test_ee_mumu_closed_form():
+    rs = 91.0
+    p = points(2, 40, rs, masses=[0.0, 0.0], seed=3)
+    proc = Process("epem_mupmum")
+    s = rs * rs
+    cos = p[:, 2, 3] / p[:, 2, 0]
+    np.testing.assert_allclose(proc.me2(p), proc.ee ** 4 * (1 + cos ** 2), rtol=1e-13)
+
+
+def _gauge_ratio(proc, p, leg):
+    ext, q = proc.external(p)
+    k = p[:, leg].astype(complex)
+    ext2 = list(ext)
+    ext2[leg] = np.broadcast_to(k[None], (2,) + k.shape).reshape(ext[leg].shape)
+    K = proc.amp.amplitude_terms(ext2, q)
+    c = proc.amp.colour_terms()
+    M = np.einsum("tc,th->ch", c, K.reshape(K.shape[0], -1))
+    single = np.max(np.abs(c)) * np.max(np.abs(K))
+    return np.max(np.abs(M)) / single
+
+
+@pytest.mark.parametrize("name,nfin", [("gg_ttxg", 3), ("gg_ttxgg", 4), ("uux_ttxgg", 4)])
+def test_gauge_invariance(name, nfin):
+    proc = Process(name, wt=0.0)
+    p = points(nfin, 6, seed=4)
+    for leg, part in enumerate(proc.particles):
+        if part == "g":
+            assert _gauge_ratio(proc, p, leg) < 1e-12
+
+
+def _random_lorentz(rng):
+    # rotation
+    A = rng.normal(size=(3, 3))
+    Q, _ = np.linalg.qr(A)
+    R = np.eye(4)
+    R[1:, 1:] = Q * np.sign(np.linalg.det(Q))
+    # boost
+    b = rng.normal(size=3)
+    b *= rng.uniform(0.1, 0.9) / np.linalg.norm(b)
+    g = 1 / math.sqrt(1 - b @ b)
+    B = np.eye(4)
+    B[0, 0] = g
+    B[0, 1:] = B[1:, 0] = g * b
+    B[1:, 1:] += (g - 1) * np.outer(b, b) / (b @ b)
+    return B @ R
+
+
+@pytest.mark.parametrize("name,nfin", [("gg_ttxg", 3), ("gg_ttxgg", 4), ("uux_ttxgg", 4)])
+def test_lorentz_invariance(name, nfin):
+    # Gamma_t = 0: a fixed-width propagator breaks gauge invariance at
+    # O(Gamma/m), and with it the frame independence of the physical-
+    # polarisation sum, so the exact statement is made at zero width
+    rng = np.random.default_rng(5)
+    proc = Process(name, wt=0.0)
+    p = points(nfin, 6, seed=6)
+    L = _random_lorentz(rng)
+    pb = np.einsum("mn,ejn->ejm", L, p)
+    np.testing.assert_allclose(proc.me2(pb), proc.me2(p), rtol=1e-11)
+
+
+def test_bose_symmetry():
+    proc = Process("gg_ttxgg", wt=1.5)
+    p = points(4, 6, seed=7)
+    ref = proc.me2(p)
+    np.testing.assert_allclose(proc.me2(p[:, [1, 0, 2, 3, 4, 5]]), ref, rtol=1e-12)
+    np.testing.assert_allclose(proc.me2(p[:, [0, 1, 2, 3, 5, 4]]), ref, rtol=1e-12)
+
+
+@pytest.mark.parametrize("name,nfin,wt", [("gg_ttx", 2, 0.0), ("gg_ttxg", 3, 0.0), ("gg_ttxg", 3, 1.5),
+                                          ("gg_ttxgg", 4, 1.5)])
+def test_recursion_agrees_with_feynman_diagrams(name, nfin, wt):
+    proc = Process(name, wt=wt)
+    p = points(nfin, 12, seed=8)
+    np.testing.assert_allclose(QQbarGluons(proc).me2(p), proc.me2(p), rtol=2e-12)
+
+
+def test_coupling_power_law():
+    p = points(4, 4, seed=9)
+    a = Process("gg_ttxgg", wt=1.5, gs=1.0).me2(p)
+    b = Process("gg_ttxgg", wt=1.5, gs=1.3).me2(p)
+    np.testing.assert_allclose(b / a, 1.3 ** 8, rtol=1e-12)
+
+
+@pytest.mark.parametrize("name,nfin", [("gg_ttxg", 3), ("gg_ttxgg", 4)])
+def test_massless_helicity_selection_and_parke_taylor(name, nfin):
+    proc = Process(name, mt=0.0)
+    bg = QQbarGluons(proc)
+    p = points(nfin, 5, rs=1000.0, masses=[0.0] * nfin, seed=10)
+    J = bg.partial_amplitudes(p)                  # [sigma, h0..h_{n-1}, N]
+    n = len(proc.particles)
+    q = np.where(np.array(proc.incoming)[None, :, None], -p, p)
+    s = lambda i, j: np.abs(mdot(q[:, i] + q[:, j], q[:, i] + q[:, j]))
+    scale = np.max(np.abs(J))
+    ratios = []
+    for hel in itertools.product((0, 1), repeat=n):
+        lam = [(-1, 1)[h] for h in hel]
+        out = [-l if inc else l for l, inc in zip(lam, proc.incoming)]   # crossing flips helicity
+        neg = [i for i in range(n) if out[i] < 0]
+        pos = [i for i in range(n) if out[i] > 0]
+        Jh = J[(slice(None),) + hel]
+        alive = out[bg.t] == -out[bg.tb] and len(neg) >= 2 and len(pos) >= 2
+        if not alive:
+            assert np.max(np.abs(Jh)) < 1e-12 * scale
+            continue
+        assert np.max(np.abs(Jh)) > 1e-6 * scale
+        if len(neg) == 2 or len(pos) == 2:
+            few = neg if len(neg) == 2 else pos
+            f1 = bg.t if bg.t in few else bg.tb
+            f2 = bg.tb if f1 == bg.t else bg.t
+            j = [i for i in few if i != f1][0]
+            for si, order in enumerate(bg.orders):
+                cyc = [bg.t] + [bg.gluons[o] for o in order] + [bg.tb]
+                den = np.prod([s(cyc[a], cyc[(a + 1) % len(cyc)]) for a in range(len(cyc))], axis=0)
+                pt = s(f1, j) ** 3 * s(f2, j) / den
+                ratios.append(np.abs(Jh[si]) ** 2 / pt)
+    ratios = np.array(ratios)
+    np.testing.assert_allclose(ratios, ratios.flat[0], rtol=1e-10)
