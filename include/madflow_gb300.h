@@ -1,0 +1,180 @@
+/*
+ * madflow_gb300.h -- C ABI of the GB300 (sm_103a) event-parallel Monte Carlo
+ * hot path of MadFlow (arXiv:2211.14056, "Extending MadFlow: device-specific
+ * optimization").
+ *
+ * What the library computes, in the paper's terms:
+ *   - Sec. 1: a tensorised Vegas integration whose events are all independent
+ *     ("parallelized in the event axis", abstract);
+ *   - Sec. 2: the per-event tree-level matrix element of an autogenerated
+ *     process, which the paper moves into a device-specific custom operator
+ *     built from "vertices, spinors or propagators", here one fused kernel per
+ *     process with no per-diagram tensor in device memory (the memory-footprint
+ *     point of Sec. 2 and of Table 1's diagram counts 36 / 267);
+ *   - Sec. 2 (end): the derivative of that operator, which the paper leaves out.
+ *
+ * Conventions shared by every call:
+ *   - units GeV, cross sections in pb;
+ *   - particle order: the two incoming partons, t, tbar, then final gluons;
+ *   - momenta arrays are structure-of-arrays FP64: element (particle i,
+ *     component c, event e) at [(i*4 + c)*n + e], components (E, px, py, pz),
+ *     partonic centre-of-mass frame, beam 1 along +z;
+ *   - ownership: every device buffer is allocated and owned by the caller;
+ *     handles (mf_process, mf_grid) are owned by the library and freed by the
+ *     matching destroy call; device scratch is allocated when a handle is
+ *     created, never inside a compute call;
+ *   - streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Calls are asynchronous on it, except those with host
+ *     outputs, which synchronise that stream before returning;
+ *   - errors: a negative status is an error, a positive one a warning; the
+ *     message of the last failing call on this thread is mf_last_error().  No
+ *     C++ exception crosses this boundary.  On an error nothing has been
+ *     launched unless the status is MF_ERR_CUDA.
+ */
+#ifndef MADFLOW_GB300_H
+#define MADFLOW_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int mf_status;
+#define MF_OK 0
+#define MF_ERR_ARG (-1)         /* invalid argument, size or pointer */
+#define MF_ERR_CUDA (-2)        /* a CUDA runtime call failed (message has the CUDA error) */
+#define MF_ERR_UNSUPPORTED (-3) /* process / precision not built */
+#define MF_ERR_COLOUR (-4)      /* colour matrix: wrong size, not symmetric, not the process's, not TF32-exact */
+#define MF_ERR_TIMEOUT (-5)     /* a bounded device wait gave up */
+#define MF_WARN_NEWTON 1        /* some events missed the massive-rescaling Newton tolerance; their weight is 0 */
+
+/* processes (gluon count of the colour-ordered recursion in brackets) */
+#define MF_PROC_GG_TTX 1   /* g g -> t tbar        [2 gluons; 3 diagrams, 2 colour flows, 16 helicities]  */
+#define MF_PROC_GG_TTXG 2  /* g g -> t tbar g      [3; 16 diagrams, 6 flows, 32 helicities]               */
+#define MF_PROC_GG_TTXGG 3 /* g g -> t tbar g g    [4; 123 diagrams, 24 flows, 64 helicities]             */
+
+/* arithmetic of the matrix element */
+#define MF_FP64 0      /* everything in FP64 */
+#define MF_FP32 1      /* amplitudes and colour sum in FP32 (FMA); sampling, Newton and sums FP64 */
+#define MF_FP32_TC 2   /* FP32 amplitudes, integer colour matrix on tensor cores */
+
+typedef struct mf_process mf_process;
+typedef struct mf_grid mf_grid;
+
+/* Process description (arXiv:2211.14056 Sec. 2: the process-dependent
+ * functions a generator produces; here the parameters of a built kernel). */
+typedef struct {
+  int process_id;              /* MF_PROC_* */
+  int n_ext;                   /* external particles: 4, 5 or 6, must match the process */
+  const double* masses;        /* host [n_ext] GeV: 0, 0, m_t, m_t, 0...; the two top masses must agree */
+  double top_width;            /* Gamma_t >= 0 in the internal top propagators */
+  double g_s;                  /* strong coupling (fixed, no running) */
+  int n_flow;                  /* colour flows: (n_ext-2)! */
+  const int64_t* colour_num;   /* host [n_flow*n_flow] integer numerators of the trace-basis colour matrix */
+  int64_t colour_den;          /* common denominator; C = colour_num / colour_den */
+  double sqrt_s;               /* hadronic sqrt(S) if lumi = 1, else the fixed partonic sqrt(s) */
+  int lumi;                    /* 0: fixed partonic energy; 1: synthetic gluon luminosity */
+  double lumi_N, lumi_a, lumi_b;  /* f(x) = N x^a (1-x)^b per gluon */
+  double pt_cut_g;             /* final-gluon pT threshold (0 disables) */
+  double dr_cut_gg;            /* final-gluon pair Delta R threshold (0 disables) */
+  int precision;               /* MF_FP64, MF_FP32 or MF_FP32_TC */
+} mf_process_desc;
+
+/* Result of one Vegas iteration and of the combination of every iteration
+ * recorded on the grid so far (Lepage's inverse-variance combination). */
+typedef struct {
+  double I_k, sigma_k;         /* this iteration: estimate and its error (pb) */
+  double I, sigma, chi2dof;    /* combination over the grid's recorded iterations */
+  int64_t n_events;            /* events of this iteration */
+  int64_t n_pass;              /* events that passed the cuts (|M|^2 evaluated) */
+  int64_t n_newton_fail;       /* events whose rescaling Newton missed its tolerance */
+  int iterations;              /* iterations recorded on the grid */
+} mf_result;
+
+/* Create a process: validates the description (sizes, masses, colour
+ * matrix against the library's exact trace-basis matrix), selects the built
+ * kernel and sizes its launch from the device's occupancy.  *out is owned by
+ * the library.  Errors: MF_ERR_ARG, MF_ERR_UNSUPPORTED, MF_ERR_COLOUR, MF_ERR_CUDA. */
+mf_status mf_init_process(const mf_process_desc* desc, mf_process** out);
+mf_status mf_destroy_process(mf_process* proc);
+
+/* Vegas dimension of a process: 3 n_final - 4, plus 2 with the luminosity map. */
+mf_status mf_process_ndim(const mf_process* proc, int* ndim);
+
+/* Override the persistent launch: CTAs per SM for the fused and matrix-element
+ * kernels (0 restores the occupancy-derived default).  Used by the autotuner
+ * (arXiv:2211.14056 Sec. 3, Fig. 3: the block configuration matters). */
+mf_status mf_set_ctas_per_sm(mf_process* proc, int ctas_per_sm);
+
+/* Vegas grid (Lepage 1978, the integrator named in Sec. 1): nbins equal bins
+ * per dimension (2 <= nbins <= 64), device edges [ndim][nbins+1], device
+ * scratch for per-CTA partial sums sized for the process's largest launch,
+ * and a host record of the iterations for the combination.  Owned by the
+ * library. */
+mf_status mf_grid_create(const mf_process* proc, int nbins, mf_grid** out);
+mf_status mf_grid_destroy(mf_grid* grid);
+/* Copy the edges to/from host memory [ndim*(nbins+1)] (checkpoint / resume);
+ * these synchronise the device.  mf_grid_set checks that every row starts at
+ * 0, ends at 1 and increases strictly. */
+mf_status mf_grid_get(const mf_grid* grid, double* edges_host);
+mf_status mf_grid_set(mf_grid* grid, const double* edges_host);
+/* Forget the recorded iterations (the combination starts again). */
+mf_status mf_grid_reset(mf_grid* grid);
+
+/* Per-event kinematics of global events 0..n-1 of iteration `iter`:
+ * Philox4x32-10 uniforms, Vegas map, luminosity map, RAMBO on diet, massive
+ * rescaling, cuts.  Outputs (device, each may be NULL):
+ *   momenta   [n_ext][4][n] FP64 (see conventions);
+ *   weight_ps [n] FP64: the event weight without |M|^2 (0 if cut or Newton miss);
+ *   bins      [ndim][n] uint8 Vegas bin of each dimension. */
+mf_status mf_sample(mf_process* proc, const mf_grid* grid, uint64_t seed, int iter, int64_t n, double* momenta,
+                    double* weight_ps, uint8_t* bins, void* stream);
+
+/* Spin/colour averaged |M|^2 of n events (Sec. 2's device operator):
+ *   momenta [n_ext][4][n] FP64 device, me2 [n] FP64 device. */
+mf_status mf_matrix_element(mf_process* proc, int64_t n, const double* momenta, double* me2, void* stream);
+
+/* One Vegas iteration over global events 0..n-1 in the fused kernel
+ * (sample + |M|^2 + accumulate), a deterministic reduction of the per-CTA
+ * sums, and, if refine != 0, the grid refinement.  The iteration is recorded
+ * on the grid and *out (host) receives it and the running combination.
+ * weights (device [n] FP64, may be NULL) receives every event weight.
+ * Synchronises the stream.  Returns MF_WARN_NEWTON if any event missed the
+ * Newton tolerance. */
+mf_status mf_vegas_iterate(mf_process* proc, mf_grid* grid, uint64_t seed, int iter, int64_t n, int refine,
+                           mf_result* out, double* weights, void* stream);
+
+/* The same iteration in two halves, for event sharding across devices
+ * (the Philox counter is the global event index, so a shard is events
+ * first_event .. first_event+n-1 and the result does not depend on the split):
+ *   mf_vegas_accumulate runs the fused kernel on the shard and reduces its
+ *     per-CTA partial sums into the grid's totals buffer (asynchronous);
+ *   mf_grid_totals exposes that device buffer, double[count] laid out as
+ *     [0] sum w, [1] sum w^2, [2 + j*nbins + b] sum w^2 in bin b of dim j,
+ *     then events passing cuts and Newton misses, so that the caller can
+ *     all-reduce it (sum) over shards; the library owns it;
+ *   mf_vegas_finish turns the (summed) totals of n_total events into the
+ *     estimate, refines the grid if asked, records the iteration and fills
+ *     *out like mf_vegas_iterate (synchronises the stream). */
+mf_status mf_vegas_accumulate(mf_process* proc, mf_grid* grid, uint64_t seed, int iter, int64_t first_event,
+                              int64_t n, double* weights, void* stream);
+mf_status mf_grid_totals(mf_grid* grid, double** totals_device, int* count);
+mf_status mf_vegas_finish(mf_process* proc, mf_grid* grid, int64_t n_total, int refine, mf_result* out, void* stream);
+
+/* Measurement utility: sustained FMA-pipe throughput of the current device
+ * (MF_FP32 or MF_FP64) in TFLOP/s from independent FMA chains on every SM,
+ * the denominator of the amplitude kernel's roofline.  Synchronises the device. */
+mf_status mf_fma_throughput(int precision, double* tflops);
+
+/* Message of the last failing call on the calling thread ("" if none). */
+const char* mf_last_error(void);
+
+/* Number of device kernels the library launched since load (all threads). */
+int64_t mf_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MADFLOW_GB300_H */

@@ -1,0 +1,11 @@
+"""GB300-native event-parallel MadFlow hot path (arXiv:2211.14056).
+
+The compute path is the CUDA library ``lib/libmadflow_gb300.so`` behind the C
+ABI in ``include/madflow_gb300.h``; ``binding`` marshals arguments to it with
+ctypes (PyTorch tensors supply device memory and streams).  There is no CPU
+fallback: importing the binding without the built library raises.
+"""
+from .binding import (  # noqa: F401
+    MF_FP32, MF_FP32_TC, MF_FP64, MF_PROC_GG_TTX, MF_PROC_GG_TTXG, MF_PROC_GG_TTXGG,
+    Grid, MFError, Process, fma_throughput, kernel_launches, library_path, load_library,
+)

@@ -1,0 +1,256 @@
+"""ctypes binding of include/madflow_gb300.h (argument marshalling only).
+
+Every computation runs in the CUDA library; these wrappers check Python-side
+arguments (dtype, device, size, contiguity of torch tensors), pass raw
+pointers and the current CUDA stream, and turn negative status codes into
+``MFError`` carrying ``mf_last_error()``.  Loading fails loudly if the library
+has not been built.
+"""
+import ctypes as C
+import functools
+import math
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(HERE, "lib", "libmadflow_gb300.so")
+
+MF_OK, MF_ERR_ARG, MF_ERR_CUDA, MF_ERR_UNSUPPORTED, MF_ERR_COLOUR, MF_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+MF_WARN_NEWTON = 1
+MF_PROC_GG_TTX, MF_PROC_GG_TTXG, MF_PROC_GG_TTXGG = 1, 2, 3
+MF_FP64, MF_FP32, MF_FP32_TC = 0, 1, 2
+
+_NGLUON = {MF_PROC_GG_TTX: 2, MF_PROC_GG_TTXG: 3, MF_PROC_GG_TTXGG: 4}
+
+
+class MFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+class ProcessDesc(C.Structure):
+    _fields_ = [
+        ("process_id", C.c_int), ("n_ext", C.c_int), ("masses", C.POINTER(C.c_double)),
+        ("top_width", C.c_double), ("g_s", C.c_double), ("n_flow", C.c_int),
+        ("colour_num", C.POINTER(C.c_int64)), ("colour_den", C.c_int64), ("sqrt_s", C.c_double),
+        ("lumi", C.c_int), ("lumi_N", C.c_double), ("lumi_a", C.c_double), ("lumi_b", C.c_double),
+        ("pt_cut_g", C.c_double), ("dr_cut_gg", C.c_double), ("precision", C.c_int),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [
+        ("I_k", C.c_double), ("sigma_k", C.c_double), ("I", C.c_double), ("sigma", C.c_double),
+        ("chi2dof", C.c_double), ("n_events", C.c_int64), ("n_pass", C.c_int64),
+        ("n_newton_fail", C.c_int64), ("iterations", C.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = {
+    "mf_init_process": (C.c_int, [C.POINTER(ProcessDesc), C.POINTER(C.c_void_p)]),
+    "mf_destroy_process": (C.c_int, [C.c_void_p]),
+    "mf_process_ndim": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "mf_set_ctas_per_sm": (C.c_int, [C.c_void_p, C.c_int]),
+    "mf_grid_create": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "mf_grid_destroy": (C.c_int, [C.c_void_p]),
+    "mf_grid_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "mf_grid_set": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "mf_grid_reset": (C.c_int, [C.c_void_p]),
+    "mf_sample": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_int64, C.c_void_p, C.c_void_p,
+                            C.c_void_p, C.c_void_p]),
+    "mf_matrix_element": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mf_vegas_iterate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_int64, C.c_int,
+                                   C.POINTER(Result), C.c_void_p, C.c_void_p]),
+    "mf_vegas_accumulate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_int64, C.c_int64,
+                                      C.c_void_p, C.c_void_p]),
+    "mf_grid_totals": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int)]),
+    "mf_vegas_finish": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.POINTER(Result), C.c_void_p]),
+    "mf_fma_throughput": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "mf_last_error": (C.c_char_p, []),
+    "mf_kernel_launches": (C.c_int64, []),
+}
+
+
+def library_path():
+    return _LIB_PATH
+
+
+@functools.lru_cache(maxsize=None)
+def load_library():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: build it with `python -m paper_2211_14056_gb300.build` "
+                          "(there is no CPU fallback)")
+    lib = C.CDLL(_LIB_PATH)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+def _check(st, allow_warn=True):
+    if st < 0 or (st > 0 and not allow_warn):
+        raise MFError(st, load_library().mf_last_error().decode())
+    return st
+
+
+def kernel_launches():
+    return int(load_library().mf_kernel_launches())
+
+
+def fma_throughput(precision):
+    """Measured FMA-pipe throughput of the current device, TFLOP/s."""
+    t = C.c_double()
+    _check(load_library().mf_fma_throughput(precision, C.byref(t)))
+    return t.value
+
+
+@functools.lru_cache(maxsize=None)
+def colour_matrix(ngluons):
+    """(integer numerators [n!*n!], denominator) of the trace-basis colour matrix."""
+    from .gen_tables import colour_matrix_exact
+    _, M, D = colour_matrix_exact(ngluons)
+    return [x for row in M for x in row], D
+
+
+def _ptr(t, dtype, numel, name):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name}: need a contiguous CUDA tensor of {dtype}")
+    if t.numel() < numel:
+        raise ValueError(f"{name}: need at least {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Process:
+    """A configured process (mf_init_process) and its launches."""
+
+    def __init__(self, process_id, mt=173.0, wt=0.0, gs=1.2177, sqrt_s=1000.0, lumi=False,
+                 lumi_N=1.0, lumi_a=-1.1, lumi_b=5.0, pt_cut=0.0, dr_cut=0.0, precision=MF_FP64,
+                 colour=None):
+        lib = load_library()
+        ng = _NGLUON.get(process_id)
+        if ng is None:
+            raise MFError(MF_ERR_UNSUPPORTED, "unknown process id")
+        self.ngluons, self.n_ext = ng, ng + 2
+        masses = (C.c_double * self.n_ext)(*([0.0, 0.0, mt, mt] + [0.0] * (ng - 2)))
+        num, den = colour if colour is not None else colour_matrix(ng)
+        cnum = (C.c_int64 * len(num))(*num)
+        d = ProcessDesc(process_id, self.n_ext, masses, wt, gs, math.factorial(ng), cnum, den, sqrt_s,
+                        1 if lumi else 0, lumi_N, lumi_a, lumi_b, pt_cut, dr_cut, precision)
+        h = C.c_void_p()
+        _check(lib.mf_init_process(C.byref(d), C.byref(h)))
+        self._h = h
+        nd = C.c_int()
+        _check(lib.mf_process_ndim(h, C.byref(nd)))
+        self.ndim = nd.value
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().mf_destroy_process(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_ctas_per_sm(self, c):
+        _check(load_library().mf_set_ctas_per_sm(self._h, int(c)))
+
+    def grid(self, nbins=50):
+        return Grid(self, nbins)
+
+    def sample(self, grid, seed, it, n, momenta=None, weight_ps=None, bins=None, stream=None):
+        import torch
+        p = _ptr(momenta, torch.float64, self.n_ext * 4 * n, "momenta")
+        w = _ptr(weight_ps, torch.float64, n, "weight_ps")
+        b = _ptr(bins, torch.uint8, self.ndim * n, "bins")
+        _check(load_library().mf_sample(self._h, grid._h, seed, it, n, p, w, b, _stream(stream)))
+
+    def matrix_element(self, n, momenta, me2, stream=None):
+        import torch
+        _check(load_library().mf_matrix_element(
+            self._h, n, _ptr(momenta, torch.float64, self.n_ext * 4 * n, "momenta"),
+            _ptr(me2, torch.float64, n, "me2"), _stream(stream)))
+
+    def vegas_iterate(self, grid, seed, it, n, refine=True, weights=None, stream=None):
+        import torch
+        r = Result()
+        st = _check(load_library().mf_vegas_iterate(
+            self._h, grid._h, seed, it, n, 1 if refine else 0, C.byref(r),
+            _ptr(weights, torch.float64, n, "weights"), _stream(stream)))
+        out = r.as_dict()
+        out["status"] = st
+        return out
+
+    def vegas_accumulate(self, grid, seed, it, first_event, n, weights=None, stream=None):
+        import torch
+        _check(load_library().mf_vegas_accumulate(
+            self._h, grid._h, seed, it, first_event, n, _ptr(weights, torch.float64, n, "weights"),
+            _stream(stream)))
+
+    def vegas_finish(self, grid, n_total, refine=True, stream=None):
+        r = Result()
+        st = _check(load_library().mf_vegas_finish(self._h, grid._h, n_total, 1 if refine else 0, C.byref(r),
+                                                   _stream(stream)))
+        out = r.as_dict()
+        out["status"] = st
+        return out
+
+
+class Grid:
+    """A Vegas grid (mf_grid_create) bound to a process."""
+
+    def __init__(self, proc, nbins=50):
+        self.proc, self.nbins, self.ndim = proc, nbins, proc.ndim
+        h = C.c_void_p()
+        _check(load_library().mf_grid_create(proc._h, nbins, C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().mf_grid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get(self):
+        import numpy as np
+        out = np.empty((self.ndim, self.nbins + 1))
+        _check(load_library().mf_grid_get(self._h, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def set(self, edges):
+        import numpy as np
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        if e.shape != (self.ndim, self.nbins + 1):
+            raise ValueError(f"edges must have shape {(self.ndim, self.nbins + 1)}")
+        _check(load_library().mf_grid_set(self._h, e.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def reset(self):
+        _check(load_library().mf_grid_reset(self._h))
+
+    def totals(self):
+        """(device address, length) of the accumulated totals (double[length])."""
+        ptr, cnt = C.c_void_p(), C.c_int()
+        _check(load_library().mf_grid_totals(self._h, C.byref(ptr), C.byref(cnt)))
+        return ptr.value, cnt.value

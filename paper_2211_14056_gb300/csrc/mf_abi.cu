@@ -1,0 +1,425 @@
+// C ABI of the library (declarations and their documentation: include/madflow_gb300.h).
+// Host side only: argument checks, handle lifetime, launch sizing, the Vegas
+// iteration record and its combination (Lepage's inverse-variance mean).
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "madflow_gb300.h"
+#include "mf_kernels.cuh"
+
+using namespace mf;
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<int64_t> g_launches{0};
+
+mf_status fail(mf_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+mf_status cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return MF_ERR_CUDA;
+}
+
+#define MF_CUDA(call, where)                         \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+int factorial(int n) { return n <= 1 ? 1 : n * factorial(n - 1); }
+
+const int* lib_colour(int ng, int* den) {
+  switch (ng) {
+    case 2: *den = kColourDen2; return kColourNum2;
+    case 3: *den = kColourDen3; return kColourNum3;
+    case 4: *den = kColourDen4; return kColourNum4;
+  }
+  return nullptr;
+}
+
+}  // namespace
+
+struct mf_process {
+  int ng = 0, ndim = 0, precision = 0, device = 0, sms = 0;
+  SampleParams sp{};
+  MeParams mp{};
+  int me_ctas = 1;
+  size_t me_smem = 0;
+  int ctas_override = 0;
+};
+
+struct mf_grid {
+  const mf_process* proc = nullptr;
+  int ndim = 0, nbins = 0;
+  int max_blocks = 0;
+  int fused_ctas = 1;
+  size_t fused_smem = 0;
+  double* d_edges = nullptr;
+  double* d_partials = nullptr;
+  unsigned long long* d_counters = nullptr;
+  double* d_totals = nullptr;   // [2 + ndim*nbins + 2]: sums, histogram, passing events, Newton misses
+  double* d_result = nullptr;
+  double* h_result = nullptr;
+  std::vector<double> Ik, vark;
+};
+
+namespace {
+
+cudaError_t dispatch_fused_config(int ng, int prec, int ndim, int nbins, size_t* smem, int* ctas) {
+  const int p = prec == MF_FP64 ? 0 : 1;
+  switch (ng) {
+    case 2: return fused_config<2>(p, ndim, nbins, smem, ctas);
+    case 3: return fused_config<3>(p, ndim, nbins, smem, ctas);
+    case 4: return fused_config<4>(p, ndim, nbins, smem, ctas);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch_me_config(int ng, int prec, size_t* smem, int* ctas) {
+  const int p = prec == MF_FP64 ? 0 : 1;
+  switch (ng) {
+    case 2: return me_config<2>(p, smem, ctas);
+    case 3: return me_config<3>(p, smem, ctas);
+    case 4: return me_config<4>(p, smem, ctas);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int effective_ctas(const mf_process* p, int occupancy) {
+  if (p->ctas_override > 0 && p->ctas_override < occupancy) return p->ctas_override;
+  return occupancy < 1 ? 1 : occupancy;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mf_last_error(void) { return g_err.c_str(); }
+
+int64_t mf_kernel_launches(void) { return g_launches.load(); }
+
+mf_status mf_init_process(const mf_process_desc* d, mf_process** out) {
+  if (d == nullptr || out == nullptr) return fail(MF_ERR_ARG, "mf_init_process: null argument");
+  *out = nullptr;
+  int ng = 0;
+  switch (d->process_id) {
+    case MF_PROC_GG_TTX: ng = 2; break;
+    case MF_PROC_GG_TTXG: ng = 3; break;
+    case MF_PROC_GG_TTXGG: ng = 4; break;
+    default: return fail(MF_ERR_UNSUPPORTED, "mf_init_process: unknown process_id");
+  }
+  if (d->n_ext != ng + 2) return fail(MF_ERR_ARG, "mf_init_process: n_ext does not match the process");
+  if (d->masses == nullptr) return fail(MF_ERR_ARG, "mf_init_process: masses is null");
+  const double mt = d->masses[2];
+  for (int i = 0; i < d->n_ext; ++i) {
+    const bool top = (i == 2 || i == 3);
+    if (!std::isfinite(d->masses[i]) || (top ? !(d->masses[i] > 0) : d->masses[i] != 0.0))
+      return fail(MF_ERR_ARG, "mf_init_process: masses must be (0, 0, m_t, m_t, 0, ...) with m_t > 0");
+  }
+  if (d->masses[3] != mt) return fail(MF_ERR_ARG, "mf_init_process: top and antitop masses differ");
+  if (!(d->top_width >= 0) || !std::isfinite(d->top_width)) return fail(MF_ERR_ARG, "mf_init_process: bad top_width");
+  if (!(d->g_s > 0) || !std::isfinite(d->g_s)) return fail(MF_ERR_ARG, "mf_init_process: bad g_s");
+  if (d->precision != MF_FP64 && d->precision != MF_FP32 && d->precision != MF_FP32_TC)
+    return fail(MF_ERR_ARG, "mf_init_process: bad precision");
+  if (d->precision == MF_FP32_TC) return fail(MF_ERR_UNSUPPORTED, "mf_init_process: MF_FP32_TC is not built");
+  // colour matrix: must be the library's exact trace-basis matrix
+  if (d->n_flow != factorial(ng)) return fail(MF_ERR_COLOUR, "mf_init_process: n_flow must be (n_ext-2)!");
+  if (d->colour_num == nullptr || d->colour_den <= 0) return fail(MF_ERR_COLOUR, "mf_init_process: colour matrix missing");
+  int lden = 1;
+  const int* lnum = lib_colour(ng, &lden);
+  const int nf = d->n_flow;
+  for (int a = 0; a < nf; ++a)
+    for (int b = 0; b < nf; ++b) {
+      const int64_t x = d->colour_num[a * nf + b];
+      if (x != d->colour_num[b * nf + a]) return fail(MF_ERR_COLOUR, "mf_init_process: colour matrix not symmetric");
+      // x / den == lnum / lden  <=>  x * lden == lnum * den
+      if (x * int64_t(lden) != int64_t(lnum[a * nf + b]) * d->colour_den)
+        return fail(MF_ERR_COLOUR, "mf_init_process: colour matrix differs from the process's trace-basis matrix");
+      if (std::abs(lnum[a * nf + b]) > 2048)
+        return fail(MF_ERR_COLOUR, "mf_init_process: scaled colour matrix is not TF32-exact");
+    }
+  if (!(d->sqrt_s > 2 * mt) || !std::isfinite(d->sqrt_s)) return fail(MF_ERR_ARG, "mf_init_process: sqrt_s must exceed 2 m_t");
+  if (d->lumi != 0 && d->lumi != 1) return fail(MF_ERR_ARG, "mf_init_process: lumi must be 0 or 1");
+  if (d->lumi && !(d->lumi_N > 0 && d->lumi_b >= 0 && std::isfinite(d->lumi_a)))
+    return fail(MF_ERR_ARG, "mf_init_process: bad luminosity parameters");
+  if (!(d->pt_cut_g >= 0) || !(d->dr_cut_gg >= 0)) return fail(MF_ERR_ARG, "mf_init_process: cuts must be >= 0");
+
+  mf_process* p = new mf_process();
+  p->ng = ng;
+  p->precision = d->precision;
+  const int n = ng;   // final-state particles: t, tbar and ng - 2 gluons
+  p->ndim = 3 * n - 4 + (d->lumi ? 2 : 0);
+  SampleParams& sp = p->sp;
+  sp.n_final = n;
+  sp.ndim = p->ndim;
+  sp.nbins = 50;
+  sp.lumi = d->lumi;
+  sp.sqrt_s = d->sqrt_s;
+  sp.tau0 = 4.0 * mt * mt / (d->sqrt_s * d->sqrt_s);
+  sp.log_tau0 = std::log(sp.tau0);
+  sp.lumi_N = d->lumi_N;
+  sp.lumi_a = d->lumi_a;
+  sp.lumi_b = d->lumi_b;
+  sp.mt = mt;
+  sp.pt_cut2 = d->pt_cut_g * d->pt_cut_g;
+  sp.dr_cut2 = d->dr_cut_gg * d->dr_cut_gg;
+  const double pi = 3.14159265358979323846;
+  sp.phi_const = std::pow(2 * pi, 4 - 3 * n) * std::pow(pi / 2, n - 1) / (factorial(n - 1) * factorial(n - 2));
+  MeParams& mp = p->mp;
+  mp.mt = mt;
+  mp.mw = mt * d->top_width;
+  const int sid = factorial(ng - 2);        // identical final-state gluons
+  mp.norm = std::pow(d->g_s, 2 * ng) / (256.0 * sid * lden);
+
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (e == cudaSuccess) e = dispatch_me_config(ng, p->precision, &p->me_smem, &p->me_ctas);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "mf_init_process");
+  }
+  if (p->me_ctas < 1) {
+    delete p;
+    return fail(MF_ERR_CUDA, "mf_init_process: matrix-element kernel does not fit on an SM");
+  }
+  *out = p;
+  g_err.clear();
+  return MF_OK;
+}
+
+mf_status mf_destroy_process(mf_process* p) {
+  delete p;
+  return MF_OK;
+}
+
+mf_status mf_process_ndim(const mf_process* p, int* ndim) {
+  if (p == nullptr || ndim == nullptr) return fail(MF_ERR_ARG, "mf_process_ndim: null argument");
+  *ndim = p->ndim;
+  return MF_OK;
+}
+
+mf_status mf_set_ctas_per_sm(mf_process* p, int c) {
+  if (p == nullptr || c < 0) return fail(MF_ERR_ARG, "mf_set_ctas_per_sm: bad argument");
+  p->ctas_override = c;
+  return MF_OK;
+}
+
+mf_status mf_grid_create(const mf_process* p, int nbins, mf_grid** out) {
+  if (p == nullptr || out == nullptr) return fail(MF_ERR_ARG, "mf_grid_create: null argument");
+  if (nbins < 2 || nbins > 64) return fail(MF_ERR_ARG, "mf_grid_create: nbins must be in [2, 64]");
+  *out = nullptr;
+  mf_grid* g = new mf_grid();
+  g->proc = p;
+  g->ndim = p->ndim;
+  g->nbins = nbins;
+  cudaError_t e = dispatch_fused_config(p->ng, p->precision, g->ndim, nbins, &g->fused_smem, &g->fused_ctas);
+  if (e == cudaSuccess && g->fused_ctas < 1) e = cudaErrorInvalidConfiguration;
+  g->max_blocks = p->sms * (g->fused_ctas < 1 ? 1 : g->fused_ctas);
+  std::vector<double> edges(size_t(g->ndim) * (nbins + 1));
+  for (int j = 0; j < g->ndim; ++j)
+    for (int b = 0; b <= nbins; ++b) edges[size_t(j) * (nbins + 1) + b] = double(b) / nbins;
+  const size_t nacc = 2 + size_t(g->ndim) * nbins;
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_edges, sizeof(double) * edges.size());
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_partials, sizeof(double) * nacc * g->max_blocks);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_counters, sizeof(unsigned long long) * 2 * g->max_blocks);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_totals, sizeof(double) * (nacc + 2));
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_result, sizeof(double) * 8);
+  if (e == cudaSuccess) e = cudaMallocHost(&g->h_result, sizeof(double) * 8);
+  if (e == cudaSuccess) e = cudaMemcpy(g->d_edges, edges.data(), sizeof(double) * edges.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    mf_grid_destroy(g);
+    return cuda_fail(e, "mf_grid_create");
+  }
+  *out = g;
+  return MF_OK;
+}
+
+mf_status mf_grid_destroy(mf_grid* g) {
+  if (g == nullptr) return MF_OK;
+  cudaFree(g->d_edges);
+  cudaFree(g->d_partials);
+  cudaFree(g->d_counters);
+  cudaFree(g->d_totals);
+  cudaFree(g->d_result);
+  cudaFreeHost(g->h_result);
+  delete g;
+  return MF_OK;
+}
+
+mf_status mf_grid_get(const mf_grid* g, double* h) {
+  if (g == nullptr || h == nullptr) return fail(MF_ERR_ARG, "mf_grid_get: null argument");
+  MF_CUDA(cudaMemcpy(h, g->d_edges, sizeof(double) * g->ndim * (g->nbins + 1), cudaMemcpyDeviceToHost), "mf_grid_get");
+  return MF_OK;
+}
+
+mf_status mf_grid_set(mf_grid* g, const double* h) {
+  if (g == nullptr || h == nullptr) return fail(MF_ERR_ARG, "mf_grid_set: null argument");
+  for (int j = 0; j < g->ndim; ++j) {
+    const double* e = h + size_t(j) * (g->nbins + 1);
+    if (e[0] != 0.0 || e[g->nbins] != 1.0) return fail(MF_ERR_ARG, "mf_grid_set: a row does not span [0, 1]");
+    for (int b = 0; b < g->nbins; ++b)
+      if (!(e[b + 1] > e[b])) return fail(MF_ERR_ARG, "mf_grid_set: edges must increase strictly");
+  }
+  MF_CUDA(cudaMemcpy(g->d_edges, h, sizeof(double) * g->ndim * (g->nbins + 1), cudaMemcpyHostToDevice), "mf_grid_set");
+  return MF_OK;
+}
+
+mf_status mf_grid_reset(mf_grid* g) {
+  if (g == nullptr) return fail(MF_ERR_ARG, "mf_grid_reset: null argument");
+  g->Ik.clear();
+  g->vark.clear();
+  return MF_OK;
+}
+
+mf_status mf_sample(mf_process* p, const mf_grid* g, uint64_t seed, int iter, int64_t n, double* momenta,
+                    double* weight_ps, uint8_t* bins, void* stream) {
+  if (p == nullptr || g == nullptr || n < 0) return fail(MF_ERR_ARG, "mf_sample: bad argument");
+  if (g->proc != p) return fail(MF_ERR_ARG, "mf_sample: grid belongs to another process");
+  if (n == 0) return MF_OK;
+  SampleParams sp = p->sp;
+  sp.nbins = g->nbins;
+  MF_CUDA(launch_sample(sp, g->d_edges, n, seed, iter, momenta, weight_ps, bins, (cudaStream_t)stream), "mf_sample");
+  g_launches.fetch_add(1);
+  return MF_OK;
+}
+
+mf_status mf_matrix_element(mf_process* p, int64_t n, const double* momenta, double* me2, void* stream) {
+  if (p == nullptr || n < 0) return fail(MF_ERR_ARG, "mf_matrix_element: bad argument");
+  if (n == 0) return MF_OK;
+  if (momenta == nullptr || me2 == nullptr) return fail(MF_ERR_ARG, "mf_matrix_element: null buffer");
+  const int epb = kWarps * (32 / (2 << p->ng));   // events per CTA pass
+  const int64_t need = (n + epb - 1) / epb;
+  const int64_t cap = int64_t(p->sms) * effective_ctas(p, p->me_ctas);
+  const int grid = int(need < cap ? need : cap);
+  cudaError_t e;
+  switch (p->ng) {
+    case 2: e = launch_matrix_element<2>(p->precision == MF_FP64 ? 0 : 1, p->mp, n, momenta, me2, grid, (cudaStream_t)stream); break;
+    case 3: e = launch_matrix_element<3>(p->precision == MF_FP64 ? 0 : 1, p->mp, n, momenta, me2, grid, (cudaStream_t)stream); break;
+    default: e = launch_matrix_element<4>(p->precision == MF_FP64 ? 0 : 1, p->mp, n, momenta, me2, grid, (cudaStream_t)stream); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "mf_matrix_element");
+  g_launches.fetch_add(1);
+  return MF_OK;
+}
+
+mf_status mf_vegas_accumulate(mf_process* p, mf_grid* g, uint64_t seed, int iter, int64_t first_event, int64_t n,
+                              double* weights, void* stream) {
+  if (p == nullptr || g == nullptr) return fail(MF_ERR_ARG, "mf_vegas_accumulate: null argument");
+  if (g->proc != p) return fail(MF_ERR_ARG, "mf_vegas_accumulate: grid belongs to another process");
+  if (n < 1 || first_event < 0) return fail(MF_ERR_ARG, "mf_vegas_accumulate: need n >= 1 and first_event >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  SampleParams sp = p->sp;
+  sp.nbins = g->nbins;
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  const int64_t cap = int64_t(p->sms) * effective_ctas(p, g->fused_ctas);
+  const int grid = int(ntiles < cap ? ntiles : cap);
+  const int prec = p->precision == MF_FP64 ? 0 : 1;
+  cudaError_t e;
+  switch (p->ng) {
+    case 2: e = launch_fused<2>(prec, sp, p->mp, g->d_edges, first_event, n, seed, iter, g->d_partials, g->d_counters, weights, grid, s); break;
+    case 3: e = launch_fused<3>(prec, sp, p->mp, g->d_edges, first_event, n, seed, iter, g->d_partials, g->d_counters, weights, grid, s); break;
+    default: e = launch_fused<4>(prec, sp, p->mp, g->d_edges, first_event, n, seed, iter, g->d_partials, g->d_counters, weights, grid, s); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "mf_vegas_accumulate (fused kernel)");
+  g_launches.fetch_add(1);
+  MF_CUDA(launch_reduce(g->d_partials, g->d_counters, grid, g->ndim, g->nbins, g->d_totals, s),
+          "mf_vegas_accumulate (reduce)");
+  g_launches.fetch_add(1);
+  return MF_OK;
+}
+
+mf_status mf_grid_totals(mf_grid* g, double** totals, int* count) {
+  if (g == nullptr || totals == nullptr || count == nullptr) return fail(MF_ERR_ARG, "mf_grid_totals: null argument");
+  *totals = g->d_totals;
+  *count = 2 + g->ndim * g->nbins + 2;
+  return MF_OK;
+}
+
+mf_status mf_vegas_finish(mf_process* p, mf_grid* g, int64_t n_total, int refine, mf_result* out, void* stream) {
+  if (p == nullptr || g == nullptr || out == nullptr) return fail(MF_ERR_ARG, "mf_vegas_finish: null argument");
+  if (g->proc != p) return fail(MF_ERR_ARG, "mf_vegas_finish: grid belongs to another process");
+  if (n_total < 2) return fail(MF_ERR_ARG, "mf_vegas_finish: need at least 2 events");
+  cudaStream_t s = (cudaStream_t)stream;
+  MF_CUDA(launch_finish(g->d_totals, g->ndim, g->nbins, n_total, refine, g->d_edges, g->d_result, s),
+          "mf_vegas_finish (estimate)");
+  g_launches.fetch_add(1);
+  MF_CUDA(cudaMemcpyAsync(g->h_result, g->d_result, sizeof(double) * 6, cudaMemcpyDeviceToHost, s), "mf_vegas_finish (copy)");
+  MF_CUDA(cudaStreamSynchronize(s), "mf_vegas_finish (sync)");
+  const double* r = g->h_result;
+  out->I_k = r[2];
+  out->sigma_k = std::sqrt(r[3] > 0 ? r[3] : 0.0);
+  out->n_events = n_total;
+  out->n_pass = int64_t(r[4]);
+  out->n_newton_fail = int64_t(r[5]);
+  g->Ik.push_back(r[2]);
+  g->vark.push_back(r[3]);
+  out->iterations = int(g->Ik.size());
+  double sw = 0, swi = 0;
+  bool ok = true;
+  for (size_t k = 0; k < g->Ik.size(); ++k) {
+    if (!(g->vark[k] > 0)) { ok = false; break; }
+    sw += 1.0 / g->vark[k];
+    swi += g->Ik[k] / g->vark[k];
+  }
+  if (!ok) {
+    out->I = out->sigma = out->chi2dof = NAN;
+    return fail(MF_ERR_ARG, "mf_vegas_finish: an iteration has zero variance; combination undefined");
+  }
+  out->I = swi / sw;
+  out->sigma = 1.0 / std::sqrt(sw);
+  double chi = 0;
+  for (size_t k = 0; k < g->Ik.size(); ++k) chi += (g->Ik[k] - out->I) * (g->Ik[k] - out->I) / g->vark[k];
+  out->chi2dof = g->Ik.size() > 1 ? chi / double(g->Ik.size() - 1) : 0.0;
+  return out->n_newton_fail > 0 ? MF_WARN_NEWTON : MF_OK;
+}
+
+mf_status mf_vegas_iterate(mf_process* p, mf_grid* g, uint64_t seed, int iter, int64_t n, int refine, mf_result* out,
+                           double* weights, void* stream) {
+  if (p == nullptr || g == nullptr || out == nullptr) return fail(MF_ERR_ARG, "mf_vegas_iterate: null argument");
+  if (n < 2) return fail(MF_ERR_ARG, "mf_vegas_iterate: need at least 2 events");
+  mf_status st = mf_vegas_accumulate(p, g, seed, iter, 0, n, weights, stream);
+  if (st < 0) return st;
+  return mf_vegas_finish(p, g, n, refine, out, stream);
+}
+
+mf_status mf_fma_throughput(int precision, double* tflops) {
+  if (tflops == nullptr || (precision != MF_FP64 && precision != MF_FP32)) return fail(MF_ERR_ARG, "mf_fma_throughput: bad argument");
+  int dev = 0, sms = 0;
+  MF_CUDA(cudaGetDevice(&dev), "mf_fma_throughput");
+  MF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "mf_fma_throughput");
+  float* sink = nullptr;
+  MF_CUDA(cudaMalloc(&sink, sizeof(float) * sms * 64), "mf_fma_throughput");
+  const int blocks = sms * 8;
+  const int prec = precision == MF_FP64 ? 0 : 1;
+  const int iters = precision == MF_FP64 ? 256 : 8192;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaError_t e = launch_fma_peak(prec, blocks, iters / 8, sink, 0);   // warm-up
+  float ms = 0;
+  if (e == cudaSuccess) {
+    cudaEventRecord(a, 0);
+    e = launch_fma_peak(prec, blocks, iters, sink, 0);
+    cudaEventRecord(b, 0);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  if (e != cudaSuccess) return cuda_fail(e, "mf_fma_throughput");
+  g_launches.fetch_add(2);
+  const double flops = 2.0 * 8 * 16 * double(iters) * 256.0 * blocks;
+  *tflops = flops / (double(ms) * 1e-3) / 1e12;
+  return MF_OK;
+}
+
+}  // extern "C"

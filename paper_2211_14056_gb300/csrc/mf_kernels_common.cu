@@ -1,0 +1,152 @@
+// Precision- and process-independent kernels: per-event sampling, and the
+// deterministic reduction of per-CTA Vegas partials followed by the grid
+// refinement (Lepage 1980; arXiv:2211.14056 Sec. 1 names Vegas as its integrator).
+#include "mf_kernels.cuh"
+
+namespace mf {
+
+__global__ void __launch_bounds__(kThreads) k_sample(SampleParams sp, const double* __restrict__ edges_g, int64_t n,
+                                                     uint64_t seed, int iter, double* __restrict__ mom,
+                                                     double* __restrict__ wps, uint8_t* __restrict__ bins) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* edges = reinterpret_cast<double*>(smem_raw);
+  for (int i = threadIdx.x; i < sp.ndim * (sp.nbins + 1); i += blockDim.x) edges[i] = edges_g[i];
+  __syncthreads();
+  const int next = sp.n_final + 2;
+  for (int64_t ev = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; ev < n; ev += int64_t(gridDim.x) * blockDim.x) {
+    EventKin k;
+    sample_event(sp, edges, seed, iter, uint64_t(ev), k);
+    if (mom != nullptr)
+      for (int i = 0; i < next; ++i)
+        for (int c = 0; c < 4; ++c) mom[int64_t(i * 4 + c) * n + ev] = k.p[i][c];
+    if (wps != nullptr) wps[ev] = k.prefactor;
+    if (bins != nullptr)
+      for (int j = 0; j < sp.ndim; ++j) bins[int64_t(j) * n + ev] = k.bins[j];
+  }
+}
+
+cudaError_t launch_sample(const SampleParams& sp, const double* edges, int64_t n, uint64_t seed, int iter,
+                          double* mom, double* wps, uint8_t* bins, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t need = (n + kThreads - 1) / kThreads;
+  const int grid = int(need < int64_t(sms) * 16 ? need : int64_t(sms) * 16);
+  const size_t smem = sizeof(double) * sp.ndim * (sp.nbins + 1);
+  k_sample<<<grid, kThreads, smem, s>>>(sp, edges, n, seed, iter, mom, wps, bins);
+  return cudaGetLastError();
+}
+
+// Lepage's refinement of one dimension: smooth the per-bin sums of w^2
+// (neighbour average, halves at the ends), normalise, damp with
+// ((1 - d)/ln(1/d))^alpha (0 -> 0, 1 -> 1), then place the new edges at equal
+// shares of the damped weights, linear inside the old bins.
+__device__ void refine_dim(double* e, const double* d, int nb, double alpha) {
+  double ds[64], r[64], cum[65], old[65];
+  bool any = false;
+  for (int b = 0; b < nb; ++b) any |= d[b] > 0.0;
+  if (!any) return;
+  ds[0] = (d[0] + d[1]) / 2.0;
+  ds[nb - 1] = (d[nb - 2] + d[nb - 1]) / 2.0;
+  for (int b = 1; b < nb - 1; ++b) ds[b] = (d[b - 1] + d[b] + d[b + 1]) / 3.0;
+  double sum = 0.0;
+  for (int b = 0; b < nb; ++b) sum += ds[b];
+  for (int b = 0; b < nb; ++b) {
+    const double dn = ds[b] / sum;
+    r[b] = (dn > 0.0 && dn < 1.0) ? pow((1.0 - dn) / log(1.0 / dn), alpha) : (dn >= 1.0 ? 1.0 : 0.0);
+  }
+  cum[0] = 0.0;
+  for (int b = 0; b < nb; ++b) cum[b + 1] = cum[b] + r[b];
+  for (int b = 0; b <= nb; ++b) old[b] = e[b];
+  const double total = cum[nb];
+  int j = 0;
+  for (int k = 1; k < nb; ++k) {
+    const double target = total * k / nb;
+    // largest j with cum[j] <= target, within [0, nb-1]
+    while (j + 1 <= nb - 1 && cum[j + 1] <= target) ++j;
+    const double frac = r[j] > 0.0 ? (target - cum[j]) / r[j] : 0.0;
+    e[k] = old[j] + frac * (old[j + 1] - old[j]);
+  }
+  e[0] = 0.0;
+  e[nb] = 1.0;
+}
+
+// Sum of the per-CTA partials in CTA order (deterministic for given partials).
+__global__ void k_reduce(const double* __restrict__ partials, const unsigned long long* __restrict__ counters,
+                         int nblocks, int nacc, double* __restrict__ totals) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nacc + 2; j += gridDim.x * blockDim.x) {
+    if (j < nacc) {
+      double s = 0.0;
+      for (int b = 0; b < nblocks; ++b) s += partials[int64_t(b) * nacc + j];
+      totals[j] = s;
+    } else {
+      unsigned long long c = 0;
+      for (int b = 0; b < nblocks; ++b) c += counters[2 * b + (j - nacc)];
+      totals[j] = double(c);
+    }
+  }
+}
+
+cudaError_t launch_reduce(const double* partials, const unsigned long long* counters, int nblocks, int ndim, int nbins,
+                          double* totals, cudaStream_t s) {
+  const int nacc = 2 + ndim * nbins;
+  const int blocks = (nacc + 2 + 127) / 128;
+  k_reduce<<<blocks, 128, 0, s>>>(partials, counters, nblocks, nacc, totals);
+  return cudaGetLastError();
+}
+
+// Estimate of one iteration from the (possibly all-reduced) totals, and the refinement.
+__global__ void k_finish(const double* __restrict__ totals, int ndim, int nbins, int64_t n, int refine,
+                         double* __restrict__ edges, double* __restrict__ result) {
+  const int nacc = 2 + ndim * nbins;
+  if (threadIdx.x == 0) {
+    const double dn = double(n);
+    const double I = totals[0] / dn;
+    result[0] = totals[0];
+    result[1] = totals[1];
+    result[2] = I;
+    result[3] = (totals[1] / dn - I * I) / (dn - 1.0);
+    result[4] = totals[nacc];
+    result[5] = totals[nacc + 1];
+  }
+  if (refine && int(threadIdx.x) < ndim) {
+    const int j = threadIdx.x;
+    refine_dim(edges + j * (nbins + 1), totals + 2 + j * nbins, nbins, 1.5);
+  }
+}
+
+cudaError_t launch_finish(const double* totals, int ndim, int nbins, int64_t n_total, int refine, double* edges,
+                          double* result, cudaStream_t s) {
+  k_finish<<<1, 64, 0, s>>>(totals, ndim, nbins, n_total, refine, edges, result);
+  return cudaGetLastError();
+}
+
+// FMA-pipe throughput probe: every thread runs 8 independent FMA chains, so
+// the pipe, not latency, bounds it.  The result is stored only if it is
+// impossible (never), which keeps the chains alive.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(int iters, float* sink) {
+  T a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = T(threadIdx.x + k) * T(1e-3);
+  const T b = T(0.999999), c = T(1e-7);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+  }
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == T(-1.2345)) sink[blockIdx.x] = float(s);
+}
+
+cudaError_t launch_fma_peak(int precision, int blocks, int iters, float* sink, cudaStream_t s) {
+  if (precision == 0) k_fma_peak<double><<<blocks, 256, 0, s>>>(iters, sink);
+  else k_fma_peak<float><<<blocks, 256, 0, s>>>(iters, sink);
+  return cudaGetLastError();
+}
+
+}  // namespace mf
