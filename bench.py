@@ -189,6 +189,10 @@ def main():
     ap.add_argument("--workload", default="gg_ttxgg_13tev")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adapt-events", type=int, default=2 ** 20)
+    ap.add_argument("--profile-case", type=int, default=0, metavar="EVENTS",
+                    help="only run 3 fused iterations of EVENTS events each (small case for ncu captures)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="arithmetic of --profile-case")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -205,6 +209,16 @@ def main():
     from paper_2211_14056_gb300.workloads import PROCESS_IDS, WORKLOADS, oracle_cfg, process_kwargs
 
     torch.cuda.set_device(local)
+    if args.profile_case:
+        w = WORKLOADS[args.workload]
+        prec = mf.MF_FP32 if args.precision == "fp32" else mf.MF_FP64
+        p = mf.Process(PROCESS_IDS[w["process"]], **process_kwargs(w, prec))
+        g = p.grid()
+        for it in range(3):
+            r = p.vegas_iterate(g, w["seed"], it, args.profile_case, refine=True)
+        print(json.dumps({"profile_case": args.workload, "events": args.profile_case, "precision": args.precision,
+                          "I": r["I"], "sigma": r["sigma"]}))
+        return 0
     dist = None
     if world > 1:
         import torch.distributed as dist
