@@ -227,7 +227,8 @@ def main():
     n = w["events"]
     ng = {"gg_ttx": 2, "gg_ttxg": 3, "gg_ttxgg": 4}[w["process"]]
     pid = PROCESS_IDS[w["process"]]
-    first = rank * n                                   # this rank's Philox event range
+    from paper_2211_14056_gb300.sharding import shard_range
+    first, _ = shard_range(rank, world, n)             # this rank's Philox event range
     p32 = mf.Process(pid, **process_kwargs(w, mf.MF_FP32))
     p64 = mf.Process(pid, **process_kwargs(w, mf.MF_FP64))
     stream = torch.cuda.current_stream()
@@ -353,19 +354,10 @@ def main():
     return 0
 
 
-class _CudaArray:
-    """__cuda_array_interface__ view of a library-owned device buffer."""
-
-    def __init__(self, ptr, count):
-        self.__cuda_array_interface__ = {"shape": (count,), "typestr": "<f8", "data": (ptr, False),
-                                         "version": 3, "strides": None}
-
-
 def _allreduce_totals(dist, grid, torch):
     """Sum the grid's device totals over ranks (NCCL), in place."""
-    ptr, cnt = grid.totals()
-    tot = torch.as_tensor(_CudaArray(ptr, cnt), device="cuda")
-    dist.all_reduce(tot)
+    from paper_2211_14056_gb300.sharding import allreduce_totals, totals_tensor
+    allreduce_totals(totals_tensor(grid))
 
 
 def _iter(proc, grid, it, refine, weights, dist, torch, w, first, n, world):
