@@ -162,6 +162,25 @@ mf_status mf_vegas_accumulate(mf_process* proc, mf_grid* grid, uint64_t seed, in
 mf_status mf_grid_totals(mf_grid* grid, double** totals_device, int* count);
 mf_status mf_vegas_finish(mf_process* proc, mf_grid* grid, int64_t n_total, int refine, mf_result* out, void* stream);
 
+/* Allocation-free mf_vegas_accumulate (the paper has no counterpart: it is an
+ * interface for host programs that forbid the libraries they load from
+ * allocating device memory, e.g. a framework that hands out all device memory
+ * from its own arena, or a process whose memory budget is already spent).
+ * Same computation as mf_vegas_accumulate, but the caller passes every buffer:
+ *   edges   device [ndim][nbins+1] FP64 Vegas edges (input; 2 <= nbins <= 64);
+ *   totals  device double[2 + ndim*nbins + 2] (output, layout of mf_grid_totals);
+ *   weights device [n] FP64 or NULL (output).
+ * The per-CTA scratch lives in a fixed 2 MiB array inside the library's device
+ * image, reserved on every device that loads the library until the process
+ * exits; a launch that would need more returns MF_ERR_ARG.  The first call on
+ * a device looks up that array's device address (make it before any stream
+ * capture).  The call allocates nothing.  All calls on a device share the one
+ * array: calls that overlap on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller.  Each call overwrites every scratch
+ * word it reads, so nothing needs clearing between calls. */
+mf_status mf_vegas_accumulate_static(mf_process* proc, const double* edges, int nbins, uint64_t seed, int iter,
+                                     int64_t first_event, int64_t n, double* totals, double* weights, void* stream);
+
 /* Measurement utility: sustained FMA-pipe throughput of the current device
  * (MF_FP32 or MF_FP64) in TFLOP/s from independent FMA chains on every SM,
  * the denominator of the amplitude kernel's roofline.  Synchronises the device. */

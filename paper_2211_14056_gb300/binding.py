@@ -69,6 +69,8 @@ EXPORTS = {
     "mf_grid_totals": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int)]),
     "mf_vegas_finish": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.POINTER(Result), C.c_void_p]),
     "mf_fma_throughput": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "mf_vegas_accumulate_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_uint64, C.c_int, C.c_int64,
+                                             C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mf_last_error": (C.c_char_p, []),
     "mf_kernel_launches": (C.c_int64, []),
 }
@@ -203,6 +205,14 @@ class Process:
         _check(load_library().mf_vegas_accumulate(
             self._h, grid._h, seed, it, first_event, n, _ptr(weights, torch.float64, n, "weights"),
             _stream(stream)))
+
+    def vegas_accumulate_static(self, edges, nbins, seed, it, first_event, n, totals, weights=None, stream=None):
+        """Allocation-free accumulation into caller-owned device buffers."""
+        import torch
+        _check(load_library().mf_vegas_accumulate_static(
+            self._h, _ptr(edges, torch.float64, self.ndim * (nbins + 1), "edges"), nbins, seed, it, first_event, n,
+            _ptr(totals, torch.float64, 2 + self.ndim * nbins + 2, "totals"),
+            _ptr(weights, torch.float64, n, "weights"), _stream(stream)))
 
     def vegas_finish(self, grid, n_total, refine=True, stream=None):
         r = Result()

@@ -2,6 +2,7 @@
 // Host side only: argument checks, handle lifetime, launch sizing, the Vegas
 // iteration record and its combination (Lepage's inverse-variance mean).
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -423,3 +424,90 @@ mf_status mf_fma_throughput(int precision, double* tflops) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of mf_vegas_accumulate.
+//
+// The fused kernel needs device scratch for its per-CTA partial sums.  Every
+// other entry point takes it from buffers that mf_grid_create allocated.  Some
+// host programs cannot allow that: a framework that carves all device memory
+// out of its own arena up front and forbids the libraries it loads from
+// calling cudaMalloc, or a process whose device-memory budget is already spent
+// by the time it integrates.  For them the scratch below is a fixed array in
+// the library's own device image, reserved when the library is loaded on a
+// device and held there until the process exits.
+//
+// Limit: kStaticScratchBytes (2 MiB), enough for every built process at its
+// full persistent launch (at most 2 + 10*64 doubles per CTA plus two counters).
+static constexpr size_t kStaticScratchBytes = size_t(2) << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+unsigned char* g_static_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_static_scratch on the current device.  Host code only
+// holds a host-side stand-in for the symbol, so the address is looked up once
+// per device (with that device current) and cached.
+cudaError_t static_scratch(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (g_static_ptr[dev] == nullptr) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_ptr[dev] = static_cast<unsigned char*>(ptr);
+  }
+  *out = g_static_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" mf_status mf_vegas_accumulate_static(mf_process* p, const double* edges, int nbins, uint64_t seed,
+                                                 int iter, int64_t first_event, int64_t n, double* totals,
+                                                 double* weights, void* stream) {
+  if (p == nullptr || edges == nullptr || totals == nullptr)
+    return fail(MF_ERR_ARG, "mf_vegas_accumulate_static: null argument");
+  if (nbins < 2 || nbins > 64) return fail(MF_ERR_ARG, "mf_vegas_accumulate_static: nbins must be in [2, 64]");
+  if (n < 1 || first_event < 0) return fail(MF_ERR_ARG, "mf_vegas_accumulate_static: need n >= 1 and first_event >= 0");
+  size_t smem = 0;
+  int ctas = 0;
+  cudaError_t e = dispatch_fused_config(p->ng, p->precision, p->ndim, nbins, &smem, &ctas);
+  if (e != cudaSuccess) return cuda_fail(e, "mf_vegas_accumulate_static (configuration)");
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  const int64_t cap = int64_t(p->sms) * effective_ctas(p, ctas);
+  const int grid = int(ntiles < cap ? ntiles : cap);
+  const size_t nacc = 2 + size_t(p->ndim) * nbins;
+  const size_t part_bytes = sizeof(double) * nacc * size_t(grid);
+  const size_t cnt_off = (part_bytes + 255) & ~size_t(255);
+  const size_t need = cnt_off + sizeof(unsigned long long) * 2 * size_t(grid);
+  if (need > kStaticScratchBytes)
+    return fail(MF_ERR_ARG, "mf_vegas_accumulate_static: this launch needs " + std::to_string(need) +
+                                " bytes of scratch, more than the " + std::to_string(kStaticScratchBytes) +
+                                " bytes reserved in the library");
+  unsigned char* scratch = nullptr;
+  e = static_scratch(&scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "mf_vegas_accumulate_static (scratch address)");
+  double* partials = reinterpret_cast<double*>(scratch);
+  unsigned long long* counters = reinterpret_cast<unsigned long long*>(scratch + cnt_off);
+  cudaStream_t s = (cudaStream_t)stream;
+  SampleParams sp = p->sp;
+  sp.nbins = nbins;
+  const int prec = p->precision == MF_FP64 ? 0 : 1;
+  switch (p->ng) {
+    case 2: e = launch_fused<2>(prec, sp, p->mp, edges, first_event, n, seed, iter, partials, counters, weights, grid, s); break;
+    case 3: e = launch_fused<3>(prec, sp, p->mp, edges, first_event, n, seed, iter, partials, counters, weights, grid, s); break;
+    default: e = launch_fused<4>(prec, sp, p->mp, edges, first_event, n, seed, iter, partials, counters, weights, grid, s); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "mf_vegas_accumulate_static (fused kernel)");
+  g_launches.fetch_add(1);
+  e = launch_reduce(partials, counters, grid, p->ndim, nbins, totals, s);
+  if (e != cudaSuccess) return cuda_fail(e, "mf_vegas_accumulate_static (reduce)");
+  g_launches.fetch_add(1);
+  return MF_OK;
+}
+
