@@ -193,6 +193,8 @@ def main():
                     help="only run 3 fused iterations of EVENTS events each (small case for ncu captures)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="arithmetic of --profile-case")
+    ap.add_argument("--profile-kernel", default="fused", choices=["fused", "me"],
+                    help="--profile-case target: the fused iteration, or sampling + the |M|^2 kernel alone")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -214,6 +216,17 @@ def main():
         prec = mf.MF_FP32 if args.precision == "fp32" else mf.MF_FP64
         p = mf.Process(PROCESS_IDS[w["process"]], **process_kwargs(w, prec))
         g = p.grid()
+        if args.profile_kernel == "me":
+            ne = args.profile_case
+            mom = torch.empty(p.n_ext * 4 * ne, dtype=torch.float64, device="cuda")
+            me = torch.empty(ne, dtype=torch.float64, device="cuda")
+            p.sample(g, w["seed"], 0, ne, momenta=mom)
+            for it in range(3):
+                p.matrix_element(ne, mom, me)
+            torch.cuda.synchronize()
+            print(json.dumps({"profile_case": args.workload, "kernel": "me", "events": ne,
+                              "precision": args.precision, "mean_me2": float(me.mean())}))
+            return 0
         for it in range(3):
             r = p.vegas_iterate(g, w["seed"], it, args.profile_case, refine=True)
         print(json.dumps({"profile_case": args.workload, "events": args.profile_case, "precision": args.precision,

@@ -1,6 +1,7 @@
 // C ABI of the library (declarations and their documentation: include/madflow_gb300.h).
 // Host side only: argument checks, handle lifetime, launch sizing, the Vegas
 // iteration record and its combination (Lepage's inverse-variance mean).
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <cmath>
@@ -37,6 +38,10 @@ mf_status cuda_fail(cudaError_t e, const char* where) {
 
 int factorial(int n) { return n <= 1 ? 1 : n * factorial(n - 1); }
 
+// events per record chunk of the two-kernel iteration (records: ~90 B/event
+// in FP32, ~160 B/event in FP64)
+constexpr int64_t kRecordChunk = int64_t(1) << 20;
+
 const int* lib_colour(int ng, int* den) {
   switch (ng) {
     case 2: *den = kColourDen2; return kColourNum2;
@@ -63,6 +68,10 @@ struct mf_grid {
   int max_blocks = 0;
   int fused_ctas = 1;
   size_t fused_smem = 0;
+  int acc_ctas = 1;            // CTAs per SM of the |M|^2-and-accumulate kernel
+  size_t acc_smem = 0;
+  int64_t chunk = 0;           // events per record chunk
+  void* d_records = nullptr;   // per-event records of one chunk
   double* d_edges = nullptr;
   double* d_partials = nullptr;
   unsigned long long* d_counters = nullptr;
@@ -80,6 +89,16 @@ cudaError_t dispatch_fused_config(int ng, int prec, int ndim, int nbins, size_t*
     case 2: return fused_config<2>(p, ndim, nbins, smem, ctas);
     case 3: return fused_config<3>(p, ndim, nbins, smem, ctas);
     case 4: return fused_config<4>(p, ndim, nbins, smem, ctas);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch_acc_config(int ng, int prec, int ndim, int nbins, size_t* smem, int* ctas) {
+  const int p = prec == MF_FP64 ? 0 : 1;
+  switch (ng) {
+    case 2: return me_acc_config<2>(p, ndim, nbins, smem, ctas);
+    case 3: return me_acc_config<3>(p, ndim, nbins, smem, ctas);
+    case 4: return me_acc_config<4>(p, ndim, nbins, smem, ctas);
   }
   return cudaErrorInvalidValue;
 }
@@ -223,7 +242,11 @@ mf_status mf_grid_create(const mf_process* p, int nbins, mf_grid** out) {
   g->nbins = nbins;
   cudaError_t e = dispatch_fused_config(p->ng, p->precision, g->ndim, nbins, &g->fused_smem, &g->fused_ctas);
   if (e == cudaSuccess && g->fused_ctas < 1) e = cudaErrorInvalidConfiguration;
-  g->max_blocks = p->sms * (g->fused_ctas < 1 ? 1 : g->fused_ctas);
+  if (e == cudaSuccess) e = dispatch_acc_config(p->ng, p->precision, g->ndim, nbins, &g->acc_smem, &g->acc_ctas);
+  if (e == cudaSuccess && g->acc_ctas < 1) e = cudaErrorInvalidConfiguration;
+  const int most = std::max(g->fused_ctas, g->acc_ctas);
+  g->max_blocks = p->sms * (most < 1 ? 1 : most);
+  g->chunk = kRecordChunk;
   std::vector<double> edges(size_t(g->ndim) * (nbins + 1));
   for (int j = 0; j < g->ndim; ++j)
     for (int b = 0; b <= nbins; ++b) edges[size_t(j) * (nbins + 1) + b] = double(b) / nbins;
@@ -232,6 +255,8 @@ mf_status mf_grid_create(const mf_process* p, int nbins, mf_grid** out) {
   if (e == cudaSuccess) e = cudaMalloc(&g->d_partials, sizeof(double) * nacc * g->max_blocks);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_counters, sizeof(unsigned long long) * 2 * g->max_blocks);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_totals, sizeof(double) * (nacc + 2));
+  if (e == cudaSuccess)
+    e = cudaMalloc(&g->d_records, record_bytes(p->precision == MF_FP64 ? 0 : 1, p->sp.n_final, g->ndim, g->chunk));
   if (e == cudaSuccess) e = cudaMalloc(&g->d_result, sizeof(double) * 8);
   if (e == cudaSuccess) e = cudaMallocHost(&g->h_result, sizeof(double) * 8);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_edges, edges.data(), sizeof(double) * edges.size(), cudaMemcpyHostToDevice);
@@ -247,6 +272,7 @@ mf_status mf_grid_destroy(mf_grid* g) {
   if (g == nullptr) return MF_OK;
   cudaFree(g->d_edges);
   cudaFree(g->d_partials);
+  cudaFree(g->d_records);
   cudaFree(g->d_counters);
   cudaFree(g->d_totals);
   cudaFree(g->d_result);
@@ -319,18 +345,26 @@ mf_status mf_vegas_accumulate(mf_process* p, mf_grid* g, uint64_t seed, int iter
   cudaStream_t s = (cudaStream_t)stream;
   SampleParams sp = p->sp;
   sp.nbins = g->nbins;
-  const int64_t ntiles = (n + kTile - 1) / kTile;
-  const int64_t cap = int64_t(p->sms) * effective_ctas(p, g->fused_ctas);
-  const int grid = int(ntiles < cap ? ntiles : cap);
   const int prec = p->precision == MF_FP64 ? 0 : 1;
-  cudaError_t e;
-  switch (p->ng) {
-    case 2: e = launch_fused<2>(prec, sp, p->mp, g->d_edges, first_event, n, seed, iter, g->d_partials, g->d_counters, weights, grid, s); break;
-    case 3: e = launch_fused<3>(prec, sp, p->mp, g->d_edges, first_event, n, seed, iter, g->d_partials, g->d_counters, weights, grid, s); break;
-    default: e = launch_fused<4>(prec, sp, p->mp, g->d_edges, first_event, n, seed, iter, g->d_partials, g->d_counters, weights, grid, s); break;
+  const int64_t cap = int64_t(p->sms) * effective_ctas(p, g->acc_ctas);
+  int grid = 0;
+  // chunks of the record buffer: sample the chunk, then |M|^2 + accumulate;
+  // the CTA partials of every chunk add up in place
+  for (int64_t done = 0, k = 0; done < n; done += g->chunk, ++k) {
+    const int64_t m = std::min(g->chunk, n - done);
+    const int64_t warps_needed = (m + 31) / 32;
+    const int64_t ctas_needed = (warps_needed + kWarps - 1) / kWarps;
+    if (k == 0) grid = int(std::min(cap, std::max<int64_t>(ctas_needed, 1)));
+    double* w = weights ? weights + done : nullptr;
+    cudaError_t e;
+    switch (p->ng) {
+      case 2: e = launch_chunk<2>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s); break;
+      case 3: e = launch_chunk<3>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s); break;
+      default: e = launch_chunk<4>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "mf_vegas_accumulate (chunk kernels)");
+    g_launches.fetch_add(2);
   }
-  if (e != cudaSuccess) return cuda_fail(e, "mf_vegas_accumulate (fused kernel)");
-  g_launches.fetch_add(1);
   MF_CUDA(launch_reduce(g->d_partials, g->d_counters, grid, g->ndim, g->nbins, g->d_totals, s),
           "mf_vegas_accumulate (reduce)");
   g_launches.fetch_add(1);

@@ -56,10 +56,27 @@ __device__ __forceinline__ unsigned pext_mask(unsigned H, unsigned mask) {
   return c;
 }
 
+// The sub-currents of one event are stored component-major, Gs[mu * NSTORE + pos]:
+// the lanes of a warp read 2^k consecutive positions of one block at a time,
+// which then fall into distinct banks.
 template <int NG, typename T>
-__device__ __forceinline__ V4<T> load_block(const V4<T>* Gs, uint8_t ref, unsigned H) {
+__device__ __forceinline__ V4<T> gs_load(const cplx<T>* Gs, int pos) {
+  V4<T> g;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) g.c[k] = Gs[k * TTNG<NG>::NSTORE + pos];
+  return g;
+}
+
+template <int NG, typename T>
+__device__ __forceinline__ void gs_store(cplx<T>* Gs, int pos, const V4<T>& g) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Gs[k * TTNG<NG>::NSTORE + pos] = g.c[k];
+}
+
+template <int NG, typename T>
+__device__ __forceinline__ V4<T> load_block(const cplx<T>* Gs, uint8_t ref, unsigned H) {
   const int id = ref & 0x7f;
-  V4<T> g = Gs[blk_off<NG>()[id] + pext_mask<NG>(H, blk_mask<NG>()[id])];
+  V4<T> g = gs_load<NG, T>(Gs, blk_off<NG>()[id] + pext_mask<NG>(H, blk_mask<NG>()[id]));
   if (ref & 0x80) g = neg(g);
   return g;
 }
@@ -75,7 +92,7 @@ __device__ __forceinline__ R4<T> block_momentum(const R4<T>* q, unsigned mask) {
 
 // one level (block length K) of the colour-ordered gluon currents
 template <int NG, int K, typename T>
-__device__ __forceinline__ void gluon_level(const R4<T>* q, V4<T>* Gs, int gl) {
+__device__ __forceinline__ void gluon_level(const R4<T>* q, cplx<T>* Gs, int gl) {
   constexpr int L = Lanes<NG>::L;
   constexpr int nblk = TTNG<NG>::FIRST[K + 1] - TTNG<NG>::FIRST[K];
   constexpr int items = nblk << K;
@@ -91,7 +108,7 @@ __device__ __forceinline__ void gluon_level(const R4<T>* q, V4<T>* Gs, int gl) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc.c[k] = {T(0), T(0)};
     const uint8_t* t3 = o3_table<NG, K>() + bl * n3 * 2;
-#pragma unroll
+#pragma unroll 1
     for (int s = 0; s < n3; ++s) {
       const uint8_t rl = t3[2 * s], rr = t3[2 * s + 1];
       const V4<T> GL = load_block<NG, T>(Gs, rl, H), GR = load_block<NG, T>(Gs, rr, H);
@@ -101,7 +118,7 @@ __device__ __forceinline__ void gluon_level(const R4<T>* q, V4<T>* Gs, int gl) {
     }
     if constexpr (K >= 3) {
       const uint8_t* t4 = o4_table<NG, K>() + bl * n4 * 3;
-#pragma unroll
+#pragma unroll 1
       for (int s = 0; s < n4; ++s) {
         const V4<T> GL = load_block<NG, T>(Gs, t4[3 * s], H);
         const V4<T> GM = load_block<NG, T>(Gs, t4[3 * s + 1], H);
@@ -114,25 +131,87 @@ __device__ __forceinline__ void gluon_level(const R4<T>* q, V4<T>* Gs, int gl) {
     V4<T> g;
 #pragma unroll
     for (int k = 0; k < 4; ++k) g.c[k] = inv * acc.c[k];
-    Gs[blk_off<NG>()[b] + c] = g;
+    gs_store<NG, T>(Gs, blk_off<NG>()[b] + c, g);
   }
 }
 
+// Shared memory of one warp: per event of the warp its gluon sub-currents
+// G(B) and the 2^NG suffix momenta, and for every lane its colour-ordered
+// amplitudes J[sigma][top helicity] (interleaved by lane: conflict-free).
+template <int NG, typename T> struct WarpMem {
+  static constexpr int EPW = Lanes<NG>::EPW;
+  static constexpr size_t gs_bytes = sizeof(V4<T>) * EPW * TTNG<NG>::NSTORE;   // EPW component-major stores
+  static constexpr size_t pt_off = gs_bytes;
+  static constexpr size_t pt_bytes = sizeof(R4<T>) * EPW * (1 << NG);
+  static constexpr size_t j_off = (pt_off + pt_bytes + 15) & ~size_t(15);
+  static constexpr size_t j_bytes = sizeof(cplx<T>) * TTNG<NG>::NPERM * 2 * 32;
+  static constexpr size_t bytes = (j_off + j_bytes + 15) & ~size_t(15);
+};
+
+// Per-lane context of the quark-line walk.
+template <typename T> struct LaneCtx {
+  const cplx<T>* Gs;    // this event's sub-currents (component-major)
+  const R4<T>* Ptab;    // -(q_tbar + sum of the gluon momenta in mask), by mask
+  uint64_t pk;          // 4-bit compressed helicity index of this lane for every gluon mask
+  S4<T> ub0, ub1;       // ubar(t) for top helicity -1, +1
+  T m, mw;
+  cplx<T>* J;           // &J[0][0][lane] of this warp
+};
+
 template <int NG, typename T>
-__device__ __forceinline__ T lane_sum_dispatch(const R4<T>* q, const R4<T>& qtb, T m, T mw, const V4<T>* Gs,
-                                               unsigned H, const S4<T>& vb, const S4<T>& ub0, const S4<T>& ub1) {
-  cplx<T> J[TTNG<NG>::NPERM][2];
-  if constexpr (NG == 2) return lane_colour_sum_2<T>(q, qtb, m, mw, Gs, H, vb, ub0, ub1, J);
-  else if constexpr (NG == 3) return lane_colour_sum_3<T>(q, qtb, m, mw, Gs, H, vb, ub0, ub1, J);
-  else return lane_colour_sum_4<T>(q, qtb, m, mw, Gs, H, vb, ub0, ub1, J);
+__device__ __forceinline__ V4<T> lane_block(const LaneCtx<T>& cx, uint8_t ref) {
+  const int id = ref & 0x7f;
+  const unsigned idx = unsigned(cx.pk >> (4 * blk_mask<NG>()[id])) & 15u;
+  V4<T> g = gs_load<NG, T>(cx.Gs, blk_off<NG>()[id] + idx);
+  if (ref & 0x80) g = neg(g);
+  return g;
+}
+
+// Depth-first walk over the ordered suffixes S of the quark line (level LV =
+// |S|): R(S) = -(P_S-slash + m)/(P_S^2 - m^2 + i m Gamma) sum_m G(S[:m])-slash R(S[m:]),
+// then at the last level every completion sigma = (a,) + S gives
+// J_sigma = ubar(t) sum_m G(sigma[:m])-slash R(sigma[m:]).  R[l] holds the
+// current path's level-l current (R[0] = v(tbar)).  All lanes of a warp walk
+// the same path (warp-uniform table reads), each with its own helicities.
+template <int NG, int LV, typename T>
+__device__ __forceinline__ void quark_walk(int parent, S4<T> (&R)[NG], const LaneCtx<T>& cx) {
+  using PT = Paths<NG>;
+  const int first = PT::template first<LV>(parent);
+#pragma unroll 1
+  for (int k = 0; k <= NG - LV; ++k) {
+    const int path = first + k;
+    S4<T> X = apply(make_slash(lane_block<NG, T>(cx, PT::template blk<LV>(path, 0))), R[LV - 1]);
+#pragma unroll
+    for (int m = 1; m < LV; ++m)
+      apply_acc(make_slash(lane_block<NG, T>(cx, PT::template blk<LV>(path, m))), R[LV - 1 - m], X);
+    R[LV] = quark_prop(cx.Ptab[PT::template mask<LV>(path)], cx.m, cx.mw, X);
+    if constexpr (LV < NG - 1) {
+      quark_walk<NG, LV + 1, T>(path, R, cx);
+    } else {
+      S4<T> W = apply(make_slash(lane_block<NG, T>(cx, PT::final_blk(path, 0))), R[NG - 1]);
+#pragma unroll
+      for (int m = 1; m < NG; ++m)
+        apply_acc(make_slash(lane_block<NG, T>(cx, PT::final_blk(path, m))), R[NG - 1 - m], W);
+      const int sig = PT::final_sigma(path);
+      cx.J[(sig * 2 + 0) * 32] = rowdot(cx.ub0, W);
+      cx.J[(sig * 2 + 1) * 32] = rowdot(cx.ub1, W);
+    }
+  }
 }
 
 // |M|^2 (without the normalisation MeParams::norm) of one event, computed by
-// its lane group; p: physical momenta in MadGraph order.  Every lane of the
-// warp must call this (the group synchronises with __syncwarp).
+// its lane group; p: physical momenta in MadGraph order; wm: this warp's
+// shared memory (WarpMem layout).  Every lane of the warp must call this (the
+// group synchronises with __syncwarp).
 template <int NG, typename T>
-__device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], V4<T>* Gs, int gl, T mt, T mw) {
+__device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* wm, int group, int gl, T mt, T mw) {
+  using WM = WarpMem<NG, T>;
   constexpr int L = Lanes<NG>::L;
+  constexpr int NP = TTNG<NG>::NPERM;
+  cplx<T>* Gs = reinterpret_cast<cplx<T>*>(wm) + group * 4 * TTNG<NG>::NSTORE;
+  R4<T>* Ptab = reinterpret_cast<R4<T>*>(wm + WM::pt_off) + group * (1 << NG);
+  cplx<T>* Jw = reinterpret_cast<cplx<T>*>(wm + WM::j_off);
+  const int lane = threadIdx.x & 31;
   R4<T> q[NG];
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
@@ -144,26 +223,53 @@ __device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], V4<T>* Gs, int g
   R4<T> qtb, pt;
 #pragma unroll
   for (int c = 0; c < 4; ++c) { qtb.v[c] = p[3][c]; pt.v[c] = p[2][c]; }
-  // level 1: polarisation vectors of every gluon, both helicities
+  // suffix momenta by gluon mask, and the polarisation vectors (level 1)
+  if (gl < (1 << NG)) {
+    R4<T> P = qtb;
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+      if ((gl >> g) & 1) P = P + q[g];
+    Ptab[gl] = -P;
+  }
   for (int it = gl; it < 2 * NG; it += L) {
     const int g = it >> 1;
     const int leg = g < 2 ? g : g + 2;
     R4<T> k;
 #pragma unroll
     for (int c = 0; c < 4; ++c) k.v[c] = p[leg][c];
-    Gs[2 * g + (it & 1)] = polarisation(k, (it & 1) ? 1 : -1, g >= 2);
+    gs_store<NG, T>(Gs, 2 * g + (it & 1), polarisation(k, (it & 1) ? 1 : -1, g >= 2));
   }
   __syncwarp();
   gluon_level<NG, 2, T>(q, Gs, gl);
   if constexpr (NG >= 3) { __syncwarp(); gluon_level<NG, 3, T>(q, Gs, gl); }
   if constexpr (NG >= 4) { __syncwarp(); gluon_level<NG, 4, T>(q, Gs, gl); }
   __syncwarp();
+  // quark line of this lane
   const unsigned H = unsigned(gl) & ((1u << NG) - 1u);
   const int ltb = ((gl >> NG) & 1) ? 1 : -1;
-  const S4<T> vb = v_out(qtb, mt, ltb);
-  const S4<T> ub0 = ubar_out(pt, mt, -1);
-  const S4<T> ub1 = ubar_out(pt, mt, 1);
-  T part = lane_sum_dispatch<NG, T>(q, qtb, mt, mw, Gs, H, vb, ub0, ub1);
+  LaneCtx<T> cx;
+  cx.Gs = Gs;
+  cx.Ptab = Ptab;
+  cx.pk = 0;
+#pragma unroll
+  for (unsigned msk = 1; msk < (1u << NG); ++msk) cx.pk |= uint64_t(pext_mask<NG>(H, msk)) << (4 * msk);
+  cx.ub0 = ubar_out(pt, mt, -1);
+  cx.ub1 = ubar_out(pt, mt, 1);
+  cx.m = mt;
+  cx.mw = mw;
+  cx.J = Jw + lane;
+  S4<T> R[NG];
+  R[0] = v_out(qtb, mt, ltb);
+  quark_walk<NG, 1, T>(0, R, cx);
+  // colour sum of both top helicities from this lane's amplitudes
+  T part = T(0);
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    cplx<T> J[NP];
+#pragma unroll
+    for (int sg = 0; sg < NP; ++sg) J[sg] = cx.J[(sg * 2 + h) * 32];
+    part += colour_form<T>(J);
+  }
 #pragma unroll
   for (int off = L / 2; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
   __syncwarp();   // the group's shared store may be overwritten after this
@@ -180,10 +286,9 @@ __global__ void __launch_bounds__(kThreads) k_matrix_element(MeParams mp, int64_
                                                              double* __restrict__ out) {
   constexpr int EPW = Lanes<NG>::EPW, L = Lanes<NG>::L, NEXT = Lanes<NG>::NEXT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V4<T>* Gs_all = reinterpret_cast<V4<T>*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int group = lane / L, gl = lane % L;
-  V4<T>* Gs = Gs_all + (warp * EPW + group) * TTNG<NG>::NSTORE;
+  unsigned char* wm = smem_raw + warp * WarpMem<NG, T>::bytes;
   const T mt = T(mp.mt), mw = T(mp.mw);
   for (int64_t base = (int64_t(blockIdx.x) * kWarps + warp) * EPW; base < n;
        base += int64_t(gridDim.x) * kWarps * EPW) {
@@ -195,7 +300,7 @@ __global__ void __launch_bounds__(kThreads) k_matrix_element(MeParams mp, int64_
     for (int i = 0; i < NEXT; ++i)
 #pragma unroll
       for (int c = 0; c < 4; ++c) p[i][c] = T(mom[int64_t(i * 4 + c) * n + e]);
-    const T v = group_me2<NG, T>(p, Gs, gl, mt, mw);
+    const T v = group_me2<NG, T>(p, wm, group, gl, mt, mw);
     if (ok && gl == 0) out[e] = double(v) * mp.norm;
   }
 }
@@ -206,7 +311,7 @@ __global__ void __launch_bounds__(kThreads) k_sample(SampleParams sp, const doub
                                                      double* __restrict__ wps, uint8_t* __restrict__ bins);
 
 // Vegas accumulators of one CTA: [0] sum w, [1] sum w^2, [2 + j*nbins + b] sum w^2 in bin b of dim j
-__device__ __forceinline__ void accumulate_event(double w, const uint8_t* b_ev, int ndim, int nbins, int stride,
+__device__ __forceinline__ void accumulate_event(double w, const uint8_t (&b_ev)[kMaxDim], int ndim, int nbins,
                                                  double* sums, double* hist) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -221,17 +326,19 @@ __device__ __forceinline__ void accumulate_event(double w, const uint8_t* b_ev, 
     atomicAdd(&sums[1], s2);
   }
   const double w2 = w * w;
+#pragma unroll 1
   for (int j = 0; j < ndim; ++j) {
-    const unsigned b = b_ev[j * stride];
+    const unsigned b = b_ev[j];
     // lanes holding the same bin form a group; reduce it with a shuffle tree
+    // (rank r adds rank r + s for s = 1, 2, 4, ...; rank 0 holds the sum)
     const unsigned peers = __match_any_sync(full, b);
-    const unsigned below = peers & ((1u << lane) - 1u);
-    const int rank = __popc(below);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    const unsigned above = peers & ~((2u << lane) - 1u);
     double v = w2;
-#pragma unroll
+#pragma unroll 1
     for (int s = 1; s < 32; s <<= 1) {
-      // lane holding rank + s in the same group (or myself if none)
-      unsigned m = peers & ~((lane == 31) ? 0xffffffffu : ((2u << lane) - 1u));
+      unsigned m = above;
+#pragma unroll 1
       for (int k = 1; k < s && m; ++k) m &= m - 1u;
       const int src = m ? (__ffs(m) - 1) : lane;
       const double o = __shfl_sync(full, v, src);
@@ -241,33 +348,30 @@ __device__ __forceinline__ void accumulate_event(double w, const uint8_t* b_ev, 
   }
 }
 
-// Shared-memory layout of k_fused (bytes), shared by host and device.
+// Shared-memory layout of k_fused (bytes), shared by host and device: the
+// CTA's grid edges and Vegas sums, then one WarpMem per warp.
 template <int NG, typename T> struct FusedLayout {
-  static constexpr int NEXT = NG + 2;
-  static constexpr int EPW = Lanes<NG>::EPW;
   __host__ __device__ static size_t al(size_t x) { return (x + 15) & ~size_t(15); }
   __host__ __device__ static size_t edges(int, int) { return 0; }
   __host__ __device__ static size_t hist(int ndim, int nbins) { return al(edges(ndim, nbins) + sizeof(double) * ndim * (nbins + 1)); }
   __host__ __device__ static size_t sums(int ndim, int nbins) { return al(hist(ndim, nbins) + sizeof(double) * ndim * nbins); }
-  __host__ __device__ static size_t pref(int ndim, int nbins) { return al(sums(ndim, nbins) + sizeof(double) * 2); }
-  __host__ __device__ static size_t me2(int ndim, int nbins) { return al(pref(ndim, nbins) + sizeof(double) * kTile); }
-  __host__ __device__ static size_t mom(int ndim, int nbins) { return al(me2(ndim, nbins) + sizeof(double) * kTile); }
-  __host__ __device__ static size_t gs(int ndim, int nbins) { return al(mom(ndim, nbins) + sizeof(T) * kTile * NEXT * 4); }
-  __host__ __device__ static size_t bins(int ndim, int nbins) {
-    return al(gs(ndim, nbins) + sizeof(V4<T>) * kWarps * EPW * TTNG<NG>::NSTORE);
+  __host__ __device__ static size_t warps(int ndim, int nbins) { return al(sums(ndim, nbins) + sizeof(double) * 2); }
+  __host__ __device__ static size_t total(int ndim, int nbins) {
+    return al(warps(ndim, nbins) + WarpMem<NG, T>::bytes * kWarps);
   }
-  __host__ __device__ static size_t plist(int ndim, int nbins) { return al(bins(ndim, nbins) + size_t(ndim) * kTile); }
-  __host__ __device__ static size_t total(int ndim, int nbins) { return al(plist(ndim, nbins) + sizeof(int) * (kTile + 4)); }
 };
 
-// Persistent fused kernel: each CTA walks tiles of kTile events.
-//   phase 1 (thread per event): Philox -> Vegas -> luminosity -> RAMBO -> cuts
-//   phase 2 (lane group per surviving event): |M|^2
-//   phase 3 (thread per event): w = |M|^2 * prefactor, Vegas sums
-// partials[blockIdx.x * nacc + k] receives the CTA's sums (nacc = 2 + ndim*nbins);
-// counters[blockIdx.x * 2 + {0,1}] = events passing cuts, Newton misses.
+// Persistent fused kernel; every warp works on its own blocks of 32 events:
+//   phase 1 (lane per event): Philox -> Vegas -> luminosity -> RAMBO -> cuts;
+//   phase 2 (lane group per event that passed): |M|^2, the event's momenta
+//     broadcast from its lane with shuffles;
+//   phase 3 (lane per event): w = |M|^2 * prefactor, Vegas sums.
+// No block-wide barrier inside the event loop.  partials[blockIdx.x * nacc + k]
+// receives the CTA's sums (nacc = 2 + ndim*nbins); counters[blockIdx.x * 2 + {0,1}]
+// = events passing cuts, Newton misses.  Weights (if w_out) are indexed by the
+// event's position 0..n-1 in this call; the Philox counter is first_event + position.
 template <int NG, typename T>
-__global__ void __launch_bounds__(kThreads) k_fused(SampleParams sp, MeParams mp, const double* __restrict__ edges_g,
+__global__ void __launch_bounds__(kThreads, 2) k_fused(SampleParams sp, MeParams mp, const double* __restrict__ edges_g,
                                                     int64_t first_event, int64_t n, uint64_t seed, int iter,
                                                     double* __restrict__ partials,
                                                     unsigned long long* __restrict__ counters,
@@ -279,82 +383,76 @@ __global__ void __launch_bounds__(kThreads) k_fused(SampleParams sp, MeParams mp
   double* edges = reinterpret_cast<double*>(smem_raw + LY::edges(ndim, nbins));
   double* hist = reinterpret_cast<double*>(smem_raw + LY::hist(ndim, nbins));
   double* sums = reinterpret_cast<double*>(smem_raw + LY::sums(ndim, nbins));
-  double* pref = reinterpret_cast<double*>(smem_raw + LY::pref(ndim, nbins));
-  double* me2 = reinterpret_cast<double*>(smem_raw + LY::me2(ndim, nbins));
-  T* mom = reinterpret_cast<T*>(smem_raw + LY::mom(ndim, nbins));
-  V4<T>* Gs_all = reinterpret_cast<V4<T>*>(smem_raw + LY::gs(ndim, nbins));
-  uint8_t* bins = smem_raw + LY::bins(ndim, nbins);
-  int* plist = reinterpret_cast<int*>(smem_raw + LY::plist(ndim, nbins));
-  int* pcount = plist + kTile;
-
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int group = lane / L, gl = lane % L;
+  unsigned char* wm = smem_raw + LY::warps(ndim, nbins) + warp * WarpMem<NG, T>::bytes;
   for (int i = t; i < ndim * (nbins + 1); i += kThreads) edges[i] = edges_g[i];
   for (int i = t; i < ndim * nbins; i += kThreads) hist[i] = 0.0;
   if (t < 2) sums[t] = 0.0;
   unsigned long long npass = 0, nfail = 0;
-  V4<T>* Gs = Gs_all + (warp * EPW + group) * TTNG<NG>::NSTORE;
   const T mt = T(mp.mt), mw = T(mp.mw);
+  const unsigned full = 0xffffffffu;
   __syncthreads();
 
-  for (int64_t tile = blockIdx.x; tile * kTile < n; tile += gridDim.x) {
-    if (t == 0) *pcount = 0;
-    __syncthreads();
-    const int64_t ev = tile * kTile + t;
+  const int64_t stride = int64_t(gridDim.x) * kWarps * 32;
+  for (int64_t base = (int64_t(blockIdx.x) * kWarps + warp) * 32; base < n; base += stride) {
+    const int64_t ev = base + lane;
     const bool valid = ev < n;
-    int pass = 0;
+    EventKin<T> k;
+    k.prefactor = 0.0;
+    k.pass = 0;
     if (valid) {
-      EventKin k;
       sample_event(sp, edges, seed, iter, uint64_t(first_event + ev), k);
-#pragma unroll
-      for (int i = 0; i < NEXT; ++i)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) mom[(t * NEXT + i) * 4 + c] = T(k.p[i][c]);
-      pref[t] = k.prefactor;
-      for (int j = 0; j < ndim; ++j) bins[j * kTile + t] = k.bins[j];
-      pass = k.pass;
-      npass += pass;
+      npass += k.pass;
       nfail += k.newton_fail;
     } else {
-      pref[t] = 0.0;
-      for (int j = 0; j < ndim; ++j) bins[j * kTile + t] = 0;
+      for (int j = 0; j < kMaxDim; ++j) k.bins[j] = 0;
     }
-    me2[t] = 0.0;
-    const unsigned bal = __ballot_sync(0xffffffffu, pass);
-    int wbase = 0;
-    if (lane == 0 && bal) wbase = atomicAdd(pcount, __popc(bal));
-    wbase = __shfl_sync(0xffffffffu, wbase, 0);
-    if (pass) plist[wbase + __popc(bal & ((1u << lane) - 1u))] = t;
-    __syncthreads();
-
-    const int np = *pcount;
-    for (int base = warp * EPW; base < np; base += kWarps * EPW) {
-      const int k = base + group;
-      const bool ok = k < np;
-      const int slot = plist[ok ? k : base];
+    T mine[NEXT][4];
+#pragma unroll
+    for (int i = 0; i < NEXT; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) mine[i][c] = k.p[i][c];
+    double me = 0.0;
+    unsigned todo = __ballot_sync(full, valid && k.pass);
+    while (todo) {
+      // the next EPW events that passed: group g takes the g-th lowest set bit
+      int src = -1;
+      unsigned rest = todo;
+#pragma unroll
+      for (int g = 0; g < EPW; ++g) {
+        const int b = rest ? __ffs(rest) - 1 : -1;
+        if (g == group) src = b;
+        if (rest) rest &= rest - 1u;
+      }
+      const int from = src < 0 ? 0 : src;
       T p[NEXT][4];
 #pragma unroll
       for (int i = 0; i < NEXT; ++i)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) p[i][c] = mom[(slot * NEXT + i) * 4 + c];
-      const T v = group_me2<NG, T>(p, Gs, gl, mt, mw);
-      if (ok && gl == 0) me2[slot] = double(v) * mp.norm;
+        for (int c = 0; c < 4; ++c) p[i][c] = __shfl_sync(full, mine[i][c], from);
+      const T v = group_me2<NG, T>(p, wm, group, gl, mt, mw);
+#pragma unroll
+      for (int g = 0; g < EPW; ++g) {
+        const T vg = __shfl_sync(full, v, g * L);
+        const int sg = __shfl_sync(full, src, g * L);
+        if (sg == lane) me = double(vg) * mp.norm;
+      }
+      todo = rest;
     }
-    __syncthreads();
-
-    const double w = valid ? me2[t] * pref[t] : 0.0;
+    const double w = valid ? me * k.prefactor : 0.0;
     if (w_out != nullptr && valid) w_out[ev] = w;
-    accumulate_event(w, bins + t, ndim, nbins, kTile, sums, hist);
-    __syncthreads();
+    accumulate_event(w, k.bins, ndim, nbins, sums, hist);
   }
+  __syncthreads();
   const int nacc = 2 + ndim * nbins;
   double* dst = partials + int64_t(blockIdx.x) * nacc;
   for (int i = t; i < ndim * nbins; i += kThreads) dst[2 + i] = hist[i];
   if (t < 2) dst[t] = sums[t];
   // CTA totals of the counters
   for (int off = 16; off > 0; off >>= 1) {
-    npass += __shfl_xor_sync(0xffffffffu, npass, off);
-    nfail += __shfl_xor_sync(0xffffffffu, nfail, off);
+    npass += __shfl_xor_sync(full, npass, off);
+    nfail += __shfl_xor_sync(full, nfail, off);
   }
   __shared__ unsigned long long cnt[2];
   if (t < 2) cnt[t] = 0;
@@ -367,6 +465,178 @@ __global__ void __launch_bounds__(kThreads) k_fused(SampleParams sp, MeParams mp
   if (t < 2) counters[blockIdx.x * 2 + t] = cnt[t];
 }
 
+// ----------------------------------------------------------------------------
+// Two-kernel iteration: k_sample_rec writes one compact record per event
+// (coalesced, SoA), k_me_acc reads the records back, evaluates |M|^2 for the
+// events that passed and accumulates the Vegas sums.  Splitting the sampling
+// (a long, branchy FP64/transcendental code path) from the amplitude loop keeps
+// the amplitude kernel's instruction footprint small; the records cost
+// ~2 x 90 bytes of HBM traffic per event, negligible next to ~1 MFLOP of
+// amplitude work.
+//
+// Record layout for a chunk of C events (K = kinematics type):
+//   mom  [n_final*4][C] K    final-state momenta (t, tbar, gluons), components E, px, py, pz
+//   rs   [C]            K    partonic sqrt(s_hat) (the beams are (rs/2)(1, 0, 0, +-1))
+//   pref [C]            f64  weight without |M|^2
+//   flag [ndim + 2][C]  u8   Vegas bin of each dimension, then pass, then Newton miss
+template <typename K> struct RecordView {
+  K* mom;
+  K* rs;
+  double* pref;
+  uint8_t* flag;
+  int64_t C;
+  __host__ __device__ static size_t bytes(int n_final, int ndim, int64_t C) {
+    const size_t a = (size_t(n_final) * 4 + 1) * sizeof(K) * C;
+    const size_t b = ((a + 255) & ~size_t(255)) + sizeof(double) * C;
+    return ((b + 255) & ~size_t(255)) + size_t(ndim + 2) * C;
+  }
+  __host__ __device__ static RecordView carve(void* base, int n_final, int ndim, int64_t C) {
+    RecordView v;
+    unsigned char* p = static_cast<unsigned char*>(base);
+    v.C = C;
+    v.mom = reinterpret_cast<K*>(p);
+    v.rs = v.mom + size_t(n_final) * 4 * C;
+    const size_t a = (size_t(n_final) * 4 + 1) * sizeof(K) * C;
+    const size_t o1 = (a + 255) & ~size_t(255);
+    v.pref = reinterpret_cast<double*>(p + o1);
+    const size_t o2 = (o1 + sizeof(double) * C + 255) & ~size_t(255);
+    v.flag = p + o2;
+    return v;
+  }
+};
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_sample_rec(SampleParams sp, const double* __restrict__ edges_g,
+                                                         int64_t first_event, int64_t n, uint64_t seed, int iter,
+                                                         RecordView<K> rec) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* edges = reinterpret_cast<double*>(smem_raw);
+  for (int i = threadIdx.x; i < sp.ndim * (sp.nbins + 1); i += blockDim.x) edges[i] = edges_g[i];
+  __syncthreads();
+  const int nf = sp.n_final;
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+    EventKin<K> k;
+    sample_event(sp, edges, seed, iter, uint64_t(first_event + e), k);
+    for (int i = 0; i < nf; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) rec.mom[int64_t(i * 4 + c) * rec.C + e] = k.p[2 + i][c];
+    rec.rs[e] = k.p[0][0] + k.p[1][0];
+    rec.pref[e] = k.prefactor;
+    for (int j = 0; j < sp.ndim; ++j) rec.flag[int64_t(j) * rec.C + e] = k.bins[j];
+    rec.flag[int64_t(sp.ndim) * rec.C + e] = uint8_t(k.pass);
+    rec.flag[int64_t(sp.ndim + 1) * rec.C + e] = uint8_t(k.newton_fail);
+  }
+}
+
+template <int NG, typename T> struct MeAccLayout {
+  __host__ __device__ static size_t al(size_t x) { return (x + 15) & ~size_t(15); }
+  __host__ __device__ static size_t hist(int) { return 0; }
+  __host__ __device__ static size_t sums(int nacc) { return al(sizeof(double) * (nacc - 2)); }
+  __host__ __device__ static size_t warps(int nacc) { return al(sums(nacc) + sizeof(double) * 2); }
+  __host__ __device__ static size_t total(int nacc) { return al(warps(nacc) + WarpMem<NG, T>::bytes * kWarps); }
+};
+
+// |M|^2 of the records that passed, weights, Vegas sums.  Every warp takes its
+// own blocks of 32 records; partials[blockIdx.x * nacc + k] receive (accumulate
+// = 0) or add (accumulate = 1) the CTA's sums, counters likewise.
+template <int NG, typename T>
+__global__ void __launch_bounds__(kThreads, 2) k_me_acc(MeParams mp, int ndim, int nbins, RecordView<T> rec,
+                                                        int64_t n, int accumulate, double* __restrict__ partials,
+                                                        unsigned long long* __restrict__ counters,
+                                                        double* __restrict__ w_out) {
+  using LY = MeAccLayout<NG, T>;
+  constexpr int EPW = Lanes<NG>::EPW, L = Lanes<NG>::L, NEXT = Lanes<NG>::NEXT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nacc = 2 + ndim * nbins;
+  double* hist = reinterpret_cast<double*>(smem_raw + LY::hist(nacc));
+  double* sums = reinterpret_cast<double*>(smem_raw + LY::sums(nacc));
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int group = lane / L, gl = lane % L;
+  unsigned char* wm = smem_raw + LY::warps(nacc) + warp * WarpMem<NG, T>::bytes;
+  for (int i = t; i < ndim * nbins; i += kThreads) hist[i] = 0.0;
+  if (t < 2) sums[t] = 0.0;
+  unsigned long long npass = 0, nfail = 0;
+  const T mt = T(mp.mt), mw = T(mp.mw);
+  const unsigned full = 0xffffffffu;
+  __syncthreads();
+
+  const int64_t stride = int64_t(gridDim.x) * kWarps * 32;
+  for (int64_t base = (int64_t(blockIdx.x) * kWarps + warp) * 32; base < n; base += stride) {
+    const int64_t e = base + lane;
+    const bool valid = e < n;
+    T mine[NEXT][4];
+    double pref = 0.0;
+    uint8_t bins[kMaxDim];
+    int pass = 0;
+    if (valid) {
+      const T rs = rec.rs[e];
+      mine[0][0] = T(0.5) * rs; mine[0][1] = T(0); mine[0][2] = T(0); mine[0][3] = T(0.5) * rs;
+      mine[1][0] = T(0.5) * rs; mine[1][1] = T(0); mine[1][2] = T(0); mine[1][3] = T(-0.5) * rs;
+#pragma unroll
+      for (int i = 0; i < NG; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) mine[2 + i][c] = rec.mom[int64_t(i * 4 + c) * rec.C + e];
+      pref = rec.pref[e];
+      for (int j = 0; j < ndim; ++j) bins[j] = rec.flag[int64_t(j) * rec.C + e];
+      pass = rec.flag[int64_t(ndim) * rec.C + e];
+      npass += pass;
+      nfail += rec.flag[int64_t(ndim + 1) * rec.C + e];
+    } else {
+#pragma unroll
+      for (int i = 0; i < NEXT; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) mine[i][c] = T(0);
+      for (int j = 0; j < kMaxDim; ++j) bins[j] = 0;
+    }
+    double me = 0.0;
+    unsigned todo = __ballot_sync(full, valid && pass);
+    while (todo) {
+      int src = -1;
+      unsigned rest = todo;
+#pragma unroll
+      for (int g = 0; g < EPW; ++g) {
+        const int b = rest ? __ffs(rest) - 1 : -1;
+        if (g == group) src = b;
+        if (rest) rest &= rest - 1u;
+      }
+      const int from = src < 0 ? 0 : src;
+      T p[NEXT][4];
+#pragma unroll
+      for (int i = 0; i < NEXT; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) p[i][c] = __shfl_sync(full, mine[i][c], from);
+      const T v = group_me2<NG, T>(p, wm, group, gl, mt, mw);
+#pragma unroll
+      for (int g = 0; g < EPW; ++g) {
+        const T vg = __shfl_sync(full, v, g * L);
+        const int sg = __shfl_sync(full, src, g * L);
+        if (sg == lane) me = double(vg) * mp.norm;
+      }
+      todo = rest;
+    }
+    const double w = valid ? me * pref : 0.0;
+    if (w_out != nullptr && valid) w_out[e] = w;
+    accumulate_event(w, bins, ndim, nbins, sums, hist);
+  }
+  __syncthreads();
+  double* dst = partials + int64_t(blockIdx.x) * nacc;
+  for (int i = t; i < ndim * nbins; i += kThreads) dst[2 + i] = (accumulate ? dst[2 + i] : 0.0) + hist[i];
+  if (t < 2) dst[t] = (accumulate ? dst[t] : 0.0) + sums[t];
+  for (int off = 16; off > 0; off >>= 1) {
+    npass += __shfl_xor_sync(full, npass, off);
+    nfail += __shfl_xor_sync(full, nfail, off);
+  }
+  __shared__ unsigned long long cnt[2];
+  if (t < 2) cnt[t] = 0;
+  __syncthreads();
+  if (lane == 0) {
+    atomicAdd(&cnt[0], npass);
+    atomicAdd(&cnt[1], nfail);
+  }
+  __syncthreads();
+  if (t < 2) counters[blockIdx.x * 2 + t] = (accumulate ? counters[blockIdx.x * 2 + t] : 0ull) + cnt[t];
+}
+
 // host-side launch helpers (defined per gluon count)
 template <int NG>
 cudaError_t launch_matrix_element(int precision, const MeParams& mp, int64_t n, const double* mom, double* out,
@@ -377,6 +647,15 @@ cudaError_t launch_fused(int precision, const SampleParams& sp, const MeParams& 
                          unsigned long long* counters, double* w_out, int grid, cudaStream_t s);
 template <int NG>
 cudaError_t fused_config(int precision, int ndim, int nbins, size_t* smem, int* ctas_per_sm);
+// two-kernel iteration over one chunk of records (rec_base: RecordView of chunk capacity C)
+template <int NG>
+cudaError_t launch_chunk(int precision, const SampleParams& sp, const MeParams& mp, const double* edges,
+                         int64_t first_event, int64_t n, int64_t C, void* rec_base, uint64_t seed, int iter,
+                         int accumulate, double* partials, unsigned long long* counters, double* w_out, int grid,
+                         cudaStream_t s);
+template <int NG>
+cudaError_t me_acc_config(int precision, int ndim, int nbins, size_t* smem, int* ctas_per_sm);
+size_t record_bytes(int precision, int n_final, int ndim, int64_t C);
 template <int NG>
 cudaError_t me_config(int precision, size_t* smem, int* ctas_per_sm);
 
@@ -398,12 +677,12 @@ cudaError_t launch_fma_peak(int precision, int blocks, int iters, float* sink, c
   cudaError_t me_config<NG>(int precision, size_t* smem, int* ctas) {                                             \
     cudaError_t e;                                                                                                \
     if (precision == 0) {                                                                                         \
-      *smem = sizeof(V4<double>) * kWarps * Lanes<NG>::EPW * TTNG<NG>::NSTORE;                                    \
+      *smem = WarpMem<NG, double>::bytes * kWarps;                                    \
       e = cudaFuncSetAttribute(k_matrix_element<NG, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(*smem)); \
       if (e != cudaSuccess) return e;                                                                             \
       return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_matrix_element<NG, double>, kThreads, *smem);  \
     }                                                                                                             \
-    *smem = sizeof(V4<float>) * kWarps * Lanes<NG>::EPW * TTNG<NG>::NSTORE;                                       \
+    *smem = WarpMem<NG, float>::bytes * kWarps;                                       \
     e = cudaFuncSetAttribute(k_matrix_element<NG, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(*smem)); \
     if (e != cudaSuccess) return e;                                                                               \
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_matrix_element<NG, float>, kThreads, *smem);     \
@@ -412,10 +691,10 @@ cudaError_t launch_fma_peak(int precision, int blocks, int iters, float* sink, c
   cudaError_t launch_matrix_element<NG>(int precision, const MeParams& mp, int64_t n, const double* mom,          \
                                         double* out, int grid, cudaStream_t s) {                                  \
     if (precision == 0) {                                                                                         \
-      const size_t sm = sizeof(V4<double>) * kWarps * Lanes<NG>::EPW * TTNG<NG>::NSTORE;                          \
+      const size_t sm = WarpMem<NG, double>::bytes * kWarps;                          \
       k_matrix_element<NG, double><<<grid, kThreads, sm, s>>>(mp, n, mom, out);                                   \
     } else {                                                                                                      \
-      const size_t sm = sizeof(V4<float>) * kWarps * Lanes<NG>::EPW * TTNG<NG>::NSTORE;                           \
+      const size_t sm = WarpMem<NG, float>::bytes * kWarps;                           \
       k_matrix_element<NG, float><<<grid, kThreads, sm, s>>>(mp, n, mom, out);                                    \
     }                                                                                                             \
     return cudaGetLastError();                                                                                    \
@@ -433,6 +712,46 @@ cudaError_t launch_fma_peak(int precision, int blocks, int iters, float* sink, c
     e = cudaFuncSetAttribute(k_fused<NG, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(*smem));        \
     if (e != cudaSuccess) return e;                                                                               \
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_fused<NG, float>, kThreads, *smem);              \
+  }                                                                                                               \
+  template <>                                                                                                     \
+  cudaError_t me_acc_config<NG>(int precision, int ndim, int nbins, size_t* smem, int* ctas) {                    \
+    cudaError_t e;                                                                                                \
+    const int nacc = 2 + ndim * nbins;                                                                            \
+    if (precision == 0) {                                                                                         \
+      *smem = MeAccLayout<NG, double>::total(nacc);                                                               \
+      e = cudaFuncSetAttribute(k_me_acc<NG, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(*smem));    \
+      if (e != cudaSuccess) return e;                                                                             \
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_me_acc<NG, double>, kThreads, *smem);          \
+    }                                                                                                             \
+    *smem = MeAccLayout<NG, float>::total(nacc);                                                                  \
+    e = cudaFuncSetAttribute(k_me_acc<NG, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(*smem));       \
+    if (e != cudaSuccess) return e;                                                                               \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_me_acc<NG, float>, kThreads, *smem);             \
+  }                                                                                                               \
+  template <>                                                                                                     \
+  cudaError_t launch_chunk<NG>(int precision, const SampleParams& sp, const MeParams& mp, const double* edges,    \
+                               int64_t first_event, int64_t n, int64_t C, void* rec_base, uint64_t seed, int iter, \
+                               int accumulate, double* partials, unsigned long long* counters, double* w_out,     \
+                               int grid, cudaStream_t s) {                                                        \
+    const int nacc = 2 + sp.ndim * sp.nbins;                                                                      \
+    const size_t esm = sizeof(double) * sp.ndim * (sp.nbins + 1);                                                 \
+    int dev = 0, sms = 0;                                                                                         \
+    cudaGetDevice(&dev);                                                                                          \
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);                                           \
+    const int64_t need = (n + kThreads - 1) / kThreads;                                                           \
+    const int sgrid = int(need < int64_t(sms) * 16 ? need : int64_t(sms) * 16);                                  \
+    if (precision == 0) {                                                                                         \
+      RecordView<double> rec = RecordView<double>::carve(rec_base, sp.n_final, sp.ndim, C);                       \
+      k_sample_rec<double><<<sgrid, kThreads, esm, s>>>(sp, edges, first_event, n, seed, iter, rec);              \
+      k_me_acc<NG, double><<<grid, kThreads, MeAccLayout<NG, double>::total(nacc), s>>>(                          \
+          mp, sp.ndim, sp.nbins, rec, n, accumulate, partials, counters, w_out);                                  \
+    } else {                                                                                                      \
+      RecordView<float> rec = RecordView<float>::carve(rec_base, sp.n_final, sp.ndim, C);                         \
+      k_sample_rec<float><<<sgrid, kThreads, esm, s>>>(sp, edges, first_event, n, seed, iter, rec);               \
+      k_me_acc<NG, float><<<grid, kThreads, MeAccLayout<NG, float>::total(nacc), s>>>(                            \
+          mp, sp.ndim, sp.nbins, rec, n, accumulate, partials, counters, w_out);                                  \
+    }                                                                                                             \
+    return cudaGetLastError();                                                                                    \
   }                                                                                                               \
   template <>                                                                                                     \
   cudaError_t launch_fused<NG>(int precision, const SampleParams& sp, const MeParams& mp, const double* edges,    \

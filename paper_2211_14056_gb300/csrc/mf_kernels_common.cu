@@ -14,7 +14,7 @@ __global__ void __launch_bounds__(kThreads) k_sample(SampleParams sp, const doub
   __syncthreads();
   const int next = sp.n_final + 2;
   for (int64_t ev = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; ev < n; ev += int64_t(gridDim.x) * blockDim.x) {
-    EventKin k;
+    EventKin<double> k;
     sample_event(sp, edges, seed, iter, uint64_t(ev), k);
     if (mom != nullptr)
       for (int i = 0; i < next; ++i)
@@ -23,6 +23,10 @@ __global__ void __launch_bounds__(kThreads) k_sample(SampleParams sp, const doub
     if (bins != nullptr)
       for (int j = 0; j < sp.ndim; ++j) bins[int64_t(j) * n + ev] = k.bins[j];
   }
+}
+
+size_t record_bytes(int precision, int n_final, int ndim, int64_t C) {
+  return precision == 0 ? RecordView<double>::bytes(n_final, ndim, C) : RecordView<float>::bytes(n_final, ndim, C);
 }
 
 cudaError_t launch_sample(const SampleParams& sp, const double* edges, int64_t n, uint64_t seed, int iter,

@@ -41,8 +41,10 @@ struct SampleParams {
   double phi_const;     // (2 pi)^(4-3n) (pi/2)^(n-1) / ((n-1)! (n-2)!)
 };
 
-struct EventKin {
-  double p[kMaxExt][4];   // physical momenta in MadGraph order (g, g, t, tbar, g...)
+// K: arithmetic of the kinematics (momenta, luminosity, cuts); the Vegas map,
+// its bins and Jacobian, the massive-rescaling Newton and the weight are FP64.
+template <typename K> struct EventKin {
+  K p[kMaxExt][4];        // physical momenta in MadGraph order (g, g, t, tbar, g...)
   double prefactor;       // weight without |M|^2 (0 if cut / failed)
   uint8_t bins[kMaxDim];
   int pass;               // 1: compute |M|^2; 0: weight is zero
@@ -78,10 +80,11 @@ __device__ __forceinline__ void draw_uniforms(uint64_t seed, int iter, uint64_t 
 }
 
 // boost p given in the rest frame of Q (mass M) into the frame of Q
-__device__ __forceinline__ void boost_from_rest(const double* Q, double M, const double* p, double* out) {
-  const double qp = Q[1] * p[1] + Q[2] * p[2] + Q[3] * p[3];
-  const double E = (Q[0] * p[0] + qp) / M;
-  const double c = (qp / (Q[0] + M) + p[0]) / M;
+template <typename K>
+__device__ __forceinline__ void boost_from_rest(const K* Q, K M, const K* p, K* out) {
+  const K qp = Q[1] * p[1] + Q[2] * p[2] + Q[3] * p[3];
+  const K E = (Q[0] * p[0] + qp) / M;
+  const K c = (qp / (Q[0] + M) + p[0]) / M;
   out[0] = E;
   out[1] = fma(c, Q[1], p[1]);
   out[2] = fma(c, Q[2], p[2]);
@@ -90,33 +93,41 @@ __device__ __forceinline__ void boost_from_rest(const double* Q, double M, const
 
 // root v in [0,1] of (k+1) v^k - k v^(k+1) = r, for k = 1 (closed form) and
 // k = 2 (trigonometric cubic solution), each followed by Newton polish
-__device__ __forceinline__ double mass_ratio(double r, int k) {
+template <typename K>
+__device__ __forceinline__ K mass_ratio(K r, int k) {
   if (k == 1) {
     // 2v - v^2 = r  ->  v = 1 - sqrt(1 - r) = r / (1 + sqrt(1 - r))
-    return r / (1.0 + sqrt(1.0 - r));
+    return r / (K(1) + sqrt(K(1) - r));
   }
   // 3 v^2 - 2 v^3 = r: v = 1/2 + cos(acos(1 - 2r)/3 - 2 pi/3)
-  double v = 0.5 + cos(acos(1.0 - 2.0 * r) * (1.0 / 3.0) - 2.0943951023931954923);
-  if (v < 0.0) v = 0.0;
-  if (v > 1.0) v = 1.0;
+  K v = K(0.5) + cos(acos(K(1) - K(2) * r) * K(1.0 / 3.0) - K(2.0943951023931954923));
+  if (v < K(0)) v = K(0);
+  if (v > K(1)) v = K(1);
   // Newton polish on f(v) = 3 v^2 - 2 v^3 - r, f' = 6 v (1 - v); restores
   // relative accuracy for small v, where the closed form cancels
-  if (v <= 0.0) v = sqrt(r / 3.0);
+  if (v <= K(0)) v = sqrt(r / K(3));
 #pragma unroll
   for (int it = 0; it < 3; ++it) {
-    const double fp = 6.0 * v * (1.0 - v);
-    if (fp > 0.0) v -= (v * v * (3.0 - 2.0 * v) - r) / fp;
+    const K fp = K(6) * v * (K(1) - v);
+    if (fp > K(0)) v -= (v * v * (K(3) - K(2) * v) - r) / fp;
   }
   return v;
 }
 
+__device__ __forceinline__ void sincos_turns(double t, double* s, double* c) { sincospi(2.0 * t, s, c); }
+__device__ __forceinline__ void sincos_turns(float t, float* s, float* c) { sincospif(2.0f * t, s, c); }
+
 // Full per-event kinematics.  edges: [ndim][nbins+1] (shared memory).
+// K = double: every step in FP64.  K = float: luminosity, RAMBO and cuts in
+// FP32; bins, map, Jacobian, Newton (polished to 1e-15 in FP64) and weight in FP64.
+template <typename K>
 __device__ __forceinline__ void sample_event(const SampleParams& sp, const double* edges, uint64_t seed, int iter,
-                                             uint64_t ev, EventKin& out) {
+                                             uint64_t ev, EventKin<K>& out) {
   double y[kMaxDim], x[kMaxDim];
   draw_uniforms(seed, iter, ev, sp.ndim, y);
   double jac = 1.0;
   const double nb = double(sp.nbins);
+#pragma unroll 1
   for (int j = 0; j < sp.ndim; ++j) {
     const double t = __dmul_rn(y[j], nb);
     int b = int(t);
@@ -131,40 +142,46 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
   double shat, lum = 1.0;
   int off = 0;
   if (sp.lumi) {
-    const double ua = x[0], ub = x[1];
-    const double lx1 = ua * sp.log_tau0;                 // ln x1
-    const double lx2 = ub * (1.0 - ua) * sp.log_tau0;    // ln x2 = ub ln(tau0/x1)
-    const double x1 = exp(lx1), x2 = exp(lx2);
-    shat = x1 * x2 * sp.sqrt_s * sp.sqrt_s;
-    const double f1 = sp.lumi_N * exp(sp.lumi_a * lx1) * pow(1.0 - x1, sp.lumi_b);
-    const double f2 = sp.lumi_N * exp(sp.lumi_a * lx2) * pow(1.0 - x2, sp.lumi_b);
-    lum = f1 * f2 * x1 * x2 * (1.0 - ua) * sp.log_tau0 * sp.log_tau0;
+    // ln x1 = u ln tau0, ln x2 = v (1 - u) ln tau0 (= v ln(tau0/x1));
+    // f(x1) f(x2) x1 x2 = N^2 exp((a + 1)(ln x1 + ln x2) + b (ln(1-x1) + ln(1-x2)))
+    const K lt = K(sp.log_tau0);
+    const K lx[2] = {K(x[0]) * lt, K(x[1]) * (K(1) - K(x[0])) * lt};
+    K l1m = K(0);
+#pragma unroll 1
+    for (int j = 0; j < 2; ++j) l1m += log1p(-exp(lx[j]));
+    const K lsum = lx[0] + lx[1];
+    shat = double(exp(lsum)) * sp.sqrt_s * sp.sqrt_s;
+    const K ff = exp(K(sp.lumi_a + 1.0) * lsum + K(sp.lumi_b) * l1m);
+    lum = sp.lumi_N * sp.lumi_N * double(ff) * (1.0 - x[0]) * sp.log_tau0 * sp.log_tau0;
     off = 2;
   } else {
     shat = sp.sqrt_s * sp.sqrt_s;
   }
   const double rs = sqrt(shat);
+  const K rsk = K(rs);
   const int n = sp.n_final;
   // RAMBO on diet: intermediate masses
-  double M[kMaxExt];
-  M[0] = rs;
-  for (int i = 2; i <= n - 1; ++i) M[i - 1] = M[i - 2] * sqrt(mass_ratio(x[off + i - 2], n - i));
-  M[n - 1] = 0.0;
-  double pm[kMaxExt][4];
-  double Q[4] = {rs, 0.0, 0.0, 0.0};
-  double MQ = rs;
+  K M[kMaxExt];
+  M[0] = rsk;
+#pragma unroll 1
+  for (int i = 2; i <= n - 1; ++i) M[i - 1] = M[i - 2] * sqrt(mass_ratio(K(x[off + i - 2]), n - i));
+  M[n - 1] = K(0);
+  K pm[kMaxExt][4];
+  K Q[4] = {rsk, K(0), K(0), K(0)};
+  K MQ = rsk;
+#pragma unroll 1
   for (int i = 1; i <= n - 1; ++i) {
-    const double Mi = M[i - 1], Mn = M[i];
-    const double q = (Mi - Mn) * (Mi + Mn) / (2.0 * Mi);
-    const double rc = x[off + n - 2 + 2 * (i - 1)];
-    const double rp = x[off + n - 2 + 2 * (i - 1) + 1];
-    const double cth = 2.0 * rc - 1.0;
-    const double sth = 2.0 * sqrt(rc * (1.0 - rc));
-    double sph, cph;
-    sincospi(2.0 * rp, &sph, &cph);
-    const double pr[4] = {q, q * sth * cph, q * sth * sph, q * cth};
-    const double Qr[4] = {Mi - q, -pr[1], -pr[2], -pr[3]};
-    double Qn[4];
+    const K Mi = M[i - 1], Mn = M[i];
+    const K q = (Mi - Mn) * (Mi + Mn) / (K(2) * Mi);
+    const K rc = K(x[off + n - 2 + 2 * (i - 1)]);
+    const K rp = K(x[off + n - 2 + 2 * (i - 1) + 1]);
+    const K cth = K(2) * rc - K(1);
+    const K sth = K(2) * sqrt(rc * (K(1) - rc));
+    K sph, cph;
+    sincos_turns(rp, &sph, &cph);
+    const K pr[4] = {q, q * sth * cph, q * sth * sph, q * cth};
+    const K Qr[4] = {Mi - q, -pr[1], -pr[2], -pr[3]};
+    K Qn[4];
     boost_from_rest(Q, MQ, pr, pm[i - 1]);
     boost_from_rest(Q, MQ, Qr, Qn);
     for (int c = 0; c < 4; ++c) Q[c] = Qn[c];
@@ -174,41 +191,67 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
   // Phi_n(s_hat)
   double phi = sp.phi_const;
   for (int i = 0; i < n - 2; ++i) phi *= shat;
-  // massive rescaling: particles 0, 1 carry mt, the rest are massless
+  // massive rescaling: particles 0, 1 carry mt, the rest are massless.
+  // sum_i sqrt(m_i^2 + xi^2 E_i^2) = sqrt(s) by Newton; with K = float the
+  // start comes from FP32 iterations, the FP64 steps then converge in 2-3.
+  // f(xi) = sum_{i=0,1} (sqrt(m^2 + xi^2 E_i^2) - m) + xi E_rest - (sqrt(s) - 2m), with
+  // sqrt(m^2 + u^2) - m = u^2 / (sqrt(m^2 + u^2) + m): no cancellation near
+  // threshold, so Newton reaches full relative precision in xi there too.
+  // Stop at |dxi| <= 1e-15 xi, or when the steps no longer shrink (the
+  // rounding floor, once below 1e-12 xi); 50 steps at most.
   const double m2 = sp.mt * sp.mt;
-  double Esum = 0.0;
-  for (int i = 0; i < n; ++i) Esum += pm[i][0];
-  double xi = sqrt(fmax(1.0 - (2.0 * sp.mt / rs) * (2.0 * sp.mt / rs), 0.0));
-  int converged = 0;
-  for (int it = 0; it < 50; ++it) {
-    double f = -rs, fp = 0.0;
-    for (int i = 0; i < n; ++i) {
-      const double E = pm[i][0];
-      if (i < 2) {
-        const double r = sqrt(fma(xi * E, xi * E, m2));
-        f += r;
-        fp += xi * E * E / r;
-      } else {
-        f += xi * E;
-        fp += E;
-      }
+  double E[kMaxExt];
+  double Erest = 0.0;
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) {
+    E[i] = double(pm[i][0]);
+    if (i >= 2) Erest += E[i];
+  }
+  const double thr = 2.0 * sp.mt;
+  const double excess = (shat - thr * thr) / (rs + thr);     // sqrt(s) - 2m
+  double xi = sqrt(fmax(excess * (rs + thr), 0.0)) / rs;     // sqrt(1 - (2m/sqrt(s))^2)
+  if constexpr (sizeof(K) < sizeof(double)) {
+    const K m2k = K(m2), mk = K(sp.mt), e0 = pm[0][0], e1 = pm[1][0], er = K(Erest), exk = K(excess);
+    K xk = K(xi);
+#pragma unroll 1
+    for (int it = 0; it < 20; ++it) {
+      const K u0 = xk * e0, u1 = xk * e1;
+      const K r0 = sqrt(fma(u0, u0, m2k)), r1 = sqrt(fma(u1, u1, m2k));
+      const K f = u0 * u0 / (r0 + mk) + u1 * u1 / (r1 + mk) + xk * er - exk;
+      const K fp = xk * (e0 * e0 / r0 + e1 * e1 / r1) + er;
+      const K d = f / fp;
+      xk -= d;
+      if (fabs(d) <= K(1e-6) * xk) break;
     }
+    if (xk > K(0) && xk < K(1)) xi = double(xk);
+  }
+  int converged = 0;
+  double prev = 0.0;
+#pragma unroll 1
+  for (int it = 0; it < 50; ++it) {
+    const double u0 = xi * E[0], u1 = xi * E[1];
+    const double r0 = sqrt(fma(u0, u0, m2)), r1 = sqrt(fma(u1, u1, m2));
+    const double f = u0 * u0 / (r0 + sp.mt) + u1 * u1 / (r1 + sp.mt) + xi * Erest - excess;
+    const double fp = xi * (E[0] * E[0] / r0 + E[1] * E[1] / r1) + Erest;
     const double dxi = f / fp;
     xi -= dxi;
-    if (fabs(dxi) <= 1e-15 * xi) { converged = 1; break; }
+    const double ad = fabs(dxi);
+    if (ad <= 1e-15 * xi || (it > 0 && ad <= 1e-12 * xi && ad >= 0.5 * prev)) { converged = 1; break; }
+    prev = ad;
   }
   double ksum = 0.0, kprod = 1.0, k2sum = 0.0;
+#pragma unroll 1
   for (int i = 0; i < n; ++i) {
-    const double E = pm[i][0];
-    const double k0 = (i < 2) ? sqrt(fma(xi * E, xi * E, m2)) : xi * E;
-    const double ka = xi * E;      // |k| = xi |p| = xi E for massless p
-    out.p[2 + i][0] = k0;
-    out.p[2 + i][1] = xi * pm[i][1];
-    out.p[2 + i][2] = xi * pm[i][2];
-    out.p[2 + i][3] = xi * pm[i][3];
+    const double ka = xi * E[i];      // |k| = xi |p| = xi E for massless p
+    const double k0 = (i < 2) ? sqrt(fma(ka, ka, m2)) : ka;
+    const double ik0 = 1.0 / k0;
+    out.p[2 + i][0] = K(k0);
+    out.p[2 + i][1] = K(xi * double(pm[i][1]));
+    out.p[2 + i][2] = K(xi * double(pm[i][2]));
+    out.p[2 + i][3] = K(xi * double(pm[i][3]));
     ksum += ka;
-    kprod *= ka / k0;
-    k2sum += ka * ka / k0;
+    kprod *= ka * ik0;
+    k2sum += ka * ka * ik0;
   }
   double wm = 1.0;
   {
@@ -216,26 +259,30 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
     for (int i = 0; i < 2 * n - 3; ++i) wm *= r;
     wm *= kprod * rs / k2sum;
   }
-  out.p[0][0] = 0.5 * rs; out.p[0][1] = 0.0; out.p[0][2] = 0.0; out.p[0][3] = 0.5 * rs;
-  out.p[1][0] = 0.5 * rs; out.p[1][1] = 0.0; out.p[1][2] = 0.0; out.p[1][3] = -0.5 * rs;
+  const K hr = K(0.5 * rs);
+  out.p[0][0] = hr; out.p[0][1] = K(0); out.p[0][2] = K(0); out.p[0][3] = hr;
+  out.p[1][0] = hr; out.p[1][1] = K(0); out.p[1][2] = K(0); out.p[1][3] = -hr;
   // cuts on the final gluons (particles 4..)
   int pass = converged;
   if (sp.pt_cut2 > 0.0) {
     for (int g = 4; g < 2 + n; ++g) {
-      const double pt2 = out.p[g][1] * out.p[g][1] + out.p[g][2] * out.p[g][2];
-      pass &= (pt2 > sp.pt_cut2) ? 1 : 0;
+      const K pt2 = out.p[g][1] * out.p[g][1] + out.p[g][2] * out.p[g][2];
+      pass &= (pt2 > K(sp.pt_cut2)) ? 1 : 0;
     }
   }
   if (sp.dr_cut2 > 0.0) {
+    // Delta y = ln[(E_g + z_g)(E_h - z_h) / ((E_g - z_g)(E_h + z_h))] / 2,
+    // Delta phi = atan2(cross, dot) of the transverse momenta (in [-pi, pi])
+#pragma unroll 1
     for (int g = 4; g < 2 + n; ++g) {
+#pragma unroll 1
       for (int h = g + 1; h < 2 + n; ++h) {
-        const double yg = 0.5 * log((out.p[g][0] + out.p[g][3]) / (out.p[g][0] - out.p[g][3]));
-        const double yh = 0.5 * log((out.p[h][0] + out.p[h][3]) / (out.p[h][0] - out.p[h][3]));
-        double dphi = atan2(out.p[g][2], out.p[g][1]) - atan2(out.p[h][2], out.p[h][1]);
-        if (dphi > kPi) dphi -= 2.0 * kPi;
-        if (dphi < -kPi) dphi += 2.0 * kPi;
-        const double dy = yg - yh;
-        pass &= (dy * dy + dphi * dphi > sp.dr_cut2) ? 1 : 0;
+        const K dy = K(0.5) * log(((out.p[g][0] + out.p[g][3]) * (out.p[h][0] - out.p[h][3])) /
+                                  ((out.p[g][0] - out.p[g][3]) * (out.p[h][0] + out.p[h][3])));
+        const K cr = out.p[g][1] * out.p[h][2] - out.p[g][2] * out.p[h][1];
+        const K dt = out.p[g][1] * out.p[h][1] + out.p[g][2] * out.p[h][2];
+        const K dphi = atan2(cr, dt);
+        pass &= (dy * dy + dphi * dphi > K(sp.dr_cut2)) ? 1 : 0;
       }
     }
   }

@@ -11,9 +11,12 @@ Writes ``csrc/mf_gen_ttng.cuh``:
 * tables of the colour-ordered gluon sub-currents ("blocks"): every ordered
   tuple of distinct gluons up to reversal, with its splits into two and three
   consecutive parts (three-gluon and four-gluon vertices);
-* straight-line device code, per gluon count, for the heavy-quark line of one
-  helicity lane: the suffix currents R(S), the colour-ordered amplitudes
-  J_sigma for both top helicities, and the colour sum J^dagger (D C) J.
+* the depth-first tree of ordered suffixes of the heavy-quark line (which
+  sub-currents build each suffix current R(S) and each amplitude J_sigma), read
+  by a loop in the kernel (compact code: every lane of a warp walks the same
+  path with its own helicities);
+* straight-line code of the colour sum J^dagger (D C) J of one helicity with
+  the integer colour matrix as immediates.
 
 The quark line is (T^{a_sigma1} ... T^{a_sigman})_{i_t j_tbar}: gluon sigma1
 sits next to the outgoing top, so with R() = v(tbar) and
@@ -154,76 +157,84 @@ def emit_tables(n, lines):
             lines.append(f"template <> __device__ __forceinline__ const uint8_t* o4_table<{n}, {k}>() {{ return kO4_{n}_{k}; }}")
 
 
-def emit_lane(n, lines, colour):
-    """Straight-line quark-line code for one helicity lane."""
+def lane_paths(n):
+    """Depth-first tree of ordered suffixes S (gluons next to the antitop).
+
+    Returns per level l = 1..n-1 a list of entries (suffix, parent index in
+    level l-1, block refs of S[:m] for m = 1..l); the entries of one parent are
+    contiguous, and level 0 is the empty suffix.  Level n-1 entries also carry
+    their completion sigma = (a,) + S: its colour-order index and block refs
+    of sigma[:m] for m = 1..n.
+    """
     bl, ids, off, nstore, first, o3, o4 = tables(n)
-    orders, M, D = colour
+    orders = list(itertools.permutations(range(n)))
     oid = {o: i for i, o in enumerate(orders)}
-    L = []
-    L.append("// One lane: fixed gluon helicities (word H) and tbar helicity (spinor vb).")
-    L.append("// Returns sum over both top helicities of J^dagger (D C) J for the")
-    L.append(f"// {math.factorial(n)} colour orderings (integer colour matrix, D = {D}).")
-    L.append("template <typename T>")
-    L.append(f"__device__ __forceinline__ T lane_colour_sum_{n}(const R4<T>* __restrict__ q, const R4<T>& qtb, T m, T mw,")
-    L.append("    const V4<T>* __restrict__ Gs, unsigned H, const S4<T>& vb, const S4<T>& ub0, const S4<T>& ub1,")
-    L.append(f"    cplx<T> (&J)[{math.factorial(n)}][2]) {{")
+    levels = [[((), -1, [])]]
+    for l in range(1, n):
+        cur = []
+        for pi, (S, _, _) in enumerate(levels[-1]):
+            for g in range(n):
+                if g in S:
+                    continue
+                T = (g,) + S
+                refs = [block_ref(T[:m], ids) for m in range(1, l + 1)]
+                cur.append((T, pi, refs))
+        levels.append(cur)
+    final = []
+    for (S, _, _) in levels[n - 1]:
+        a = [g for g in range(n) if g not in S][0]
+        sig = (a,) + S
+        final.append((oid[sig], [block_ref(sig[:m], ids) for m in range(1, n + 1)]))
+    return levels, final
 
-    def need(t):
-        """Slash matrix of block t at this lane's helicities, loaded where used."""
-        i, s = block_ref(tuple(t), ids)
-        msk = mask(bl[i])
-        bits = [g for g in range(n) if msk >> g & 1]
-        ex = " | ".join(f"(((H >> {g}) & 1u) << {j})" for j, g in enumerate(bits))
-        ld = f"Gs[{off[i]} + ({ex})]"
-        return f"make_slash({ld})" if s > 0 else f"make_slash(neg({ld}))"
 
-    body = []
-
-    def psum(S):
-        terms = " + ".join(f"q[{g}]" for g in S)
-        return f"-(qtb + {terms})"
-
-    def rec(suffix, rnames, depth):
-        # suffix: tuple of gluons already placed at the tbar end (ordered)
-        remaining = [g for g in range(n) if g not in suffix]
-        if len(remaining) == 1:
-            a = remaining[0]
-            sigma = (a,) + suffix
-            parts = []
-            for l in range(1, n + 1):
-                B, Sp = sigma[:l], sigma[l:]
-                rn = rnames[Sp] if Sp else "vb"
-                parts.append((need(B), rn))
-            ind = "  " * depth
-            body.append(f"{ind}{{ S4<T> W = apply({parts[0][0]}, {parts[0][1]});")
-            for sl, rn in parts[1:]:
-                body.append(f"{ind}  apply_acc({sl}, {rn}, W);")
-            k = oid[sigma]
-            body.append(f"{ind}  J[{k}][0] = rowdot(ub0, W); J[{k}][1] = rowdot(ub1, W); }}")
-            return
-        for b in remaining:
-            S = (b,) + suffix
-            name = "R" + "".join(map(str, S))
-            ind = "  " * depth
-            body.append(f"{ind}{{ S4<T> {name};")
-            body.append(f"{ind}  {{ S4<T> X = apply({need(S[:1])}, {rnames[S[1:]] if S[1:] else 'vb'});")
-            for l in range(2, len(S) + 1):
-                B, Sp = S[:l], S[l:]
-                body.append(f"{ind}    apply_acc({need(B)}, {rnames[Sp] if Sp else 'vb'}, X);")
-            body.append(f"{ind}    {name} = quark_prop(R4<T>({psum(S)}), m, mw, X); }}")
-            rn = dict(rnames)
-            rn[S] = name
-            rec(S, rn, depth + 1)
-            body.append(f"{ind}}}")
-
-    rec((), {}, 1)
-    L += body
-    # colour sum
-    L.append("  T tot = T(0);")
-    L.append("#pragma unroll")
-    L.append("  for (int h = 0; h < 2; ++h) {")
-    L.append("    T s = T(0);")
+def emit_lane(n, lines, colour):
+    """Path tables of the quark line and the colour sum of one helicity lane."""
+    levels, final = lane_paths(n)
+    orders, M, D = colour
     P = len(orders)
+    # per level: first child of every parent, suffix mask, block refs
+    child0 = [0] * (n + 1)
+    for l in range(1, n):
+        rows_mask = [mask(S) for (S, _, _) in levels[l]]
+        refs = [_pack(i, sg) for (_, _, r) in levels[l] for (i, sg) in r]
+        firsts = []
+        for pi in range(len(levels[l - 1])):
+            firsts.append(next(k for k, e in enumerate(levels[l]) if e[1] == pi))
+        lines.append(f"static __constant__ uint8_t kPathMask{n}_{l}[{len(rows_mask)}] = {{{', '.join(map(str, rows_mask))}}};")
+        lines.append(f"static __constant__ uint8_t kPathBlk{n}_{l}[{len(refs)}] = {{{', '.join(map(str, refs))}}};")
+        lines.append(f"static __constant__ uint8_t kPathFirst{n}_{l}[{len(firsts)}] = {{{', '.join(map(str, firsts))}}};")
+    fsig = [o for (o, _) in final]
+    frefs = [_pack(i, sg) for (_, r) in final for (i, sg) in r]
+    lines.append(f"static __constant__ uint8_t kFinalSigma{n}[{len(fsig)}] = {{{', '.join(map(str, fsig))}}};")
+    lines.append(f"static __constant__ uint8_t kFinalBlk{n}[{len(frefs)}] = {{{', '.join(map(str, frefs))}}};")
+    lines.append(f"template <> struct Paths<{n}> {{")
+    for l in range(1, n):
+        lines.append(f"  static __device__ __forceinline__ const uint8_t* mask_{l}() {{ return kPathMask{n}_{l}; }}")
+    lines.append("  template <int LV> static __device__ __forceinline__ uint8_t mask(int p) {")
+    for l in range(1, n):
+        lines.append(f"    if constexpr (LV == {l}) return kPathMask{n}_{l}[p];")
+    lines.append("    return 0;")
+    lines.append("  }")
+    lines.append("  template <int LV> static __device__ __forceinline__ uint8_t blk(int p, int m) {")
+    for l in range(1, n):
+        lines.append(f"    if constexpr (LV == {l}) return kPathBlk{n}_{l}[p * {l} + m];")
+    lines.append("    return 0;")
+    lines.append("  }")
+    lines.append("  template <int LV> static __device__ __forceinline__ int first(int parent) {")
+    for l in range(1, n):
+        lines.append(f"    if constexpr (LV == {l}) return kPathFirst{n}_{l}[parent];")
+    lines.append("    return 0;")
+    lines.append("  }")
+    lines.append(f"  static __device__ __forceinline__ uint8_t final_sigma(int p) {{ return kFinalSigma{n}[p]; }}")
+    lines.append(f"  static __device__ __forceinline__ uint8_t final_blk(int p, int m) {{ return kFinalBlk{n}[p * {n} + m]; }}")
+    lines.append("};")
+    # colour sum of one helicity from J held in registers
+    L = []
+    L.append(f"// J^dagger (D C) J of one helicity over the {P} colour orderings (D = {D}).")
+    L.append("template <typename T>")
+    L.append(f"__device__ __forceinline__ T colour_form_{n}(const cplx<T> (&J)[{P}]) {{")
+    L.append("  T s = T(0);")
     for a in range(P):
         terms = []
         for b in range(a, P):
@@ -235,14 +246,13 @@ def emit_lane(n, lines, colour):
         if not terms:
             continue
         b0, c0 = terms[0]
-        L.append(f"    {{ cplx<T> y = T({float(c0)!r}) * J[{b0}][h];")
+        L.append(f"  {{ cplx<T> y = T({float(c0)!r}) * J[{b0}];")
         for b, c in terms[1:]:
-            L.append(f"      y = rfma(T({float(c)!r}), J[{b}][h], y);")
-        L.append(f"      s = fma(J[{a}][h].r, y.r, fma(J[{a}][h].i, y.i, s)); }}")
-    L.append("    tot += T(2) * s;")
-    L.append("  }")
-    L.append("  return tot;")
+            L.append(f"    y = rfma(T({float(c)!r}), J[{b}], y);")
+        L.append(f"    s = fma(J[{a}].r, y.r, fma(J[{a}].i, y.i, s)); }}")
+    L.append("  return T(2) * s;")
     L.append("}")
+    L.append(f"template <typename T> __device__ __forceinline__ T colour_form(const cplx<T> (&J)[{P}]) {{ return colour_form_{n}<T>(J); }}")
     lines += L
 
 
@@ -260,6 +270,7 @@ def render():
         "template <int NG, int K> __device__ __forceinline__ const uint8_t* o4_table();",
         "template <int NG> __device__ __forceinline__ const uint8_t* blk_mask();",
         "template <int NG> __device__ __forceinline__ const uint16_t* blk_off();",
+        "template <int NG> struct Paths;",
         "template <typename T> __device__ __forceinline__ V4<T> neg(const V4<T>& a) {",
         "  V4<T> o;",
         "#pragma unroll",
