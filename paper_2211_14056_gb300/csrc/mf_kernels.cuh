@@ -467,28 +467,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused(SampleParams sp, MeParams
 
 // ----------------------------------------------------------------------------
 // Two-kernel iteration: k_sample_rec writes one compact record per event
-// (coalesced, SoA), k_me_acc reads the records back, evaluates |M|^2 for the
-// events that passed and accumulates the Vegas sums.  Splitting the sampling
-// (a long, branchy FP64/transcendental code path) from the amplitude loop keeps
-// the amplitude kernel's instruction footprint small; the records cost
-// ~2 x 90 bytes of HBM traffic per event, negligible next to ~1 MFLOP of
-// amplitude work.
+// (coalesced, SoA) and the list of events that passed the cuts; k_me_acc
+// walks that list with one lane group per event, like k_matrix_element,
+// evaluates |M|^2 and accumulates the Vegas sums (events that failed add 0 to
+// every sum).  Splitting the sampling (a long, branchy FP64/transcendental
+// code path) from the amplitude loop keeps the amplitude kernel's instruction
+// working set small and its warps in step; the records cost ~2 x 90 bytes of
+// HBM traffic per event, negligible next to ~1 MFLOP of amplitude work.
 //
 // Record layout for a chunk of C events (K = kinematics type):
 //   mom  [n_final*4][C] K    final-state momenta (t, tbar, gluons), components E, px, py, pz
 //   rs   [C]            K    partonic sqrt(s_hat) (the beams are (rs/2)(1, 0, 0, +-1))
 //   pref [C]            f64  weight without |M|^2
-//   flag [ndim + 2][C]  u8   Vegas bin of each dimension, then pass, then Newton miss
+//   flag [ndim][C]      u8   Vegas bin of each dimension
+//   list [C]            i32  positions of the events that passed (first *count entries)
+//   count[2]            u32  events that passed, Newton misses
 template <typename K> struct RecordView {
   K* mom;
   K* rs;
   double* pref;
   uint8_t* flag;
+  int* list;
+  unsigned* count;
   int64_t C;
+  __host__ __device__ static size_t al(size_t x) { return (x + 255) & ~size_t(255); }
   __host__ __device__ static size_t bytes(int n_final, int ndim, int64_t C) {
-    const size_t a = (size_t(n_final) * 4 + 1) * sizeof(K) * C;
-    const size_t b = ((a + 255) & ~size_t(255)) + sizeof(double) * C;
-    return ((b + 255) & ~size_t(255)) + size_t(ndim + 2) * C;
+    size_t o = al((size_t(n_final) * 4 + 1) * sizeof(K) * C);
+    o = al(o + sizeof(double) * C);
+    o = al(o + size_t(ndim) * C);
+    o = al(o + sizeof(int) * C);
+    return o + 2 * sizeof(unsigned);
   }
   __host__ __device__ static RecordView carve(void* base, int n_final, int ndim, int64_t C) {
     RecordView v;
@@ -496,35 +504,57 @@ template <typename K> struct RecordView {
     v.C = C;
     v.mom = reinterpret_cast<K*>(p);
     v.rs = v.mom + size_t(n_final) * 4 * C;
-    const size_t a = (size_t(n_final) * 4 + 1) * sizeof(K) * C;
-    const size_t o1 = (a + 255) & ~size_t(255);
-    v.pref = reinterpret_cast<double*>(p + o1);
-    const size_t o2 = (o1 + sizeof(double) * C + 255) & ~size_t(255);
-    v.flag = p + o2;
+    size_t o = al((size_t(n_final) * 4 + 1) * sizeof(K) * C);
+    v.pref = reinterpret_cast<double*>(p + o);
+    o = al(o + sizeof(double) * C);
+    v.flag = p + o;
+    o = al(o + size_t(ndim) * C);
+    v.list = reinterpret_cast<int*>(p + o);
+    o = al(o + sizeof(int) * C);
+    v.count = reinterpret_cast<unsigned*>(p + o);
     return v;
   }
 };
 
+// rec.count must be zero on entry.  Weights of the events that failed are
+// written here (0); k_me_acc writes the others.
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_sample_rec(SampleParams sp, const double* __restrict__ edges_g,
                                                          int64_t first_event, int64_t n, uint64_t seed, int iter,
-                                                         RecordView<K> rec) {
+                                                         RecordView<K> rec, double* __restrict__ w_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* edges = reinterpret_cast<double*>(smem_raw);
   for (int i = threadIdx.x; i < sp.ndim * (sp.nbins + 1); i += blockDim.x) edges[i] = edges_g[i];
   __syncthreads();
   const int nf = sp.n_final;
-  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
-    EventKin<K> k;
-    sample_event(sp, edges, seed, iter, uint64_t(first_event + e), k);
-    for (int i = 0; i < nf; ++i)
+  const int lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < n; base += stride) {
+    const int64_t e = base + threadIdx.x;
+    int pass = 0, fail = 0;
+    if (e < n) {
+      EventKin<K> k;
+      sample_event(sp, edges, seed, iter, uint64_t(first_event + e), k);
+      for (int i = 0; i < nf; ++i)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) rec.mom[int64_t(i * 4 + c) * rec.C + e] = k.p[2 + i][c];
-    rec.rs[e] = k.p[0][0] + k.p[1][0];
-    rec.pref[e] = k.prefactor;
-    for (int j = 0; j < sp.ndim; ++j) rec.flag[int64_t(j) * rec.C + e] = k.bins[j];
-    rec.flag[int64_t(sp.ndim) * rec.C + e] = uint8_t(k.pass);
-    rec.flag[int64_t(sp.ndim + 1) * rec.C + e] = uint8_t(k.newton_fail);
+        for (int c = 0; c < 4; ++c) rec.mom[int64_t(i * 4 + c) * rec.C + e] = k.p[2 + i][c];
+      rec.rs[e] = k.p[0][0] + k.p[1][0];
+      rec.pref[e] = k.prefactor;
+      for (int j = 0; j < sp.ndim; ++j) rec.flag[int64_t(j) * rec.C + e] = k.bins[j];
+      pass = k.pass;
+      fail = k.newton_fail;
+      if (!pass && w_out != nullptr) w_out[e] = 0.0;
+    }
+    const unsigned bal = __ballot_sync(full, pass);
+    const unsigned fbal = __ballot_sync(full, fail);
+    unsigned pos = 0;
+    if (lane == 0) {
+      if (bal) pos = atomicAdd(&rec.count[0], unsigned(__popc(bal)));
+      if (fbal) atomicAdd(&rec.count[1], unsigned(__popc(fbal)));
+    }
+    pos = __shfl_sync(full, pos, 0);
+    if (pass) rec.list[pos + __popc(bal & ((1u << lane) - 1u))] = int(e);
   }
 }
 
@@ -536,12 +566,12 @@ template <int NG, typename T> struct MeAccLayout {
   __host__ __device__ static size_t total(int nacc) { return al(warps(nacc) + WarpMem<NG, T>::bytes * kWarps); }
 };
 
-// |M|^2 of the records that passed, weights, Vegas sums.  Every warp takes its
-// own blocks of 32 records; partials[blockIdx.x * nacc + k] receive (accumulate
-// = 0) or add (accumulate = 1) the CTA's sums, counters likewise.
+// |M|^2 of the listed events, weights, Vegas sums.  partials[blockIdx.x * nacc + k]
+// receive (accumulate = 0) or add (accumulate = 1) the CTA's sums; block 0
+// also carries the chunk's counters.
 template <int NG, typename T>
 __global__ void __launch_bounds__(kThreads, 2) k_me_acc(MeParams mp, int ndim, int nbins, RecordView<T> rec,
-                                                        int64_t n, int accumulate, double* __restrict__ partials,
+                                                        int accumulate, double* __restrict__ partials,
                                                         unsigned long long* __restrict__ counters,
                                                         double* __restrict__ w_out) {
   using LY = MeAccLayout<NG, T>;
@@ -555,86 +585,52 @@ __global__ void __launch_bounds__(kThreads, 2) k_me_acc(MeParams mp, int ndim, i
   unsigned char* wm = smem_raw + LY::warps(nacc) + warp * WarpMem<NG, T>::bytes;
   for (int i = t; i < ndim * nbins; i += kThreads) hist[i] = 0.0;
   if (t < 2) sums[t] = 0.0;
-  unsigned long long npass = 0, nfail = 0;
   const T mt = T(mp.mt), mw = T(mp.mw);
   const unsigned full = 0xffffffffu;
+  const int64_t npass = rec.count[0];
+  double s1 = 0.0, s2 = 0.0;
   __syncthreads();
 
-  const int64_t stride = int64_t(gridDim.x) * kWarps * 32;
-  for (int64_t base = (int64_t(blockIdx.x) * kWarps + warp) * 32; base < n; base += stride) {
-    const int64_t e = base + lane;
-    const bool valid = e < n;
-    T mine[NEXT][4];
-    double pref = 0.0;
-    uint8_t bins[kMaxDim];
-    int pass = 0;
-    if (valid) {
-      const T rs = rec.rs[e];
-      mine[0][0] = T(0.5) * rs; mine[0][1] = T(0); mine[0][2] = T(0); mine[0][3] = T(0.5) * rs;
-      mine[1][0] = T(0.5) * rs; mine[1][1] = T(0); mine[1][2] = T(0); mine[1][3] = T(-0.5) * rs;
+  const int64_t stride = int64_t(gridDim.x) * kWarps * EPW;
+  for (int64_t base = (int64_t(blockIdx.x) * kWarps + warp) * EPW; base < npass; base += stride) {
+    const int64_t k = base + group;
+    const bool ok = k < npass;
+    const int64_t e = rec.list[ok ? k : base];
+    T p[NEXT][4];
+    const T rs = rec.rs[e];
+    p[0][0] = T(0.5) * rs; p[0][1] = T(0); p[0][2] = T(0); p[0][3] = T(0.5) * rs;
+    p[1][0] = T(0.5) * rs; p[1][1] = T(0); p[1][2] = T(0); p[1][3] = T(-0.5) * rs;
 #pragma unroll
-      for (int i = 0; i < NG; ++i)
+    for (int i = 0; i < NG; ++i)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) mine[2 + i][c] = rec.mom[int64_t(i * 4 + c) * rec.C + e];
-      pref = rec.pref[e];
-      for (int j = 0; j < ndim; ++j) bins[j] = rec.flag[int64_t(j) * rec.C + e];
-      pass = rec.flag[int64_t(ndim) * rec.C + e];
-      npass += pass;
-      nfail += rec.flag[int64_t(ndim + 1) * rec.C + e];
-    } else {
-#pragma unroll
-      for (int i = 0; i < NEXT; ++i)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) mine[i][c] = T(0);
-      for (int j = 0; j < kMaxDim; ++j) bins[j] = 0;
-    }
-    double me = 0.0;
-    unsigned todo = __ballot_sync(full, valid && pass);
-    while (todo) {
-      int src = -1;
-      unsigned rest = todo;
-#pragma unroll
-      for (int g = 0; g < EPW; ++g) {
-        const int b = rest ? __ffs(rest) - 1 : -1;
-        if (g == group) src = b;
-        if (rest) rest &= rest - 1u;
+      for (int c = 0; c < 4; ++c) p[2 + i][c] = rec.mom[int64_t(i * 4 + c) * rec.C + e];
+    const T v = group_me2<NG, T>(p, wm, group, gl, mt, mw);
+    if (ok) {
+      const double w = double(v) * mp.norm * rec.pref[e];
+      if (gl == 0) {
+        s1 += w;
+        s2 += w * w;
+        if (w_out != nullptr) w_out[e] = w;
       }
-      const int from = src < 0 ? 0 : src;
-      T p[NEXT][4];
-#pragma unroll
-      for (int i = 0; i < NEXT; ++i)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) p[i][c] = __shfl_sync(full, mine[i][c], from);
-      const T v = group_me2<NG, T>(p, wm, group, gl, mt, mw);
-#pragma unroll
-      for (int g = 0; g < EPW; ++g) {
-        const T vg = __shfl_sync(full, v, g * L);
-        const int sg = __shfl_sync(full, src, g * L);
-        if (sg == lane) me = double(vg) * mp.norm;
-      }
-      todo = rest;
+      if (gl < ndim) atomicAdd(&hist[gl * nbins + rec.flag[int64_t(gl) * rec.C + e]], w * w);
     }
-    const double w = valid ? me * pref : 0.0;
-    if (w_out != nullptr && valid) w_out[e] = w;
-    accumulate_event(w, bins, ndim, nbins, sums, hist);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    s1 += __shfl_xor_sync(full, s1, off);
+    s2 += __shfl_xor_sync(full, s2, off);
+  }
+  if (lane == 0) {
+    atomicAdd(&sums[0], s1);
+    atomicAdd(&sums[1], s2);
   }
   __syncthreads();
   double* dst = partials + int64_t(blockIdx.x) * nacc;
   for (int i = t; i < ndim * nbins; i += kThreads) dst[2 + i] = (accumulate ? dst[2 + i] : 0.0) + hist[i];
   if (t < 2) dst[t] = (accumulate ? dst[t] : 0.0) + sums[t];
-  for (int off = 16; off > 0; off >>= 1) {
-    npass += __shfl_xor_sync(full, npass, off);
-    nfail += __shfl_xor_sync(full, nfail, off);
+  if (t < 2) {
+    const unsigned long long c = blockIdx.x == 0 ? (unsigned long long)rec.count[t] : 0ull;
+    counters[blockIdx.x * 2 + t] = (accumulate ? counters[blockIdx.x * 2 + t] : 0ull) + c;
   }
-  __shared__ unsigned long long cnt[2];
-  if (t < 2) cnt[t] = 0;
-  __syncthreads();
-  if (lane == 0) {
-    atomicAdd(&cnt[0], npass);
-    atomicAdd(&cnt[1], nfail);
-  }
-  __syncthreads();
-  if (t < 2) counters[blockIdx.x * 2 + t] = (accumulate ? counters[blockIdx.x * 2 + t] : 0ull) + cnt[t];
 }
 
 // host-side launch helpers (defined per gluon count)
@@ -742,14 +738,18 @@ cudaError_t launch_fma_peak(int precision, int blocks, int iters, float* sink, c
     const int sgrid = int(need < int64_t(sms) * 16 ? need : int64_t(sms) * 16);                                  \
     if (precision == 0) {                                                                                         \
       RecordView<double> rec = RecordView<double>::carve(rec_base, sp.n_final, sp.ndim, C);                       \
-      k_sample_rec<double><<<sgrid, kThreads, esm, s>>>(sp, edges, first_event, n, seed, iter, rec);              \
+      cudaError_t e = cudaMemsetAsync(rec.count, 0, 2 * sizeof(unsigned), s);                                    \
+      if (e != cudaSuccess) return e;                                                                             \
+      k_sample_rec<double><<<sgrid, kThreads, esm, s>>>(sp, edges, first_event, n, seed, iter, rec, w_out);       \
       k_me_acc<NG, double><<<grid, kThreads, MeAccLayout<NG, double>::total(nacc), s>>>(                          \
-          mp, sp.ndim, sp.nbins, rec, n, accumulate, partials, counters, w_out);                                  \
+          mp, sp.ndim, sp.nbins, rec, accumulate, partials, counters, w_out);                                     \
     } else {                                                                                                      \
       RecordView<float> rec = RecordView<float>::carve(rec_base, sp.n_final, sp.ndim, C);                         \
-      k_sample_rec<float><<<sgrid, kThreads, esm, s>>>(sp, edges, first_event, n, seed, iter, rec);               \
+      cudaError_t e = cudaMemsetAsync(rec.count, 0, 2 * sizeof(unsigned), s);                                     \
+      if (e != cudaSuccess) return e;                                                                             \
+      k_sample_rec<float><<<sgrid, kThreads, esm, s>>>(sp, edges, first_event, n, seed, iter, rec, w_out);        \
       k_me_acc<NG, float><<<grid, kThreads, MeAccLayout<NG, float>::total(nacc), s>>>(                            \
-          mp, sp.ndim, sp.nbins, rec, n, accumulate, partials, counters, w_out);                                  \
+          mp, sp.ndim, sp.nbins, rec, accumulate, partials, counters, w_out);                                     \
     }                                                                                                             \
     return cudaGetLastError();                                                                                    \
   }                                                                                                               \
