@@ -265,10 +265,12 @@ def main():
     r32 = _iter(p32, g32, 1000, False, w32, dist, torch, w, first, n, world)
     r64 = _iter(p64, g64, 1000, False, w64, dist, torch, w, first, n, world)
     sig_err = abs(r32["I_k"] / r64["I_k"] - 1)
-    nz = w64 != 0
-    relw = ((w32[nz] - w64[nz]).abs() / w64[nz].abs()).double()
+    both = (w64 != 0) & (w32 != 0)
+    flips = int(((w64 != 0) ^ (w32 != 0)).sum())      # cut / threshold decisions taken differently
+    relw = ((w32[both] - w64[both]).abs() / w64[both].abs()).double()
     ev_err = {"max": float(relw.max()), "median": float(relw.median()),
-              "p999": float(torch.quantile(relw[: 2 ** 24].float(), 0.999))}
+              "p999": float(torch.quantile(relw[: 2 ** 24].float(), 0.999)),
+              "decision_flips": flips, "events_compared": int(both.sum())}
     del w32, w64
 
     # 3. FP64 arm timing (1 warm-up + 2 steps)
@@ -277,7 +279,8 @@ def main():
     def timed(proc, grid, steps, warm, base_it):
         for i in range(warm):
             _iter(proc, grid, base_it + i, True, None, dist, torch, w, first, n, world)
-        times, acc_times, passes = [], [], []
+        grid.profile(True)
+        times, acc_times, passes, me_times = [], [], [], []
         launches0 = mf.kernel_launches()
         for i in range(steps):
             flush.fill_(float(i))
@@ -296,15 +299,18 @@ def main():
             times.append(e0.elapsed_time(e2))
             acc_times.append(e0.elapsed_time(e1))
             passes.append(r["n_pass"])
+            smp_ms, me_ms, chunks = grid.profile_read()
+            me_times.append((me_ms, chunks, smp_ms))
         launches = mf.kernel_launches() - launches0
-        return times, acc_times, passes, launches
+        grid.profile(False)
+        return times, acc_times, passes, launches, me_times
 
-    t64, a64, pass64, _ = timed(p64, g64, 2, 1, 2000)
+    t64, a64, pass64, _, me64 = timed(p64, g64, 2, 1, 2000)
     ms64 = _max_over_ranks(statistics.mean(t64), dist, torch)
 
     # 4. headline FP32 arm: K timed steps (clocks sampled meanwhile)
     with ClockSampler(local) as clk:
-        t32, a32, pass32, launches = timed(p32, g32, args.steps, args.warmup, 3000)
+        t32, a32, pass32, launches, me32 = timed(p32, g32, args.steps, args.warmup, 3000)
     ms32 = _max_over_ranks(sum(t32) / args.steps, dist, torch)
     value = n * world / (ms32 * 1e-3)
     value64 = n * world / (ms64 * 1e-3)
@@ -319,13 +325,16 @@ def main():
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_value = n / e2e_s
 
-    # 6. roofline of the fused kernel (FMA pipes): algorithmic flops / measured time
+    # 6. roofline of the dominant kernel, k_me_acc (FMA pipes): algorithmic
+    #    flops of the events it evaluates / its CUDA-event time on the stream
     fpe = mflops.me2_flops_per_event(ng)
-    acc_ms = statistics.mean(a32)
-    achieved = fpe * statistics.mean(pass32) / world / (acc_ms * 1e-3) / 1e12
+    me_ms = statistics.mean(m[0] for m in me32)
+    chunks = me32[0][1]
+    achieved = fpe * statistics.mean(pass32) / (me_ms * 1e-3) / 1e12
     peak_meas = mf.fma_throughput(mf.MF_FP32)
     peak64_meas = mf.fma_throughput(mf.MF_FP64)
-    achieved64 = fpe * statistics.mean(pass64) / world / (statistics.mean(a64) * 1e-3) / 1e12
+    achieved64 = fpe * statistics.mean(pass64) / (statistics.mean(m[0] for m in me64) * 1e-3) / 1e12
+    traffic = _ncu_traffic("k_me_acc_gg_ttxgg_fp32")
 
     # 7. CPU baseline: the oracle on the host cores (rank 0 only, N = 1 only)
     cpu = None
@@ -350,10 +359,14 @@ def main():
             "sigma_rel_err_fp32_vs_fp64": sig_err, "event_rel_err_fp32": ev_err,
             "pass_fraction": statistics.mean(pass32) / (n * world),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_meas, "unit": "TFLOP/s",
-                         "frac": achieved / peak_meas, "traffic": None,
-                         "kernel": "k_fused<4,float>", "flops_per_event": fpe,
-                         "peak_source": "measured FP32 FMA chains on all SMs (mf_fma_throughput)",
-                         "fp64": {"achieved": achieved64, "peak": peak64_meas, "frac": achieved64 / peak64_meas}},
+                         "frac": achieved / peak_meas, "traffic": traffic,
+                         "kernel": "k_me_acc<4,float>", "flops_per_event": fpe,
+                         "launch_ms": me_ms / chunks, "launches_per_step": chunks,
+                         "sampling_ms_per_step": statistics.mean(m[2] for m in me32),
+                         "peak_source": "measured FP32 FMA chains on all SMs (mf_fma_throughput), "
+                                        "'of measured'",
+                         "fp64": {"kernel": "k_me_acc<4,double>", "achieved": achieved64, "peak": peak64_meas,
+                                  "frac": achieved64 / peak64_meas}},
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": int(frozen.nbytes),
                     "d2h_bytes_per_step": 48},
             "gpu_launches": launches,
@@ -365,6 +378,24 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def _ncu_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", name + ".json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2211_14056_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    if rec.get("sources_sha256") != h.hexdigest():
+        return None
+    return rec.get("dram_bytes_per_launch")
 
 
 def _allreduce_totals(dist, grid, torch):

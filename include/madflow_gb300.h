@@ -181,10 +181,51 @@ mf_status mf_vegas_finish(mf_process* proc, mf_grid* grid, int64_t n_total, int 
 mf_status mf_vegas_accumulate_static(mf_process* proc, const double* edges, int nbins, uint64_t seed, int iter,
                                      int64_t first_event, int64_t n, double* totals, double* weights, void* stream);
 
+/* Measurement utility: when enabled, mf_vegas_accumulate records CUDA events
+ * around its per-chunk kernels (the iteration runs in chunks of 2^20 events:
+ * a sampling kernel writes per-event records, the |M|^2 kernel reads them);
+ * mf_grid_profile_read waits for the last call's events and returns the
+ * summed device time of the sampling kernels and of the |M|^2-and-accumulate
+ * kernels, and the number of chunks (the per-launch time of the |M|^2 kernel
+ * is me_ms / chunks). */
+mf_status mf_grid_profile(mf_grid* grid, int enable);
+mf_status mf_grid_profile_read(mf_grid* grid, double* sample_ms, double* me_ms, int* chunks);
+
 /* Measurement utility: sustained FMA-pipe throughput of the current device
  * (MF_FP32 or MF_FP64) in TFLOP/s from independent FMA chains on every SM,
  * the denominator of the amplitude kernel's roofline.  Synchronises the device. */
 mf_status mf_fma_throughput(int precision, double* tflops);
+
+/* Mixed launch: up to 4 processes integrated together, each with its own
+ * grid and event count (arXiv:2211.14056 Sec. 3, Fig. 3: how the work is
+ * spread over blocks and threads sets the run time).  One sampling launch
+ * for every process, one persistent |M|^2 launch whose warps take tiles of
+ * events from a single work queue ordered by cost (most gluons first), then
+ * the per-process reduction and refinement.  The processes must share a
+ * precision; grids belong to their processes.
+ *   mf_mixed_create   reserves per-event records for n[k] events on each grid
+ *                     (a configuration call; device memory grows once);
+ *   mf_mixed_run      one iteration, out[k] receives process k's result like
+ *                     mf_vegas_iterate (synchronises the stream);
+ *   mf_mixed_set_launch  CTAs per SM of the |M|^2 launch (0 = occupancy) and
+ *                     events per work item;
+ *   mf_mixed_use_graph  capture the whole iteration as a CUDA graph on the
+ *                     next run (per stream and refine flag) and replay it with
+ *                     a new seed/iteration (copied from pinned host memory by
+ *                     a node of the graph); the legacy default stream (NULL)
+ *                     cannot be captured, so there the iteration runs uncaptured;
+ *   mf_mixed_autotune times each candidate (ctas_per_sm, tile) on one
+ *                     unrefined iteration (results not recorded), writes the
+ *                     times (ms) and the index of the fastest, and keeps it. */
+typedef struct mf_mixed mf_mixed;
+mf_status mf_mixed_create(mf_process* const* procs, mf_grid* const* grids, const int64_t* n, int nproc,
+                          mf_mixed** out);
+mf_status mf_mixed_destroy(mf_mixed* plan);
+mf_status mf_mixed_run(mf_mixed* plan, uint64_t seed, int iter, int refine, mf_result* out, void* stream);
+mf_status mf_mixed_set_launch(mf_mixed* plan, int ctas_per_sm, int tile);
+mf_status mf_mixed_use_graph(mf_mixed* plan, int enable);
+mf_status mf_mixed_autotune(mf_mixed* plan, uint64_t seed, int ncand, const int* cand_ctas, const int* cand_tile,
+                            double* ms, int* best, void* stream);
 
 /* Message of the last failing call on the calling thread ("" if none). */
 const char* mf_last_error(void);

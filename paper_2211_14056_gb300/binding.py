@@ -69,8 +69,18 @@ EXPORTS = {
     "mf_grid_totals": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int)]),
     "mf_vegas_finish": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.POINTER(Result), C.c_void_p]),
     "mf_fma_throughput": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "mf_grid_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "mf_grid_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "mf_vegas_accumulate_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_uint64, C.c_int, C.c_int64,
                                              C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mf_mixed_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_int,
+                                  C.POINTER(C.c_void_p)]),
+    "mf_mixed_destroy": (C.c_int, [C.c_void_p]),
+    "mf_mixed_run": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.c_int, C.POINTER(Result), C.c_void_p]),
+    "mf_mixed_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "mf_mixed_use_graph": (C.c_int, [C.c_void_p, C.c_int]),
+    "mf_mixed_autotune": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p]),
     "mf_last_error": (C.c_char_p, []),
     "mf_kernel_launches": (C.c_int64, []),
 }
@@ -259,8 +269,67 @@ class Grid:
     def reset(self):
         _check(load_library().mf_grid_reset(self._h))
 
+    def profile(self, enable=True):
+        _check(load_library().mf_grid_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """(sampling ms, |M|^2 ms, chunks) of the last accumulation."""
+        a, b, c = C.c_double(), C.c_double(), C.c_int()
+        _check(load_library().mf_grid_profile_read(self._h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
     def totals(self):
         """(device address, length) of the accumulated totals (double[length])."""
         ptr, cnt = C.c_void_p(), C.c_int()
         _check(load_library().mf_grid_totals(self._h, C.byref(ptr), C.byref(cnt)))
         return ptr.value, cnt.value
+
+
+class Mixed:
+    """Several processes in one iteration (mf_mixed_*): one sampling launch,
+    one persistent |M|^2 launch with a cost-ordered work queue."""
+
+    def __init__(self, procs, grids, n):
+        k = len(procs)
+        self.procs, self.grids, self.n = list(procs), list(grids), list(n)
+        ph = (C.c_void_p * k)(*[p._h.value for p in procs])
+        gh = (C.c_void_p * k)(*[g._h.value for g in grids])
+        nn = (C.c_int64 * k)(*n)
+        h = C.c_void_p()
+        _check(load_library().mf_mixed_create(ph, gh, nn, k, C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().mf_mixed_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, seed, it, refine=True, stream=None):
+        out = (Result * len(self.procs))()
+        st = _check(load_library().mf_mixed_run(self._h, seed, it, 1 if refine else 0, out, _stream(stream)))
+        res = [r.as_dict() for r in out]
+        for r in res:
+            r["status"] = st
+        return res
+
+    def set_launch(self, ctas_per_sm, tile):
+        _check(load_library().mf_mixed_set_launch(self._h, ctas_per_sm, tile))
+
+    def use_graph(self, enable=True):
+        _check(load_library().mf_mixed_use_graph(self._h, 1 if enable else 0))
+
+    def autotune(self, seed, candidates, stream=None):
+        """candidates: list of (ctas_per_sm, tile); returns (times_ms, best index)."""
+        k = len(candidates)
+        cc = (C.c_int * k)(*[c for c, _ in candidates])
+        ct = (C.c_int * k)(*[t for _, t in candidates])
+        ms = (C.c_double * k)()
+        best = C.c_int()
+        _check(load_library().mf_mixed_autotune(self._h, seed, k, cc, ct, ms, C.byref(best), _stream(stream)))
+        return list(ms), best.value

@@ -10,12 +10,12 @@
 #include <string>
 #include <vector>
 
-#include "madflow_gb300.h"
-#include "mf_kernels.cuh"
+#include "mf_internal.h"
 
 using namespace mf;
 
-namespace {
+namespace mf {
+namespace detail {
 
 thread_local std::string g_err;
 std::atomic<int64_t> g_launches{0};
@@ -30,11 +30,14 @@ mf_status cuda_fail(cudaError_t e, const char* where) {
   return MF_ERR_CUDA;
 }
 
-#define MF_CUDA(call, where)                         \
-  do {                                               \
-    cudaError_t e_ = (call);                         \
-    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
-  } while (0)
+void count_launches(int k) { g_launches.fetch_add(k); }
+
+}  // namespace detail
+}  // namespace mf
+
+using namespace mf::detail;
+
+namespace {
 
 int factorial(int n) { return n <= 1 ? 1 : n * factorial(n - 1); }
 
@@ -53,33 +56,24 @@ const int* lib_colour(int ng, int* den) {
 
 }  // namespace
 
-struct mf_process {
-  int ng = 0, ndim = 0, precision = 0, device = 0, sms = 0;
-  SampleParams sp{};
-  MeParams mp{};
-  int me_ctas = 1;
-  size_t me_smem = 0;
-  int ctas_override = 0;
-};
+namespace mf {
+namespace detail {
+cudaError_t dispatch_acc_config(int ng, int prec, int ndim, int nbins, size_t* smem, int* ctas) {
+  const int p = prec == MF_FP64 ? 0 : 1;
+  switch (ng) {
+    case 2: return me_acc_config<2>(p, ndim, nbins, smem, ctas);
+    case 3: return me_acc_config<3>(p, ndim, nbins, smem, ctas);
+    case 4: return me_acc_config<4>(p, ndim, nbins, smem, ctas);
+  }
+  return cudaErrorInvalidValue;
+}
 
-struct mf_grid {
-  const mf_process* proc = nullptr;
-  int ndim = 0, nbins = 0;
-  int max_blocks = 0;
-  int fused_ctas = 1;
-  size_t fused_smem = 0;
-  int acc_ctas = 1;            // CTAs per SM of the |M|^2-and-accumulate kernel
-  size_t acc_smem = 0;
-  int64_t chunk = 0;           // events per record chunk
-  void* d_records = nullptr;   // per-event records of one chunk
-  double* d_edges = nullptr;
-  double* d_partials = nullptr;
-  unsigned long long* d_counters = nullptr;
-  double* d_totals = nullptr;   // [2 + ndim*nbins + 2]: sums, histogram, passing events, Newton misses
-  double* d_result = nullptr;
-  double* h_result = nullptr;
-  std::vector<double> Ik, vark;
-};
+int effective_ctas(const mf_process* p, int occupancy) {
+  if (p->ctas_override > 0 && p->ctas_override < occupancy) return p->ctas_override;
+  return occupancy < 1 ? 1 : occupancy;
+}
+}  // namespace detail
+}  // namespace mf
 
 namespace {
 
@@ -89,16 +83,6 @@ cudaError_t dispatch_fused_config(int ng, int prec, int ndim, int nbins, size_t*
     case 2: return fused_config<2>(p, ndim, nbins, smem, ctas);
     case 3: return fused_config<3>(p, ndim, nbins, smem, ctas);
     case 4: return fused_config<4>(p, ndim, nbins, smem, ctas);
-  }
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t dispatch_acc_config(int ng, int prec, int ndim, int nbins, size_t* smem, int* ctas) {
-  const int p = prec == MF_FP64 ? 0 : 1;
-  switch (ng) {
-    case 2: return me_acc_config<2>(p, ndim, nbins, smem, ctas);
-    case 3: return me_acc_config<3>(p, ndim, nbins, smem, ctas);
-    case 4: return me_acc_config<4>(p, ndim, nbins, smem, ctas);
   }
   return cudaErrorInvalidValue;
 }
@@ -113,12 +97,50 @@ cudaError_t dispatch_me_config(int ng, int prec, size_t* smem, int* ctas) {
   return cudaErrorInvalidValue;
 }
 
-int effective_ctas(const mf_process* p, int occupancy) {
-  if (p->ctas_override > 0 && p->ctas_override < occupancy) return p->ctas_override;
-  return occupancy < 1 ? 1 : occupancy;
-}
 
 }  // namespace
+
+namespace mf {
+namespace detail {
+mf_status record_iteration(mf_grid* g, const double* r, int64_t n_total, mf_result* out) {
+  out->I_k = r[2];
+  out->sigma_k = std::sqrt(r[3] > 0 ? r[3] : 0.0);
+  out->n_events = n_total;
+  out->n_pass = int64_t(r[4]);
+  out->n_newton_fail = int64_t(r[5]);
+  g->Ik.push_back(r[2]);
+  g->vark.push_back(r[3]);
+  out->iterations = int(g->Ik.size());
+  double sw = 0, swi = 0;
+  bool ok = true;
+  for (size_t k = 0; k < g->Ik.size(); ++k) {
+    if (!(g->vark[k] > 0)) { ok = false; break; }
+    sw += 1.0 / g->vark[k];
+    swi += g->Ik[k] / g->vark[k];
+  }
+  if (!ok) {
+    out->I = out->sigma = out->chi2dof = NAN;
+    return fail(MF_ERR_ARG, "mf_vegas_finish: an iteration has zero variance; combination undefined");
+  }
+  out->I = swi / sw;
+  out->sigma = 1.0 / std::sqrt(sw);
+  double chi = 0;
+  for (size_t k = 0; k < g->Ik.size(); ++k) chi += (g->Ik[k] - out->I) * (g->Ik[k] - out->I) / g->vark[k];
+  out->chi2dof = g->Ik.size() > 1 ? chi / double(g->Ik.size() - 1) : 0.0;
+  return out->n_newton_fail > 0 ? MF_WARN_NEWTON : MF_OK;
+}
+mf_status grid_reserve(mf_grid* g, int64_t events) {
+  if (events <= g->chunk) return MF_OK;
+  void* buf = nullptr;
+  MF_CUDA(cudaMalloc(&buf, record_bytes(g->proc->precision == MF_FP64 ? 0 : 1, g->proc->sp.n_final, g->ndim, events)),
+          "grid_reserve");
+  cudaFree(g->d_records);
+  g->d_records = buf;
+  g->chunk = events;
+  return MF_OK;
+}
+}  // namespace detail
+}  // namespace mf
 
 extern "C" {
 
@@ -273,6 +295,7 @@ mf_status mf_grid_destroy(mf_grid* g) {
   cudaFree(g->d_edges);
   cudaFree(g->d_partials);
   cudaFree(g->d_records);
+  for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
   cudaFree(g->d_counters);
   cudaFree(g->d_totals);
   cudaFree(g->d_result);
@@ -348,6 +371,15 @@ mf_status mf_vegas_accumulate(mf_process* p, mf_grid* g, uint64_t seed, int iter
   const int prec = p->precision == MF_FP64 ? 0 : 1;
   const int64_t cap = int64_t(p->sms) * effective_ctas(p, g->acc_ctas);
   int grid = 0;
+  if (g->profile) {
+    const size_t need = size_t(3) * size_t((n + g->chunk - 1) / g->chunk);
+    while (g->ev.size() < need) {
+      cudaEvent_t e;
+      MF_CUDA(cudaEventCreate(&e), "mf_vegas_accumulate (profiling events)");
+      g->ev.push_back(e);
+    }
+    g->ev_used = int(need);
+  }
   // chunks of the record buffer: sample the chunk, then |M|^2 + accumulate;
   // the CTA partials of every chunk add up in place
   for (int64_t done = 0, k = 0; done < n; done += g->chunk, ++k) {
@@ -356,11 +388,12 @@ mf_status mf_vegas_accumulate(mf_process* p, mf_grid* g, uint64_t seed, int iter
     const int64_t ctas_needed = (warps_needed + kWarps - 1) / kWarps;
     if (k == 0) grid = int(std::min(cap, std::max<int64_t>(ctas_needed, 1)));
     double* w = weights ? weights + done : nullptr;
+    cudaEvent_t* evk = g->profile ? &g->ev[size_t(3) * k] : nullptr;
     cudaError_t e;
     switch (p->ng) {
-      case 2: e = launch_chunk<2>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s); break;
-      case 3: e = launch_chunk<3>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s); break;
-      default: e = launch_chunk<4>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s); break;
+      case 2: e = launch_chunk<2>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
+      case 3: e = launch_chunk<3>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
+      default: e = launch_chunk<4>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "mf_vegas_accumulate (chunk kernels)");
     g_launches.fetch_add(2);
@@ -368,6 +401,30 @@ mf_status mf_vegas_accumulate(mf_process* p, mf_grid* g, uint64_t seed, int iter
   MF_CUDA(launch_reduce(g->d_partials, g->d_counters, grid, g->ndim, g->nbins, g->d_totals, s),
           "mf_vegas_accumulate (reduce)");
   g_launches.fetch_add(1);
+  return MF_OK;
+}
+
+mf_status mf_grid_profile(mf_grid* g, int enable) {
+  if (g == nullptr) return fail(MF_ERR_ARG, "mf_grid_profile: null argument");
+  g->profile = enable != 0;
+  g->ev_used = 0;
+  return MF_OK;
+}
+
+mf_status mf_grid_profile_read(mf_grid* g, double* sample_ms, double* me_ms, int* chunks) {
+  if (g == nullptr || sample_ms == nullptr || me_ms == nullptr || chunks == nullptr)
+    return fail(MF_ERR_ARG, "mf_grid_profile_read: null argument");
+  *sample_ms = *me_ms = 0.0;
+  *chunks = g->ev_used / 3;
+  if (g->ev_used == 0) return MF_OK;
+  MF_CUDA(cudaEventSynchronize(g->ev[g->ev_used - 1]), "mf_grid_profile_read");
+  for (int k = 0; k < g->ev_used / 3; ++k) {
+    float a = 0, b = 0;
+    MF_CUDA(cudaEventElapsedTime(&a, g->ev[3 * k], g->ev[3 * k + 1]), "mf_grid_profile_read");
+    MF_CUDA(cudaEventElapsedTime(&b, g->ev[3 * k + 1], g->ev[3 * k + 2]), "mf_grid_profile_read");
+    *sample_ms += a;
+    *me_ms += b;
+  }
   return MF_OK;
 }
 
@@ -388,32 +445,7 @@ mf_status mf_vegas_finish(mf_process* p, mf_grid* g, int64_t n_total, int refine
   g_launches.fetch_add(1);
   MF_CUDA(cudaMemcpyAsync(g->h_result, g->d_result, sizeof(double) * 6, cudaMemcpyDeviceToHost, s), "mf_vegas_finish (copy)");
   MF_CUDA(cudaStreamSynchronize(s), "mf_vegas_finish (sync)");
-  const double* r = g->h_result;
-  out->I_k = r[2];
-  out->sigma_k = std::sqrt(r[3] > 0 ? r[3] : 0.0);
-  out->n_events = n_total;
-  out->n_pass = int64_t(r[4]);
-  out->n_newton_fail = int64_t(r[5]);
-  g->Ik.push_back(r[2]);
-  g->vark.push_back(r[3]);
-  out->iterations = int(g->Ik.size());
-  double sw = 0, swi = 0;
-  bool ok = true;
-  for (size_t k = 0; k < g->Ik.size(); ++k) {
-    if (!(g->vark[k] > 0)) { ok = false; break; }
-    sw += 1.0 / g->vark[k];
-    swi += g->Ik[k] / g->vark[k];
-  }
-  if (!ok) {
-    out->I = out->sigma = out->chi2dof = NAN;
-    return fail(MF_ERR_ARG, "mf_vegas_finish: an iteration has zero variance; combination undefined");
-  }
-  out->I = swi / sw;
-  out->sigma = 1.0 / std::sqrt(sw);
-  double chi = 0;
-  for (size_t k = 0; k < g->Ik.size(); ++k) chi += (g->Ik[k] - out->I) * (g->Ik[k] - out->I) / g->vark[k];
-  out->chi2dof = g->Ik.size() > 1 ? chi / double(g->Ik.size() - 1) : 0.0;
-  return out->n_newton_fail > 0 ? MF_WARN_NEWTON : MF_OK;
+  return record_iteration(g, g->h_result, n_total, out);
 }
 
 mf_status mf_vegas_iterate(mf_process* p, mf_grid* g, uint64_t seed, int iter, int64_t n, int refine, mf_result* out,

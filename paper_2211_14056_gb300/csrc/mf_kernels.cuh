@@ -648,7 +648,7 @@ template <int NG>
 cudaError_t launch_chunk(int precision, const SampleParams& sp, const MeParams& mp, const double* edges,
                          int64_t first_event, int64_t n, int64_t C, void* rec_base, uint64_t seed, int iter,
                          int accumulate, double* partials, unsigned long long* counters, double* w_out, int grid,
-                         cudaStream_t s);
+                         cudaStream_t s, cudaEvent_t* ev = nullptr);
 template <int NG>
 cudaError_t me_acc_config(int precision, int ndim, int nbins, size_t* smem, int* ctas_per_sm);
 size_t record_bytes(int precision, int n_final, int ndim, int64_t C);
@@ -728,7 +728,7 @@ cudaError_t launch_fma_peak(int precision, int blocks, int iters, float* sink, c
   cudaError_t launch_chunk<NG>(int precision, const SampleParams& sp, const MeParams& mp, const double* edges,    \
                                int64_t first_event, int64_t n, int64_t C, void* rec_base, uint64_t seed, int iter, \
                                int accumulate, double* partials, unsigned long long* counters, double* w_out,     \
-                               int grid, cudaStream_t s) {                                                        \
+                               int grid, cudaStream_t s, cudaEvent_t* ev) {                                       \
     const int nacc = 2 + sp.ndim * sp.nbins;                                                                      \
     const size_t esm = sizeof(double) * sp.ndim * (sp.nbins + 1);                                                 \
     int dev = 0, sms = 0;                                                                                         \
@@ -740,16 +740,22 @@ cudaError_t launch_fma_peak(int precision, int blocks, int iters, float* sink, c
       RecordView<double> rec = RecordView<double>::carve(rec_base, sp.n_final, sp.ndim, C);                       \
       cudaError_t e = cudaMemsetAsync(rec.count, 0, 2 * sizeof(unsigned), s);                                    \
       if (e != cudaSuccess) return e;                                                                             \
+      if (ev) cudaEventRecord(ev[0], s);                                                                          \
       k_sample_rec<double><<<sgrid, kThreads, esm, s>>>(sp, edges, first_event, n, seed, iter, rec, w_out);       \
+      if (ev) cudaEventRecord(ev[1], s);                                                                          \
       k_me_acc<NG, double><<<grid, kThreads, MeAccLayout<NG, double>::total(nacc), s>>>(                          \
           mp, sp.ndim, sp.nbins, rec, accumulate, partials, counters, w_out);                                     \
+      if (ev) cudaEventRecord(ev[2], s);                                                                          \
     } else {                                                                                                      \
       RecordView<float> rec = RecordView<float>::carve(rec_base, sp.n_final, sp.ndim, C);                         \
       cudaError_t e = cudaMemsetAsync(rec.count, 0, 2 * sizeof(unsigned), s);                                     \
       if (e != cudaSuccess) return e;                                                                             \
+      if (ev) cudaEventRecord(ev[0], s);                                                                          \
       k_sample_rec<float><<<sgrid, kThreads, esm, s>>>(sp, edges, first_event, n, seed, iter, rec, w_out);        \
+      if (ev) cudaEventRecord(ev[1], s);                                                                          \
       k_me_acc<NG, float><<<grid, kThreads, MeAccLayout<NG, float>::total(nacc), s>>>(                            \
           mp, sp.ndim, sp.nbins, rec, accumulate, partials, counters, w_out);                                     \
+      if (ev) cudaEventRecord(ev[2], s);                                                                          \
     }                                                                                                             \
     return cudaGetLastError();                                                                                    \
   }                                                                                                               \

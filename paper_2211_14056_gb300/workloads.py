@@ -23,6 +23,12 @@ WORKLOADS = {
 }
 
 
+# the batched mixed launch: three gluon-initiated processes together, each with
+# its own Vegas grid (the processes' own set-ups above), FP32 amplitudes
+MIXED = {"workloads": ["gg_ttx_1tev", "gg_ttxg_13tev", "gg_ttxgg_13tev"],
+         "events": [4_000_000, 1_000_000, 250_000], "seed": 4}
+
+
 def oracle_cfg(w):
     """The same workload as the keyword dict oracle.integrate.Setup takes."""
     keys = ("process", "mt", "wt", "gs", "sqrt_s", "lumi", "pt_cut", "dr_cut")
