@@ -135,8 +135,9 @@ mf_status mf_sample(mf_process* proc, const mf_grid* grid, uint64_t seed, int it
  *   momenta [n_ext][4][n] FP64 device, me2 [n] FP64 device. */
 mf_status mf_matrix_element(mf_process* proc, int64_t n, const double* momenta, double* me2, void* stream);
 
-/* One Vegas iteration over global events 0..n-1 in the fused kernel
- * (sample + |M|^2 + accumulate), a deterministic reduction of the per-CTA
+/* One Vegas iteration over global events 0..n-1 (chunks of 2^20 events: a
+ * sampling kernel writes per-event records and the list of events passing the
+ * cuts, the |M|^2 kernel reads them and accumulates), a deterministic reduction of the per-CTA
  * sums, and, if refine != 0, the grid refinement.  The iteration is recorded
  * on the grid and *out (host) receives it and the running combination.
  * weights (device [n] FP64, may be NULL) receives every event weight.
@@ -148,7 +149,7 @@ mf_status mf_vegas_iterate(mf_process* proc, mf_grid* grid, uint64_t seed, int i
 /* The same iteration in two halves, for event sharding across devices
  * (the Philox counter is the global event index, so a shard is events
  * first_event .. first_event+n-1 and the result does not depend on the split):
- *   mf_vegas_accumulate runs the fused kernel on the shard and reduces its
+ *   mf_vegas_accumulate runs the iteration's kernels on the shard and reduces its
  *     per-CTA partial sums into the grid's totals buffer (asynchronous);
  *   mf_grid_totals exposes that device buffer, double[count] laid out as
  *     [0] sum w, [1] sum w^2, [2 + j*nbins + b] sum w^2 in bin b of dim j,
@@ -180,6 +181,31 @@ mf_status mf_vegas_finish(mf_process* proc, mf_grid* grid, int64_t n_total, int 
  * word it reads, so nothing needs clearing between calls. */
 mf_status mf_vegas_accumulate_static(mf_process* proc, const double* edges, int nbins, uint64_t seed, int iter,
                                      int64_t first_event, int64_t n, double* totals, double* weights, void* stream);
+
+/* Derivatives of one iteration's estimate (arXiv:2211.14056 Sec. 2: the
+ * device operator is differentiable in principle; the paper leaves its
+ * derivative for later).  Over global events 0..n-1 of iteration `iter` on the
+ * grid's current edges (the same events and weights as mf_vegas_iterate):
+ *   *sigma          host: I = (1/n) sum w, in pb;
+ *   dsigma          host double[3]: dI/dg_s, dI/dm_t, dI/dGamma_t at the
+ *                   process's parameters (m_t moves the external top masses,
+ *                   the phase-space threshold and the propagators together);
+ *   dw_dtheta       device [3][n] FP64 or NULL: per-event dw/dg_s, dw/dm_t,
+ *                   dw/dGamma_t;
+ *   dw_dy           device [ndim][n] FP64 or NULL: per-event dw/dy_j, the
+ *                   derivative with respect to the Vegas uniform of
+ *                   dimension j inside its bin.
+ * Forward mode: every pass recomputes the kinematics and |M|^2 with two
+ * tangent directions (dual numbers); pass 0 carries m_t and Gamma_t, each
+ * further pass (only with dw_dy) two uniforms.  dI/dg_s is exact:
+ * |M|^2 is proportional to g_s^(2 n_gluons).  Bins, cuts and the Newton
+ * decision are piecewise constant and give no derivative, so dI/dtheta is
+ * the derivative of the estimator at fixed uniforms, not of the integral
+ * across a moving cut boundary.  Arithmetic in the process's precision
+ * (FP32 kinematics and amplitudes with MF_FP32, the weight in FP64).  Uses
+ * the grid's scratch; synchronises the stream. */
+mf_status mf_grad(mf_process* proc, const mf_grid* grid, uint64_t seed, int iter, int64_t n, double* sigma,
+                  double* dsigma, double* dw_dtheta, double* dw_dy, void* stream);
 
 /* Measurement utility: when enabled, mf_vegas_accumulate records CUDA events
  * around its per-chunk kernels (the iteration runs in chunks of 2^20 events:

@@ -218,6 +218,8 @@ mf_status mf_init_process(const mf_process_desc* d, mf_process** out) {
   MeParams& mp = p->mp;
   mp.mt = mt;
   mp.mw = mt * d->top_width;
+  p->g_s = d->g_s;
+  p->width = d->top_width;
   const int sid = factorial(ng - 2);        // identical final-state gluons
   mp.norm = std::pow(d->g_s, 2 * ng) / (256.0 * sid * lden);
 

@@ -31,6 +31,7 @@ struct mf_process {
   int me_ctas = 1;
   size_t me_smem = 0;
   int ctas_override = 0;
+  double g_s = 0.0, width = 0.0;   // strong coupling and top width of the descriptor
 };
 
 struct mf_grid {

@@ -271,7 +271,7 @@ __device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* w
     part += colour_form<T>(J);
   }
 #pragma unroll
-  for (int off = L / 2; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+  for (int off = L / 2; off > 0; off >>= 1) part += shfl_xor_any(0xffffffffu, part, off);
   __syncwarp();   // the group's shared store may be overwritten after this
   return part;
 }

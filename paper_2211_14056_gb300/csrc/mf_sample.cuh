@@ -21,6 +21,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "mf_dual.cuh"
+
 namespace mf {
 
 constexpr int kMaxDim = 10;
@@ -41,11 +43,12 @@ struct SampleParams {
   double phi_const;     // (2 pi)^(4-3n) (pi/2)^(n-1) / ((n-1)! (n-2)!)
 };
 
-// K: arithmetic of the kinematics (momenta, luminosity, cuts); the Vegas map,
-// its bins and Jacobian, the massive-rescaling Newton and the weight are FP64.
-template <typename K> struct EventKin {
+// K: arithmetic of the kinematics (momenta, luminosity, cuts); D: that of the
+// Vegas map, the massive-rescaling Newton and the weight (FP64, or FP64 dual
+// numbers in the derivative kernels).
+template <typename K, typename D = double> struct EventKin {
   K p[kMaxExt][4];        // physical momenta in MadGraph order (g, g, t, tbar, g...)
-  double prefactor;       // weight without |M|^2 (0 if cut / failed)
+  D prefactor;            // weight without |M|^2 (0 if cut / failed)
   uint8_t bins[kMaxDim];
   int pass;               // 1: compute |M|^2; 0: weight is zero
   int newton_fail;
@@ -117,13 +120,27 @@ __device__ __forceinline__ K mass_ratio(K r, int k) {
 __device__ __forceinline__ void sincos_turns(double t, double* s, double* c) { sincospi(2.0 * t, s, c); }
 __device__ __forceinline__ void sincos_turns(float t, float* s, float* c) { sincospif(2.0f * t, s, c); }
 
+// Tangent seeds of the derivative kernels: tangent slot of each Vegas
+// dimension's uniform and of m_t (-1: none).
+struct TangentSeeds {
+  int y_slot[kMaxDim];
+  int mt_slot;
+};
+
+template <typename X> __device__ __forceinline__ void seed_tangent(X&, int) {}
+template <typename B, int N> __device__ __forceinline__ void seed_tangent(Dual<B, N>& x, int slot) {
+  if (slot >= 0 && slot < N) x.d[slot] = B(1);
+}
+
 // Full per-event kinematics.  edges: [ndim][nbins+1] (shared memory).
 // K = double: every step in FP64.  K = float: luminosity, RAMBO and cuts in
-// FP32; bins, map, Jacobian, Newton (polished to 1e-15 in FP64) and weight in FP64.
-template <typename K>
+// FP32; bins, map, Jacobian, Newton (polished to 1e-15 in FP64) and weight in
+// FP64.  D = dual numbers: the same steps carry tangents seeded by ts.
+template <typename K, typename D = double>
 __device__ __forceinline__ void sample_event(const SampleParams& sp, const double* edges, uint64_t seed, int iter,
-                                             uint64_t ev, EventKin<K>& out) {
-  double y[kMaxDim], x[kMaxDim];
+                                             uint64_t ev, EventKin<K, D>& out, const TangentSeeds* ts = nullptr) {
+  double y[kMaxDim];
+  D x[kMaxDim];
   draw_uniforms(seed, iter, ev, sp.ndim, y);
   double jac = 1.0;
   const double nb = double(sp.nbins);
@@ -134,30 +151,42 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
     if (b > sp.nbins - 1) b = sp.nbins - 1;
     const double e0 = edges[j * (sp.nbins + 1) + b], e1 = edges[j * (sp.nbins + 1) + b + 1];
     const double w = e1 - e0;
-    x[j] = fma(t - double(b), w, e0);
+    if constexpr (is_dual<D>::value) {
+      D yd = D(y[j]);
+      if (ts) seed_tangent(yd, ts->y_slot[j]);
+      x[j] = (yd * nb - double(b)) * w + e0;
+    } else {
+      x[j] = fma(t - double(b), w, e0);
+    }
     jac *= nb * w;
     out.bins[j] = uint8_t(b);
   }
+  D mtd = D(sp.mt);
+  if (ts) seed_tangent(mtd, ts->mt_slot);
   // partonic energy and luminosity
-  double shat, lum = 1.0;
+  D shat, lum = D(1.0), excess;
+  const D thr = D(2.0) * mtd;
   int off = 0;
   if (sp.lumi) {
     // ln x1 = u ln tau0, ln x2 = v (1 - u) ln tau0 (= v ln(tau0/x1));
     // f(x1) f(x2) x1 x2 = N^2 exp((a + 1)(ln x1 + ln x2) + b (ln(1-x1) + ln(1-x2)))
-    const K lt = K(sp.log_tau0);
+    D log_tau0;
+    if constexpr (is_dual<D>::value) log_tau0 = log(thr * thr / D(sp.sqrt_s * sp.sqrt_s));
+    else log_tau0 = sp.log_tau0;
+    const K lt = K(log_tau0);
     const K lx[2] = {K(x[0]) * lt, K(x[1]) * (K(1) - K(x[0])) * lt};
     K l1m = K(0);
 #pragma unroll 1
     for (int j = 0; j < 2; ++j) l1m += log1p(-exp(lx[j]));
     const K lsum = lx[0] + lx[1];
-    shat = double(exp(lsum)) * sp.sqrt_s * sp.sqrt_s;
+    shat = D(exp(lsum)) * (sp.sqrt_s * sp.sqrt_s);
     const K ff = exp(K(sp.lumi_a + 1.0) * lsum + K(sp.lumi_b) * l1m);
-    lum = sp.lumi_N * sp.lumi_N * double(ff) * (1.0 - x[0]) * sp.log_tau0 * sp.log_tau0;
+    lum = D(ff) * (D(1.0) - x[0]) * log_tau0 * log_tau0 * (sp.lumi_N * sp.lumi_N);
     off = 2;
   } else {
-    shat = sp.sqrt_s * sp.sqrt_s;
+    shat = D(sp.sqrt_s * sp.sqrt_s);
   }
-  const double rs = sqrt(shat);
+  const D rs = sqrt(shat);
   const K rsk = K(rs);
   const int n = sp.n_final;
   // RAMBO on diet: intermediate masses
@@ -189,77 +218,90 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
   }
   for (int c = 0; c < 4; ++c) pm[n - 1][c] = Q[c];
   // Phi_n(s_hat)
-  double phi = sp.phi_const;
-  for (int i = 0; i < n - 2; ++i) phi *= shat;
-  // massive rescaling: particles 0, 1 carry mt, the rest are massless.
-  // sum_i sqrt(m_i^2 + xi^2 E_i^2) = sqrt(s) by Newton; with K = float the
-  // start comes from FP32 iterations, the FP64 steps then converge in 2-3.
+  D phi = D(sp.phi_const);
+  for (int i = 0; i < n - 2; ++i) phi = phi * shat;
   // f(xi) = sum_{i=0,1} (sqrt(m^2 + xi^2 E_i^2) - m) + xi E_rest - (sqrt(s) - 2m), with
   // sqrt(m^2 + u^2) - m = u^2 / (sqrt(m^2 + u^2) + m): no cancellation near
   // threshold, so Newton reaches full relative precision in xi there too.
   // Stop at |dxi| <= 1e-15 xi, or when the steps no longer shrink (the
-  // rounding floor, once below 1e-12 xi); 50 steps at most.
-  const double m2 = sp.mt * sp.mt;
-  double E[kMaxExt];
-  double Erest = 0.0;
+  // rounding floor, once below 1e-12 xi); 50 steps at most.  With dual
+  // numbers the converged xi is refined by one more step, which carries the
+  // implicit-function derivative d xi = -(df/dtheta) / f'.
+  const D m2 = mtd * mtd;
+  D E[kMaxExt];
+  D Erest = D(0.0);
 #pragma unroll 1
   for (int i = 0; i < n; ++i) {
-    E[i] = double(pm[i][0]);
-    if (i >= 2) Erest += E[i];
+    E[i] = D(pm[i][0]);
+    if (i >= 2) Erest = Erest + E[i];
   }
-  const double thr = 2.0 * sp.mt;
-  const double excess = (shat - thr * thr) / (rs + thr);     // sqrt(s) - 2m
-  double xi = sqrt(fmax(excess * (rs + thr), 0.0)) / rs;     // sqrt(1 - (2m/sqrt(s))^2)
-  if constexpr (sizeof(K) < sizeof(double)) {
-    const K m2k = K(m2), mk = K(sp.mt), e0 = pm[0][0], e1 = pm[1][0], er = K(Erest), exk = K(excess);
-    K xk = K(xi);
+  excess = (shat - thr * thr) / (rs + thr);     // sqrt(s) - 2m
+  double xi0 = sqrt(fmax(value_of(excess) * value_of(rs + thr), 0.0)) / value_of(rs);
+  if constexpr (sizeof(value_of(K(0))) < sizeof(double)) {
+    using KB = decltype(value_of(K(0)));
+    const KB m2k = KB(value_of(m2)), mk = KB(value_of(mtd)), e0 = value_of(pm[0][0]), e1 = value_of(pm[1][0]),
+             er = KB(value_of(Erest)), exk = KB(value_of(excess));
+    KB xk = KB(xi0);
 #pragma unroll 1
     for (int it = 0; it < 20; ++it) {
-      const K u0 = xk * e0, u1 = xk * e1;
-      const K r0 = sqrt(fma(u0, u0, m2k)), r1 = sqrt(fma(u1, u1, m2k));
-      const K f = u0 * u0 / (r0 + mk) + u1 * u1 / (r1 + mk) + xk * er - exk;
-      const K fp = xk * (e0 * e0 / r0 + e1 * e1 / r1) + er;
-      const K d = f / fp;
+      const KB u0 = xk * e0, u1 = xk * e1;
+      const KB r0 = sqrt(fma(u0, u0, m2k)), r1 = sqrt(fma(u1, u1, m2k));
+      const KB f = u0 * u0 / (r0 + mk) + u1 * u1 / (r1 + mk) + xk * er - exk;
+      const KB fp = xk * (e0 * e0 / r0 + e1 * e1 / r1) + er;
+      const KB d = f / fp;
       xk -= d;
-      if (fabs(d) <= K(1e-6) * xk) break;
+      if (fabs(d) <= KB(1e-6) * xk) break;
     }
-    if (xk > K(0) && xk < K(1)) xi = double(xk);
+    if (xk > KB(0) && xk < KB(1)) xi0 = double(xk);
   }
   int converged = 0;
-  double prev = 0.0;
+  {
+    const double mv = value_of(mtd), m2v = value_of(m2), e0 = value_of(E[0]), e1 = value_of(E[1]);
+    const double er = value_of(Erest), exv = value_of(excess);
+    double xi = xi0, prev = 0.0;
 #pragma unroll 1
-  for (int it = 0; it < 50; ++it) {
-    const double u0 = xi * E[0], u1 = xi * E[1];
-    const double r0 = sqrt(fma(u0, u0, m2)), r1 = sqrt(fma(u1, u1, m2));
-    const double f = u0 * u0 / (r0 + sp.mt) + u1 * u1 / (r1 + sp.mt) + xi * Erest - excess;
-    const double fp = xi * (E[0] * E[0] / r0 + E[1] * E[1] / r1) + Erest;
-    const double dxi = f / fp;
-    xi -= dxi;
-    const double ad = fabs(dxi);
-    if (ad <= 1e-15 * xi || (it > 0 && ad <= 1e-12 * xi && ad >= 0.5 * prev)) { converged = 1; break; }
-    prev = ad;
+    for (int it = 0; it < 50; ++it) {
+      const double u0 = xi * e0, u1 = xi * e1;
+      const double r0 = sqrt(fma(u0, u0, m2v)), r1 = sqrt(fma(u1, u1, m2v));
+      const double f = u0 * u0 / (r0 + mv) + u1 * u1 / (r1 + mv) + xi * er - exv;
+      const double fp = xi * (e0 * e0 / r0 + e1 * e1 / r1) + er;
+      const double dxi = f / fp;
+      xi -= dxi;
+      const double ad = fabs(dxi);
+      if (ad <= 1e-15 * xi || (it > 0 && ad <= 1e-12 * xi && ad >= 0.5 * prev)) { converged = 1; break; }
+      prev = ad;
+    }
+    xi0 = xi;
   }
-  double ksum = 0.0, kprod = 1.0, k2sum = 0.0;
+  D xi = D(xi0);
+  if constexpr (is_dual<D>::value) {
+    const D u0 = xi * E[0], u1 = xi * E[1];
+    const D r0 = sqrt(u0 * u0 + m2), r1 = sqrt(u1 * u1 + m2);
+    const D f = u0 * u0 / (r0 + mtd) + u1 * u1 / (r1 + mtd) + xi * Erest - excess;
+    const D fp = xi * (E[0] * E[0] / r0 + E[1] * E[1] / r1) + Erest;
+    xi = xi - f / fp;
+  }
+  D ksum = D(0.0), kprod = D(1.0), k2sum = D(0.0);
 #pragma unroll 1
   for (int i = 0; i < n; ++i) {
-    const double ka = xi * E[i];      // |k| = xi |p| = xi E for massless p
-    const double k0 = (i < 2) ? sqrt(fma(ka, ka, m2)) : ka;
-    const double ik0 = 1.0 / k0;
+    const D ka = xi * E[i];      // |k| = xi |p| = xi E for massless p
+    const D k0 = (i < 2) ? sqrt(ka * ka + m2) : ka;
+    const D ik0 = D(1.0) / k0;
     out.p[2 + i][0] = K(k0);
-    out.p[2 + i][1] = K(xi * double(pm[i][1]));
-    out.p[2 + i][2] = K(xi * double(pm[i][2]));
-    out.p[2 + i][3] = K(xi * double(pm[i][3]));
-    ksum += ka;
-    kprod *= ka * ik0;
-    k2sum += ka * ka * ik0;
+    out.p[2 + i][1] = K(xi * D(pm[i][1]));
+    out.p[2 + i][2] = K(xi * D(pm[i][2]));
+    out.p[2 + i][3] = K(xi * D(pm[i][3]));
+    ksum = ksum + ka;
+    kprod = kprod * (ka * ik0);
+    k2sum = k2sum + ka * ka * ik0;
   }
-  double wm = 1.0;
+  D wm = D(1.0);
   {
-    const double r = ksum / rs;
-    for (int i = 0; i < 2 * n - 3; ++i) wm *= r;
-    wm *= kprod * rs / k2sum;
+    const D r = ksum / rs;
+    for (int i = 0; i < 2 * n - 3; ++i) wm = wm * r;
+    wm = wm * (kprod * rs / k2sum);
   }
-  const K hr = K(0.5 * rs);
+  const K hr = K(D(0.5) * rs);
   out.p[0][0] = hr; out.p[0][1] = K(0); out.p[0][2] = K(0); out.p[0][3] = hr;
   out.p[1][0] = hr; out.p[1][1] = K(0); out.p[1][2] = K(0); out.p[1][3] = -hr;
   // cuts on the final gluons (particles 4..)
@@ -288,7 +330,7 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
   }
   out.pass = pass;
   out.newton_fail = converged ? 0 : 1;
-  out.prefactor = pass ? phi * wm * jac * lum / (2.0 * shat) * kGeV2pb : 0.0;
+  out.prefactor = pass ? phi * wm * lum / (D(2.0) * shat) * (jac * kGeV2pb) : D(0.0);
 }
 
 }  // namespace mf
