@@ -1,4 +1,4 @@
-"""Benchmark of the fused Vegas + |M|^2 hot path (g g -> t tbar g g, 2^22 events/step).
+"""Benchmark of the Vegas + |M|^2 hot path (g g -> t tbar g g, 2^22 events/step).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload gg_ttxgg_13tev] [--no-cpu-baseline]
@@ -9,8 +9,12 @@ colour sums), Vegas accumulation, deterministic reduction and grid refinement.
 The headline arm (FP32 amplitudes) is timed with CUDA events per step, with an
 L2 flush between steps outside the timed region; the FP64 arm, the FP32/FP64
 cross-section error on an identical frozen grid, an end-to-end number through
-the C ABI with host buffers, the FMA-pipe roofline of the fused kernel and the
-oracle timed on the host cores are added to the one JSON line rank 0 prints.
+the C ABI with host buffers, the FMA-pipe roofline of the |M|^2 kernel, the
+derivative workload (mf_grad, 2^20 events), the mixed multi-process launch and
+the oracle timed on the host cores are added to the one JSON line rank 0 prints.
+An iteration runs in chunks of 2^20 events: a sampling kernel writes per-event
+records and the list of events passing the cuts, the |M|^2 kernel (k_me_acc)
+evaluates the listed events and accumulates the Vegas sums.
 
 ``--impl reference`` times the FP64 CPU oracle (there is no runnable reference
 implementation: the paper ships no code), on the host cores, on a bounded
@@ -39,6 +43,14 @@ METRIC = "ggâ†’ttÌ„gg events/s on 1 GB300, FP32/TC vs FP64 fused at Ïƒ rel.errâ‰
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def _measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
 
 
 # --------------------------------------------------------------------------- oracle (CPU) legs
@@ -188,13 +200,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gg_ttxgg_13tev")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the derivative and mixed-launch legs")
     ap.add_argument("--adapt-events", type=int, default=2 ** 20)
     ap.add_argument("--profile-case", type=int, default=0, metavar="EVENTS",
-                    help="only run 3 fused iterations of EVENTS events each (small case for ncu captures)")
+                    help="only run 3 iterations of EVENTS events each (small case for ncu captures)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="arithmetic of --profile-case")
-    ap.add_argument("--profile-kernel", default="fused", choices=["fused", "me"],
-                    help="--profile-case target: the fused iteration, or sampling + the |M|^2 kernel alone")
+    ap.add_argument("--profile-kernel", default="iterate", choices=["iterate", "me"],
+                    help="--profile-case target: whole iterations, or sampling + the |M|^2 kernel alone")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -335,8 +348,16 @@ def main():
     peak64_meas = mf.fma_throughput(mf.MF_FP64)
     achieved64 = fpe * statistics.mean(pass64) / (statistics.mean(m[0] for m in me64) * 1e-3) / 1e12
     traffic = _ncu_traffic("k_me_acc_gg_ttxgg_fp32")
+    sm_max = _measured_peaks().get("sm_max_mhz", 2070.0)
+    peak_derived = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
 
-    # 7. CPU baseline: the oracle on the host cores (rank 0 only, N = 1 only)
+    # 7. the derivative and mixed-launch workloads (N = 1 only)
+    grad = mixed = None
+    if world == 1 and not args.no_extras:
+        grad = _grad_leg(p32, p64, g32, g64, w, torch)
+        mixed = _mixed_leg(mf, torch)
+
+    # 8. CPU baseline: the oracle on the host cores (rank 0 only, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
@@ -358,20 +379,26 @@ def main():
             "speedup_fp32_vs_fp64": value / value64,
             "sigma_rel_err_fp32_vs_fp64": sig_err, "event_rel_err_fp32": ev_err,
             "pass_fraction": statistics.mean(pass32) / (n * world),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_meas, "unit": "TFLOP/s",
-                         "frac": achieved / peak_meas, "traffic": traffic,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_derived, "unit": "TFLOP/s",
+                         "frac": achieved / peak_derived, "traffic": traffic,
                          "kernel": "k_me_acc<4,float>", "flops_per_event": fpe,
                          "launch_ms": me_ms / chunks, "launches_per_step": chunks,
                          "sampling_ms_per_step": statistics.mean(m[2] for m in me32),
-                         "peak_source": "measured FP32 FMA chains on all SMs (mf_fma_throughput), "
-                                        "'of measured'",
-                         "fp64": {"kernel": "k_me_acc<4,double>", "achieved": achieved64, "peak": peak64_meas,
-                                  "frac": achieved64 / peak64_meas}},
+                         "peak_source": f"derived: {SM_COUNT_NOMINAL} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x "
+                                        f"2 flop x {sm_max:.0f} MHz",
+                         "peak_measured_fma": peak_meas, "frac_of_measured_fma": achieved / peak_meas,
+                         "fp64": {"kernel": "k_me_acc<4,double>", "achieved": achieved64, "peak": FP64_NOMINAL_TFLOPS,
+                                  "frac": achieved64 / FP64_NOMINAL_TFLOPS, "peak_source": "nominal FP64 rate",
+                                  "peak_measured_fma": peak64_meas, "frac_of_measured_fma": achieved64 / peak64_meas}},
             "e2e": {"value": e2e_value, "unit": "events/s", "h2d_bytes_per_step": int(frozen.nbytes),
                     "d2h_bytes_per_step": 48},
             "gpu_launches": launches,
             "clocks": clk.summary(),
         }
+        if grad is not None:
+            line["grad"] = grad
+        if mixed is not None:
+            line["mixed"] = mixed
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -380,22 +407,104 @@ def main():
     return 0
 
 
+def _grad_leg(p32, p64, g32, g64, w, torch):
+    """mf_grad on the frozen grid: d sigma/d(g_s, m_t, Gamma_t) and the
+    per-event derivatives with respect to every uniform; events/s."""
+    out = {}
+    for name, p, g, n, reps in (("fp32", p32, g32, 2 ** 20, 2), ("fp64", p64, g64, 2 ** 18, 1)):
+        th = torch.empty(3 * n, dtype=torch.float64, device="cuda")
+        dy = torch.empty(p.ndim * n, dtype=torch.float64, device="cuda")
+        p.grad(g, w["seed"], 5000, 4096, th, dy)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for r in range(reps):
+            sigma, ds = p.grad(g, w["seed"], 5001 + r, n, th, dy)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"events": n, "ms": ms, "events_per_s": n / (ms * 1e-3), "sigma_pb": sigma,
+                     "dsigma_dgs_dmt_dwt": ds, "tangent_passes": 1 + (p.ndim + 1) // 2,
+                     "per_event_outputs": "dw/d(g_s, m_t, Gamma_t) [3, n], dw/dy [ndim, n]"}
+        del th, dy
+    return out
+
+
+def _mixed_leg(mf, torch, iters=5):
+    """The batched launch of several processes (own grids, FP32): the
+    autotuner's candidates, then graph-replayed iterations; against the same
+    processes iterated one after the other through mf_vegas_iterate."""
+    from paper_2211_14056_gb300.workloads import MIXED, PROCESS_IDS, WORKLOADS, process_kwargs
+    seed = MIXED["seed"]
+
+    def make():
+        procs, grids = [], []
+        for name in MIXED["workloads"]:
+            wk = WORKLOADS[name]
+            p = mf.Process(PROCESS_IDS[wk["process"]], **process_kwargs(wk, mf.MF_FP32))
+            procs.append(p)
+            grids.append(p.grid())
+        return procs, grids
+
+    procs, grids = make()
+    m = mf.Mixed(procs, grids, MIXED["events"])
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        for it in range(3):
+            m.run(seed, it, refine=True, stream=side)
+        cands = [(c, t) for c in (1, 2, 0) for t in (8, 32, 128, 512)]
+        times, best = m.autotune(seed, cands, stream=side)
+        m.use_graph(True)
+        m.run(seed, 3, refine=True, stream=side)          # capture
+        side.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        for i in range(iters):
+            res = m.run(seed, 4 + i, refine=True, stream=side)
+        e1.record(side)
+        side.synchronize()
+    ms_mixed = e0.elapsed_time(e1) / iters
+    sprocs, sgrids = make()
+    for it in range(3):
+        for p, g, n in zip(sprocs, sgrids, MIXED["events"]):
+            p.vegas_iterate(g, seed, it, n, refine=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(iters):
+        for p, g, n in zip(sprocs, sgrids, MIXED["events"]):
+            p.vegas_iterate(g, seed, 3 + i, n, refine=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_sep = e0.elapsed_time(e1) / iters
+    total = sum(MIXED["events"])
+    return {"workloads": MIXED["workloads"], "events": MIXED["events"], "ms_per_iteration": ms_mixed,
+            "events_per_s": total / (ms_mixed * 1e-3), "separate_ms_per_iteration": ms_sep,
+            "speedup_vs_separate": ms_sep / ms_mixed,
+            "autotune": {"candidates": cands, "ms": times, "best": cands[best]},
+            "graph": True, "I_pb": [r["I"] for r in res]}
+
+
 def _ncu_traffic(name):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current kernel sources (else None)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", name + ".json")
+    path = os.path.join(ROOT, "profiles", name + ".md")
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path))
+    rec = {}
+    for line in open(path):
+        k, _, v = line.strip().partition(":")
+        if k in ("dram_bytes_per_launch", "sources_sha256"):
+            rec[k] = v.strip()
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2211_14056_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         if f.endswith((".cu", ".cuh")):
             h.update(open(os.path.join(csrc, f), "rb").read())
-    if rec.get("sources_sha256") != h.hexdigest():
+    if rec.get("sources_sha256") != h.hexdigest() or "dram_bytes_per_launch" not in rec:
         return None
-    return rec.get("dram_bytes_per_launch")
+    return int(rec["dram_bytes_per_launch"])
 
 
 def _allreduce_totals(dist, grid, torch):
