@@ -256,6 +256,7 @@ def main():
     from paper_2211_14056_gb300.sharding import shard_range
     first, _ = shard_range(rank, world, n)             # this rank's Philox event range
     p32 = mf.Process(pid, **process_kwargs(w, mf.MF_FP32))
+    ptc = mf.Process(pid, **process_kwargs(w, mf.MF_FP32_TC))
     p64 = mf.Process(pid, **process_kwargs(w, mf.MF_FP64))
     stream = torch.cuda.current_stream()
 
@@ -269,6 +270,8 @@ def main():
         p64.vegas_finish(g64, adapt_n * world, refine=True)
     frozen = g64.get()
     g32 = p32.grid()
+    gtc = ptc.grid()
+    gtc.set(frozen)
     g32.set(frozen)
     g64.set(frozen)
 
@@ -278,6 +281,8 @@ def main():
     r32 = _iter(p32, g32, 1000, False, w32, dist, torch, w, first, n, world)
     r64 = _iter(p64, g64, 1000, False, w64, dist, torch, w, first, n, world)
     sig_err = abs(r32["I_k"] / r64["I_k"] - 1)
+    rtc = _iter(ptc, gtc, 1000, False, None, dist, torch, w, first, n, world)
+    sig_err_tc = abs(rtc["I_k"] / r64["I_k"] - 1)
     both = (w64 != 0) & (w32 != 0)
     flips = int(((w64 != 0) ^ (w32 != 0)).sum())      # cut / threshold decisions taken differently
     relw = ((w32[both] - w64[both]).abs() / w64[both].abs()).double()
@@ -324,6 +329,8 @@ def main():
     # 4. headline FP32 arm: K timed steps (clocks sampled meanwhile)
     with ClockSampler(local) as clk:
         t32, a32, pass32, launches, me32 = timed(p32, g32, args.steps, args.warmup, 3000)
+        ttc, _, _, _, metc = timed(ptc, gtc, args.steps, args.warmup, 3000)
+    mstc = _max_over_ranks(sum(ttc) / args.steps, dist, torch)
     ms32 = _max_over_ranks(sum(t32) / args.steps, dist, torch)
     value = n * world / (ms32 * 1e-3)
     value64 = n * world / (ms64 * 1e-3)
@@ -376,6 +383,10 @@ def main():
                        "l2": "flushed (512 MB write) between timed steps; inputs are generated in-kernel",
                        "grid": "adapted by 5 FP64 iterations of 2^20 events, then refined every step"},
             "fp64": {"value": value64, "unit": "events/s", "ms_per_step": ms64},
+            "fp32_tc": {"value": n * world / (mstc * 1e-3), "unit": "events/s", "ms_per_step": mstc,
+                        "me_ms_per_step": statistics.mean(m[0] for m in metc), "sigma_rel_err_vs_fp64": sig_err_tc,
+                        "colour_sum": "integer D C on the tensor cores (mma.m16n8k8 TF32, J split hi + lo, FP32 "
+                                      "accumulate); same steps, same frozen grid and events as the headline arm"},
             "speedup_fp32_vs_fp64": value / value64,
             "sigma_rel_err_fp32_vs_fp64": sig_err, "event_rel_err_fp32": ev_err,
             "pass_fraction": statistics.mean(pass32) / (n * world),

@@ -57,7 +57,8 @@ typedef int mf_status;
 /* arithmetic of the matrix element */
 #define MF_FP64 0      /* everything in FP64 */
 #define MF_FP32 1      /* amplitudes and colour sum in FP32 (FMA); sampling, Newton and sums FP64 */
-#define MF_FP32_TC 2   /* FP32 amplitudes, integer colour matrix on tensor cores */
+#define MF_FP32_TC 2   /* FP32 amplitudes; colour sum J^T (D C) J with the integer matrix D C on the
+                          tensor cores (mma.m16n8k8 TF32, J split into TF32 hi + lo, FP32 accumulate) */
 
 typedef struct mf_process mf_process;
 typedef struct mf_grid mf_grid;

@@ -171,7 +171,6 @@ mf_status mf_init_process(const mf_process_desc* d, mf_process** out) {
   if (!(d->g_s > 0) || !std::isfinite(d->g_s)) return fail(MF_ERR_ARG, "mf_init_process: bad g_s");
   if (d->precision != MF_FP64 && d->precision != MF_FP32 && d->precision != MF_FP32_TC)
     return fail(MF_ERR_ARG, "mf_init_process: bad precision");
-  if (d->precision == MF_FP32_TC) return fail(MF_ERR_UNSUPPORTED, "mf_init_process: MF_FP32_TC is not built");
   // colour matrix: must be the library's exact trace-basis matrix
   if (d->n_flow != factorial(ng)) return fail(MF_ERR_COLOUR, "mf_init_process: n_flow must be (n_ext-2)!");
   if (d->colour_num == nullptr || d->colour_den <= 0) return fail(MF_ERR_COLOUR, "mf_init_process: colour matrix missing");
@@ -218,6 +217,7 @@ mf_status mf_init_process(const mf_process_desc* d, mf_process** out) {
   MeParams& mp = p->mp;
   mp.mt = mt;
   mp.mw = mt * d->top_width;
+  mp.colour_tc = d->precision == MF_FP32_TC ? 1 : 0;
   p->g_s = d->g_s;
   p->width = d->top_width;
   const int sid = factorial(ng - 2);        // identical final-state gluons

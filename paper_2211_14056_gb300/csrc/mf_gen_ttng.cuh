@@ -11,6 +11,8 @@ template <int NG, int K> __device__ __forceinline__ const uint8_t* o4_table();
 template <int NG> __device__ __forceinline__ const uint8_t* blk_mask();
 template <int NG> __device__ __forceinline__ const uint16_t* blk_off();
 template <int NG> struct Paths;
+template <int NG> struct ColourTC;
+template <int NG> __device__ __forceinline__ const float* colour_frag_a();
 template <typename T> __device__ __forceinline__ V4<T> neg(const V4<T>& a) {
   V4<T> o;
 #pragma unroll
@@ -67,6 +69,10 @@ __device__ __forceinline__ T colour_form_2(const cplx<T> (&J)[2]) {
   return T(2) * s;
 }
 template <typename T> __device__ __forceinline__ T colour_form(const cplx<T> (&J)[2]) { return colour_form_2<T>(J); }
+// D C as TF32 A fragments of mma.m16n8k8: [m-tile][k-step][register][lane]
+template <> struct ColourTC<2> { static constexpr int MT = 1, KS = 1; };
+static __device__ const float kColourFragA2[128] = {16.f, -2.f, 0.f, 0.f, -2.f, 16.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+template <> __device__ __forceinline__ const float* colour_frag_a<2>() { return kColourFragA2; }
 // colour matrix, 3 gluons: C = M / 9; orderings lexicographic
 static constexpr int kColourDen3 = 9;
 static const int kColourNum3[36] = {64, -8, -8, 1, 1, 10, -8, 64, 1, 10, -8, 1, -8, 1, 64, -8, 10, 1, 1, 10, -8, 64, 1, -8, 1, -8, 10, 1, 64, -8, 10, 1, 1, -8, -8, 64};
@@ -150,6 +156,10 @@ __device__ __forceinline__ T colour_form_3(const cplx<T> (&J)[6]) {
   return T(2) * s;
 }
 template <typename T> __device__ __forceinline__ T colour_form(const cplx<T> (&J)[6]) { return colour_form_3<T>(J); }
+// D C as TF32 A fragments of mma.m16n8k8: [m-tile][k-step][register][lane]
+template <> struct ColourTC<3> { static constexpr int MT = 1, KS = 1; };
+static __device__ const float kColourFragA3[128] = {64.f, -8.f, -8.f, 1.f, -8.f, 64.f, 1.f, 10.f, -8.f, 1.f, 64.f, -8.f, 1.f, 10.f, -8.f, 64.f, 1.f, -8.f, 10.f, 1.f, 10.f, 1.f, 1.f, -8.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 10.f, 0.f, 0.f, -8.f, 1.f, 0.f, 0.f, 10.f, 1.f, 0.f, 0.f, 1.f, -8.f, 0.f, 0.f, 64.f, -8.f, 0.f, 0.f, -8.f, 64.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+template <> __device__ __forceinline__ const float* colour_frag_a<3>() { return kColourFragA3; }
 // colour matrix, 4 gluons: C = M / 54; orderings lexicographic
 static constexpr int kColourDen4 = 54;
 static const int kColourNum4[576] = {512, -64, -64, 8, 8, 80, -64, 8, 8, -1, -1, -10, 8, -1, 80, -10, 71, 62, -1, -10, -10, 62, 62, -28, -64, 512, 8, 80, -64, 8, 8, -64, -1, -10, 8, -1, -1, -10, -10, 62, 62, -28, 8, -1, 80, -10, 71, 62, -64, 8, 512, -64, 80, 8, 8, -1, 80, -10, 71, 62, -64, 8, 8, -1, -1, -10, -10, -1, 62, -28, -10, 62, 8, 80, -64, 512, 8, -64, -1, -10, -10, 62, 62, -28, 8, -64, -1, -10, 8, -1, -1, 8, 71, 62, 80, -10, 8, -64, 80, 8, 512, -64, -1, 8, 71, 62, 80, -10, -10, -1, 62, -28, -10, 62, -64, 8, 8, -1, -1, -10, 80, 8, 8, -64, -64, 512, -10, -1, 62, -28, -10, 62, -1, 8, 71, 62, 80, -10, 8, -64, -1, -10, 8, -1, -64, 8, 8, -1, -1, -10, 512, -64, -64, 8, 8, 80, 80, -10, 8, -1, 62, 71, -10, 62, -1, -10, -28, 62, 8, -64, -1, -10, 8, -1, -64, 512, 8, 80, -64, 8, -10, 62, -1, -10, -28, 62, 80, -10, 8, -1, 62, 71, 8, -1, 80, -10, 71, 62, -64, 8, 512, -64, 80, 8, 8, -1, -64, 8, -10, -1, 62, -28, -10, -1, 62, -10, -1, -10, -10, 62, 62, -28, 8, 80, -64, 512, 8, -64, -1, -10, 8, -64, -1, 8, 71, 62, -1, 8, -10, 80, -1, 8, 71, 62, 80, -10, 8, -64, 80, 8, 512, -64, 62, -28, -10, -1, 62, -10, 8, -1, -64, 8, -10, -1, -10, -1, 62, -28, -10, 62, 80, 8, 8, -64, -64, 512, 71, 62, -1, 8, -10, 80, -1, -10, 8, -64, -1, 8, 8, -1, -64, 8, -10, -1, 80, -10, 8, -1, 62, 71, 512, -64, -64, 8, 8, 80, 62, -10, -28, 62, -1, -10, -1, -10, 8, -64, -1, 8, -10, 62, -1, -10, -28, 62, -64, 512, 8, 80, -64, 8, -10, 80, 62, 71, 8, -1, 80, -10, 8, -1, 62, 71, 8, -1, -64, 8, -10, -1, -64, 8, 512, -64, 80, 8, -28, 62, 62, -10, -10, -1, -10, 62, -1, -10, -28, 62, -1, -10, 8, -64, -1, 8, 8, 80, -64, 512, 8, -64, 62, 71, -10, 80, -1, 8, 71, 62, -1, 8, -10, 80, 62, -28, -10, -1, 62, -10, 8, -64, 80, 8, 512, -64, -1, 8, -10, -1, -64, 8, 62, -28, -10, -1, 62, -10, 71, 62, -1, 8, -10, 80, 80, 8, 8, -64, -64, 512, -10, -1, -1, 8, 8, -64, -1, 8, -10, -1, -64, 8, -10, 80, 62, 71, 8, -1, 62, -10, -28, 62, -1, -10, 512, -64, -64, 8, 8, 80, -10, -1, -1, 8, 8, -64, 62, -10, -28, 62, -1, -10, -10, 80, 62, 71, 8, -1, -64, 512, 8, 80, -64, 8, -10, 80, 62, 71, 8, -1, -1, 8, -10, -1, -64, 8, -28, 62, 62, -10, -10, -1, -64, 8, 512, -64, 80, 8, 62, -10, -28, 62, -1, -10, -10, -1, -1, 8, 8, -64, 62, 71, -10, 80, -1, 8, 8, 80, -64, 512, 8, -64, 62, 71, -10, 80, -1, 8, -28, 62, 62, -10, -10, -1, -1, 8, -10, -1, -64, 8, 8, -64, 80, 8, 512, -64, -28, 62, 62, -10, -10, -1, 62, 71, -10, 80, -1, 8, -10, -1, -1, 8, 8, -64, 80, 8, 8, -64, -64, 512};
@@ -541,4 +551,8 @@ __device__ __forceinline__ T colour_form_4(const cplx<T> (&J)[24]) {
   return T(2) * s;
 }
 template <typename T> __device__ __forceinline__ T colour_form(const cplx<T> (&J)[24]) { return colour_form_4<T>(J); }
+// D C as TF32 A fragments of mma.m16n8k8: [m-tile][k-step][register][lane]
+template <> struct ColourTC<4> { static constexpr int MT = 2, KS = 3; };
+static __device__ const float kColourFragA4[768] = {512.f, -64.f, -64.f, 8.f, -64.f, 512.f, 8.f, 80.f, -64.f, 8.f, 512.f, -64.f, 8.f, 80.f, -64.f, 512.f, 8.f, -64.f, 80.f, 8.f, 80.f, 8.f, 8.f, -64.f, -64.f, 8.f, 8.f, -1.f, 8.f, -64.f, -1.f, -10.f, 8.f, -1.f, 80.f, -10.f, -1.f, -10.f, -10.f, 62.f, -1.f, 8.f, 71.f, 62.f, -10.f, -1.f, 62.f, -28.f, 8.f, -1.f, -64.f, 8.f, -1.f, -10.f, 8.f, -64.f, 80.f, -10.f, 8.f, -1.f, -10.f, 62.f, -1.f, -10.f, 8.f, 80.f, -64.f, 8.f, -64.f, 8.f, 8.f, -64.f, 80.f, 8.f, 8.f, -1.f, 8.f, -64.f, -1.f, -10.f, 512.f, -64.f, -1.f, 8.f, -64.f, 512.f, -10.f, -1.f, -1.f, -10.f, 512.f, -64.f, 8.f, -1.f, -64.f, 512.f, 71.f, 62.f, -64.f, 8.f, 62.f, -28.f, 8.f, 80.f, 80.f, -10.f, 8.f, -64.f, -10.f, 62.f, 80.f, 8.f, -10.f, -1.f, 80.f, -10.f, -1.f, 8.f, -10.f, 62.f, 62.f, 71.f, 8.f, -1.f, -28.f, 62.f, -1.f, -10.f, 8.f, -1.f, -1.f, -10.f, -1.f, -10.f, 8.f, -1.f, 80.f, -10.f, 71.f, 62.f, -10.f, 62.f, 62.f, -28.f, 71.f, 62.f, 80.f, -10.f, 62.f, -28.f, -10.f, 62.f, -64.f, 8.f, 8.f, 80.f, 8.f, 80.f, -64.f, 8.f, 512.f, -64.f, 80.f, 8.f, -64.f, 512.f, 8.f, -64.f, 80.f, 8.f, 512.f, -64.f, 8.f, -64.f, -64.f, 512.f, 8.f, -1.f, 62.f, 71.f, -1.f, -10.f, -28.f, 62.f, -64.f, 8.f, -10.f, -1.f, 8.f, -64.f, -1.f, 8.f, 8.f, -1.f, 80.f, -10.f, -1.f, -10.f, -10.f, 62.f, -64.f, 8.f, 8.f, -1.f, 8.f, -64.f, -1.f, -10.f, -10.f, -1.f, 62.f, -28.f, -1.f, 8.f, 71.f, 62.f, 80.f, -10.f, 8.f, -1.f, -10.f, 62.f, -1.f, -10.f, 8.f, -1.f, -64.f, 8.f, -1.f, -10.f, 8.f, -64.f, 62.f, -28.f, -10.f, -1.f, 71.f, 62.f, -1.f, 8.f, 512.f, -64.f, -64.f, 8.f, -64.f, 512.f, 8.f, 80.f, -64.f, 8.f, 512.f, -64.f, 8.f, 80.f, -64.f, 512.f, 71.f, 62.f, -1.f, -10.f, 62.f, -28.f, 8.f, -1.f, -1.f, -10.f, -10.f, -1.f, 8.f, -1.f, -1.f, 8.f, -10.f, 62.f, -64.f, 8.f, 80.f, -10.f, 8.f, -64.f, 62.f, 71.f, -10.f, 62.f, -28.f, 62.f, 80.f, -10.f, -10.f, -1.f, 62.f, -28.f, -1.f, 8.f, 71.f, 62.f, 62.f, -10.f, 8.f, -1.f, -10.f, 80.f, -1.f, -10.f, 8.f, 80.f, 62.f, -10.f, -64.f, 8.f, -10.f, 80.f, 80.f, 8.f, -28.f, 62.f, 8.f, -64.f, 62.f, 71.f, -10.f, 62.f, 62.f, -28.f, 80.f, -10.f, 71.f, 62.f, 62.f, -28.f, -10.f, 62.f, 71.f, 62.f, 80.f, -10.f, 8.f, -1.f, -1.f, -10.f, -1.f, -10.f, 8.f, -1.f, -1.f, -10.f, -28.f, 62.f, 8.f, -1.f, 62.f, 71.f, -10.f, -1.f, 62.f, -10.f, -1.f, 8.f, -10.f, 80.f, -64.f, 8.f, -10.f, -1.f, 8.f, -64.f, -1.f, 8.f, -28.f, 62.f, -1.f, -10.f, 62.f, 71.f, 8.f, -1.f, 62.f, -10.f, -10.f, -1.f, -10.f, 80.f, -1.f, 8.f, 71.f, 62.f, -1.f, 8.f, 62.f, -28.f, -10.f, -1.f, -1.f, 8.f, -10.f, -1.f, -10.f, -1.f, -1.f, 8.f, -10.f, 80.f, 62.f, 71.f, 62.f, -10.f, -28.f, 62.f, 62.f, 71.f, -10.f, 80.f, -28.f, 62.f, 62.f, -10.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -10.f, 80.f, 62.f, -28.f, 62.f, -10.f, 71.f, 62.f, -64.f, 8.f, -10.f, 80.f, 8.f, -64.f, 62.f, -10.f, 8.f, -1.f, -1.f, 8.f, -1.f, -10.f, -10.f, -1.f, -1.f, 8.f, -28.f, 62.f, -10.f, -1.f, 62.f, 71.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -10.f, -1.f, 62.f, -10.f, -1.f, 8.f, -10.f, 80.f, 62.f, 71.f, 8.f, -1.f, -28.f, 62.f, -1.f, -10.f, -10.f, -1.f, -64.f, 8.f, -1.f, 8.f, 8.f, -64.f, 62.f, -10.f, -10.f, -1.f, -10.f, 80.f, -1.f, 8.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 8.f, -64.f, 80.f, 8.f, 80.f, 8.f, 8.f, -64.f, 62.f, -10.f, -28.f, 62.f, -10.f, 80.f, 62.f, 71.f, -28.f, 62.f, 62.f, -10.f, 62.f, 71.f, -10.f, 80.f, -1.f, 8.f, -10.f, -1.f, -10.f, -1.f, -1.f, 8.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 512.f, -64.f, -1.f, 8.f, -64.f, 512.f, -10.f, -1.f, -1.f, -10.f, 512.f, -64.f, 8.f, -1.f, -64.f, 512.f, -10.f, -1.f, -64.f, 8.f, -1.f, 8.f, 8.f, 80.f, -64.f, 8.f, 8.f, -64.f, 8.f, -64.f, 80.f, 8.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -10.f, -1.f, -64.f, 8.f, -1.f, 8.f, 8.f, -64.f, -64.f, 8.f, 8.f, 80.f, 8.f, 80.f, -64.f, 8.f, 512.f, -64.f, 80.f, 8.f, -64.f, 512.f, 8.f, -64.f, 80.f, 8.f, 512.f, -64.f, 8.f, -64.f, -64.f, 512.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+template <> __device__ __forceinline__ const float* colour_frag_a<4>() { return kColourFragA4; }
 }  // namespace mf

@@ -18,6 +18,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <type_traits>
 
 #include "mf_device.cuh"
 #include "mf_gen_ttng.cuh"
@@ -28,6 +29,7 @@ namespace mf {
 struct MeParams {
   double mt, mw;     // top mass, mass * width
   double norm;       // g^(2 NG) / (spin-colour average * identical-particle factor * colour denominator)
+  int colour_tc;     // 1: FP32 colour sum on the tensor cores (MF_FP32_TC)
 };
 
 template <int NG> struct Lanes {
@@ -137,14 +139,21 @@ __device__ __forceinline__ void gluon_level(const R4<T>* q, cplx<T>* Gs, int gl)
 
 // Shared memory of one warp: per event of the warp its gluon sub-currents
 // G(B) and the 2^NG suffix momenta, and for every lane its colour-ordered
-// amplitudes J[sigma][top helicity] (interleaved by lane: conflict-free).
+// amplitudes J[sigma][top helicity], kept in two planes (real, imaginary
+// parts), each [row = sigma * 2 + top helicity][kJStride] with the lane as the
+// column.  The padded stride (36 = 4 mod 16 words) keeps both the
+// lane-parallel stores and the tensor-core colour sum's fragment loads free of
+// bank conflicts.
+constexpr int kJStride = 36;
+template <int NG> constexpr int kJPlane = TTNG<NG>::NPERM * 2 * kJStride;
+
 template <int NG, typename T> struct WarpMem {
   static constexpr int EPW = Lanes<NG>::EPW;
   static constexpr size_t gs_bytes = sizeof(V4<T>) * EPW * TTNG<NG>::NSTORE;   // EPW component-major stores
   static constexpr size_t pt_off = gs_bytes;
   static constexpr size_t pt_bytes = sizeof(R4<T>) * EPW * (1 << NG);
   static constexpr size_t j_off = (pt_off + pt_bytes + 15) & ~size_t(15);
-  static constexpr size_t j_bytes = sizeof(cplx<T>) * TTNG<NG>::NPERM * 2 * 32;
+  static constexpr size_t j_bytes = sizeof(T) * 2 * kJPlane<NG>;
   static constexpr size_t bytes = (j_off + j_bytes + 15) & ~size_t(15);
 };
 
@@ -155,7 +164,7 @@ template <typename T> struct LaneCtx {
   uint64_t pk;          // 4-bit compressed helicity index of this lane for every gluon mask
   S4<T> ub0, ub1;       // ubar(t) for top helicity -1, +1
   T m, mw;
-  cplx<T>* J;           // &J[0][0][lane] of this warp
+  T* J;                 // &Jre[0][lane] of this warp (the imaginary plane follows at kJPlane)
 };
 
 template <int NG, typename T>
@@ -193,24 +202,124 @@ __device__ __forceinline__ void quark_walk(int parent, S4<T> (&R)[NG], const Lan
       for (int m = 1; m < NG; ++m)
         apply_acc(make_slash(lane_block<NG, T>(cx, PT::final_blk(path, m))), R[NG - 1 - m], W);
       const int sig = PT::final_sigma(path);
-      cx.J[(sig * 2 + 0) * 32] = rowdot(cx.ub0, W);
-      cx.J[(sig * 2 + 1) * 32] = rowdot(cx.ub1, W);
+      const cplx<T> j0 = rowdot(cx.ub0, W), j1 = rowdot(cx.ub1, W);
+      cx.J[(sig * 2 + 0) * kJStride] = j0.r;
+      cx.J[(sig * 2 + 0) * kJStride + kJPlane<NG>] = j0.i;
+      cx.J[(sig * 2 + 1) * kJStride] = j1.r;
+      cx.J[(sig * 2 + 1) * kJStride + kJPlane<NG>] = j1.i;
     }
   }
 }
 
+// ----------------------------------------------------------------------------
+// Colour sum on the tensor cores (MF_FP32_TC).  The warp's amplitudes form
+// B[sigma][n] with 128 columns n = (real/imaginary, top helicity, lane); the
+// quadratic form of every column with C is Y = (D C) B followed by
+// sum_sigma B[sigma][n] Y[sigma][n], and an event's |M|^2 sums the columns of
+// its lanes.  Y comes from mma.m16n8k8 in TF32 with FP32 accumulation: the
+// integer matrix D C (|entries| <= 2048) is exact in TF32, and B is split as
+// B_hi + B_lo (both TF32), so Y = (D C) B_hi + (D C) B_lo carries ~22 bits of
+// B.  Fragment layouts (PTX ISA, mma.m16n8k8 .tf32): A register r of lane l is
+// (row l/4 + 8 (r & 1), column l%4 + 4 (r >> 1)); B register r is (row l%4 + 4 r,
+// column l/4); accumulator register r is (row l/4 + 8 (r >> 1), column
+// 2 (l%4) + (r & 1)).
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// J^dagger (D C) J summed over the columns of each event of the warp; returns
+// the sum of this lane's event (the value of group `group`).  J: the warp's
+// real plane (the imaginary plane follows at kJPlane).  All 32 lanes call it.
+template <int NG>
+__device__ __forceinline__ float colour_sum_tc(const float* J, int group) {
+  constexpr int NP = TTNG<NG>::NPERM, MT = ColourTC<NG>::MT, KS = ColourTC<NG>::KS;
+  constexpr int L = Lanes<NG>::L, EPW = Lanes<NG>::EPW;
+  const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+  uint32_t a[MT][KS][4];
+  const float* fa = colour_frag_a<NG>();
+#pragma unroll
+  for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[mi][ks][r] = __float_as_uint(__ldg(fa + ((mi * KS + ks) * 4 + r) * 32 + lane));
+  float part[EPW];
+#pragma unroll
+  for (int e = 0; e < EPW; ++e) part[e] = 0.f;
+#pragma unroll 1
+  for (int u = 0; u < 4; ++u) {                 // u = 2 * (imaginary plane) + top helicity
+    const float* P = J + (u >> 1) * kJPlane<NG>;
+    const int h = u & 1;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {               // columns: lanes 8c .. 8c + 7
+      const int lc0 = 8 * c;
+      float d[MT][4];
+#pragma unroll
+      for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) d[mi][r] = 0.f;
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        const int s0 = 8 * ks + tig, s1 = s0 + 4;
+        const float x0 = s0 < NP ? P[(s0 * 2 + h) * kJStride + lc0 + gid] : 0.f;
+        const float x1 = s1 < NP ? P[(s1 * 2 + h) * kJStride + lc0 + gid] : 0.f;
+        const uint32_t h0 = tf32_bits(x0), h1 = tf32_bits(x1);
+        const uint32_t l0 = tf32_bits(x0 - __uint_as_float(h0)), l1 = tf32_bits(x1 - __uint_as_float(h1));
+#pragma unroll
+        for (int mi = 0; mi < MT; ++mi) {
+          mma_tf32(d[mi], a[mi][ks], h0, h1);
+          mma_tf32(d[mi], a[mi][ks], l0, l1);
+        }
+      }
+      float s = 0.f;
+#pragma unroll
+      for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          const int sg = 16 * mi + gid + 8 * hf;
+          if (sg < NP) {
+            const float2 b = *reinterpret_cast<const float2*>(P + (sg * 2 + h) * kJStride + lc0 + 2 * tig);
+            s = fmaf(d[mi][2 * hf], b.x, fmaf(d[mi][2 * hf + 1], b.y, s));
+          }
+        }
+      part[lc0 / L] += s;
+    }
+  }
+  float mine = 0.f;
+#pragma unroll
+  for (int e = 0; e < EPW; ++e) {
+    float v = part[e];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (e == group) mine = v;
+  }
+  return mine;
+}
+
 // |M|^2 (without the normalisation MeParams::norm) of one event, computed by
 // its lane group; p: physical momenta in MadGraph order; wm: this warp's
-// shared memory (WarpMem layout).  Every lane of the warp must call this (the
-// group synchronises with __syncwarp).
+// shared memory (WarpMem layout); tc: colour sum on the tensor cores (FP32
+// only).  Every lane of the warp must call this (the group synchronises with
+// __syncwarp).
 template <int NG, typename T>
-__device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* wm, int group, int gl, T mt, T mw) {
+__device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* wm, int group, int gl, T mt, T mw,
+                                       int tc = 0) {
   using WM = WarpMem<NG, T>;
   constexpr int L = Lanes<NG>::L;
   constexpr int NP = TTNG<NG>::NPERM;
   cplx<T>* Gs = reinterpret_cast<cplx<T>*>(wm) + group * 4 * TTNG<NG>::NSTORE;
   R4<T>* Ptab = reinterpret_cast<R4<T>*>(wm + WM::pt_off) + group * (1 << NG);
-  cplx<T>* Jw = reinterpret_cast<cplx<T>*>(wm + WM::j_off);
+  T* Jw = reinterpret_cast<T*>(wm + WM::j_off);
   const int lane = threadIdx.x & 31;
   R4<T> q[NG];
 #pragma unroll
@@ -261,13 +370,21 @@ __device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* w
   S4<T> R[NG];
   R[0] = v_out(qtb, mt, ltb);
   quark_walk<NG, 1, T>(0, R, cx);
+  if constexpr (std::is_same<T, float>::value) {
+    if (tc) {
+      __syncwarp();   // every lane's J is in shared memory
+      const float v = colour_sum_tc<NG>(Jw, group);
+      __syncwarp();   // the warp's shared store may be overwritten after this
+      return v;
+    }
+  }
   // colour sum of both top helicities from this lane's amplitudes
   T part = T(0);
 #pragma unroll 1
   for (int h = 0; h < 2; ++h) {
     cplx<T> J[NP];
 #pragma unroll
-    for (int sg = 0; sg < NP; ++sg) J[sg] = cx.J[(sg * 2 + h) * 32];
+    for (int sg = 0; sg < NP; ++sg) J[sg] = {cx.J[(sg * 2 + h) * kJStride], cx.J[(sg * 2 + h) * kJStride + kJPlane<NG>]};
     part += colour_form<T>(J);
   }
 #pragma unroll
@@ -300,7 +417,7 @@ __global__ void __launch_bounds__(kThreads) k_matrix_element(MeParams mp, int64_
     for (int i = 0; i < NEXT; ++i)
 #pragma unroll
       for (int c = 0; c < 4; ++c) p[i][c] = T(mom[int64_t(i * 4 + c) * n + e]);
-    const T v = group_me2<NG, T>(p, wm, group, gl, mt, mw);
+    const T v = group_me2<NG, T>(p, wm, group, gl, mt, mw, mp.colour_tc);
     if (ok && gl == 0) out[e] = double(v) * mp.norm;
   }
 }
@@ -431,7 +548,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused(SampleParams sp, MeParams
       for (int i = 0; i < NEXT; ++i)
 #pragma unroll
         for (int c = 0; c < 4; ++c) p[i][c] = __shfl_sync(full, mine[i][c], from);
-      const T v = group_me2<NG, T>(p, wm, group, gl, mt, mw);
+      const T v = group_me2<NG, T>(p, wm, group, gl, mt, mw, mp.colour_tc);
 #pragma unroll
       for (int g = 0; g < EPW; ++g) {
         const T vg = __shfl_sync(full, v, g * L);
@@ -604,7 +721,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_me_acc(MeParams mp, int ndim, i
     for (int i = 0; i < NG; ++i)
 #pragma unroll
       for (int c = 0; c < 4; ++c) p[2 + i][c] = rec.mom[int64_t(i * 4 + c) * rec.C + e];
-    const T v = group_me2<NG, T>(p, wm, group, gl, mt, mw);
+    const T v = group_me2<NG, T>(p, wm, group, gl, mt, mw, mp.colour_tc);
     if (ok) {
       const double w = double(v) * mp.norm * rec.pref[e];
       if (gl == 0) {

@@ -127,7 +127,7 @@ __device__ __forceinline__ void mixed_tile(const MixedArgs<T>& a, int p, int64_t
     for (int i = 0; i < NG; ++i)
 #pragma unroll
       for (int c = 0; c < 4; ++c) pp[2 + i][c] = r.mom[int64_t(i * 4 + c) * r.C + e];
-    const T v = group_me2<NG, T>(pp, wm, group, gl, mt, mw);
+    const T v = group_me2<NG, T>(pp, wm, group, gl, mt, mw, mp.colour_tc);
     if (ok) {
       const double w = double(v) * mp.norm * r.pref[e];
       if (gl == 0) {

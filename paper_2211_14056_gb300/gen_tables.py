@@ -256,6 +256,37 @@ def emit_lane(n, lines, colour):
     lines += L
 
 
+def colour_tc_fragments(n, colour):
+    """(m-tiles, k-steps, values) of D C as the A operand of mma.m16n8k8 (TF32,
+    row-major 16 x 8 tiles), laid out [m-tile][k-step][register][lane]:
+    register r of lane l holds row 16 mi + l//4 + 8 (r & 1), column
+    8 ks + l % 4 + 4 (r >> 1); rows and columns beyond the orderings are 0.
+    The entries are integers of magnitude <= 2048, exact in TF32."""
+    orders, M, D = colour
+    P = len(orders)
+    mt, ks = (P + 15) // 16, (P + 7) // 8
+    vals = []
+    for mi in range(mt):
+        for k in range(ks):
+            for r in range(4):
+                for lane in range(32):
+                    row = 16 * mi + lane // 4 + 8 * (r & 1)
+                    col = 8 * k + lane % 4 + 4 * (r >> 1)
+                    v = M[row][col] if row < P and col < P else 0
+                    assert abs(v) <= 2048
+                    vals.append(v)
+    return mt, ks, vals
+
+
+def emit_colour_tc(n, lines, colour):
+    mt, ks, vals = colour_tc_fragments(n, colour)
+    lines.append(f"// D C as TF32 A fragments of mma.m16n8k8: [m-tile][k-step][register][lane]")
+    lines.append(f"template <> struct ColourTC<{n}> {{ static constexpr int MT = {mt}, KS = {ks}; }};")
+    lines.append(f"static __device__ const float kColourFragA{n}[{len(vals)}] = "
+                 f"{{{', '.join(f'{v}.f' for v in vals)}}};")
+    lines.append(f"template <> __device__ __forceinline__ const float* colour_frag_a<{n}>() {{ return kColourFragA{n}; }}")
+
+
 def render():
     lines = [
         "// GENERATED by paper_2211_14056_gb300/gen_tables.py -- do not edit.",
@@ -271,6 +302,8 @@ def render():
         "template <int NG> __device__ __forceinline__ const uint8_t* blk_mask();",
         "template <int NG> __device__ __forceinline__ const uint16_t* blk_off();",
         "template <int NG> struct Paths;",
+        "template <int NG> struct ColourTC;",
+        "template <int NG> __device__ __forceinline__ const float* colour_frag_a();",
         "template <typename T> __device__ __forceinline__ V4<T> neg(const V4<T>& a) {",
         "  V4<T> o;",
         "#pragma unroll",
@@ -289,6 +322,7 @@ def render():
         lines.append(f"static const int kColourNum{n}[{P * P}] = {{{', '.join(map(str, flat))}}};")
         emit_tables(n, lines)
         emit_lane(n, lines, colours[n])
+        emit_colour_tc(n, lines, colours[n])
     lines.append("}  // namespace mf")
     return "\n".join(lines) + "\n"
 

@@ -27,7 +27,7 @@ def _procs(mf, precision):
             for k in NAMES]
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_mixed_matches_separate_iterations(mf, precision):
     # FP64: identical up to summation order, over two refined iterations.
     # FP32: the two kernels inline the amplitude code differently (FMA

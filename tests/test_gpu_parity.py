@@ -116,10 +116,13 @@ def test_matrix_element_fp64_matches_feynman_oracle(mf, name, nev, frac):
     assert_fp64_parity(out.cpu().numpy(), ref, frac=frac)
 
 
+@pytest.mark.parametrize("tc", [False, True])
 @pytest.mark.parametrize("name,nev", [("gg_ttx_1tev", 1000), ("gg_ttxg_13tev", 500), ("gg_ttxgg_13tev", 200)])
-def test_matrix_element_fp32_error(mf, name, nev):
-    """FP32 amplitudes: the error statement of the single-precision path."""
-    p, w = _proc(mf, name, mf.MF_FP32)
+def test_matrix_element_fp32_error(mf, name, nev, tc):
+    """FP32 amplitudes (colour sum on the FMA pipes, or on the tensor cores
+    with the TF32 hi/lo split): the error statement of the single-precision
+    path."""
+    p, w = _proc(mf, name, mf.MF_FP32_TC if tc else mf.MF_FP32)
     st = _oracle_setup(w)
     po = _cut_events(st, 6, nev)
     ref = st.proc.me2_batched(po)
@@ -127,9 +130,46 @@ def test_matrix_element_fp32_error(mf, name, nev):
     p.matrix_element(len(po), _aos_to_soa(po), out)
     torch.cuda.synchronize()
     rel = np.abs(out.cpu().numpy() / ref - 1)
-    print(f"{name} FP32 |M|^2 rel. error: max {rel.max():.2e} p99 {np.quantile(rel, 0.99):.2e} "
+    print(f"{name} FP32{'/TC' if tc else ''} |M|^2 rel. error: max {rel.max():.2e} p99 {np.quantile(rel, 0.99):.2e} "
           f"median {np.median(rel):.2e}")
     assert np.median(rel) < 1e-5 and np.quantile(rel, 0.99) < 1e-4 and rel.max() < 5e-3
+
+
+@pytest.mark.parametrize("name,nev", [("gg_ttx_1tev", 4096), ("gg_ttxg_13tev", 4096), ("gg_ttxgg_13tev", 2048)])
+def test_tensor_core_colour_sum_matches_fma(mf, name, nev):
+    """Same FP32 amplitudes, colour sum on the tensor cores vs on the FMA
+    pipes: the difference is the colour sum's own rounding (TF32 hi/lo split
+    of J, FP32 accumulation in another order), ~1e-7 relative."""
+    p32, w = _proc(mf, name, mf.MF_FP32)
+    ptc, _ = _proc(mf, name, mf.MF_FP32_TC)
+    st = _oracle_setup(w)
+    po = _cut_events(st, 7, nev)
+    a = torch.empty(len(po), dtype=torch.float64, device="cuda")
+    b = torch.empty(len(po), dtype=torch.float64, device="cuda")
+    mom = _aos_to_soa(po)
+    p32.matrix_element(len(po), mom, a)
+    ptc.matrix_element(len(po), mom, b)
+    torch.cuda.synchronize()
+    rel = (b / a - 1).abs().cpu().numpy()
+    print(f"{name} TC vs FMA colour sum: median {np.median(rel):.2e} max {rel.max():.2e}")
+    assert np.median(rel) < 1e-6 and rel.max() < 1e-5
+
+
+def test_tensor_core_iteration_sigma_error(mf):
+    """One iteration of gg -> t tbar g g on a frozen random grid in FP64, FP32
+    and FP32/TC on identical events: the arithmetic error of sigma."""
+    name, n = "gg_ttxgg_13tev", 1 << 16
+    res = {}
+    for prec in (mf.MF_FP64, mf.MF_FP32, mf.MF_FP32_TC):
+        p, _ = _proc(mf, name, prec)
+        g = p.grid()
+        g.set(random_grid(p.ndim, seed=13))
+        res[prec] = p.vegas_iterate(g, seed=17, it=0, n=n, refine=False)
+    e32 = abs(res[mf.MF_FP32]["I_k"] / res[mf.MF_FP64]["I_k"] - 1)
+    etc = abs(res[mf.MF_FP32_TC]["I_k"] / res[mf.MF_FP64]["I_k"] - 1)
+    print(f"sigma rel. error: FP32 {e32:.2e}, FP32/TC {etc:.2e}")
+    assert etc < 1e-5 and e32 < 1e-5
+    assert res[mf.MF_FP32_TC]["n_pass"] == res[mf.MF_FP32]["n_pass"]
 
 
 def test_matrix_element_edge_cases(mf):
