@@ -463,7 +463,8 @@ def _mixed_leg(mf, torch, iters=5):
     with torch.cuda.stream(side):
         for it in range(3):
             m.run(seed, it, refine=True, stream=side)
-        cands = [(c, t) for c in (1, 2, 0) for t in (8, 32, 128, 512)]
+        # tile 0: every process in its own specialised |M|^2 kernel within the iteration
+        cands = [(c, t) for c in (1, 2, 0) for t in (8, 32, 128, 512)] + [(0, 0), (2, 0)]
         times, best = m.autotune(seed, cands, stream=side)
         m.use_graph(True)
         m.run(seed, 3, refine=True, stream=side)          # capture

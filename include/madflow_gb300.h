@@ -235,15 +235,19 @@ mf_status mf_fma_throughput(int precision, double* tflops);
  *   mf_mixed_run      one iteration, out[k] receives process k's result like
  *                     mf_vegas_iterate (synchronises the stream);
  *   mf_mixed_set_launch  CTAs per SM of the |M|^2 launch (0 = occupancy) and
- *                     events per work item;
+ *                     events per work item; tile = 0 selects the per-process
+ *                     form instead: no shared queue, every process runs its own
+ *                     specialised |M|^2 kernel (most gluons first) at its own
+ *                     occupancy, inside the same iteration (and graph);
  *   mf_mixed_use_graph  capture the whole iteration as a CUDA graph on the
  *                     next run (per stream and refine flag) and replay it with
  *                     a new seed/iteration (copied from pinned host memory by
  *                     a node of the graph); the legacy default stream (NULL)
  *                     cannot be captured, so there the iteration runs uncaptured;
- *   mf_mixed_autotune times each candidate (ctas_per_sm, tile) on one
- *                     unrefined iteration (results not recorded), writes the
- *                     times (ms) and the index of the fastest, and keeps it. */
+ *   mf_mixed_autotune times each candidate (ctas_per_sm, tile), tile = 0
+ *                     being the per-process form, on one unrefined iteration
+ *                     (results not recorded), writes the times (ms) and the
+ *                     index of the fastest, and keeps it. */
 typedef struct mf_mixed mf_mixed;
 mf_status mf_mixed_create(mf_process* const* procs, mf_grid* const* grids, const int64_t* n, int nproc,
                           mf_mixed** out);

@@ -760,6 +760,11 @@ cudaError_t launch_fused(int precision, const SampleParams& sp, const MeParams& 
                          unsigned long long* counters, double* w_out, int grid, cudaStream_t s);
 template <int NG>
 cudaError_t fused_config(int precision, int ndim, int nbins, size_t* smem, int* ctas_per_sm);
+// |M|^2 + accumulation of records already sampled (rec_base: RecordView of capacity C)
+template <int NG>
+cudaError_t launch_me_acc(int precision, const MeParams& mp, int n_final, int ndim, int nbins, void* rec_base,
+                          int64_t C, int accumulate, double* partials, unsigned long long* counters, double* w_out,
+                          int grid, cudaStream_t s);
 // two-kernel iteration over one chunk of records (rec_base: RecordView of chunk capacity C)
 template <int NG>
 cudaError_t launch_chunk(int precision, const SampleParams& sp, const MeParams& mp, const double* edges,
@@ -873,6 +878,22 @@ cudaError_t launch_fma_peak(int precision, int blocks, int iters, float* sink, c
       k_me_acc<NG, float><<<grid, kThreads, MeAccLayout<NG, float>::total(nacc), s>>>(                            \
           mp, sp.ndim, sp.nbins, rec, accumulate, partials, counters, w_out);                                     \
       if (ev) cudaEventRecord(ev[2], s);                                                                          \
+    }                                                                                                             \
+    return cudaGetLastError();                                                                                    \
+  }                                                                                                               \
+  template <>                                                                                                     \
+  cudaError_t launch_me_acc<NG>(int precision, const MeParams& mp, int n_final, int ndim, int nbins,              \
+                                void* rec_base, int64_t C, int accumulate, double* partials,                      \
+                                unsigned long long* counters, double* w_out, int grid, cudaStream_t s) {          \
+    const int nacc = 2 + ndim * nbins;                                                                            \
+    if (precision == 0) {                                                                                         \
+      RecordView<double> rec = RecordView<double>::carve(rec_base, n_final, ndim, C);                             \
+      k_me_acc<NG, double><<<grid, kThreads, MeAccLayout<NG, double>::total(nacc), s>>>(                          \
+          mp, ndim, nbins, rec, accumulate, partials, counters, w_out);                                           \
+    } else {                                                                                                      \
+      RecordView<float> rec = RecordView<float>::carve(rec_base, n_final, ndim, C);                               \
+      k_me_acc<NG, float><<<grid, kThreads, MeAccLayout<NG, float>::total(nacc), s>>>(                            \
+          mp, ndim, nbins, rec, accumulate, partials, counters, w_out);                                           \
     }                                                                                                             \
     return cudaGetLastError();                                                                                    \
   }                                                                                                               \

@@ -42,38 +42,75 @@ cudaError_t launch_sample(const SampleParams& sp, const double* edges, int64_t n
   return cudaGetLastError();
 }
 
-// Lepage's refinement of one dimension: smooth the per-bin sums of w^2
-// (neighbour average, halves at the ends), normalise, damp with
+// Lepage's refinement of one dimension by one warp: smooth the per-bin sums
+// of w^2 (neighbour average, halves at the ends), normalise, damp with
 // ((1 - d)/ln(1/d))^alpha (0 -> 0, 1 -> 1), then place the new edges at equal
-// shares of the damped weights, linear inside the old bins.
-__device__ void refine_dim(double* e, const double* d, int nb, double alpha) {
-  double ds[64], r[64], cum[65], old[65];
+// shares of the damped weights, linear inside the old bins.  Lane l holds
+// bins l and l + 32 (nb <= 64); the normalising sum is a shuffle reduction,
+// the cumulative weights an in-order prefix scan, and each new edge finds its
+// old bin by binary search (the largest j < nb with cum[j] <= target).
+// cum, old, rw: this dimension's shared scratch (nb + 1, nb + 1, nb doubles).
+__device__ void refine_dim_warp(double* e, const double* d, int nb, double alpha, double* cum, double* old,
+                                double* rw) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   bool any = false;
-  for (int b = 0; b < nb; ++b) any |= d[b] > 0.0;
-  if (!any) return;
-  ds[0] = (d[0] + d[1]) / 2.0;
-  ds[nb - 1] = (d[nb - 2] + d[nb - 1]) / 2.0;
-  for (int b = 1; b < nb - 1; ++b) ds[b] = (d[b - 1] + d[b] + d[b + 1]) / 3.0;
-  double sum = 0.0;
-  for (int b = 0; b < nb; ++b) sum += ds[b];
-  for (int b = 0; b < nb; ++b) {
-    const double dn = ds[b] / sum;
-    r[b] = (dn > 0.0 && dn < 1.0) ? pow((1.0 - dn) / log(1.0 / dn), alpha) : (dn >= 1.0 ? 1.0 : 0.0);
+  double ds[2], r[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int b = lane + 32 * q;
+    ds[q] = 0.0;
+    if (b < nb) {
+      any |= d[b] > 0.0;
+      if (b == 0) ds[q] = (d[0] + d[1]) / 2.0;
+      else if (b == nb - 1) ds[q] = (d[nb - 2] + d[nb - 1]) / 2.0;
+      else ds[q] = (d[b - 1] + d[b] + d[b + 1]) / 3.0;
+    }
   }
-  cum[0] = 0.0;
-  for (int b = 0; b < nb; ++b) cum[b + 1] = cum[b] + r[b];
-  for (int b = 0; b <= nb; ++b) old[b] = e[b];
+  if (!__any_sync(full, any)) return;
+  double sum = ds[0] + ds[1];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(full, sum, off);
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const double dn = ds[q] / sum;
+    r[q] = (dn > 0.0 && dn < 1.0) ? pow((1.0 - dn) / log(1.0 / dn), alpha) : (dn >= 1.0 ? 1.0 : 0.0);
+  }
+  // inclusive prefix sums in bin order: bins 0..31, then 32..63 offset by the first half
+  double base = 0.0;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    double x = r[q];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const double y = __shfl_up_sync(full, x, off);
+      if (lane >= off) x += y;
+    }
+    const int b = lane + 32 * q;
+    if (b < nb) {
+      cum[b + 1] = base + x;
+      rw[b] = r[q];
+    }
+    base += __shfl_sync(full, x, 31);
+  }
+  for (int b = lane; b <= nb; b += 32) old[b] = e[b];
+  if (lane == 0) cum[0] = 0.0;
+  __syncwarp();
   const double total = cum[nb];
-  int j = 0;
-  for (int k = 1; k < nb; ++k) {
+  for (int k = 1 + lane; k < nb; k += 32) {
     const double target = total * k / nb;
-    // largest j with cum[j] <= target, within [0, nb-1]
-    while (j + 1 <= nb - 1 && cum[j + 1] <= target) ++j;
-    const double frac = r[j] > 0.0 ? (target - cum[j]) / r[j] : 0.0;
-    e[k] = old[j] + frac * (old[j + 1] - old[j]);
+    int lo = 0, hi = nb - 1;                  // cum[lo] <= target always (cum[0] = 0)
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (cum[mid] <= target) lo = mid; else hi = mid - 1;
+    }
+    const double frac = rw[lo] > 0.0 ? (target - cum[lo]) / rw[lo] : 0.0;
+    e[k] = old[lo] + frac * (old[lo + 1] - old[lo]);
   }
-  e[0] = 0.0;
-  e[nb] = 1.0;
+  if (lane == 0) {
+    e[0] = 0.0;
+    e[nb] = 1.0;
+  }
 }
 
 // Sum of the per-CTA partials in CTA order (deterministic for given partials).
@@ -100,9 +137,11 @@ cudaError_t launch_reduce(const double* partials, const unsigned long long* coun
   return cudaGetLastError();
 }
 
-// Estimate of one iteration from the (possibly all-reduced) totals, and the refinement.
+// Estimate of one iteration from the (possibly all-reduced) totals, and the
+// refinement: warp j refines dimension j.
 __global__ void k_finish(const double* __restrict__ totals, int ndim, int nbins, int64_t n, int refine,
                          double* __restrict__ edges, double* __restrict__ result) {
+  __shared__ double cum[kMaxDim][65], old[kMaxDim][65], rw[kMaxDim][64];
   const int nacc = 2 + ndim * nbins;
   if (threadIdx.x == 0) {
     const double dn = double(n);
@@ -114,15 +153,15 @@ __global__ void k_finish(const double* __restrict__ totals, int ndim, int nbins,
     result[4] = totals[nacc];
     result[5] = totals[nacc + 1];
   }
-  if (refine && int(threadIdx.x) < ndim) {
-    const int j = threadIdx.x;
-    refine_dim(edges + j * (nbins + 1), totals + 2 + j * nbins, nbins, 1.5);
-  }
+  const int j = threadIdx.x >> 5;
+  if (refine && j < ndim)
+    refine_dim_warp(edges + j * (nbins + 1), totals + 2 + j * nbins, nbins, 1.5, cum[j], old[j], rw[j]);
 }
 
 cudaError_t launch_finish(const double* totals, int ndim, int nbins, int64_t n_total, int refine, double* edges,
                           double* result, cudaStream_t s) {
-  k_finish<<<1, 64, 0, s>>>(totals, ndim, nbins, n_total, refine, edges, result);
+  if (ndim < 1 || ndim > kMaxDim || nbins < 2 || nbins > 64) return cudaErrorInvalidValue;
+  k_finish<<<1, 32 * ndim, 0, s>>>(totals, ndim, nbins, n_total, refine, edges, result);
   return cudaGetLastError();
 }
 

@@ -218,7 +218,8 @@ struct mf_mixed {
   int order[kMaxProc] = {};          // processes by decreasing cost (gluon count)
   int ctas_per_sm = 0;               // 0 = occupancy
   int occupancy = 1;
-  int tile = 32;
+  int tile = 32;                     // listed events per work item; 0: per-process kernels
+  int acc_occ[kMaxProc] = {};        // occupancy of each process's own |M|^2 kernel
   size_t me_smem = 0, sample_smem = 0;
   unsigned* d_queue = nullptr;
   unsigned* d_iter = nullptr;        // [iteration, seed lo, seed hi]
@@ -234,6 +235,22 @@ namespace {
 int me_grid(const mf_mixed* m) {
   const int c = m->ctas_per_sm > 0 && m->ctas_per_sm < m->occupancy ? m->ctas_per_sm : m->occupancy;
   return m->sms * (c < 1 ? 1 : c);
+}
+
+// CTAs of process k's own |M|^2 kernel (per-process mode)
+int acc_grid(const mf_mixed* m, int k) {
+  const int occ = m->acc_occ[k];
+  const int c = m->ctas_per_sm > 0 && m->ctas_per_sm < occ ? m->ctas_per_sm : occ;
+  return m->sms * (c < 1 ? 1 : c);
+}
+
+cudaError_t launch_acc_dispatch(int ng, int prec, const MeParams& mp, int n_final, int ndim, int nbins, void* rec,
+                                int64_t C, double* partials, unsigned long long* counters, int grid, cudaStream_t s) {
+  switch (ng) {
+    case 2: return launch_me_acc<2>(prec, mp, n_final, ndim, nbins, rec, C, 0, partials, counters, nullptr, grid, s);
+    case 3: return launch_me_acc<3>(prec, mp, n_final, ndim, nbins, rec, C, 0, partials, counters, nullptr, grid, s);
+    default: return launch_me_acc<4>(prec, mp, n_final, ndim, nbins, rec, C, 0, partials, counters, nullptr, grid, s);
+  }
 }
 
 template <typename K>
@@ -283,20 +300,34 @@ mf_status enqueue(mf_mixed* m, int refine, cudaStream_t s) {
   const int64_t need = (total + kThreads - 1) / kThreads;
   const int sgrid = int(need < int64_t(m->sms) * 16 ? need : int64_t(m->sms) * 16);
   const int grid = me_grid(m);
+  const bool queue = m->tile > 0;
   if (m->precision == 0) {
     const MixedArgs<double> a = make_args<double>(m);
     k_sample_mixed<double><<<sgrid, kThreads, m->sample_smem, s>>>(a);
-    k_me_mixed<double><<<grid, kThreads, m->me_smem, s>>>(a);
+    if (queue) k_me_mixed<double><<<grid, kThreads, m->me_smem, s>>>(a);
   } else {
     const MixedArgs<float> a = make_args<float>(m);
     k_sample_mixed<float><<<sgrid, kThreads, m->sample_smem, s>>>(a);
-    k_me_mixed<float><<<grid, kThreads, m->me_smem, s>>>(a);
+    if (queue) k_me_mixed<float><<<grid, kThreads, m->me_smem, s>>>(a);
   }
   MF_CUDA(cudaGetLastError(), "mf_mixed (kernels)");
-  count_launches(2);
+  count_launches(queue ? 2 : 1);
+  if (!queue) {
+    // per-process mode: each process's own |M|^2 kernel, most expensive first
+    for (int k = 0; k < m->nproc; ++k) {
+      const int i = m->order[k];
+      const mf_process* p = m->procs[i];
+      mf_grid* g = m->grids[i];
+      MF_CUDA(launch_acc_dispatch(p->ng, m->precision, p->mp, p->sp.n_final, g->ndim, g->nbins, g->d_records,
+                                  g->chunk, g->d_partials, g->d_counters, acc_grid(m, i), s),
+              "mf_mixed (per-process kernel)");
+      count_launches(1);
+    }
+  }
   for (int k = 0; k < m->nproc; ++k) {
     mf_grid* g = m->grids[k];
-    MF_CUDA(launch_reduce(g->d_partials, g->d_counters, grid, g->ndim, g->nbins, g->d_totals, s), "mf_mixed (reduce)");
+    const int pgrid = queue ? grid : acc_grid(m, k);
+    MF_CUDA(launch_reduce(g->d_partials, g->d_counters, pgrid, g->ndim, g->nbins, g->d_totals, s), "mf_mixed (reduce)");
     MF_CUDA(launch_finish(g->d_totals, g->ndim, g->nbins, m->n[k], refine, g->d_edges, g->d_result, s), "mf_mixed (finish)");
     MF_CUDA(cudaMemcpyAsync(g->h_result, g->d_result, sizeof(double) * 6, cudaMemcpyDeviceToHost, s), "mf_mixed (copy)");
     count_launches(2);
@@ -365,6 +396,11 @@ mf_status mf_mixed_create(mf_process* const* procs, mf_grid* const* grids, const
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m->occupancy, k_me_mixed<float>, kThreads, m->me_smem);
   }
   if (e == cudaSuccess && m->occupancy < 1) e = cudaErrorInvalidConfiguration;
+  for (int k = 0; k < nproc && e == cudaSuccess; ++k) {
+    size_t asm_ = 0;
+    e = dispatch_acc_config(procs[k]->ng, m->precision, grids[k]->ndim, grids[k]->nbins, &asm_, &m->acc_occ[k]);
+    if (e == cudaSuccess && m->acc_occ[k] < 1) e = cudaErrorInvalidConfiguration;
+  }
   // per-grid records for the whole event count, and partial slots for the mixed grid
   for (int k = 0; k < nproc && e == cudaSuccess; ++k) {
     mf_status st = grid_reserve(grids[k], n[k]);
@@ -372,7 +408,7 @@ mf_status mf_mixed_create(mf_process* const* procs, mf_grid* const* grids, const
       delete m;
       return st;
     }
-    if (grids[k]->max_blocks < m->sms * m->occupancy) {
+    if (grids[k]->max_blocks < m->sms * std::max(m->occupancy, m->acc_occ[k])) {
       delete m;
       return fail(MF_ERR_ARG, "mf_mixed_create: grid scratch smaller than the mixed launch");
     }
@@ -399,7 +435,7 @@ mf_status mf_mixed_destroy(mf_mixed* m) {
 }
 
 mf_status mf_mixed_set_launch(mf_mixed* m, int ctas_per_sm, int tile) {
-  if (m == nullptr || ctas_per_sm < 0 || tile < 1) return fail(MF_ERR_ARG, "mf_mixed_set_launch: bad argument");
+  if (m == nullptr || ctas_per_sm < 0 || tile < 0) return fail(MF_ERR_ARG, "mf_mixed_set_launch: bad argument");
   m->ctas_per_sm = ctas_per_sm;
   m->tile = tile;
   drop_graphs(m);
@@ -458,6 +494,8 @@ mf_status mf_mixed_autotune(mf_mixed* m, uint64_t seed, int ncand, const int* ca
                             double* ms, int* best, void* stream) {
   if (m == nullptr || ncand < 1 || cand_ctas == nullptr || cand_tile == nullptr || ms == nullptr || best == nullptr)
     return fail(MF_ERR_ARG, "mf_mixed_autotune: bad argument");
+  for (int c = 0; c < ncand; ++c)
+    if (cand_ctas[c] < 0 || cand_tile[c] < 0) return fail(MF_ERR_ARG, "mf_mixed_autotune: bad candidate");
   cudaStream_t s = (cudaStream_t)stream;
   const int keep_c = m->ctas_per_sm, keep_t = m->tile;
   const bool keep_g = m->use_graph;
@@ -475,7 +513,7 @@ mf_status mf_mixed_autotune(mf_mixed* m, uint64_t seed, int ncand, const int* ca
   mf_status st = MF_OK;
   for (int c = 0; c < ncand && st >= 0; ++c) {
     m->ctas_per_sm = cand_ctas[c];
-    m->tile = cand_tile[c] > 0 ? cand_tile[c] : 1;
+    m->tile = cand_tile[c];
     m->h_iter[0] = 0;
     m->h_iter[1] = unsigned(seed);
     m->h_iter[2] = unsigned(seed >> 32);
@@ -506,7 +544,7 @@ mf_status mf_mixed_autotune(mf_mixed* m, uint64_t seed, int ncand, const int* ca
     return st;
   }
   m->ctas_per_sm = cand_ctas[*best];
-  m->tile = cand_tile[*best] > 0 ? cand_tile[*best] : 1;
+  m->tile = cand_tile[*best];
   return MF_OK;
 }
 

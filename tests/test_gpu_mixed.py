@@ -27,8 +27,8 @@ def _procs(mf, precision):
             for k in NAMES]
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2])
-def test_mixed_matches_separate_iterations(mf, precision):
+@pytest.mark.parametrize("precision,tile", [(0, 32), (1, 32), (2, 32), (0, 0), (1, 0)])
+def test_mixed_matches_separate_iterations(mf, precision, tile):
     # FP64: identical up to summation order, over two refined iterations.
     # FP32: the two kernels inline the amplitude code differently (FMA
     # contraction), so events agree to FP32 rounding; after a refinement the
@@ -41,6 +41,7 @@ def test_mixed_matches_separate_iterations(mf, precision):
     mixed_grids = [p.grid() for p in procs]
     solo_grids = [p.grid() for p in procs]
     mx = mf.Mixed(procs, mixed_grids, n)
+    mx.set_launch(0, tile)                       # tile 0: each process's own |M|^2 kernel
     for it in range(iters):
         res = mx.run(seed=21, it=it, refine=True)
         for k, p in enumerate(procs):
@@ -61,9 +62,10 @@ def test_mixed_graph_replay_and_autotune(mf):
     graph = mf.Mixed(procs, gb, n)
     graph.use_graph(True)
     side = torch.cuda.Stream()                   # capture needs a non-default stream
-    times, best = graph.autotune(seed=5, candidates=[(1, 8), (2, 8), (1, 32), (2, 32)], stream=side)
-    assert len(times) == 4 and 0 <= best < 4 and all(t > 0 for t in times)
-    plain.set_launch(*[(1, 8), (2, 8), (1, 32), (2, 32)][best])
+    cands = [(1, 8), (2, 8), (1, 32), (2, 32), (0, 0)]
+    times, best = graph.autotune(seed=5, candidates=cands, stream=side)
+    assert len(times) == 5 and 0 <= best < 5 and all(t > 0 for t in times)
+    plain.set_launch(*cands[best])
     for it in range(3):
         a = plain.run(seed=5, it=it, refine=True)
         b = graph.run(seed=5, it=it, refine=True, stream=side)
@@ -85,3 +87,8 @@ def test_mixed_rejects_bad_plans(mf):
         mf.Mixed([procs[0]], [g[1]], [10])                                 # grid of another process
     with pytest.raises(mf.MFError):
         mf.Mixed(procs, g, [10, 1, 10])                                    # too few events
+    plan = mf.Mixed(procs, g, [10, 10, 10])
+    with pytest.raises(mf.MFError):
+        plan.set_launch(0, -1)                                             # negative tile
+    with pytest.raises(mf.MFError):
+        plan.autotune(seed=1, candidates=[(1, 8), (-1, 8)])                # negative CTAs per SM
