@@ -118,6 +118,23 @@ __device__ __forceinline__ S4<T> quark_prop(const R4<T>& P, T m, T mw, const S4<
   return o;
 }
 
+// The same with the factor f = -1/(P^2 - m^2 + i m Gamma) precomputed per
+// suffix (it depends on no helicity): X -> (P-slash + m) X f.
+template <typename T>
+__device__ __forceinline__ S4<T> quark_prop_f(const R4<T>& P, T m, cplx<T> f, const S4<T>& X) {
+  const T a = P.v[0] + P.v[3], b = P.v[0] - P.v[3];
+  const cplx<T> c = {P.v[1], P.v[2]}, d = {P.v[1], -P.v[2]};
+  S4<T> y;
+  y.c[0] = rfma(b, X.c[2], rfma(m, X.c[0], -(d * X.c[3])));
+  y.c[1] = rfma(a, X.c[3], rfma(m, X.c[1], -(c * X.c[2])));
+  y.c[2] = rfma(a, X.c[0], rfma(m, X.c[2], d * X.c[1]));
+  y.c[3] = rfma(b, X.c[1], rfma(m, X.c[3], c * X.c[0]));
+  S4<T> o;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.c[k] = y.c[k] * f;
+  return o;
+}
+
 template <typename T> __device__ __forceinline__ cplx<T> rowdot(const S4<T>& row, const S4<T>& col) {
   cplx<T> s = row.c[0] * col.c[0];
   s = cfma(row.c[1], col.c[1], s);

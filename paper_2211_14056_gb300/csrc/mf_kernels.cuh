@@ -38,25 +38,66 @@ template <int NG> struct Lanes {
   static constexpr int NEXT = NG + 2;
 };
 
+// Bit deposit / extract on the gluon-helicity masks (at most 4 gluons) by
+// table: nibble x of kPdep4[m] is x's bits deposited at the set bits of m
+// (ascending), nibble x of kPext4[m] is the bits of x at the set bits of m,
+// packed.  One constant load, a shift and a mask replace a loop over the bits.
+constexpr uint64_t nibble_table(unsigned m, bool deposit) {
+  uint64_t t = 0;
+  for (unsigned x = 0; x < 16; ++x) {
+    unsigned r = 0, j = 0;
+    for (unsigned g = 0; g < 4; ++g)
+      if ((m >> g) & 1u) {
+        if (deposit) r |= ((x >> j) & 1u) << g;
+        else r |= ((x >> g) & 1u) << j;
+        ++j;
+      }
+    t |= uint64_t(r) << (4 * x);
+  }
+  return t;
+}
+static __constant__ uint64_t kPdep4[16] = {
+    nibble_table(0, true),  nibble_table(1, true),  nibble_table(2, true),  nibble_table(3, true),
+    nibble_table(4, true),  nibble_table(5, true),  nibble_table(6, true),  nibble_table(7, true),
+    nibble_table(8, true),  nibble_table(9, true),  nibble_table(10, true), nibble_table(11, true),
+    nibble_table(12, true), nibble_table(13, true), nibble_table(14, true), nibble_table(15, true)};
+static __constant__ uint64_t kPext4[16] = {
+    nibble_table(0, false),  nibble_table(1, false),  nibble_table(2, false),  nibble_table(3, false),
+    nibble_table(4, false),  nibble_table(5, false),  nibble_table(6, false),  nibble_table(7, false),
+    nibble_table(8, false),  nibble_table(9, false),  nibble_table(10, false), nibble_table(11, false),
+    nibble_table(12, false), nibble_table(13, false), nibble_table(14, false), nibble_table(15, false)};
+
 template <int NG>
 __device__ __forceinline__ unsigned pdep_mask(unsigned c, unsigned mask) {
-  unsigned H = 0;
-  int j = 0;
-#pragma unroll
-  for (int g = 0; g < NG; ++g)
-    if (mask >> g & 1u) { H |= ((c >> j) & 1u) << g; ++j; }
-  return H;
+  static_assert(NG <= 4, "helicity tables cover at most 4 gluons");
+  return unsigned(kPdep4[mask] >> (4 * c)) & 15u;
 }
 
 template <int NG>
 __device__ __forceinline__ unsigned pext_mask(unsigned H, unsigned mask) {
-  unsigned c = 0;
-  int j = 0;
-#pragma unroll
-  for (int g = 0; g < NG; ++g)
-    if (mask >> g & 1u) { c |= ((H >> g) & 1u) << j; ++j; }
-  return c;
+  static_assert(NG <= 4, "helicity tables cover at most 4 gluons");
+  return unsigned(kPext4[mask] >> (4 * H)) & 15u;
 }
+
+// Per-event quantities that depend on a subset (mask) of the gluons but on no
+// helicity, computed once per event by the lane group and kept in shared
+// memory: ptab = -(q_tbar + K), qsum = K = sum of the gluon momenta in the
+// mask (incoming ones negated), ginv = 1/K^2 (masks of two or more gluons),
+// qf = -1/(P^2 - m^2 + i m Gamma) for P = q_tbar + K, the heavy-quark
+// propagator factor of the suffix with these gluons.
+template <int NG, typename T> struct MaskTab {
+  static constexpr int M = 1 << NG;
+  static constexpr size_t bytes = size_t(M) * (2 * sizeof(R4<T>) + sizeof(T) + sizeof(cplx<T>));
+  R4<T>* ptab;
+  R4<T>* qsum;
+  T* ginv;
+  cplx<T>* qf;
+  __device__ __forceinline__ explicit MaskTab(unsigned char* base)
+      : ptab(reinterpret_cast<R4<T>*>(base)),
+        qsum(reinterpret_cast<R4<T>*>(base + M * sizeof(R4<T>))),
+        ginv(reinterpret_cast<T*>(base + 2 * M * sizeof(R4<T>))),
+        qf(reinterpret_cast<cplx<T>*>(base + 2 * M * sizeof(R4<T>) + M * sizeof(T))) {}
+};
 
 // The sub-currents of one event are stored component-major, Gs[mu * NSTORE + pos]:
 // the lanes of a warp read 2^k consecutive positions of one block at a time,
@@ -83,18 +124,9 @@ __device__ __forceinline__ V4<T> load_block(const cplx<T>* Gs, uint8_t ref, unsi
   return g;
 }
 
-template <int NG, typename T>
-__device__ __forceinline__ R4<T> block_momentum(const R4<T>* q, unsigned mask) {
-  R4<T> P = {{T(0), T(0), T(0), T(0)}};
-#pragma unroll
-  for (int g = 0; g < NG; ++g)
-    if (mask >> g & 1u) P = P + q[g];
-  return P;
-}
-
 // one level (block length K) of the colour-ordered gluon currents
 template <int NG, int K, typename T>
-__device__ __forceinline__ void gluon_level(const R4<T>* q, cplx<T>* Gs, int gl) {
+__device__ __forceinline__ void gluon_level(const MaskTab<NG, T>& mt, cplx<T>* Gs, int gl) {
   constexpr int L = Lanes<NG>::L;
   constexpr int nblk = TTNG<NG>::FIRST[K + 1] - TTNG<NG>::FIRST[K];
   constexpr int items = nblk << K;
@@ -114,8 +146,8 @@ __device__ __forceinline__ void gluon_level(const R4<T>* q, cplx<T>* Gs, int gl)
     for (int s = 0; s < n3; ++s) {
       const uint8_t rl = t3[2 * s], rr = t3[2 * s + 1];
       const V4<T> GL = load_block<NG, T>(Gs, rl, H), GR = load_block<NG, T>(Gs, rr, H);
-      const R4<T> PL = block_momentum<NG, T>(q, blk_mask<NG>()[rl & 0x7f]);
-      const R4<T> PR = block_momentum<NG, T>(q, blk_mask<NG>()[rr & 0x7f]);
+      const R4<T> PL = mt.qsum[blk_mask<NG>()[rl & 0x7f]];
+      const R4<T> PR = mt.qsum[blk_mask<NG>()[rr & 0x7f]];
       o3_sub(GL, GR, PL, PR, acc);
     }
     if constexpr (K >= 3) {
@@ -128,8 +160,7 @@ __device__ __forceinline__ void gluon_level(const R4<T>* q, cplx<T>* Gs, int gl)
         o4_add(GL, GM, GR, acc);
       }
     }
-    const R4<T> P = block_momentum<NG, T>(q, mb);
-    const T inv = T(1) / mdot(P, P);
+    const T inv = mt.ginv[mb];
     V4<T> g;
 #pragma unroll
     for (int k = 0; k < 4; ++k) g.c[k] = inv * acc.c[k];
@@ -151,7 +182,7 @@ template <int NG, typename T> struct WarpMem {
   static constexpr int EPW = Lanes<NG>::EPW;
   static constexpr size_t gs_bytes = sizeof(V4<T>) * EPW * TTNG<NG>::NSTORE;   // EPW component-major stores
   static constexpr size_t pt_off = gs_bytes;
-  static constexpr size_t pt_bytes = sizeof(R4<T>) * EPW * (1 << NG);
+  static constexpr size_t pt_bytes = MaskTab<NG, T>::bytes * EPW;       // EPW mask tables
   static constexpr size_t j_off = (pt_off + pt_bytes + 15) & ~size_t(15);
   static constexpr size_t j_bytes = sizeof(T) * 2 * kJPlane<NG>;
   static constexpr size_t bytes = (j_off + j_bytes + 15) & ~size_t(15);
@@ -161,6 +192,7 @@ template <int NG, typename T> struct WarpMem {
 template <typename T> struct LaneCtx {
   const cplx<T>* Gs;    // this event's sub-currents (component-major)
   const R4<T>* Ptab;    // -(q_tbar + sum of the gluon momenta in mask), by mask
+  const cplx<T>* qf;    // heavy-quark propagator factor, by mask
   uint64_t pk;          // 4-bit compressed helicity index of this lane for every gluon mask
   S4<T> ub0, ub1;       // ubar(t) for top helicity -1, +1
   T m, mw;
@@ -193,7 +225,8 @@ __device__ __forceinline__ void quark_walk(int parent, S4<T> (&R)[NG], const Lan
 #pragma unroll
     for (int m = 1; m < LV; ++m)
       apply_acc(make_slash(lane_block<NG, T>(cx, PT::template blk<LV>(path, m))), R[LV - 1 - m], X);
-    R[LV] = quark_prop(cx.Ptab[PT::template mask<LV>(path)], cx.m, cx.mw, X);
+    const uint8_t msk = PT::template mask<LV>(path);
+    R[LV] = quark_prop_f(cx.Ptab[msk], cx.m, cx.qf[msk], X);
     if constexpr (LV < NG - 1) {
       quark_walk<NG, LV + 1, T>(path, R, cx);
     } else {
@@ -318,7 +351,7 @@ __device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* w
   constexpr int L = Lanes<NG>::L;
   constexpr int NP = TTNG<NG>::NPERM;
   cplx<T>* Gs = reinterpret_cast<cplx<T>*>(wm) + group * 4 * TTNG<NG>::NSTORE;
-  R4<T>* Ptab = reinterpret_cast<R4<T>*>(wm + WM::pt_off) + group * (1 << NG);
+  const MaskTab<NG, T> mtab(wm + WM::pt_off + group * MaskTab<NG, T>::bytes);
   T* Jw = reinterpret_cast<T*>(wm + WM::j_off);
   const int lane = threadIdx.x & 31;
   R4<T> q[NG];
@@ -332,13 +365,37 @@ __device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* w
   R4<T> qtb, pt;
 #pragma unroll
   for (int c = 0; c < 4; ++c) { qtb.v[c] = p[3][c]; pt.v[c] = p[2][c]; }
-  // suffix momenta by gluon mask, and the polarisation vectors (level 1)
+  // the mask table (one mask per lane), and the polarisation vectors (level 1)
   if (gl < (1 << NG)) {
-    R4<T> P = qtb;
+    R4<T> K = {{T(0), T(0), T(0), T(0)}};
 #pragma unroll
     for (int g = 0; g < NG; ++g)
-      if ((gl >> g) & 1) P = P + q[g];
-    Ptab[gl] = -P;
+      if ((gl >> g) & 1) K = K + q[g];
+    const R4<T> P = qtb + K;
+    mtab.qsum[gl] = K;
+    mtab.ptab[gl] = -P;
+    const T k2 = mdot(K, K);
+    T den = mdot(P, P) - mt * mt;
+    if constexpr (sizeof(value_of(T(0))) == sizeof(float)) {
+      // FP32, subsets of outgoing gluons only (the top propagator that can come
+      // near its pole, t -> t + soft or collinear g): with massless gluons and
+      // an on-shell antitop, P^2 - m^2 = 2 q_tbar.K + sum_{i<j} 2 q_i.q_j, a sum
+      // of non-negative terms, free of the cancellation of P^2 against m^2
+      // that costs ~E^2/|P^2 - m^2| ulps.  With an incoming gluon the terms
+      // have both signs and the direct form is kept.
+      if ((gl & 3) == 0) {
+        T pairs = T(0);
+#pragma unroll
+        for (int i = 2; i < NG; ++i)
+#pragma unroll
+          for (int j = i + 1; j < NG; ++j)
+            if (((gl >> i) & 1) && ((gl >> j) & 1)) pairs += T(2) * mdot(q[i], q[j]);
+        den = fma(T(2), mdot(qtb, K), pairs);
+      }
+    }
+    mtab.ginv[gl] = __popc(unsigned(gl)) >= 2 ? T(1) / k2 : T(0);
+    const T inv = T(-1) / fma(den, den, mw * mw);
+    mtab.qf[gl] = {den * inv, -mw * inv};     // -1/den = -conj(den)/|den|^2
   }
   for (int it = gl; it < 2 * NG; it += L) {
     const int g = it >> 1;
@@ -349,16 +406,17 @@ __device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* w
     gs_store<NG, T>(Gs, 2 * g + (it & 1), polarisation(k, (it & 1) ? 1 : -1, g >= 2));
   }
   __syncwarp();
-  gluon_level<NG, 2, T>(q, Gs, gl);
-  if constexpr (NG >= 3) { __syncwarp(); gluon_level<NG, 3, T>(q, Gs, gl); }
-  if constexpr (NG >= 4) { __syncwarp(); gluon_level<NG, 4, T>(q, Gs, gl); }
+  gluon_level<NG, 2, T>(mtab, Gs, gl);
+  if constexpr (NG >= 3) { __syncwarp(); gluon_level<NG, 3, T>(mtab, Gs, gl); }
+  if constexpr (NG >= 4) { __syncwarp(); gluon_level<NG, 4, T>(mtab, Gs, gl); }
   __syncwarp();
   // quark line of this lane
   const unsigned H = unsigned(gl) & ((1u << NG) - 1u);
   const int ltb = ((gl >> NG) & 1) ? 1 : -1;
   LaneCtx<T> cx;
   cx.Gs = Gs;
-  cx.Ptab = Ptab;
+  cx.Ptab = mtab.ptab;
+  cx.qf = mtab.qf;
   cx.pk = 0;
 #pragma unroll
   for (unsigned msk = 1; msk < (1u << NG); ++msk) cx.pk |= uint64_t(pext_mask<NG>(H, msk)) << (4 * msk);

@@ -9,7 +9,11 @@ per-primitive counts of ``csrc/mf_device.cuh``:
     complex multiply 6, complex FMA 8, real*complex FMA 4, complex add 2,
     Minkowski product complex.complex 30, real.complex 14, real.real 7,
     slash matrix 8, slash*spinor 56 (accumulating 64), spinor row.column 30,
-    quark propagator 95, three-gluon vertex 158, four-gluon vertex 188.
+    quark propagator with its precomputed factor 80, three-gluon vertex 158,
+    four-gluon vertex 188.
+
+Per event, the mask table (momentum sums, 1/K^2 and the propagator factors,
+which depend on no helicity) is built once per gluon subset.
 
 External wavefunctions (square roots, divisions) are counted as 30 each.
 """
@@ -21,23 +25,37 @@ CMUL, CFMA, RFMA, CADD = 6, 8, 4, 2
 MDOT_VV, MDOT_RV, MDOT_RR = CMUL + 3 * CFMA, 2 + 3 * RFMA, 7
 SLASH = 4 * CADD
 APPLY, APPLY_ACC = 4 * (CMUL + CFMA), 4 * 2 * CFMA
-QPROP = 4 * (CMUL + 2 * RFMA) + MDOT_RR + 2 + 3 + 1 + 2 + 4 * CMUL
+QPROP = 4 * (CMUL + 2 * RFMA) + 4 * CMUL
 ROWDOT = CMUL + 3 * CFMA
 O3 = 20 + MDOT_VV + 2 * MDOT_RV + 4 * (RFMA + 2 * CFMA)
 O4 = 3 * MDOT_VV + 2 + 4 * 3 * CFMA
 EXT = 30
 
 
+def mask_table_flops(ng):
+    """Per-event mask table: for every subset of the gluons the momentum sum,
+    P = q_tbar + K, K^2, the propagator denominator (for subsets of outgoing
+    gluons also its pair-product form, FP32) and its factor."""
+    total = 0
+    for m in range(1 << ng):
+        k = bin(m).count("1")
+        total += 4 * k + 4 + MDOT_RR + (MDOT_RR + 1) + 1 + (2 + 1) + 3
+        if m & 3 == 0 and m:
+            pairs = k * (k - 1) // 2
+            total += pairs * (MDOT_RR + 2) + (MDOT_RR + 2)
+    return total
+
+
 def gluon_current_flops(ng):
     """Shared-memory gluon sub-currents of one event (all helicities)."""
     bl, ids, off, nstore, first, o3, o4 = tables(ng)
-    total = 2 * ng * EXT
+    total = 2 * ng * EXT + mask_table_flops(ng)
     for k in range(2, ng + 1):
         nblk = first[k + 1] - first[k]
         items = nblk << k
         n3, n4 = k - 1, (k - 1) * (k - 2) // 2
-        # each split also sums the momenta of its two sub-blocks (4 adds per gluon)
-        per = n3 * (O3 + 4 * k) + n4 * O4 + 4 * k + MDOT_RR + 1 + 8
+        # vertices, then the scaling by the tabulated 1/K^2
+        per = n3 * O3 + n4 * O4 + 8
         total += items * per
     return total
 
