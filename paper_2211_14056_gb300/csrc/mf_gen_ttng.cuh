@@ -6,8 +6,8 @@
 #include "mf_device.cuh"
 namespace mf {
 template <int NG> struct TTNG;
-template <int NG, int K> __device__ __forceinline__ const uint8_t* o3_table();
-template <int NG, int K> __device__ __forceinline__ const uint8_t* o4_table();
+template <int NG, int K> __device__ __forceinline__ const uint16_t* o3_table();
+template <int NG, int K> __device__ __forceinline__ const uint16_t* o4_table();
 template <int NG> __device__ __forceinline__ const uint8_t* blk_mask();
 template <int NG> __device__ __forceinline__ const uint16_t* blk_off();
 template <int NG> struct Paths;
@@ -33,20 +33,20 @@ static __constant__ uint8_t kBlkMask2[3] = {1, 2, 3};
 static __constant__ uint16_t kBlkOff2[3] = {0, 2, 4};
 template <> __device__ __forceinline__ const uint8_t* blk_mask<2>() { return kBlkMask2; }
 template <> __device__ __forceinline__ const uint16_t* blk_off<2>() { return kBlkOff2; }
-static __constant__ uint8_t kO3_2_2[2] = {0, 1};
-template <> __device__ __forceinline__ const uint8_t* o3_table<2, 2>() { return kO3_2_2; }
+static __constant__ uint16_t kO3_2_2[2] = {512, 1026};
+template <> __device__ __forceinline__ const uint16_t* o3_table<2, 2>() { return kO3_2_2; }
 static __constant__ uint8_t kPathMask2_1[2] = {1, 2};
-static __constant__ uint8_t kPathBlk2_1[2] = {0, 1};
+static __constant__ uint16_t kPathBlk2_1[2] = {512, 1026};
 static __constant__ uint8_t kPathFirst2_1[1] = {0};
 static __constant__ uint8_t kFinalSigma2[2] = {1, 0};
-static __constant__ uint8_t kFinalBlk2[4] = {1, 130, 0, 2};
+static __constant__ uint16_t kFinalBlk2[4] = {1026, 9732, 512, 1540};
 template <> struct Paths<2> {
   static __device__ __forceinline__ const uint8_t* mask_1() { return kPathMask2_1; }
   template <int LV> static __device__ __forceinline__ uint8_t mask(int p) {
     if constexpr (LV == 1) return kPathMask2_1[p];
     return 0;
   }
-  template <int LV> static __device__ __forceinline__ uint8_t blk(int p, int m) {
+  template <int LV> static __device__ __forceinline__ uint16_t blk(int p, int m) {
     if constexpr (LV == 1) return kPathBlk2_1[p * 1 + m];
     return 0;
   }
@@ -55,7 +55,7 @@ template <> struct Paths<2> {
     return 0;
   }
   static __device__ __forceinline__ uint8_t final_sigma(int p) { return kFinalSigma2[p]; }
-  static __device__ __forceinline__ uint8_t final_blk(int p, int m) { return kFinalBlk2[p * 2 + m]; }
+  static __device__ __forceinline__ uint16_t final_blk(int p, int m) { return kFinalBlk2[p * 2 + m]; }
 };
 // J^dagger (D C) J of one helicity over the 2 colour orderings (D = 3).
 template <typename T>
@@ -87,20 +87,20 @@ static __constant__ uint8_t kBlkMask3[9] = {1, 2, 4, 3, 5, 6, 7, 7, 7};
 static __constant__ uint16_t kBlkOff3[9] = {0, 2, 4, 6, 10, 14, 18, 26, 34};
 template <> __device__ __forceinline__ const uint8_t* blk_mask<3>() { return kBlkMask3; }
 template <> __device__ __forceinline__ const uint16_t* blk_off<3>() { return kBlkOff3; }
-static __constant__ uint8_t kO3_3_2[6] = {0, 1, 0, 2, 1, 2};
-template <> __device__ __forceinline__ const uint8_t* o3_table<3, 2>() { return kO3_3_2; }
-static __constant__ uint8_t kO3_3_3[12] = {0, 5, 3, 2, 0, 133, 4, 1, 1, 4, 131, 2};
-template <> __device__ __forceinline__ const uint8_t* o3_table<3, 3>() { return kO3_3_3; }
-static __constant__ uint8_t kO4_3_3[9] = {0, 1, 2, 0, 2, 1, 1, 0, 2};
-template <> __device__ __forceinline__ const uint8_t* o4_table<3, 3>() { return kO4_3_3; }
+static __constant__ uint16_t kO3_3_2[6] = {512, 1026, 512, 2052, 1026, 2052};
+template <> __device__ __forceinline__ const uint16_t* o3_table<3, 2>() { return kO3_3_2; }
+static __constant__ uint16_t kO3_3_3[12] = {512, 3086, 1542, 2052, 512, 11278, 2570, 1026, 1026, 2570, 9734, 2052};
+template <> __device__ __forceinline__ const uint16_t* o3_table<3, 3>() { return kO3_3_3; }
+static __constant__ uint16_t kO4_3_3[9] = {512, 1026, 2052, 512, 2052, 1026, 1026, 512, 2052};
+template <> __device__ __forceinline__ const uint16_t* o4_table<3, 3>() { return kO4_3_3; }
 static __constant__ uint8_t kPathMask3_1[3] = {1, 2, 4};
-static __constant__ uint8_t kPathBlk3_1[3] = {0, 1, 2};
+static __constant__ uint16_t kPathBlk3_1[3] = {512, 1026, 2052};
 static __constant__ uint8_t kPathFirst3_1[1] = {0};
 static __constant__ uint8_t kPathMask3_2[6] = {3, 5, 3, 6, 5, 6};
-static __constant__ uint8_t kPathBlk3_2[12] = {1, 131, 2, 132, 0, 3, 2, 133, 0, 4, 1, 5};
+static __constant__ uint16_t kPathBlk3_2[12] = {1026, 9734, 2052, 10762, 512, 1542, 2052, 11278, 512, 2570, 1026, 3086};
 static __constant__ uint8_t kPathFirst3_2[3] = {0, 2, 4};
 static __constant__ uint8_t kFinalSigma3[6] = {5, 3, 4, 1, 2, 0};
-static __constant__ uint8_t kFinalBlk3[18] = {2, 133, 6, 1, 5, 7, 2, 132, 8, 0, 4, 7, 1, 131, 8, 0, 3, 6};
+static __constant__ uint16_t kFinalBlk3[18] = {2052, 11278, 3602, 1026, 3086, 3610, 2052, 10762, 3618, 512, 2570, 3610, 1026, 9734, 3618, 512, 1542, 3602};
 template <> struct Paths<3> {
   static __device__ __forceinline__ const uint8_t* mask_1() { return kPathMask3_1; }
   static __device__ __forceinline__ const uint8_t* mask_2() { return kPathMask3_2; }
@@ -109,7 +109,7 @@ template <> struct Paths<3> {
     if constexpr (LV == 2) return kPathMask3_2[p];
     return 0;
   }
-  template <int LV> static __device__ __forceinline__ uint8_t blk(int p, int m) {
+  template <int LV> static __device__ __forceinline__ uint16_t blk(int p, int m) {
     if constexpr (LV == 1) return kPathBlk3_1[p * 1 + m];
     if constexpr (LV == 2) return kPathBlk3_2[p * 2 + m];
     return 0;
@@ -120,7 +120,7 @@ template <> struct Paths<3> {
     return 0;
   }
   static __device__ __forceinline__ uint8_t final_sigma(int p) { return kFinalSigma3[p]; }
-  static __device__ __forceinline__ uint8_t final_blk(int p, int m) { return kFinalBlk3[p * 3 + m]; }
+  static __device__ __forceinline__ uint16_t final_blk(int p, int m) { return kFinalBlk3[p * 3 + m]; }
 };
 // J^dagger (D C) J of one helicity over the 6 colour orderings (D = 9).
 template <typename T>
@@ -174,27 +174,27 @@ static __constant__ uint8_t kBlkMask4[34] = {1, 2, 4, 8, 3, 5, 9, 6, 10, 12, 7, 
 static __constant__ uint16_t kBlkOff4[34] = {0, 2, 4, 6, 8, 12, 16, 20, 24, 28, 32, 40, 48, 56, 64, 72, 80, 88, 96, 104, 112, 120, 128, 144, 160, 176, 192, 208, 224, 240, 256, 272, 288, 304};
 template <> __device__ __forceinline__ const uint8_t* blk_mask<4>() { return kBlkMask4; }
 template <> __device__ __forceinline__ const uint16_t* blk_off<4>() { return kBlkOff4; }
-static __constant__ uint8_t kO3_4_2[12] = {0, 1, 0, 2, 0, 3, 1, 2, 1, 3, 2, 3};
-template <> __device__ __forceinline__ const uint8_t* o3_table<4, 2>() { return kO3_4_2; }
-static __constant__ uint8_t kO3_4_3[48] = {0, 7, 4, 2, 0, 8, 4, 3, 0, 135, 5, 1, 0, 9, 5, 3, 0, 136, 6, 1, 0, 137, 6, 2, 1, 5, 132, 2, 1, 6, 132, 3, 1, 9, 7, 3, 1, 137, 8, 2, 2, 6, 133, 3, 2, 8, 135, 3};
-template <> __device__ __forceinline__ const uint8_t* o3_table<4, 3>() { return kO3_4_3; }
-static __constant__ uint8_t kO4_4_3[36] = {0, 1, 2, 0, 1, 3, 0, 2, 1, 0, 2, 3, 0, 3, 1, 0, 3, 2, 1, 0, 2, 1, 0, 3, 1, 2, 3, 1, 3, 2, 2, 0, 3, 2, 1, 3};
-template <> __device__ __forceinline__ const uint8_t* o4_table<4, 3>() { return kO4_4_3; }
-static __constant__ uint8_t kO3_4_4[72] = {0, 18, 4, 9, 10, 3, 0, 19, 4, 137, 11, 2, 0, 21, 5, 8, 12, 3, 0, 19, 5, 136, 13, 1, 0, 21, 6, 7, 14, 2, 0, 18, 6, 135, 15, 1, 1, 13, 132, 9, 16, 3, 1, 15, 132, 137, 17, 2, 1, 20, 7, 6, 12, 3, 1, 20, 8, 5, 14, 2, 2, 11, 133, 8, 16, 3, 2, 17, 135, 6, 10, 3};
-template <> __device__ __forceinline__ const uint8_t* o3_table<4, 4>() { return kO3_4_4; }
-static __constant__ uint8_t kO4_4_4[108] = {0, 1, 9, 0, 7, 3, 4, 2, 3, 0, 1, 137, 0, 8, 2, 4, 3, 2, 0, 2, 8, 0, 135, 3, 5, 1, 3, 0, 2, 136, 0, 9, 1, 5, 3, 1, 0, 3, 7, 0, 136, 2, 6, 1, 2, 0, 3, 135, 0, 137, 1, 6, 2, 1, 1, 0, 9, 1, 5, 3, 132, 2, 3, 1, 0, 137, 1, 6, 2, 132, 3, 2, 1, 2, 6, 1, 133, 3, 7, 0, 3, 1, 3, 5, 1, 134, 2, 8, 0, 2, 2, 0, 8, 2, 4, 3, 133, 1, 3, 2, 1, 6, 2, 132, 3, 135, 0, 3};
-template <> __device__ __forceinline__ const uint8_t* o4_table<4, 4>() { return kO4_4_4; }
+static __constant__ uint16_t kO3_4_2[12] = {512, 1026, 512, 2052, 512, 4102, 1026, 2052, 1026, 4102, 2052, 4102};
+template <> __device__ __forceinline__ const uint16_t* o3_table<4, 2>() { return kO3_4_2; }
+static __constant__ uint16_t kO3_4_3[48] = {512, 3092, 1544, 2052, 512, 5144, 1544, 4102, 512, 11284, 2572, 1026, 512, 6172, 2572, 4102, 512, 13336, 4624, 1026, 512, 14364, 4624, 2052, 1026, 2572, 9736, 2052, 1026, 4624, 9736, 4102, 1026, 6172, 3092, 4102, 1026, 14364, 5144, 2052, 2052, 4624, 10764, 4102, 2052, 5144, 11284, 4102};
+template <> __device__ __forceinline__ const uint16_t* o3_table<4, 3>() { return kO3_4_3; }
+static __constant__ uint16_t kO4_4_3[36] = {512, 1026, 2052, 512, 1026, 4102, 512, 2052, 1026, 512, 2052, 4102, 512, 4102, 1026, 512, 4102, 2052, 1026, 512, 2052, 1026, 512, 4102, 1026, 2052, 4102, 1026, 4102, 2052, 2052, 512, 4102, 2052, 1026, 4102};
+template <> __device__ __forceinline__ const uint16_t* o4_table<4, 3>() { return kO4_4_3; }
+static __constant__ uint16_t kO3_4_4[72] = {512, 7264, 1544, 6172, 3616, 4102, 512, 7272, 1544, 14364, 5672, 2052, 512, 7288, 2572, 5144, 3632, 4102, 512, 7272, 2572, 13336, 6712, 1026, 512, 7288, 4624, 3092, 5696, 2052, 512, 7264, 4624, 11284, 6728, 1026, 1026, 6712, 9736, 6172, 3664, 4102, 1026, 6728, 9736, 14364, 5720, 2052, 1026, 6768, 3092, 4624, 3632, 4102, 1026, 6768, 5144, 2572, 5696, 2052, 2052, 5672, 10764, 5144, 3664, 4102, 2052, 5720, 11284, 4624, 3616, 4102};
+template <> __device__ __forceinline__ const uint16_t* o3_table<4, 4>() { return kO3_4_4; }
+static __constant__ uint16_t kO4_4_4[108] = {512, 1026, 6172, 512, 3092, 4102, 1544, 2052, 4102, 512, 1026, 14364, 512, 5144, 2052, 1544, 4102, 2052, 512, 2052, 5144, 512, 11284, 4102, 2572, 1026, 4102, 512, 2052, 13336, 512, 6172, 1026, 2572, 4102, 1026, 512, 4102, 3092, 512, 13336, 2052, 4624, 1026, 2052, 512, 4102, 11284, 512, 14364, 1026, 4624, 2052, 1026, 1026, 512, 6172, 1026, 2572, 4102, 9736, 2052, 4102, 1026, 512, 14364, 1026, 4624, 2052, 9736, 4102, 2052, 1026, 2052, 4624, 1026, 10764, 4102, 3092, 512, 4102, 1026, 4102, 2572, 1026, 12816, 2052, 5144, 512, 2052, 2052, 512, 5144, 2052, 1544, 4102, 10764, 1026, 4102, 2052, 1026, 4624, 2052, 9736, 4102, 11284, 512, 4102};
+template <> __device__ __forceinline__ const uint16_t* o4_table<4, 4>() { return kO4_4_4; }
 static __constant__ uint8_t kPathMask4_1[4] = {1, 2, 4, 8};
-static __constant__ uint8_t kPathBlk4_1[4] = {0, 1, 2, 3};
+static __constant__ uint16_t kPathBlk4_1[4] = {512, 1026, 2052, 4102};
 static __constant__ uint8_t kPathFirst4_1[1] = {0};
 static __constant__ uint8_t kPathMask4_2[12] = {3, 5, 9, 3, 6, 10, 5, 6, 12, 9, 10, 12};
-static __constant__ uint8_t kPathBlk4_2[24] = {1, 132, 2, 133, 3, 134, 0, 4, 2, 135, 3, 136, 0, 5, 1, 7, 3, 137, 0, 6, 1, 8, 2, 9};
+static __constant__ uint16_t kPathBlk4_2[24] = {1026, 9736, 2052, 10764, 4102, 12816, 512, 1544, 2052, 11284, 4102, 13336, 512, 2572, 1026, 3092, 4102, 14364, 512, 4624, 1026, 5144, 2052, 6172};
 static __constant__ uint8_t kPathFirst4_2[4] = {0, 3, 6, 9};
 static __constant__ uint8_t kPathMask4_3[24] = {7, 11, 7, 13, 11, 13, 7, 11, 7, 14, 11, 14, 7, 13, 7, 14, 13, 14, 11, 13, 11, 14, 13, 14};
-static __constant__ uint8_t kPathBlk4_3[72] = {2, 135, 10, 3, 136, 11, 1, 7, 12, 3, 137, 13, 1, 8, 14, 2, 9, 15, 2, 133, 16, 3, 134, 17, 0, 5, 12, 3, 137, 18, 0, 6, 14, 2, 9, 19, 1, 132, 16, 3, 134, 20, 0, 4, 10, 3, 136, 21, 0, 6, 15, 1, 8, 19, 1, 132, 17, 2, 133, 20, 0, 4, 11, 2, 135, 21, 0, 5, 13, 1, 7, 18};
+static __constant__ uint16_t kPathBlk4_3[72] = {2052, 11284, 3616, 4102, 13336, 5672, 1026, 3092, 3632, 4102, 14364, 6712, 1026, 5144, 5696, 2052, 6172, 6728, 2052, 10764, 3664, 4102, 12816, 5720, 512, 2572, 3632, 4102, 14364, 7264, 512, 4624, 5696, 2052, 6172, 7272, 1026, 9736, 3664, 4102, 12816, 6768, 512, 1544, 3616, 4102, 13336, 7288, 512, 4624, 6728, 1026, 5144, 7272, 1026, 9736, 5720, 2052, 10764, 6768, 512, 1544, 5672, 2052, 11284, 7288, 512, 2572, 6712, 1026, 3092, 7264};
 static __constant__ uint8_t kPathFirst4_3[12] = {0, 2, 4, 6, 8, 10, 12, 14, 16, 18, 20, 22};
 static __constant__ uint8_t kFinalSigma4[24] = {23, 17, 21, 11, 15, 9, 22, 16, 19, 5, 13, 3, 20, 10, 18, 4, 7, 1, 14, 8, 12, 2, 6, 0};
-static __constant__ uint8_t kFinalBlk4[96] = {3, 137, 18, 150, 2, 9, 19, 151, 3, 136, 21, 152, 1, 8, 19, 153, 2, 135, 21, 154, 1, 7, 18, 155, 3, 137, 13, 156, 2, 9, 15, 157, 3, 134, 20, 158, 0, 6, 15, 27, 2, 133, 20, 159, 0, 5, 13, 25, 3, 136, 11, 160, 1, 8, 14, 31, 3, 134, 17, 161, 0, 6, 14, 26, 1, 132, 17, 29, 0, 4, 11, 23, 2, 135, 10, 33, 1, 7, 12, 30, 2, 133, 16, 32, 0, 5, 12, 24, 1, 132, 16, 28, 0, 4, 10, 22};
+static __constant__ uint16_t kFinalBlk4[96] = {4102, 14364, 7264, 16000, 2052, 6172, 7272, 16016, 4102, 13336, 7288, 16032, 1026, 5144, 7272, 16048, 2052, 11284, 7288, 16064, 1026, 3092, 7264, 16080, 4102, 14364, 6712, 16096, 2052, 6172, 6728, 16112, 4102, 12816, 6768, 16128, 512, 4624, 6728, 7888, 2052, 10764, 6768, 16144, 512, 2572, 6712, 7856, 4102, 13336, 5672, 16160, 1026, 5144, 5696, 7952, 4102, 12816, 5720, 16176, 512, 4624, 5696, 7872, 1026, 9736, 5720, 7920, 512, 1544, 5672, 7824, 2052, 11284, 3616, 7984, 1026, 3092, 3632, 7936, 2052, 10764, 3664, 7968, 512, 2572, 3632, 7840, 1026, 9736, 3664, 7904, 512, 1544, 3616, 7808};
 template <> struct Paths<4> {
   static __device__ __forceinline__ const uint8_t* mask_1() { return kPathMask4_1; }
   static __device__ __forceinline__ const uint8_t* mask_2() { return kPathMask4_2; }
@@ -205,7 +205,7 @@ template <> struct Paths<4> {
     if constexpr (LV == 3) return kPathMask4_3[p];
     return 0;
   }
-  template <int LV> static __device__ __forceinline__ uint8_t blk(int p, int m) {
+  template <int LV> static __device__ __forceinline__ uint16_t blk(int p, int m) {
     if constexpr (LV == 1) return kPathBlk4_1[p * 1 + m];
     if constexpr (LV == 2) return kPathBlk4_2[p * 2 + m];
     if constexpr (LV == 3) return kPathBlk4_3[p * 3 + m];
@@ -218,7 +218,7 @@ template <> struct Paths<4> {
     return 0;
   }
   static __device__ __forceinline__ uint8_t final_sigma(int p) { return kFinalSigma4[p]; }
-  static __device__ __forceinline__ uint8_t final_blk(int p, int m) { return kFinalBlk4[p * 4 + m]; }
+  static __device__ __forceinline__ uint16_t final_blk(int p, int m) { return kFinalBlk4[p * 4 + m]; }
 };
 // J^dagger (D C) J of one helicity over the 24 colour orderings (D = 54).
 template <typename T>

@@ -116,11 +116,16 @@ __device__ __forceinline__ void gs_store(cplx<T>* Gs, int pos, const V4<T>& g) {
   for (int k = 0; k < 4; ++k) Gs[k * TTNG<NG>::NSTORE + pos] = g.c[k];
 }
 
+// Block references (generated tables): shared-memory offset of the block's
+// stored currents in bits 0-8, gluon mask in bits 9-12, reversal sign in bit 13.
+__device__ __forceinline__ int ref_off(uint16_t ref) { return ref & 511; }
+__device__ __forceinline__ unsigned ref_mask(uint16_t ref) { return (ref >> 9) & 15u; }
+__device__ __forceinline__ bool ref_neg(uint16_t ref) { return (ref >> 13) & 1u; }
+
 template <int NG, typename T>
-__device__ __forceinline__ V4<T> load_block(const cplx<T>* Gs, uint8_t ref, unsigned H) {
-  const int id = ref & 0x7f;
-  V4<T> g = gs_load<NG, T>(Gs, blk_off<NG>()[id] + pext_mask<NG>(H, blk_mask<NG>()[id]));
-  if (ref & 0x80) g = neg(g);
+__device__ __forceinline__ V4<T> load_block(const cplx<T>* Gs, uint16_t ref, unsigned H) {
+  V4<T> g = gs_load<NG, T>(Gs, ref_off(ref) + pext_mask<NG>(H, ref_mask(ref)));
+  if (ref_neg(ref)) g = neg(g);
   return g;
 }
 
@@ -141,17 +146,17 @@ __device__ __forceinline__ void gluon_level(const MaskTab<NG, T>& mt, cplx<T>* G
     V4<T> acc;
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc.c[k] = {T(0), T(0)};
-    const uint8_t* t3 = o3_table<NG, K>() + bl * n3 * 2;
+    const uint16_t* t3 = o3_table<NG, K>() + bl * n3 * 2;
 #pragma unroll 1
     for (int s = 0; s < n3; ++s) {
-      const uint8_t rl = t3[2 * s], rr = t3[2 * s + 1];
+      const uint16_t rl = t3[2 * s], rr = t3[2 * s + 1];
       const V4<T> GL = load_block<NG, T>(Gs, rl, H), GR = load_block<NG, T>(Gs, rr, H);
-      const R4<T> PL = mt.qsum[blk_mask<NG>()[rl & 0x7f]];
-      const R4<T> PR = mt.qsum[blk_mask<NG>()[rr & 0x7f]];
+      const R4<T> PL = mt.qsum[ref_mask(rl)];
+      const R4<T> PR = mt.qsum[ref_mask(rr)];
       o3_sub(GL, GR, PL, PR, acc);
     }
     if constexpr (K >= 3) {
-      const uint8_t* t4 = o4_table<NG, K>() + bl * n4 * 3;
+      const uint16_t* t4 = o4_table<NG, K>() + bl * n4 * 3;
 #pragma unroll 1
       for (int s = 0; s < n4; ++s) {
         const V4<T> GL = load_block<NG, T>(Gs, t4[3 * s], H);
@@ -200,11 +205,10 @@ template <typename T> struct LaneCtx {
 };
 
 template <int NG, typename T>
-__device__ __forceinline__ V4<T> lane_block(const LaneCtx<T>& cx, uint8_t ref) {
-  const int id = ref & 0x7f;
-  const unsigned idx = unsigned(cx.pk >> (4 * blk_mask<NG>()[id])) & 15u;
-  V4<T> g = gs_load<NG, T>(cx.Gs, blk_off<NG>()[id] + idx);
-  if (ref & 0x80) g = neg(g);
+__device__ __forceinline__ V4<T> lane_block(const LaneCtx<T>& cx, uint16_t ref) {
+  const unsigned idx = unsigned(cx.pk >> (4 * ref_mask(ref))) & 15u;
+  V4<T> g = gs_load<NG, T>(cx.Gs, ref_off(ref) + idx);
+  if (ref_neg(ref)) g = neg(g);
   return g;
 }
 

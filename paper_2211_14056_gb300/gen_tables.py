@@ -124,8 +124,11 @@ def tables(n):
 
 # ---------------------------------------------------------------------------
 # emission
-def _pack(i, s):
-    return i | (0x80 if s < 0 else 0)
+def _pack(i, s, bl, off):
+    """16-bit block reference: shared-memory offset of the block's stored
+    currents (bits 0-8), its gluon mask (bits 9-12), reversal sign (bit 13)."""
+    assert off[i] + (1 << len(bl[i])) <= 512
+    return off[i] | (mask(bl[i]) << 9) | ((1 << 13) if s < 0 else 0)
 
 
 def emit_tables(n, lines):
@@ -145,16 +148,16 @@ def emit_tables(n, lines):
         flat3 = []
         for row in o3[k]:
             for (a, sa, b, sb) in row:
-                flat3 += [_pack(a, sa), _pack(b, sb)]
-        lines.append(f"static __constant__ uint8_t kO3_{n}_{k}[{len(flat3)}] = {{{', '.join(map(str, flat3))}}};")
-        lines.append(f"template <> __device__ __forceinline__ const uint8_t* o3_table<{n}, {k}>() {{ return kO3_{n}_{k}; }}")
+                flat3 += [_pack(a, sa, bl, off), _pack(b, sb, bl, off)]
+        lines.append(f"static __constant__ uint16_t kO3_{n}_{k}[{len(flat3)}] = {{{', '.join(map(str, flat3))}}};")
+        lines.append(f"template <> __device__ __forceinline__ const uint16_t* o3_table<{n}, {k}>() {{ return kO3_{n}_{k}; }}")
         if k >= 3:
             flat4 = []
             for row in o4[k]:
                 for (a, sa, b, sb, c, sc) in row:
-                    flat4 += [_pack(a, sa), _pack(b, sb), _pack(c, sc)]
-            lines.append(f"static __constant__ uint8_t kO4_{n}_{k}[{len(flat4)}] = {{{', '.join(map(str, flat4))}}};")
-            lines.append(f"template <> __device__ __forceinline__ const uint8_t* o4_table<{n}, {k}>() {{ return kO4_{n}_{k}; }}")
+                    flat4 += [_pack(a, sa, bl, off), _pack(b, sb, bl, off), _pack(c, sc, bl, off)]
+            lines.append(f"static __constant__ uint16_t kO4_{n}_{k}[{len(flat4)}] = {{{', '.join(map(str, flat4))}}};")
+            lines.append(f"template <> __device__ __forceinline__ const uint16_t* o4_table<{n}, {k}>() {{ return kO4_{n}_{k}; }}")
 
 
 def lane_paths(n):
@@ -191,23 +194,24 @@ def lane_paths(n):
 def emit_lane(n, lines, colour):
     """Path tables of the quark line and the colour sum of one helicity lane."""
     levels, final = lane_paths(n)
+    bl, _, off, _, _, _, _ = tables(n)
     orders, M, D = colour
     P = len(orders)
     # per level: first child of every parent, suffix mask, block refs
     child0 = [0] * (n + 1)
     for l in range(1, n):
         rows_mask = [mask(S) for (S, _, _) in levels[l]]
-        refs = [_pack(i, sg) for (_, _, r) in levels[l] for (i, sg) in r]
+        refs = [_pack(i, sg, bl, off) for (_, _, r) in levels[l] for (i, sg) in r]
         firsts = []
         for pi in range(len(levels[l - 1])):
             firsts.append(next(k for k, e in enumerate(levels[l]) if e[1] == pi))
         lines.append(f"static __constant__ uint8_t kPathMask{n}_{l}[{len(rows_mask)}] = {{{', '.join(map(str, rows_mask))}}};")
-        lines.append(f"static __constant__ uint8_t kPathBlk{n}_{l}[{len(refs)}] = {{{', '.join(map(str, refs))}}};")
+        lines.append(f"static __constant__ uint16_t kPathBlk{n}_{l}[{len(refs)}] = {{{', '.join(map(str, refs))}}};")
         lines.append(f"static __constant__ uint8_t kPathFirst{n}_{l}[{len(firsts)}] = {{{', '.join(map(str, firsts))}}};")
     fsig = [o for (o, _) in final]
-    frefs = [_pack(i, sg) for (_, r) in final for (i, sg) in r]
+    frefs = [_pack(i, sg, bl, off) for (_, r) in final for (i, sg) in r]
     lines.append(f"static __constant__ uint8_t kFinalSigma{n}[{len(fsig)}] = {{{', '.join(map(str, fsig))}}};")
-    lines.append(f"static __constant__ uint8_t kFinalBlk{n}[{len(frefs)}] = {{{', '.join(map(str, frefs))}}};")
+    lines.append(f"static __constant__ uint16_t kFinalBlk{n}[{len(frefs)}] = {{{', '.join(map(str, frefs))}}};")
     lines.append(f"template <> struct Paths<{n}> {{")
     for l in range(1, n):
         lines.append(f"  static __device__ __forceinline__ const uint8_t* mask_{l}() {{ return kPathMask{n}_{l}; }}")
@@ -216,7 +220,7 @@ def emit_lane(n, lines, colour):
         lines.append(f"    if constexpr (LV == {l}) return kPathMask{n}_{l}[p];")
     lines.append("    return 0;")
     lines.append("  }")
-    lines.append("  template <int LV> static __device__ __forceinline__ uint8_t blk(int p, int m) {")
+    lines.append("  template <int LV> static __device__ __forceinline__ uint16_t blk(int p, int m) {")
     for l in range(1, n):
         lines.append(f"    if constexpr (LV == {l}) return kPathBlk{n}_{l}[p * {l} + m];")
     lines.append("    return 0;")
@@ -227,7 +231,7 @@ def emit_lane(n, lines, colour):
     lines.append("    return 0;")
     lines.append("  }")
     lines.append(f"  static __device__ __forceinline__ uint8_t final_sigma(int p) {{ return kFinalSigma{n}[p]; }}")
-    lines.append(f"  static __device__ __forceinline__ uint8_t final_blk(int p, int m) {{ return kFinalBlk{n}[p * {n} + m]; }}")
+    lines.append(f"  static __device__ __forceinline__ uint16_t final_blk(int p, int m) {{ return kFinalBlk{n}[p * {n} + m]; }}")
     lines.append("};")
     # colour sum of one helicity from J held in registers
     L = []
@@ -297,8 +301,8 @@ def render():
         "#include \"mf_device.cuh\"",
         "namespace mf {",
         "template <int NG> struct TTNG;",
-        "template <int NG, int K> __device__ __forceinline__ const uint8_t* o3_table();",
-        "template <int NG, int K> __device__ __forceinline__ const uint8_t* o4_table();",
+        "template <int NG, int K> __device__ __forceinline__ const uint16_t* o3_table();",
+        "template <int NG, int K> __device__ __forceinline__ const uint16_t* o4_table();",
         "template <int NG> __device__ __forceinline__ const uint8_t* blk_mask();",
         "template <int NG> __device__ __forceinline__ const uint16_t* blk_off();",
         "template <int NG> struct Paths;",
