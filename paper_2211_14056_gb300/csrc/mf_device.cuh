@@ -152,9 +152,9 @@ template <typename T> __device__ __forceinline__ cplx<T> rowdot(const S4<T>& row
 //   gluon propagator -i / P^2.
 // Together: G(B) = [ -sum O3 + sum O4 ] / P_B^2.
 template <typename T>
-__device__ __forceinline__ void o3_sub(const V4<T>& GL, const V4<T>& GR, const R4<T>& PL, const R4<T>& PR,
+__device__ __forceinline__ void o3_sub(const V4<T>& GL, const V4<T>& GR, const R4<T>& PL, const R4<T>& PR, T sg,
                                        V4<T>& acc) {
-  // O3 = (GL.GR)(PR - PL) - GR ((PL + 2 PR).GL) + GL ((2 PL + PR).GR); acc -= O3
+  // O3 = (GL.GR)(PR - PL) - GR ((PL + 2 PR).GL) + GL ((2 PL + PR).GR); acc -= sg O3
   R4<T> a, b, c;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -162,9 +162,9 @@ __device__ __forceinline__ void o3_sub(const V4<T>& GL, const V4<T>& GR, const R
     b.v[k] = fma(T(2), PR.v[k], PL.v[k]);
     c.v[k] = fma(T(2), PL.v[k], PR.v[k]);
   }
-  const cplx<T> s0 = mdot(GL, GR);
-  const cplx<T> s1 = mdot(b, GL);
-  const cplx<T> s2 = mdot(c, GR);
+  const cplx<T> s0 = sg * mdot(GL, GR);
+  const cplx<T> s1 = sg * mdot(b, GL);
+  const cplx<T> s2 = sg * mdot(c, GR);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     cplx<T> t = rfma(-a.v[k], s0, acc.c[k]);
@@ -174,9 +174,10 @@ __device__ __forceinline__ void o3_sub(const V4<T>& GL, const V4<T>& GR, const R
 }
 
 template <typename T>
-__device__ __forceinline__ void o4_add(const V4<T>& GL, const V4<T>& GM, const V4<T>& GR, V4<T>& acc) {
-  const cplx<T> lr = mdot(GL, GR), lm = mdot(GL, GM), mr = mdot(GM, GR);
-  const cplx<T> lr2 = {T(2) * lr.r, T(2) * lr.i};
+__device__ __forceinline__ void o4_add(const V4<T>& GL, const V4<T>& GM, const V4<T>& GR, T sg, V4<T>& acc) {
+  // acc += sg [2 (L.R) M - (L.M) R - (M.R) L]
+  const cplx<T> lr = mdot(GL, GR), lm = sg * mdot(GL, GM), mr = sg * mdot(GM, GR);
+  const cplx<T> lr2 = {T(2) * sg * lr.r, T(2) * sg * lr.i};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     cplx<T> t = cfma(lr2, GM.c[k], acc.c[k]);

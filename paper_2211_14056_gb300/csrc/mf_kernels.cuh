@@ -122,11 +122,10 @@ __device__ __forceinline__ int ref_off(uint16_t ref) { return ref & 511; }
 __device__ __forceinline__ unsigned ref_mask(uint16_t ref) { return (ref >> 9) & 15u; }
 __device__ __forceinline__ bool ref_neg(uint16_t ref) { return (ref >> 13) & 1u; }
 
+// stored currents of a block for helicities H, without the reversal sign
 template <int NG, typename T>
 __device__ __forceinline__ V4<T> load_block(const cplx<T>* Gs, uint16_t ref, unsigned H) {
-  V4<T> g = gs_load<NG, T>(Gs, ref_off(ref) + pext_mask<NG>(H, ref_mask(ref)));
-  if (ref_neg(ref)) g = neg(g);
-  return g;
+  return gs_load<NG, T>(Gs, ref_off(ref) + pext_mask<NG>(H, ref_mask(ref)));
 }
 
 // one level (block length K) of the colour-ordered gluon currents
@@ -153,16 +152,18 @@ __device__ __forceinline__ void gluon_level(const MaskTab<NG, T>& mt, cplx<T>* G
       const V4<T> GL = load_block<NG, T>(Gs, rl, H), GR = load_block<NG, T>(Gs, rr, H);
       const R4<T> PL = mt.qsum[ref_mask(rl)];
       const R4<T> PR = mt.qsum[ref_mask(rr)];
-      o3_sub(GL, GR, PL, PR, acc);
+      // the vertex is bilinear: the blocks' reversal signs multiply it
+      o3_sub(GL, GR, PL, PR, (ref_neg(rl) != ref_neg(rr)) ? T(-1) : T(1), acc);
     }
     if constexpr (K >= 3) {
       const uint16_t* t4 = o4_table<NG, K>() + bl * n4 * 3;
 #pragma unroll 1
       for (int s = 0; s < n4; ++s) {
-        const V4<T> GL = load_block<NG, T>(Gs, t4[3 * s], H);
-        const V4<T> GM = load_block<NG, T>(Gs, t4[3 * s + 1], H);
-        const V4<T> GR = load_block<NG, T>(Gs, t4[3 * s + 2], H);
-        o4_add(GL, GM, GR, acc);
+        const uint16_t r0 = t4[3 * s], r1 = t4[3 * s + 1], r2 = t4[3 * s + 2];
+        const V4<T> GL = load_block<NG, T>(Gs, r0, H);
+        const V4<T> GM = load_block<NG, T>(Gs, r1, H);
+        const V4<T> GR = load_block<NG, T>(Gs, r2, H);
+        o4_add(GL, GM, GR, (ref_neg(r0) ^ ref_neg(r1) ^ ref_neg(r2)) ? T(-1) : T(1), acc);
       }
     }
     const T inv = mt.ginv[mb];

@@ -9,8 +9,8 @@ per-primitive counts of ``csrc/mf_device.cuh``:
     complex multiply 6, complex FMA 8, real*complex FMA 4, complex add 2,
     Minkowski product complex.complex 30, real.complex 14, real.real 7,
     slash matrix 8, slash*spinor 56 (accumulating 64), spinor row.column 30,
-    quark propagator with its precomputed factor 80, three-gluon vertex 158,
-    four-gluon vertex 188.
+    quark propagator with its precomputed factor 80, three-gluon vertex 164,
+    four-gluon vertex 194 (both including the blocks' reversal sign).
 
 Per event, the mask table (momentum sums, 1/K^2 and the propagator factors,
 which depend on no helicity) is built once per gluon subset.
@@ -27,8 +27,8 @@ SLASH = 4 * CADD
 APPLY, APPLY_ACC = 4 * (CMUL + CFMA), 4 * 2 * CFMA
 QPROP = 4 * (CMUL + 2 * RFMA) + 4 * CMUL
 ROWDOT = CMUL + 3 * CFMA
-O3 = 20 + MDOT_VV + 2 * MDOT_RV + 4 * (RFMA + 2 * CFMA)
-O4 = 3 * MDOT_VV + 2 + 4 * 3 * CFMA
+O3 = 20 + MDOT_VV + 2 * MDOT_RV + 4 * (RFMA + 2 * CFMA) + 6
+O4 = 3 * MDOT_VV + 4 + 4 * 3 * CFMA + 4
 EXT = 30
 
 
