@@ -135,6 +135,13 @@ __device__ __forceinline__ S4<T> quark_prop_f(const R4<T>& P, T m, cplx<T> f, co
   return o;
 }
 
+template <typename T> __device__ __forceinline__ S4<T> neg(const S4<T>& a) {
+  S4<T> o;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.c[k] = -a.c[k];
+  return o;
+}
+
 template <typename T> __device__ __forceinline__ cplx<T> rowdot(const S4<T>& row, const S4<T>& col) {
   cplx<T> s = row.c[0] * col.c[0];
   s = cfma(row.c[1], col.c[1], s);

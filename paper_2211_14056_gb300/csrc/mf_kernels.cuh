@@ -191,7 +191,12 @@ template <int NG, typename T> struct WarpMem {
   static constexpr size_t pt_bytes = MaskTab<NG, T>::bytes * EPW;       // EPW mask tables
   static constexpr size_t j_off = (pt_off + pt_bytes + 15) & ~size_t(15);
   static constexpr size_t j_bytes = sizeof(T) * 2 * kJPlane<NG>;
-  static constexpr size_t bytes = (j_off + j_bytes + 15) & ~size_t(15);
+  // per event: the two-gluon suffix currents R(S), |S| = 2, for every ordered
+  // pair, helicity pair and antitop helicity (component-major, NR2 each)
+  static constexpr int NR2 = NG >= 3 ? NG * (NG - 1) * 8 : 0;
+  static constexpr size_t r2_off = (j_off + j_bytes + 15) & ~size_t(15);
+  static constexpr size_t r2_bytes = sizeof(cplx<T>) * 4 * NR2 * EPW;
+  static constexpr size_t bytes = (r2_off + r2_bytes + 15) & ~size_t(15);
 };
 
 // Per-lane context of the quark-line walk.
@@ -203,6 +208,8 @@ template <typename T> struct LaneCtx {
   S4<T> ub0, ub1;       // ubar(t) for top helicity -1, +1
   T m, mw;
   T* J;                 // &Jre[0][lane] of this warp (the imaginary plane follows at kJPlane)
+  const cplx<T>* R2;    // this event's two-gluon suffix currents (component-major)
+  unsigned ltb;         // antitop helicity bit of this lane
 };
 
 template <int NG, typename T>
@@ -226,12 +233,20 @@ __device__ __forceinline__ void quark_walk(int parent, S4<T> (&R)[NG], const Lan
 #pragma unroll 1
   for (int k = 0; k <= NG - LV; ++k) {
     const int path = first + k;
-    S4<T> X = apply(make_slash(lane_block<NG, T>(cx, PT::template blk<LV>(path, 0))), R[LV - 1]);
-#pragma unroll
-    for (int m = 1; m < LV; ++m)
-      apply_acc(make_slash(lane_block<NG, T>(cx, PT::template blk<LV>(path, m))), R[LV - 1 - m], X);
     const uint8_t msk = PT::template mask<LV>(path);
-    R[LV] = quark_prop_f(cx.Ptab[msk], cx.m, cx.qf[msk], X);
+    if constexpr (LV == 2) {
+      // computed once per event by the group (shared_suffixes)
+      constexpr int NR2 = WarpMem<NG, T>::NR2;
+      const int idx = path * 8 + int((unsigned(cx.pk >> (4 * msk)) & 15u) | (cx.ltb << 2));
+#pragma unroll
+      for (int c = 0; c < 4; ++c) R[2].c[c] = cx.R2[c * NR2 + idx];
+    } else {
+      S4<T> X = apply(make_slash(lane_block<NG, T>(cx, PT::template blk<LV>(path, 0))), R[LV - 1]);
+#pragma unroll
+      for (int m = 1; m < LV; ++m)
+        apply_acc(make_slash(lane_block<NG, T>(cx, PT::template blk<LV>(path, m))), R[LV - 1 - m], X);
+      R[LV] = quark_prop_f(cx.Ptab[msk], cx.m, cx.qf[msk], X);
+    }
     if constexpr (LV < NG - 1) {
       quark_walk<NG, LV + 1, T>(path, R, cx);
     } else {
@@ -246,6 +261,39 @@ __device__ __forceinline__ void quark_walk(int parent, S4<T> (&R)[NG], const Lan
       cx.J[(sig * 2 + 1) * kJStride] = j1.r;
       cx.J[(sig * 2 + 1) * kJStride + kJPlane<NG>] = j1.i;
     }
+  }
+}
+
+// The two-gluon suffix currents R(S) = -(P_S-slash + m)/(P_S^2 - m^2 + i m Gamma)
+// [G(S[:1])-slash R(S[1:]) + G(S)-slash v] depend on the helicities of two
+// gluons and of the antitop only, so every lane of the group would compute
+// each of them 2^(NG-2) times; the group computes each once (item = ordered
+// pair, two gluon helicities, antitop helicity) and the lanes' walks read
+// them.  Level-1 currents are recomputed per item.  Level-2 paths of one
+// level-1 parent p1 are p1 (NG - 1) .. p1 (NG - 1) + NG - 2 (generator order).
+template <int NG, typename T>
+__device__ __forceinline__ void shared_suffixes(const cplx<T>* Gs, const MaskTab<NG, T>& mtab, const R4<T>& qtb, T mt,
+                                                cplx<T>* R2, int gl) {
+  using PT = Paths<NG>;
+  constexpr int L = Lanes<NG>::L, NR2 = WarpMem<NG, T>::NR2;
+  for (int it = gl; it < NR2; it += L) {
+    const int p2 = it >> 3, sub = it & 7, p1 = p2 / (NG - 1);
+    const unsigned m1 = PT::template mask<1>(p1), m2 = PT::template mask<2>(p2);
+    const unsigned Hi = pdep_mask<NG>(unsigned(sub & 3), m2);
+    const S4<T> v = v_out(qtb, mt, (sub & 4) ? 1 : -1);
+    const uint16_t b1 = PT::template blk<1>(p1, 0), b20 = PT::template blk<2>(p2, 0), b21 = PT::template blk<2>(p2, 1);
+    const S4<T> X1 = apply(make_slash(load_block<NG, T>(Gs, b1, Hi)), v);
+    S4<T> R1 = quark_prop_f(mtab.ptab[m1], mt, mtab.qf[m1], X1);
+    if (ref_neg(b1)) R1 = neg(R1);
+    S4<T> X2 = apply(make_slash(load_block<NG, T>(Gs, b20, Hi)), R1);
+    if (ref_neg(b20)) X2 = neg(X2);
+    S4<T> Y = apply(make_slash(load_block<NG, T>(Gs, b21, Hi)), v);
+    if (ref_neg(b21)) Y = neg(Y);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) X2.c[c] = X2.c[c] + Y.c[c];
+    const S4<T> R = quark_prop_f(mtab.ptab[m2], mt, mtab.qf[m2], X2);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) R2[c * NR2 + it] = R.c[c];
   }
 }
 
@@ -358,6 +406,7 @@ __device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* w
   cplx<T>* Gs = reinterpret_cast<cplx<T>*>(wm) + group * 4 * TTNG<NG>::NSTORE;
   const MaskTab<NG, T> mtab(wm + WM::pt_off + group * MaskTab<NG, T>::bytes);
   T* Jw = reinterpret_cast<T*>(wm + WM::j_off);
+  cplx<T>* R2 = reinterpret_cast<cplx<T>*>(wm + WM::r2_off) + group * 4 * WM::NR2;
   const int lane = threadIdx.x & 31;
   R4<T> q[NG];
 #pragma unroll
@@ -415,6 +464,10 @@ __device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* w
   if constexpr (NG >= 3) { __syncwarp(); gluon_level<NG, 3, T>(mtab, Gs, gl); }
   if constexpr (NG >= 4) { __syncwarp(); gluon_level<NG, 4, T>(mtab, Gs, gl); }
   __syncwarp();
+  if constexpr (NG >= 3) {
+    shared_suffixes<NG, T>(Gs, mtab, qtb, mt, R2, gl);
+    __syncwarp();
+  }
   // quark line of this lane
   const unsigned H = unsigned(gl) & ((1u << NG) - 1u);
   const int ltb = ((gl >> NG) & 1) ? 1 : -1;
@@ -430,6 +483,8 @@ __device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* w
   cx.m = mt;
   cx.mw = mw;
   cx.J = Jw + lane;
+  cx.R2 = R2;
+  cx.ltb = unsigned((gl >> NG) & 1);
   S4<T> R[NG];
   R[0] = v_out(qtb, mt, ltb);
   quark_walk<NG, 1, T>(0, R, cx);

@@ -60,11 +60,23 @@ def gluon_current_flops(ng):
     return total
 
 
+def shared_suffix_flops(ng):
+    """Two-gluon suffix currents, computed once per event by the group: per
+    (ordered pair, two helicities, antitop helicity) the v spinor, the level-1
+    current and the level-2 current."""
+    if ng < 3:
+        return 0
+    items = ng * (ng - 1) * 8
+    return items * (EXT + (SLASH + APPLY + QPROP) + (2 * SLASH + 2 * APPLY + 8 + QPROP))
+
+
 def lane_flops(ng):
     """Quark line, amplitudes and colour sum of one helicity lane."""
     total = 3 * EXT
-    # suffix currents R(S)
+    # suffix currents R(S) (the two-gluon ones are shared, see above)
     for l in range(1, ng):
+        if l == 2 and ng >= 3:
+            continue
         count = math.factorial(ng) // math.factorial(ng - l)
         total += count * (APPLY + (l - 1) * APPLY_ACC + l * SLASH + 4 * l + QPROP)
     # colour-ordered amplitudes, both top helicities
@@ -84,7 +96,7 @@ def lane_flops(ng):
 def me2_flops_per_event(ng):
     """Real FP operations of one event's |M|^2 (gluon currents + every lane)."""
     lanes = 2 << ng
-    return gluon_current_flops(ng) + lanes * (lane_flops(ng) + int(math.log2(lanes)))
+    return gluon_current_flops(ng) + shared_suffix_flops(ng) + lanes * (lane_flops(ng) + int(math.log2(lanes)))
 
 
 if __name__ == "__main__":

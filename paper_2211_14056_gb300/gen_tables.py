@@ -205,6 +205,8 @@ def emit_lane(n, lines, colour):
         firsts = []
         for pi in range(len(levels[l - 1])):
             firsts.append(next(k for k, e in enumerate(levels[l]) if e[1] == pi))
+        # the kernel's shared two-gluon suffixes find a level-2 path's parent as p2 // (n - 1)
+        assert firsts == [pi * (n - l + 1) for pi in range(len(levels[l - 1]))]
         lines.append(f"static __constant__ uint8_t kPathMask{n}_{l}[{len(rows_mask)}] = {{{', '.join(map(str, rows_mask))}}};")
         lines.append(f"static __constant__ uint16_t kPathBlk{n}_{l}[{len(refs)}] = {{{', '.join(map(str, refs))}}};")
         lines.append(f"static __constant__ uint8_t kPathFirst{n}_{l}[{len(firsts)}] = {{{', '.join(map(str, firsts))}}};")
