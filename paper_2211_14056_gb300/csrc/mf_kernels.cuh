@@ -136,6 +136,7 @@ __device__ __forceinline__ void gluon_level(const MaskTab<NG, T>& mt, cplx<T>* G
   constexpr int items = nblk << K;
   constexpr int n3 = K - 1;
   constexpr int n4 = (K - 1) * (K - 2) / 2;
+#pragma unroll 2
   for (int it = gl; it < items; it += L) {
     const int bl = it >> K;
     const unsigned c = unsigned(it) & ((1u << K) - 1u);
@@ -146,7 +147,7 @@ __device__ __forceinline__ void gluon_level(const MaskTab<NG, T>& mt, cplx<T>* G
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc.c[k] = {T(0), T(0)};
     const uint16_t* t3 = o3_table<NG, K>() + bl * n3 * 2;
-#pragma unroll 1
+#pragma unroll
     for (int s = 0; s < n3; ++s) {
       const uint16_t rl = t3[2 * s], rr = t3[2 * s + 1];
       const V4<T> GL = load_block<NG, T>(Gs, rl, H), GR = load_block<NG, T>(Gs, rr, H);
@@ -157,7 +158,7 @@ __device__ __forceinline__ void gluon_level(const MaskTab<NG, T>& mt, cplx<T>* G
     }
     if constexpr (K >= 3) {
       const uint16_t* t4 = o4_table<NG, K>() + bl * n4 * 3;
-#pragma unroll 1
+#pragma unroll
       for (int s = 0; s < n4; ++s) {
         const uint16_t r0 = t4[3 * s], r1 = t4[3 * s + 1], r2 = t4[3 * s + 2];
         const V4<T> GL = load_block<NG, T>(Gs, r0, H);
@@ -230,7 +231,7 @@ template <int NG, int LV, typename T>
 __device__ __forceinline__ void quark_walk(int parent, S4<T> (&R)[NG], const LaneCtx<T>& cx) {
   using PT = Paths<NG>;
   const int first = PT::template first<LV>(parent);
-#pragma unroll 1
+#pragma unroll (LV == NG - 1 ? 2 : 1)
   for (int k = 0; k <= NG - LV; ++k) {
     const int path = first + k;
     const uint8_t msk = PT::template mask<LV>(path);
