@@ -25,125 +25,172 @@ struct GradArgs {
   MeParams mp;
   double width;               // Gamma_t
   const double* edges;
-  int64_t n;
+  int64_t first, n;           // events first .. first + n - 1 of this chunk
   uint64_t seed;
   int iter;
   TangentSeeds ts;
   int mt_slot, wt_slot;       // tangent slots of m_t and Gamma_t in the amplitude (-1: none)
+  int accumulate;             // add to the partial sums (later chunks)
   double* partials;           // [gridDim.x][1 + N]: sum w, sum dw/d(slot)
-  double* w_out;              // [n] or null: w * w_scale
+  double* w_out;              // [n_total] or null: w * w_scale (indexed by global event - first of call)
   double w_scale;
-  double* dw_out[kGradTangents];   // [n] each, or null
+  double* dw_out[kGradTangents];   // [n_total] each, or null
 };
 
-template <int NG, typename B> struct GradMem {
+// Dual per-event records of one chunk of C events (the derivative pass's
+// counterpart of RecordView): momenta and sqrt(s_hat) with their tangents in
+// the amplitude's type, the weight prefactor with its tangents in FP64, and
+// the list of events that passed.
+template <typename B> struct GradRec {
   using T = Dual<B, kGradTangents>;
-  static constexpr int kWarpsPerCta = sizeof(B) == sizeof(float) ? 2 : 1;
-  __host__ __device__ static size_t al(size_t x) { return (x + 15) & ~size_t(15); }
-  __host__ __device__ static size_t warps(int ndim, int nbins) { return al(sizeof(double) * ndim * (nbins + 1)); }
-  __host__ __device__ static size_t total(int ndim, int nbins) {
-    return warps(ndim, nbins) + WarpMem<NG, T>::bytes * kWarpsPerCta;
+  using DD = Dual<double, kGradTangents>;
+  T* mom;                     // [n_final * 4][C]
+  T* rs;                      // [C]
+  DD* pref;                   // [C]
+  int* list;                  // [C]
+  unsigned* count;            // [2]
+  int64_t C;
+  __host__ __device__ static size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+  __host__ __device__ static size_t bytes(int n_final, int64_t C) {
+    size_t o = al(sizeof(T) * (size_t(n_final) * 4 + 1) * C);
+    o = al(o + sizeof(DD) * C);
+    o = al(o + sizeof(int) * C);
+    return o + 2 * sizeof(unsigned);
+  }
+  __host__ __device__ static GradRec carve(void* base, int n_final, int64_t C) {
+    GradRec r;
+    unsigned char* p = static_cast<unsigned char*>(base);
+    r.C = C;
+    r.mom = reinterpret_cast<T*>(p);
+    r.rs = r.mom + size_t(n_final) * 4 * C;
+    size_t o = al(sizeof(T) * (size_t(n_final) * 4 + 1) * C);
+    r.pref = reinterpret_cast<DD*>(p + o);
+    o = al(o + sizeof(DD) * C);
+    r.list = reinterpret_cast<int*>(p + o);
+    o = al(o + sizeof(int) * C);
+    r.count = reinterpret_cast<unsigned*>(p + o);
+    return r;
   }
 };
 
-template <int NG, typename B>
-__global__ void __launch_bounds__(32 * GradMem<NG, B>::kWarpsPerCta) k_grad(GradArgs a) {
+// Dual sampling: one thread per event; events that fail the cuts get zero
+// outputs here, the others are listed for the amplitude kernel.
+template <typename B>
+__global__ void __launch_bounds__(kThreads) k_grad_sample(GradArgs a, GradRec<B> rec, int64_t out_off) {
   using T = Dual<B, kGradTangents>;
   using DD = Dual<double, kGradTangents>;
-  constexpr int W = GradMem<NG, B>::kWarpsPerCta;
-  constexpr int EPW = Lanes<NG>::EPW, L = Lanes<NG>::L, NEXT = Lanes<NG>::NEXT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* edges = reinterpret_cast<double*>(smem_raw);
-  const int ndim = a.sp.ndim, nbins = a.sp.nbins;
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int group = lane / L, gl = lane % L;
-  unsigned char* wm = smem_raw + GradMem<NG, B>::warps(ndim, nbins) + warp * WarpMem<NG, T>::bytes;
-  for (int i = t; i < ndim * (nbins + 1); i += blockDim.x) edges[i] = a.edges[i];
+  for (int i = threadIdx.x; i < a.sp.ndim * (a.sp.nbins + 1); i += blockDim.x) edges[i] = a.edges[i];
   __syncthreads();
-  // amplitude parameters with their tangents
+  const int nf = a.sp.n_final;
+  const int lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < a.n; base += stride) {
+    const int64_t e = base + threadIdx.x;
+    int pass = 0;
+    if (e < a.n) {
+      EventKin<T, DD> k;
+      sample_event<T, DD>(a.sp, edges, a.seed, a.iter, uint64_t(a.first + e), k, &a.ts);
+      for (int i = 0; i < nf; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) rec.mom[int64_t(i * 4 + c) * rec.C + e] = k.p[2 + i][c];
+      rec.rs[e] = k.p[0][0] + k.p[1][0];
+      rec.pref[e] = k.prefactor;
+      pass = k.pass;
+      if (!pass) {
+        const int64_t o = out_off + e;
+        if (a.w_out) a.w_out[o] = 0.0;
+        for (int s = 0; s < kGradTangents; ++s)
+          if (a.dw_out[s]) a.dw_out[s][o] = 0.0;
+      }
+    }
+    const unsigned bal = __ballot_sync(full, pass);
+    unsigned pos = 0;
+    if (lane == 0 && bal) pos = atomicAdd(&rec.count[0], unsigned(__popc(bal)));
+    pos = __shfl_sync(full, pos, 0);
+    if (pass) rec.list[pos + __popc(bal & ((1u << lane) - 1u))] = int(e);
+  }
+}
+
+// Dual |M|^2 of the listed events (one lane group per event, as in the plain
+// list-based kernel), the weight and its tangents, per-CTA sums.
+template <int NG, typename B>
+__global__ void __launch_bounds__(32) k_grad_me(GradArgs a, GradRec<B> rec, int64_t out_off) {
+  using T = Dual<B, kGradTangents>;
+  using DD = Dual<double, kGradTangents>;
+  constexpr int EPW = Lanes<NG>::EPW, L = Lanes<NG>::L, NEXT = Lanes<NG>::NEXT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* wm = smem_raw;
+  const int lane = threadIdx.x & 31, group = lane / L, gl = lane % L;
   T mt = T(B(a.mp.mt)), wt = T(B(a.width));
   if (a.mt_slot >= 0) mt.d[a.mt_slot] = B(1);
   if (a.wt_slot >= 0) wt.d[a.wt_slot] = B(1);
   const T mw = mt * wt;
   const unsigned full = 0xffffffffu;
+  const int64_t npass = rec.count[0];
   double s0 = 0.0, s1[kGradTangents] = {0.0, 0.0};
-  const int64_t stride = int64_t(gridDim.x) * W * 32;
-  for (int64_t base = (int64_t(blockIdx.x) * W + warp) * 32; base < a.n; base += stride) {
-    const int64_t e = base + lane;
-    const bool valid = e < a.n;
-    EventKin<T, DD> k;
-    k.pass = 0;
-    k.prefactor = DD(0.0);
-    if (valid) sample_event<T, DD>(a.sp, edges, a.seed, a.iter, uint64_t(e), k, &a.ts);
-    if (!valid) {
-      for (int i = 0; i < NEXT; ++i)
-        for (int c = 0; c < 4; ++c) k.p[i][c] = T(B(0));
-    }
-    DD me = DD(0.0);
-    unsigned todo = __ballot_sync(full, valid && k.pass);
-    while (todo) {
-      int src = -1;
-      unsigned rest = todo;
+  for (int64_t base = int64_t(blockIdx.x) * EPW; base < npass; base += int64_t(gridDim.x) * EPW) {
+    const int64_t k = base + group;
+    const bool ok = k < npass;
+    const int64_t e = rec.list[ok ? k : base];
+    T p[NEXT][4];
+    const T rs = rec.rs[e];
+    const T h = rs * B(0.5);
+    p[0][0] = h; p[0][1] = T(B(0)); p[0][2] = T(B(0)); p[0][3] = h;
+    p[1][0] = h; p[1][1] = T(B(0)); p[1][2] = T(B(0)); p[1][3] = -h;
 #pragma unroll
-      for (int g = 0; g < EPW; ++g) {
-        const int b = rest ? __ffs(rest) - 1 : -1;
-        if (g == group) src = b;
-        if (rest) rest &= rest - 1u;
-      }
-      const int from = src < 0 ? 0 : src;
-      T p[NEXT][4];
+    for (int i = 0; i < NG; ++i)
 #pragma unroll
-      for (int i = 0; i < NEXT; ++i)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) p[i][c] = shfl_any(full, k.p[i][c], from);
-      const T v = group_me2<NG, T>(p, wm, group, gl, mt, mw);
-#pragma unroll
-      for (int g = 0; g < EPW; ++g) {
-        const T vg = shfl_any(full, v, g * L);
-        const int sg = __shfl_sync(full, src, g * L);
-        if (sg == lane) me = DD(vg) * a.mp.norm;
-      }
-      todo = rest;
-    }
-    const DD w = valid ? me * k.prefactor : DD(0.0);
-    if (valid) {
-      if (a.w_out) a.w_out[e] = w.v * a.w_scale;
+      for (int c = 0; c < 4; ++c) p[2 + i][c] = rec.mom[int64_t(i * 4 + c) * rec.C + e];
+    const T v = group_me2<NG, T>(p, wm, group, gl, mt, mw);
+    if (ok && gl == 0) {
+      const DD w = DD(v) * a.mp.norm * rec.pref[e];
+      const int64_t o = out_off + e;
+      if (a.w_out) a.w_out[o] = w.v * a.w_scale;
       for (int s = 0; s < kGradTangents; ++s)
-        if (a.dw_out[s]) a.dw_out[s][e] = w.d[s];
+        if (a.dw_out[s]) a.dw_out[s][o] = w.d[s];
+      s0 += w.v;
+      for (int s = 0; s < kGradTangents; ++s) s1[s] += w.d[s];
     }
-    s0 += w.v;
-    for (int s = 0; s < kGradTangents; ++s) s1[s] += w.d[s];
   }
   for (int off = 16; off > 0; off >>= 1) {
     s0 += __shfl_xor_sync(full, s0, off);
     for (int s = 0; s < kGradTangents; ++s) s1[s] += __shfl_xor_sync(full, s1[s], off);
   }
-  __shared__ double acc[1 + kGradTangents];
-  if (t <= kGradTangents) acc[t] = 0.0;
-  __syncthreads();
-  if (lane == 0) {
-    atomicAdd(&acc[0], s0);
-    for (int s = 0; s < kGradTangents; ++s) atomicAdd(&acc[1 + s], s1[s]);
+  if (lane <= kGradTangents) {
+    const double v = lane == 0 ? s0 : s1[lane - 1];
+    double* dst = a.partials + int64_t(blockIdx.x) * (1 + kGradTangents) + lane;
+    *dst = (a.accumulate ? *dst : 0.0) + v;
   }
-  __syncthreads();
-  if (t <= kGradTangents) a.partials[int64_t(blockIdx.x) * (1 + kGradTangents) + t] = acc[t];
 }
 
 template <int NG, typename B>
-cudaError_t launch_grad(const GradArgs& a, int sms, int max_grid, int* grid_out, cudaStream_t s) {
-  const size_t sm = GradMem<NG, B>::total(a.sp.ndim, a.sp.nbins);
-  cudaError_t e = cudaFuncSetAttribute(k_grad<NG, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+cudaError_t grad_me_config(int* occ, size_t* smem) {
+  using T = Dual<B, kGradTangents>;
+  *smem = WarpMem<NG, T>::bytes;
+  cudaError_t e = cudaFuncSetAttribute(k_grad_me<NG, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(*smem));
   if (e != cudaSuccess) return e;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_grad<NG, B>, 32 * GradMem<NG, B>::kWarpsPerCta, sm);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_grad_me<NG, B>, 32, *smem);
+}
+
+// one chunk: sampling, then the amplitude kernel on a fixed persistent grid
+template <int NG, typename B>
+cudaError_t launch_grad_chunk(const GradArgs& a, void* rec_base, int64_t C, int me_grid, int64_t out_off,
+                              cudaStream_t s) {
+  GradRec<B> rec = GradRec<B>::carve(rec_base, a.sp.n_final, C);
+  cudaError_t e = cudaMemsetAsync(rec.count, 0, 2 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  if (occ < 1) return cudaErrorInvalidConfiguration;
-  const int64_t per = 32 * GradMem<NG, B>::kWarpsPerCta;
-  int64_t grid = (a.n + per - 1) / per;
-  if (grid > int64_t(sms) * occ) grid = int64_t(sms) * occ;
-  if (grid > max_grid) grid = max_grid;
-  k_grad<NG, B><<<int(grid), 32 * GradMem<NG, B>::kWarpsPerCta, sm, s>>>(a);
-  *grid_out = int(grid);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t need = (a.n + kThreads - 1) / kThreads;
+  const int sgrid = int(need < int64_t(sms) * 8 ? need : int64_t(sms) * 8);
+  const size_t esm = sizeof(double) * a.sp.ndim * (a.sp.nbins + 1);
+  k_grad_sample<B><<<sgrid, kThreads, esm, s>>>(a, rec, out_off);
+  using T = Dual<B, kGradTangents>;
+  k_grad_me<NG, B><<<me_grid, 32, WarpMem<NG, T>::bytes, s>>>(a, rec, out_off);
   return cudaGetLastError();
 }
 
@@ -152,34 +199,26 @@ cudaError_t launch_grad(const GradArgs& a, int sms, int max_grid, int* grid_out,
 using namespace mf;
 using namespace mf::detail;
 
-extern "C" mf_status mf_grad(mf_process* p, const mf_grid* g, uint64_t seed, int iter, int64_t n, double* sigma,
-                             double* dsigma, double* dw_dtheta, double* dw_dy, void* stream) {
-  if (p == nullptr || g == nullptr || dsigma == nullptr || sigma == nullptr)
-    return fail(MF_ERR_ARG, "mf_grad: null argument");
-  if (g->proc != p) return fail(MF_ERR_ARG, "mf_grad: grid belongs to another process");
-  if (n < 1) return fail(MF_ERR_ARG, "mf_grad: n must be >= 1");
-  if (iter < 0) return fail(MF_ERR_ARG, "mf_grad: iter must be >= 0");
-  cudaStream_t s = (cudaStream_t)stream;
-  GradArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.sp = p->sp;
-  a.sp.nbins = g->nbins;
-  a.mp = p->mp;
-  a.width = p->width;
-  a.edges = g->d_edges;
-  a.n = n;
-  a.seed = seed;
-  a.iter = iter;
-  a.partials = g->d_partials;
+namespace {
+
+template <int NG, typename B>
+mf_status grad_passes(mf_process* p, const mf_grid* g, GradArgs& a, int64_t n, double* dw_dtheta, double* dw_dy,
+                      int power, double* sums, cudaStream_t s) {
   const int ndim = g->ndim;
+  int occ = 0;
+  size_t msm = 0;
+  MF_CUDA((grad_me_config<NG, B>(&occ, &msm)), "mf_grad (configuration)");
+  if (occ < 1) return fail(MF_ERR_CUDA, "mf_grad: amplitude kernel does not fit on an SM");
   // the grid's partial-sum scratch holds max_blocks * (2 + ndim * nbins) doubles
   const int64_t slots = int64_t(g->max_blocks) * (2 + int64_t(ndim) * g->nbins);
-  const int max_grid = int(slots / (1 + kGradTangents));
-  const int power = 2 * p->ng;   // |M|^2 is proportional to g_s^(2 n_gluons)
-  double sw = 0.0, dm = 0.0, dg = 0.0;
-  // pass 0: (m_t, Gamma_t); passes 1, 2, ...: pairs of Vegas uniforms
+  int me_grid = p->sms * occ;
+  if (int64_t(me_grid) * (1 + kGradTangents) > slots) me_grid = int(slots / (1 + kGradTangents));
+  const int64_t C = n < (int64_t(1) << 18) ? n : (int64_t(1) << 18);
+  void* rec = nullptr;
+  MF_CUDA(cudaMallocAsync(&rec, GradRec<B>::bytes(p->sp.n_final, C), s), "mf_grad (records)");
   const int passes = 1 + (dw_dy != nullptr ? (ndim + 1) / 2 : 0);
-  for (int pass = 0; pass < passes; ++pass) {
+  mf_status st = MF_OK;
+  for (int pass = 0; pass < passes && st == MF_OK; ++pass) {
     for (int j = 0; j < kMaxDim; ++j) a.ts.y_slot[j] = -1;
     a.ts.mt_slot = -1;
     a.mt_slot = a.wt_slot = -1;
@@ -205,33 +244,67 @@ extern "C" mf_status mf_grad(mf_process* p, const mf_grid* g, uint64_t seed, int
         a.dw_out[1] = dw_dy + int64_t(j0 + 1) * n;
       }
     }
-    int grid = 0;
-    cudaError_t e;
-    const bool fp64 = p->precision == MF_FP64;
-    switch (p->ng) {
-      case 2: e = fp64 ? launch_grad<2, double>(a, p->sms, max_grid, &grid, s) : launch_grad<2, float>(a, p->sms, max_grid, &grid, s); break;
-      case 3: e = fp64 ? launch_grad<3, double>(a, p->sms, max_grid, &grid, s) : launch_grad<3, float>(a, p->sms, max_grid, &grid, s); break;
-      default: e = fp64 ? launch_grad<4, double>(a, p->sms, max_grid, &grid, s) : launch_grad<4, float>(a, p->sms, max_grid, &grid, s); break;
+    for (int64_t done = 0; done < n; done += C) {
+      const int64_t m = n - done < C ? n - done : C;
+      a.first = done;
+      a.n = m;
+      a.accumulate = done > 0;
+      cudaError_t e = launch_grad_chunk<NG, B>(a, rec, C, me_grid, done, s);
+      if (e != cudaSuccess) { st = cuda_fail(e, "mf_grad (kernels)"); break; }
+      count_launches(2);
     }
-    if (e != cudaSuccess) return cuda_fail(e, "mf_grad (kernel)");
-    count_launches(1);
-    if (pass == 0) {
-      std::vector<double> host(size_t(grid) * (1 + kGradTangents));
-      MF_CUDA(cudaMemcpyAsync(host.data(), g->d_partials, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, s),
-              "mf_grad (copy)");
-      MF_CUDA(cudaStreamSynchronize(s), "mf_grad (sync)");
-      for (int b = 0; b < grid; ++b) {
-        sw += host[size_t(b) * 3 + 0];
-        dm += host[size_t(b) * 3 + 1];
-        dg += host[size_t(b) * 3 + 2];
-      }
+    if (st == MF_OK && pass == 0) {
+      std::vector<double> host(size_t(me_grid) * (1 + kGradTangents));
+      cudaError_t e = cudaMemcpyAsync(host.data(), g->d_partials, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) { st = cuda_fail(e, "mf_grad (sums)"); break; }
+      for (int b = 0; b < me_grid; ++b)
+        for (int k = 0; k <= kGradTangents; ++k) sums[k] += host[size_t(b) * (1 + kGradTangents) + k];
     }
   }
+  cudaFreeAsync(rec, s);
+  return st;
+}
+
+}  // namespace
+
+extern "C" mf_status mf_grad(mf_process* p, const mf_grid* g, uint64_t seed, int iter, int64_t n, double* sigma,
+                             double* dsigma, double* dw_dtheta, double* dw_dy, void* stream) {
+  if (p == nullptr || g == nullptr || dsigma == nullptr || sigma == nullptr)
+    return fail(MF_ERR_ARG, "mf_grad: null argument");
+  if (g->proc != p) return fail(MF_ERR_ARG, "mf_grad: grid belongs to another process");
+  if (n < 1) return fail(MF_ERR_ARG, "mf_grad: n must be >= 1");
+  if (n > (int64_t(1) << 40)) return fail(MF_ERR_ARG, "mf_grad: n too large");
+  if (iter < 0) return fail(MF_ERR_ARG, "mf_grad: iter must be >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  GradArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.sp = p->sp;
+  a.sp.nbins = g->nbins;
+  a.mp = p->mp;
+  a.width = p->width;
+  a.edges = g->d_edges;
+  a.seed = seed;
+  a.iter = iter;
+  a.partials = g->d_partials;
+  const int power = 2 * p->ng;   // |M|^2 is proportional to g_s^(2 n_gluons)
+  double sums[1 + kGradTangents] = {0.0, 0.0, 0.0};
+  const bool fp64 = p->precision == MF_FP64;
+  mf_status st;
+  switch (p->ng) {
+    case 2: st = fp64 ? grad_passes<2, double>(p, g, a, n, dw_dtheta, dw_dy, power, sums, s)
+                      : grad_passes<2, float>(p, g, a, n, dw_dtheta, dw_dy, power, sums, s); break;
+    case 3: st = fp64 ? grad_passes<3, double>(p, g, a, n, dw_dtheta, dw_dy, power, sums, s)
+                      : grad_passes<3, float>(p, g, a, n, dw_dtheta, dw_dy, power, sums, s); break;
+    default: st = fp64 ? grad_passes<4, double>(p, g, a, n, dw_dtheta, dw_dy, power, sums, s)
+                       : grad_passes<4, float>(p, g, a, n, dw_dtheta, dw_dy, power, sums, s); break;
+  }
+  if (st != MF_OK) return st;
   MF_CUDA(cudaStreamSynchronize(s), "mf_grad (sync)");
   const double dn = double(n);
-  *sigma = sw / dn;
+  *sigma = sums[0] / dn;
   dsigma[0] = power * (*sigma) / p->g_s;
-  dsigma[1] = dm / dn;
-  dsigma[2] = dg / dn;
+  dsigma[1] = sums[1] / dn;
+  dsigma[2] = sums[2] / dn;
   return MF_OK;
 }

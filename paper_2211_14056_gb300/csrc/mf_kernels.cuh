@@ -179,11 +179,15 @@ __device__ __forceinline__ void gluon_level(const MaskTab<NG, T>& mt, cplx<T>* G
 // G(B) and the 2^NG suffix momenta, and for every lane its colour-ordered
 // amplitudes J[sigma][top helicity], kept in two planes (real, imaginary
 // parts), each [row = sigma * 2 + top helicity][kJStride] with the lane as the
-// column.  The padded stride (36 = 4 mod 16 words) keeps both the
+// column.  For FP32 the padded stride (36 = 4 mod 16 words) keeps both the
 // lane-parallel stores and the tensor-core colour sum's fragment loads free of
-// bank conflicts.
-constexpr int kJStride = 36;
-template <int NG> constexpr int kJPlane = TTNG<NG>::NPERM * 2 * kJStride;
+// bank conflicts; the other types (no tensor-core path) use 32.
+template <typename T> constexpr int kJStride = std::is_same<T, float>::value ? 36 : 32;
+template <int NG, typename T> constexpr int kJPlane = TTNG<NG>::NPERM * 2 * kJStride<T>;
+// The two-gluon suffix currents are shared through shared memory for plain
+// FP32/FP64; the dual-number instantiations (derivative kernels) recompute
+// them per lane, which keeps their (three times larger) shared footprint down.
+template <typename T> constexpr bool kShareSuffixes = std::is_same<T, float>::value || std::is_same<T, double>::value;
 
 template <int NG, typename T> struct WarpMem {
   static constexpr int EPW = Lanes<NG>::EPW;
@@ -191,10 +195,10 @@ template <int NG, typename T> struct WarpMem {
   static constexpr size_t pt_off = gs_bytes;
   static constexpr size_t pt_bytes = MaskTab<NG, T>::bytes * EPW;       // EPW mask tables
   static constexpr size_t j_off = (pt_off + pt_bytes + 15) & ~size_t(15);
-  static constexpr size_t j_bytes = sizeof(T) * 2 * kJPlane<NG>;
+  static constexpr size_t j_bytes = sizeof(T) * 2 * kJPlane<NG, T>;
   // per event: the two-gluon suffix currents R(S), |S| = 2, for every ordered
   // pair, helicity pair and antitop helicity (component-major, NR2 each)
-  static constexpr int NR2 = NG >= 3 ? NG * (NG - 1) * 8 : 0;
+  static constexpr int NR2 = (NG >= 3 && kShareSuffixes<T>) ? NG * (NG - 1) * 8 : 0;
   static constexpr size_t r2_off = (j_off + j_bytes + 15) & ~size_t(15);
   static constexpr size_t r2_bytes = sizeof(cplx<T>) * 4 * NR2 * EPW;
   static constexpr size_t bytes = (r2_off + r2_bytes + 15) & ~size_t(15);
@@ -235,7 +239,7 @@ __device__ __forceinline__ void quark_walk(int parent, S4<T> (&R)[NG], const Lan
   for (int k = 0; k <= NG - LV; ++k) {
     const int path = first + k;
     const uint8_t msk = PT::template mask<LV>(path);
-    if constexpr (LV == 2) {
+    if constexpr (LV == 2 && kShareSuffixes<T>) {
       // computed once per event by the group (shared_suffixes)
       constexpr int NR2 = WarpMem<NG, T>::NR2;
       const int idx = path * 8 + int((unsigned(cx.pk >> (4 * msk)) & 15u) | (cx.ltb << 2));
@@ -257,10 +261,10 @@ __device__ __forceinline__ void quark_walk(int parent, S4<T> (&R)[NG], const Lan
         apply_acc(make_slash(lane_block<NG, T>(cx, PT::final_blk(path, m))), R[NG - 1 - m], W);
       const int sig = PT::final_sigma(path);
       const cplx<T> j0 = rowdot(cx.ub0, W), j1 = rowdot(cx.ub1, W);
-      cx.J[(sig * 2 + 0) * kJStride] = j0.r;
-      cx.J[(sig * 2 + 0) * kJStride + kJPlane<NG>] = j0.i;
-      cx.J[(sig * 2 + 1) * kJStride] = j1.r;
-      cx.J[(sig * 2 + 1) * kJStride + kJPlane<NG>] = j1.i;
+      cx.J[(sig * 2 + 0) * kJStride<T>] = j0.r;
+      cx.J[(sig * 2 + 0) * kJStride<T> + kJPlane<NG, T>] = j0.i;
+      cx.J[(sig * 2 + 1) * kJStride<T>] = j1.r;
+      cx.J[(sig * 2 + 1) * kJStride<T> + kJPlane<NG, T>] = j1.i;
     }
   }
 }
@@ -345,7 +349,7 @@ __device__ __forceinline__ float colour_sum_tc(const float* J, int group) {
   for (int e = 0; e < EPW; ++e) part[e] = 0.f;
 #pragma unroll 1
   for (int u = 0; u < 4; ++u) {                 // u = 2 * (imaginary plane) + top helicity
-    const float* P = J + (u >> 1) * kJPlane<NG>;
+    const float* P = J + (u >> 1) * kJPlane<NG, float>;
     const int h = u & 1;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {               // columns: lanes 8c .. 8c + 7
@@ -358,8 +362,8 @@ __device__ __forceinline__ float colour_sum_tc(const float* J, int group) {
 #pragma unroll
       for (int ks = 0; ks < KS; ++ks) {
         const int s0 = 8 * ks + tig, s1 = s0 + 4;
-        const float x0 = s0 < NP ? P[(s0 * 2 + h) * kJStride + lc0 + gid] : 0.f;
-        const float x1 = s1 < NP ? P[(s1 * 2 + h) * kJStride + lc0 + gid] : 0.f;
+        const float x0 = s0 < NP ? P[(s0 * 2 + h) * kJStride<float> + lc0 + gid] : 0.f;
+        const float x1 = s1 < NP ? P[(s1 * 2 + h) * kJStride<float> + lc0 + gid] : 0.f;
         const uint32_t h0 = tf32_bits(x0), h1 = tf32_bits(x1);
         const uint32_t l0 = tf32_bits(x0 - __uint_as_float(h0)), l1 = tf32_bits(x1 - __uint_as_float(h1));
 #pragma unroll
@@ -375,7 +379,7 @@ __device__ __forceinline__ float colour_sum_tc(const float* J, int group) {
         for (int hf = 0; hf < 2; ++hf) {
           const int sg = 16 * mi + gid + 8 * hf;
           if (sg < NP) {
-            const float2 b = *reinterpret_cast<const float2*>(P + (sg * 2 + h) * kJStride + lc0 + 2 * tig);
+            const float2 b = *reinterpret_cast<const float2*>(P + (sg * 2 + h) * kJStride<float> + lc0 + 2 * tig);
             s = fmaf(d[mi][2 * hf], b.x, fmaf(d[mi][2 * hf + 1], b.y, s));
           }
         }
@@ -465,7 +469,7 @@ __device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* w
   if constexpr (NG >= 3) { __syncwarp(); gluon_level<NG, 3, T>(mtab, Gs, gl); }
   if constexpr (NG >= 4) { __syncwarp(); gluon_level<NG, 4, T>(mtab, Gs, gl); }
   __syncwarp();
-  if constexpr (NG >= 3) {
+  if constexpr (NG >= 3 && kShareSuffixes<T>) {
     shared_suffixes<NG, T>(Gs, mtab, qtb, mt, R2, gl);
     __syncwarp();
   }
@@ -503,7 +507,8 @@ __device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* w
   for (int h = 0; h < 2; ++h) {
     cplx<T> J[NP];
 #pragma unroll
-    for (int sg = 0; sg < NP; ++sg) J[sg] = {cx.J[(sg * 2 + h) * kJStride], cx.J[(sg * 2 + h) * kJStride + kJPlane<NG>]};
+    for (int sg = 0; sg < NP; ++sg)
+      J[sg] = {cx.J[(sg * 2 + h) * kJStride<T>], cx.J[(sg * 2 + h) * kJStride<T> + kJPlane<NG, T>]};
     part += colour_form<T>(J);
   }
 #pragma unroll

@@ -210,7 +210,10 @@ def test_sizes_and_arguments(mf):
     g.set(edges)
     s_all, d_all, th, _ = _grad(p, edges, 2, 0, 333)
     s_row, d_row = p.grad(g, 2, 0, 333)               # no per-event rows
-    assert s_row == s_all and d_row == d_all
+    # the sums follow the list of passing events, whose order comes from the
+    # sampling kernel's atomics: equal up to summation order
+    assert s_row == pytest.approx(s_all, rel=1e-13)
+    np.testing.assert_allclose(d_row, d_all, rtol=1e-12)
     s1, d1, th1, _ = _grad(p, edges, 2, 0, 1)
     assert th1[1, 0] == th[1, 0] and s1 == pytest.approx(th[0, 0] * w["gs"] / 6, rel=1e-15, abs=0)
     with pytest.raises(mf.MFError):
@@ -238,8 +241,8 @@ def test_autograd_cross_section(mf):
     I = cross_section(theta, PROCESS_IDS[w["process"]], edges, seed, 0, n, **kw)
     I.backward()
     sigma, ds, _, _ = _grad(p, edges, seed, 0, n)
-    assert I.item() == sigma
-    np.testing.assert_array_equal(theta.grad.numpy(), np.array(ds))
+    assert I.item() == pytest.approx(sigma, rel=1e-13)              # summation order
+    np.testing.assert_allclose(theta.grad.numpy(), np.array(ds), rtol=1e-12)
     step = 1e-6 * theta.detach() * torch.sign(theta.grad)
     I2 = cross_section(theta.detach() + step, PROCESS_IDS[w["process"]], edges, seed, 0, n, **kw)
     pred = float((theta.grad * step).sum())
