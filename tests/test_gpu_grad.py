@@ -6,7 +6,8 @@ What pins them:
     a different code path: the plain iteration kernels with shifted
     parameters), per event, for m_t and Gamma_t;
   * the oracle's FP64 weights at y +- h e_j and at m_t +- h (a few events,
-    fully independent of the CUDA path);
+    fully independent of the CUDA path), as plain central differences and,
+    for a tight bar, Richardson-extrapolated;
   * g_s: I(g_s) is a homogeneous polynomial of degree 2 n_gluons, so the
     central difference of the library's own I agrees to O(h^2);
   * sigma and the per-event weights equal those of mf_vegas_iterate.
@@ -171,6 +172,59 @@ def test_uniform_and_mass_derivatives_match_oracle_differences(mf, name, k):
     _report(f"{name} dw/dmt vs oracle", err)
     assert keep.sum() >= k - 1
     assert np.mean(err <= 1e-5) >= 0.9 and err.max() <= 1e-3
+
+
+def _richardson(f, h):
+    """Derivative at 0 from central differences at h and h/2, extrapolated
+    (Richardson): truncation O(h^4), rounding O(eps / h)."""
+    d1 = (f(h) - f(-h)) / (2 * h)
+    d2 = (f(h / 2) - f(-h / 2)) / h
+    return (4 * d2 - d1) / 3
+
+
+@pytest.mark.parametrize("name,k", [("gg_ttx_1tev", 40), ("gg_ttxg_13tev", 30), ("gg_ttxgg_13tev", 20)])
+def test_derivatives_match_extrapolated_oracle_differences(mf, name, k):
+    """FP64 dw/dy_j and dw/dm_t against the oracle's Richardson-extrapolated
+    central differences (h = 1e-4 in y, 1e-3 m_t in m_t), accurate to ~1e-10
+    (the oracle's extrapolations at h and 2h agree to a median of 1e-11).
+    Events whose bins or cut decision change within +-h are excluded; events
+    with a large fourth derivative inside +-h (a few near-singular ones) are
+    the tail the 99% bar leaves out."""
+    seed, it, n = 33, 1, 256
+    p, w = _proc(mf, name, mf.MF_FP64)
+    edges = random_grid(p.ndim, seed=9)
+    _, _, th, dy = _grad(p, edges, seed, it, n)
+    amp = "feynman" if name == "gg_ttx_1tev" else "bg"
+    st = _oracle_setup(w, amp)
+    y = oph.uniforms(seed, it, np.arange(n, dtype=np.uint64), st.ndim)
+    w0, b0 = st.weights(y, edges)
+    sel = np.flatnonzero(w0 > 0)[:k]
+    ys = y[:, sel]
+    errs = []
+    for j in range(st.ndim):
+        def f(h, j=j):
+            yy = ys.copy()
+            yy[j] += h
+            ww, bb = st.weights(yy, edges)
+            return np.where((ww > 0) & np.all(bb == b0[:, sel], axis=0), ww, np.nan)
+        ref = _richardson(f, 1e-4)
+        ok = np.isfinite(ref)
+        scale = np.maximum(np.abs(ref[ok]), 1e-2 * np.abs(w0[sel][ok]))
+        errs.append(np.abs(dy[j, sel][ok] - ref[ok]) / scale)
+    err = np.concatenate(errs)
+    _report(f"{name} dw/dy vs extrapolated oracle", err)
+    assert err.size >= 0.8 * k * st.ndim
+    assert np.median(err) < 1e-9 and np.quantile(err, 0.95) < 1e-7 and np.mean(err < 1e-6) >= 0.99
+    mt = w["mt"]
+    def fm(h):
+        ww, _ = _oracle_setup(w, amp, mt=mt + h).weights(ys, edges)
+        return np.where(ww > 0, ww, np.nan)
+    ref = _richardson(fm, 1e-3 * mt)
+    ok = np.isfinite(ref)
+    scale = np.maximum(np.abs(ref[ok]), 1e-2 * np.abs(w0[sel][ok]) / mt)
+    err = np.abs(th[1, sel][ok] - ref[ok]) / scale
+    _report(f"{name} dw/dmt vs extrapolated oracle", err)
+    assert ok.sum() >= k - 1 and err.max() < 1e-8
 
 
 @pytest.mark.parametrize("name,n", [("gg_ttxg_13tev", 20000), ("gg_ttxgg_13tev", 4000)])
