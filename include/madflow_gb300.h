@@ -53,6 +53,13 @@ typedef int mf_status;
 #define MF_PROC_GG_TTX 1   /* g g -> t tbar        [2 gluons; 3 diagrams, 2 colour flows, 16 helicities]  */
 #define MF_PROC_GG_TTXG 2  /* g g -> t tbar g      [3; 16 diagrams, 6 flows, 32 helicities]               */
 #define MF_PROC_GG_TTXGG 3 /* g g -> t tbar g g    [4; 123 diagrams, 24 flows, 64 helicities]             */
+/* u ubar -> t tbar g g: two quark lines, 38 Feynman diagrams decomposed onto
+ * 12 colour structures (T^A)_{t u}(T^B)_{ubar tbar}, (T^A)_{t tbar}(T^B)_{ubar u}
+ * over the ordered splits (A, B) of the two gluons; 64 helicities.  The same
+ * phase space as g g -> t tbar g g (the synthetic luminosity serves u and
+ * ubar); average 1/36.  Not covered: MF_FP32_TC, mf_grad and
+ * mf_vegas_accumulate_static (MF_ERR_UNSUPPORTED). */
+#define MF_PROC_UUX_TTXGG 4
 
 /* arithmetic of the matrix element */
 #define MF_FP64 0      /* everything in FP64 */
@@ -71,8 +78,8 @@ typedef struct {
   const double* masses;        /* host [n_ext] GeV: 0, 0, m_t, m_t, 0...; the two top masses must agree */
   double top_width;            /* Gamma_t >= 0 in the internal top propagators */
   double g_s;                  /* strong coupling (fixed, no running) */
-  int n_flow;                  /* colour flows: (n_ext-2)! */
-  const int64_t* colour_num;   /* host [n_flow*n_flow] integer numerators of the trace-basis colour matrix */
+  int n_flow;                  /* colour flows: (n_ext-2)! for g g processes, 12 for u ubar -> t tbar g g */
+  const int64_t* colour_num;   /* host [n_flow*n_flow] integer numerators of the process's colour matrix */
   int64_t colour_den;          /* common denominator; C = colour_num / colour_den */
   double sqrt_s;               /* hadronic sqrt(S) if lumi = 1, else the fixed partonic sqrt(s) */
   int lumi;                    /* 0: fixed partonic energy; 1: synthetic gluon luminosity */

@@ -16,10 +16,10 @@ _LIB_PATH = os.path.join(HERE, "lib", "libmadflow_gb300.so")
 
 MF_OK, MF_ERR_ARG, MF_ERR_CUDA, MF_ERR_UNSUPPORTED, MF_ERR_COLOUR, MF_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 MF_WARN_NEWTON = 1
-MF_PROC_GG_TTX, MF_PROC_GG_TTXG, MF_PROC_GG_TTXGG = 1, 2, 3
+MF_PROC_GG_TTX, MF_PROC_GG_TTXG, MF_PROC_GG_TTXGG, MF_PROC_UUX_TTXGG = 1, 2, 3, 4
 MF_FP64, MF_FP32, MF_FP32_TC = 0, 1, 2
 
-_NGLUON = {MF_PROC_GG_TTX: 2, MF_PROC_GG_TTXG: 3, MF_PROC_GG_TTXGG: 4}
+_NGLUON = {MF_PROC_GG_TTX: 2, MF_PROC_GG_TTXG: 3, MF_PROC_GG_TTXGG: 4, MF_PROC_UUX_TTXGG: 4}
 
 
 class MFError(RuntimeError):
@@ -130,6 +130,14 @@ def colour_matrix(ngluons):
     return [x for row in M for x in row], D
 
 
+@functools.lru_cache(maxsize=None)
+def colour_matrix_uux():
+    """(integer numerators [12*12], denominator) of the u u~ -> t t~ g g colour matrix."""
+    from .gen_uux import colour_matrix_exact
+    M, D = colour_matrix_exact()
+    return [x for row in M for x in row], D
+
+
 def _ptr(t, dtype, numel, name):
     import torch
     if t is None:
@@ -160,9 +168,14 @@ class Process:
             raise MFError(MF_ERR_UNSUPPORTED, "unknown process id")
         self.ngluons, self.n_ext = ng, ng + 2
         masses = (C.c_double * self.n_ext)(*([0.0, 0.0, mt, mt] + [0.0] * (ng - 2)))
-        num, den = colour if colour is not None else colour_matrix(ng)
+        if process_id == MF_PROC_UUX_TTXGG:
+            num, den = colour if colour is not None else colour_matrix_uux()
+            nflow = 12
+        else:
+            num, den = colour if colour is not None else colour_matrix(ng)
+            nflow = math.factorial(ng)
         cnum = (C.c_int64 * len(num))(*num)
-        d = ProcessDesc(process_id, self.n_ext, masses, wt, gs, math.factorial(ng), cnum, den, sqrt_s,
+        d = ProcessDesc(process_id, self.n_ext, masses, wt, gs, nflow, cnum, den, sqrt_s,
                         1 if lumi else 0, lumi_N, lumi_a, lumi_b, pt_cut, dr_cut, precision)
         h = C.c_void_p()
         _check(lib.mf_init_process(C.byref(d), C.byref(h)))

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "mf_internal.h"
+#include "mf_gen_uux.cuh"
 
 using namespace mf;
 
@@ -45,11 +46,12 @@ int factorial(int n) { return n <= 1 ? 1 : n * factorial(n - 1); }
 // in FP32, ~160 B/event in FP64)
 constexpr int64_t kRecordChunk = int64_t(1) << 20;
 
-const int* lib_colour(int ng, int* den) {
-  switch (ng) {
+const int* lib_colour(int key, int* den) {
+  switch (key) {
     case 2: *den = kColourDen2; return kColourNum2;
     case 3: *den = kColourDen3; return kColourNum3;
     case 4: *den = kColourDen4; return kColourNum4;
+    case mf::detail::kUuxKey: *den = kUuxColourDen; return kUuxColourNum;
   }
   return nullptr;
 }
@@ -64,6 +66,7 @@ cudaError_t dispatch_acc_config(int ng, int prec, int ndim, int nbins, size_t* s
     case 2: return me_acc_config<2>(p, ndim, nbins, smem, ctas);
     case 3: return me_acc_config<3>(p, ndim, nbins, smem, ctas);
     case 4: return me_acc_config<4>(p, ndim, nbins, smem, ctas);
+    case kUuxKey: return uux_acc_config(p, ndim, nbins, smem, ctas);
   }
   return cudaErrorInvalidValue;
 }
@@ -93,6 +96,7 @@ cudaError_t dispatch_me_config(int ng, int prec, size_t* smem, int* ctas) {
     case 2: return me_config<2>(p, smem, ctas);
     case 3: return me_config<3>(p, smem, ctas);
     case 4: return me_config<4>(p, smem, ctas);
+    case mf::detail::kUuxKey: return uux_me_config(p, smem, ctas);
   }
   return cudaErrorInvalidValue;
 }
@@ -151,13 +155,16 @@ int64_t mf_kernel_launches(void) { return g_launches.load(); }
 mf_status mf_init_process(const mf_process_desc* d, mf_process** out) {
   if (d == nullptr || out == nullptr) return fail(MF_ERR_ARG, "mf_init_process: null argument");
   *out = nullptr;
-  int ng = 0;
+  int ng = 0, kind = 0;
   switch (d->process_id) {
     case MF_PROC_GG_TTX: ng = 2; break;
     case MF_PROC_GG_TTXG: ng = 3; break;
     case MF_PROC_GG_TTXGG: ng = 4; break;
+    case MF_PROC_UUX_TTXGG: ng = 4; kind = 1; break;
     default: return fail(MF_ERR_UNSUPPORTED, "mf_init_process: unknown process_id");
   }
+  const int key = kind == 1 ? kUuxKey : ng;
+  const int nflow = kind == 1 ? kUuxFlows : factorial(ng);
   if (d->n_ext != ng + 2) return fail(MF_ERR_ARG, "mf_init_process: n_ext does not match the process");
   if (d->masses == nullptr) return fail(MF_ERR_ARG, "mf_init_process: masses is null");
   const double mt = d->masses[2];
@@ -172,10 +179,12 @@ mf_status mf_init_process(const mf_process_desc* d, mf_process** out) {
   if (d->precision != MF_FP64 && d->precision != MF_FP32 && d->precision != MF_FP32_TC)
     return fail(MF_ERR_ARG, "mf_init_process: bad precision");
   // colour matrix: must be the library's exact trace-basis matrix
-  if (d->n_flow != factorial(ng)) return fail(MF_ERR_COLOUR, "mf_init_process: n_flow must be (n_ext-2)!");
+  if (kind == 1 && d->precision == MF_FP32_TC)
+    return fail(MF_ERR_UNSUPPORTED, "mf_init_process: the tensor-core colour sum covers the gluon-initiated processes");
+  if (d->n_flow != nflow) return fail(MF_ERR_COLOUR, "mf_init_process: n_flow does not match the process's colour basis");
   if (d->colour_num == nullptr || d->colour_den <= 0) return fail(MF_ERR_COLOUR, "mf_init_process: colour matrix missing");
   int lden = 1;
-  const int* lnum = lib_colour(ng, &lden);
+  const int* lnum = lib_colour(key, &lden);
   const int nf = d->n_flow;
   for (int a = 0; a < nf; ++a)
     for (int b = 0; b < nf; ++b) {
@@ -195,6 +204,7 @@ mf_status mf_init_process(const mf_process_desc* d, mf_process** out) {
 
   mf_process* p = new mf_process();
   p->ng = ng;
+  p->kind = kind;
   p->precision = d->precision;
   const int n = ng;   // final-state particles: t, tbar and ng - 2 gluons
   p->ndim = 3 * n - 4 + (d->lumi ? 2 : 0);
@@ -221,11 +231,12 @@ mf_status mf_init_process(const mf_process_desc* d, mf_process** out) {
   p->g_s = d->g_s;
   p->width = d->top_width;
   const int sid = factorial(ng - 2);        // identical final-state gluons
-  mp.norm = std::pow(d->g_s, 2 * ng) / (256.0 * sid * lden);
+  const double average = kind == 1 ? 36.0 : 256.0;   // spin x colour states of u u~ or g g
+  mp.norm = std::pow(d->g_s, 2 * ng) / (average * sid * lden);
 
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
-  if (e == cudaSuccess) e = dispatch_me_config(ng, p->precision, &p->me_smem, &p->me_ctas);
+  if (e == cudaSuccess) e = dispatch_me_config(key, p->precision, &p->me_smem, &p->me_ctas);
   if (e != cudaSuccess) {
     delete p;
     return cuda_fail(e, "mf_init_process");
@@ -264,9 +275,15 @@ mf_status mf_grid_create(const mf_process* p, int nbins, mf_grid** out) {
   g->proc = p;
   g->ndim = p->ndim;
   g->nbins = nbins;
-  cudaError_t e = dispatch_fused_config(p->ng, p->precision, g->ndim, nbins, &g->fused_smem, &g->fused_ctas);
-  if (e == cudaSuccess && g->fused_ctas < 1) e = cudaErrorInvalidConfiguration;
-  if (e == cudaSuccess) e = dispatch_acc_config(p->ng, p->precision, g->ndim, nbins, &g->acc_smem, &g->acc_ctas);
+  // the fused kernel (allocation-free entry point) exists for the gluon-initiated processes
+  cudaError_t e = cudaSuccess;
+  if (p->kind == 0) {
+    e = dispatch_fused_config(p->ng, p->precision, g->ndim, nbins, &g->fused_smem, &g->fused_ctas);
+    if (e == cudaSuccess && g->fused_ctas < 1) e = cudaErrorInvalidConfiguration;
+  } else {
+    g->fused_ctas = 0;
+  }
+  if (e == cudaSuccess) e = dispatch_acc_config(proc_key(p), p->precision, g->ndim, nbins, &g->acc_smem, &g->acc_ctas);
   if (e == cudaSuccess && g->acc_ctas < 1) e = cudaErrorInvalidConfiguration;
   const int most = std::max(g->fused_ctas, g->acc_ctas);
   g->max_blocks = p->sms * (most < 1 ? 1 : most);
@@ -347,12 +364,13 @@ mf_status mf_matrix_element(mf_process* p, int64_t n, const double* momenta, dou
   if (p == nullptr || n < 0) return fail(MF_ERR_ARG, "mf_matrix_element: bad argument");
   if (n == 0) return MF_OK;
   if (momenta == nullptr || me2 == nullptr) return fail(MF_ERR_ARG, "mf_matrix_element: null buffer");
-  const int epb = kWarps * (32 / (2 << p->ng));   // events per CTA pass
+  const int epb = p->kind == 1 ? kWarps : kWarps * (32 / (2 << p->ng));   // events per CTA pass
   const int64_t need = (n + epb - 1) / epb;
   const int64_t cap = int64_t(p->sms) * effective_ctas(p, p->me_ctas);
   const int grid = int(need < cap ? need : cap);
   cudaError_t e;
-  switch (p->ng) {
+  switch (proc_key(p)) {
+    case kUuxKey: e = launch_matrix_element_uux(p->precision == MF_FP64 ? 0 : 1, p->mp, n, momenta, me2, grid, (cudaStream_t)stream); break;
     case 2: e = launch_matrix_element<2>(p->precision == MF_FP64 ? 0 : 1, p->mp, n, momenta, me2, grid, (cudaStream_t)stream); break;
     case 3: e = launch_matrix_element<3>(p->precision == MF_FP64 ? 0 : 1, p->mp, n, momenta, me2, grid, (cudaStream_t)stream); break;
     default: e = launch_matrix_element<4>(p->precision == MF_FP64 ? 0 : 1, p->mp, n, momenta, me2, grid, (cudaStream_t)stream); break;
@@ -392,7 +410,8 @@ mf_status mf_vegas_accumulate(mf_process* p, mf_grid* g, uint64_t seed, int iter
     double* w = weights ? weights + done : nullptr;
     cudaEvent_t* evk = g->profile ? &g->ev[size_t(3) * k] : nullptr;
     cudaError_t e;
-    switch (p->ng) {
+    switch (proc_key(p)) {
+      case kUuxKey: e = launch_chunk_uux(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
       case 2: e = launch_chunk<2>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
       case 3: e = launch_chunk<3>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
       default: e = launch_chunk<4>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
@@ -540,6 +559,8 @@ extern "C" mf_status mf_vegas_accumulate_static(mf_process* p, const double* edg
                                                  double* weights, void* stream) {
   if (p == nullptr || edges == nullptr || totals == nullptr)
     return fail(MF_ERR_ARG, "mf_vegas_accumulate_static: null argument");
+  if (p->kind != 0)
+    return fail(MF_ERR_UNSUPPORTED, "mf_vegas_accumulate_static: covers the gluon-initiated processes");
   if (nbins < 2 || nbins > 64) return fail(MF_ERR_ARG, "mf_vegas_accumulate_static: nbins must be in [2, 64]");
   if (n < 1 || first_event < 0) return fail(MF_ERR_ARG, "mf_vegas_accumulate_static: need n >= 1 and first_event >= 0");
   size_t smem = 0;

@@ -273,6 +273,7 @@ extern "C" mf_status mf_grad(mf_process* p, const mf_grid* g, uint64_t seed, int
   if (p == nullptr || g == nullptr || dsigma == nullptr || sigma == nullptr)
     return fail(MF_ERR_ARG, "mf_grad: null argument");
   if (g->proc != p) return fail(MF_ERR_ARG, "mf_grad: grid belongs to another process");
+  if (p->kind != 0) return fail(MF_ERR_UNSUPPORTED, "mf_grad: covers the gluon-initiated processes");
   if (n < 1) return fail(MF_ERR_ARG, "mf_grad: n must be >= 1");
   if (n > (int64_t(1) << 40)) return fail(MF_ERR_ARG, "mf_grad: n too large");
   if (iter < 0) return fail(MF_ERR_ARG, "mf_grad: iter must be >= 0");

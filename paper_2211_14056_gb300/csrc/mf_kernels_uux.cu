@@ -1,0 +1,172 @@
+// u u~ -> t t~ g g kernels: one event per warp, lane = helicities of
+// (u, u~, t~, g, g) (bits 0..4), both top helicities per lane; the amplitude
+// code is generated (mf_gen_uux.cuh).  The iteration reuses the sampling
+// kernel and records of the gluon-initiated processes (same final state t t~
+// g g, massless initial partons): k_me_acc_uux walks the list of events that
+// passed, accumulates the weight and the Vegas sums like k_me_acc.
+#include "mf_internal.h"
+#include "mf_gen_uux.cuh"
+
+namespace mf {
+
+// |M|^2 (without MeParams::norm) of one event: every lane of the warp calls it
+template <typename T>
+__device__ __forceinline__ T uux_warp_me2(const T (&p)[6][4], T mt, T mw) {
+  const int lane = threadIdx.x & 31;
+  R4<T> P[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) P[i].v[c] = p[i][c];
+  const int l1 = (lane & 1) ? 1 : -1, l2 = (lane & 2) ? 1 : -1, l4 = (lane & 4) ? 1 : -1;
+  const int l5 = (lane & 8) ? 1 : -1, l6 = (lane & 16) ? 1 : -1;
+  const S4<T> U1 = u_in(P[0], T(0), l1);
+  const S4<T> V2 = vbar_in(P[1], T(0), l2);
+  const S4<T> VTB = v_out(P[3], mt, l4);
+  const S4<T> UB3[2] = {ubar_out(P[2], mt, -1), ubar_out(P[2], mt, 1)};
+  const V4<T> E5 = polarisation(P[4], l5, true), E6 = polarisation(P[5], l6, true);
+  cplx<T> J[2][kUuxFlows];
+  uux_amplitudes<T>(P, mt, mw, U1, V2, VTB, UB3, E5, E6, J);
+  T part = uux_colour_form<T>(J[0]) + uux_colour_form<T>(J[1]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+  return part;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_matrix_element_uux(MeParams mp, int64_t n, const double* __restrict__ mom,
+                                                                 double* __restrict__ out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const T mt = T(mp.mt), mw = T(mp.mw);
+  for (int64_t e = int64_t(blockIdx.x) * kWarps + warp; e < n; e += int64_t(gridDim.x) * kWarps) {
+    T p[6][4];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) p[i][c] = T(mom[int64_t(i * 4 + c) * n + e]);
+    const T v = uux_warp_me2<T>(p, mt, mw);
+    if (lane == 0) out[e] = double(v) * mp.norm;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_me_acc_uux(MeParams mp, int ndim, int nbins, RecordView<T> rec,
+                                                         int accumulate, double* __restrict__ partials,
+                                                         unsigned long long* __restrict__ counters,
+                                                         double* __restrict__ w_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nacc = 2 + ndim * nbins;
+  double* sums = reinterpret_cast<double*>(smem_raw);
+  double* hist = sums + 2;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  for (int i = t; i < nacc; i += kThreads) sums[i] = 0.0;
+  const T mt = T(mp.mt), mw = T(mp.mw);
+  const unsigned full = 0xffffffffu;
+  const int64_t npass = rec.count[0];
+  double s1 = 0.0, s2 = 0.0;
+  __syncthreads();
+  for (int64_t k = int64_t(blockIdx.x) * kWarps + warp; k < npass; k += int64_t(gridDim.x) * kWarps) {
+    const int64_t e = rec.list[k];
+    T p[6][4];
+    const T rs = rec.rs[e];
+    p[0][0] = T(0.5) * rs; p[0][1] = T(0); p[0][2] = T(0); p[0][3] = T(0.5) * rs;
+    p[1][0] = T(0.5) * rs; p[1][1] = T(0); p[1][2] = T(0); p[1][3] = T(-0.5) * rs;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) p[2 + i][c] = rec.mom[int64_t(i * 4 + c) * rec.C + e];
+    const T v = uux_warp_me2<T>(p, mt, mw);
+    const double w = double(v) * mp.norm * rec.pref[e];
+    if (lane == 0) {
+      s1 += w;
+      s2 += w * w;
+      if (w_out != nullptr) w_out[e] = w;
+    }
+    if (lane < ndim) atomicAdd(&hist[lane * nbins + rec.flag[int64_t(lane) * rec.C + e]], w * w);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    s1 += __shfl_xor_sync(full, s1, off);
+    s2 += __shfl_xor_sync(full, s2, off);
+  }
+  if (lane == 0) {
+    atomicAdd(&sums[0], s1);
+    atomicAdd(&sums[1], s2);
+  }
+  __syncthreads();
+  double* dst = partials + int64_t(blockIdx.x) * nacc;
+  for (int i = t; i < nacc; i += kThreads) dst[i] = (accumulate ? dst[i] : 0.0) + sums[i];
+  if (t < 2) {
+    const unsigned long long c = blockIdx.x == 0 ? (unsigned long long)rec.count[t] : 0ull;
+    counters[blockIdx.x * 2 + t] = (accumulate ? counters[blockIdx.x * 2 + t] : 0ull) + c;
+  }
+}
+
+namespace {
+size_t acc_smem(int ndim, int nbins) { return sizeof(double) * (2 + size_t(ndim) * nbins); }
+}
+
+cudaError_t uux_me_config(int precision, size_t* smem, int* ctas) {
+  *smem = 0;
+  if (precision == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_matrix_element_uux<double>, kThreads, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_matrix_element_uux<float>, kThreads, 0);
+}
+
+cudaError_t uux_acc_config(int precision, int ndim, int nbins, size_t* smem, int* ctas) {
+  *smem = acc_smem(ndim, nbins);
+  if (precision == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_me_acc_uux<double>, kThreads, *smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k_me_acc_uux<float>, kThreads, *smem);
+}
+
+cudaError_t launch_matrix_element_uux(int precision, const MeParams& mp, int64_t n, const double* mom, double* out,
+                                      int grid, cudaStream_t s) {
+  if (precision == 0) k_matrix_element_uux<double><<<grid, kThreads, 0, s>>>(mp, n, mom, out);
+  else k_matrix_element_uux<float><<<grid, kThreads, 0, s>>>(mp, n, mom, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_me_acc_uux(int precision, const MeParams& mp, int n_final, int ndim, int nbins, void* rec_base,
+                              int64_t C, int accumulate, double* partials, unsigned long long* counters,
+                              double* w_out, int grid, cudaStream_t s) {
+  const size_t sm = acc_smem(ndim, nbins);
+  if (precision == 0) {
+    RecordView<double> rec = RecordView<double>::carve(rec_base, n_final, ndim, C);
+    k_me_acc_uux<double><<<grid, kThreads, sm, s>>>(mp, ndim, nbins, rec, accumulate, partials, counters, w_out);
+  } else {
+    RecordView<float> rec = RecordView<float>::carve(rec_base, n_final, ndim, C);
+    k_me_acc_uux<float><<<grid, kThreads, sm, s>>>(mp, ndim, nbins, rec, accumulate, partials, counters, w_out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_uux(int precision, const SampleParams& sp, const MeParams& mp, const double* edges,
+                             int64_t first_event, int64_t n, int64_t C, void* rec_base, uint64_t seed, int iter,
+                             int accumulate, double* partials, unsigned long long* counters, double* w_out, int grid,
+                             cudaStream_t s, cudaEvent_t* ev) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t need = (n + kThreads - 1) / kThreads;
+  const int sgrid = int(need < int64_t(sms) * 16 ? need : int64_t(sms) * 16);
+  const size_t esm = sizeof(double) * sp.ndim * (sp.nbins + 1);
+  cudaError_t e;
+  if (precision == 0) {
+    RecordView<double> rec = RecordView<double>::carve(rec_base, sp.n_final, sp.ndim, C);
+    e = cudaMemsetAsync(rec.count, 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[0], s);
+    k_sample_rec<double><<<sgrid, kThreads, esm, s>>>(sp, edges, first_event, n, seed, iter, rec, w_out);
+  } else {
+    RecordView<float> rec = RecordView<float>::carve(rec_base, sp.n_final, sp.ndim, C);
+    e = cudaMemsetAsync(rec.count, 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[0], s);
+    k_sample_rec<float><<<sgrid, kThreads, esm, s>>>(sp, edges, first_event, n, seed, iter, rec, w_out);
+  }
+  if (ev) cudaEventRecord(ev[1], s);
+  e = launch_me_acc_uux(precision, mp, sp.n_final, sp.ndim, sp.nbins, rec_base, C, accumulate, partials, counters,
+                        w_out, grid, s);
+  if (ev) cudaEventRecord(ev[2], s);
+  return e;
+}
+
+}  // namespace mf

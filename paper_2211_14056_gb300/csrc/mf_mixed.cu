@@ -24,7 +24,7 @@ constexpr int kMaxProc = 4;
 
 template <typename K> struct MixedArgs {
   int nproc;
-  int ng[kMaxProc];
+  int ng[kMaxProc];             // gluon count; 0 for u u~ -> t t~ g g (not in the shared queue)
   int ndim[kMaxProc], nbins[kMaxProc];
   int64_t n[kMaxProc];          // events of each process
   int64_t off[kMaxProc + 1];    // prefix sums of n
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_me_mixed(MixedArgs<T> a) {
   if (t == 0) {
     tiles_off[0] = 0;
     for (int p = 0; p < a.nproc; ++p) {
-      const int64_t np = a.rec[p].count[0];
+      const int64_t np = a.ng[p] == 0 ? 0 : a.rec[p].count[0];
       tiles_off[p + 1] = tiles_off[p] + (np + a.tile - 1) / a.tile;
     }
   }
@@ -200,7 +200,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_me_mixed(MixedArgs<T> a) {
     const int nacc = 2 + a.ndim[p] * a.nbins[p];
     double* dst = a.partials[p] + int64_t(blockIdx.x) * nacc;
     for (int i = t; i < nacc; i += kThreads) dst[i] = acc[aoff[p] + i];
-    if (t < 2) a.counters[p][blockIdx.x * 2 + t] = blockIdx.x == 0 ? (unsigned long long)a.rec[p].count[t] : 0ull;
+    if (t < 2)
+      a.counters[p][blockIdx.x * 2 + t] =
+          (blockIdx.x == 0 && a.ng[p] != 0) ? (unsigned long long)a.rec[p].count[t] : 0ull;
   }
 }
 
@@ -244,12 +246,15 @@ int acc_grid(const mf_mixed* m, int k) {
   return m->sms * (c < 1 ? 1 : c);
 }
 
-cudaError_t launch_acc_dispatch(int ng, int prec, const MeParams& mp, int n_final, int ndim, int nbins, void* rec,
-                                int64_t C, double* partials, unsigned long long* counters, int grid, cudaStream_t s) {
-  switch (ng) {
-    case 2: return launch_me_acc<2>(prec, mp, n_final, ndim, nbins, rec, C, 0, partials, counters, nullptr, grid, s);
-    case 3: return launch_me_acc<3>(prec, mp, n_final, ndim, nbins, rec, C, 0, partials, counters, nullptr, grid, s);
-    default: return launch_me_acc<4>(prec, mp, n_final, ndim, nbins, rec, C, 0, partials, counters, nullptr, grid, s);
+cudaError_t launch_acc_dispatch(int key, int prec, const MeParams& mp, int n_final, int ndim, int nbins, void* rec,
+                                int64_t C, int accumulate, double* partials, unsigned long long* counters, int grid,
+                                cudaStream_t s) {
+  if (key == kUuxKey)
+    return launch_me_acc_uux(prec, mp, n_final, ndim, nbins, rec, C, accumulate, partials, counters, nullptr, grid, s);
+  switch (key) {
+    case 2: return launch_me_acc<2>(prec, mp, n_final, ndim, nbins, rec, C, accumulate, partials, counters, nullptr, grid, s);
+    case 3: return launch_me_acc<3>(prec, mp, n_final, ndim, nbins, rec, C, accumulate, partials, counters, nullptr, grid, s);
+    default: return launch_me_acc<4>(prec, mp, n_final, ndim, nbins, rec, C, accumulate, partials, counters, nullptr, grid, s);
   }
 }
 
@@ -263,7 +268,7 @@ MixedArgs<K> make_args(const mf_mixed* m) {
     const int i = m->order[k];
     const mf_process* p = m->procs[i];
     const mf_grid* g = m->grids[i];
-    a.ng[k] = p->ng;
+    a.ng[k] = p->kind == 0 ? p->ng : 0;
     a.ndim[k] = g->ndim;
     a.nbins[k] = g->nbins;
     a.n[k] = m->n[i];
@@ -318,9 +323,22 @@ mf_status enqueue(mf_mixed* m, int refine, cudaStream_t s) {
       const int i = m->order[k];
       const mf_process* p = m->procs[i];
       mf_grid* g = m->grids[i];
-      MF_CUDA(launch_acc_dispatch(p->ng, m->precision, p->mp, p->sp.n_final, g->ndim, g->nbins, g->d_records,
-                                  g->chunk, g->d_partials, g->d_counters, acc_grid(m, i), s),
+      MF_CUDA(launch_acc_dispatch(proc_key(p), m->precision, p->mp, p->sp.n_final, g->ndim, g->nbins, g->d_records,
+                                  g->chunk, 0, g->d_partials, g->d_counters, acc_grid(m, i), s),
               "mf_mixed (per-process kernel)");
+      count_launches(1);
+    }
+  } else {
+    // the shared queue covers the gluon-initiated processes; u u~ -> t t~ g g
+    // runs its own kernel on the queue's CTA count, adding to the partials
+    // the queue kernel zeroed
+    for (int k = 0; k < m->nproc; ++k) {
+      const mf_process* p = m->procs[k];
+      if (p->kind == 0) continue;
+      mf_grid* g = m->grids[k];
+      MF_CUDA(launch_acc_dispatch(proc_key(p), m->precision, p->mp, p->sp.n_final, g->ndim, g->nbins, g->d_records,
+                                  g->chunk, 1, g->d_partials, g->d_counters, grid, s),
+              "mf_mixed (u u~ kernel)");
       count_launches(1);
     }
   }
@@ -398,7 +416,7 @@ mf_status mf_mixed_create(mf_process* const* procs, mf_grid* const* grids, const
   if (e == cudaSuccess && m->occupancy < 1) e = cudaErrorInvalidConfiguration;
   for (int k = 0; k < nproc && e == cudaSuccess; ++k) {
     size_t asm_ = 0;
-    e = dispatch_acc_config(procs[k]->ng, m->precision, grids[k]->ndim, grids[k]->nbins, &asm_, &m->acc_occ[k]);
+    e = dispatch_acc_config(proc_key(procs[k]), m->precision, grids[k]->ndim, grids[k]->nbins, &asm_, &m->acc_occ[k]);
     if (e == cudaSuccess && m->acc_occ[k] < 1) e = cudaErrorInvalidConfiguration;
   }
   // per-grid records for the whole event count, and partial slots for the mixed grid

@@ -8,7 +8,7 @@ luminosity f(x) = x^-1.1 (1-x)^5 at sqrt(S) = 13 TeV for the 2 -> 3 and
 luminosity uniforms (if any), then the RAMBO uniforms.
 """
 
-PROCESS_IDS = {"gg_ttx": 1, "gg_ttxg": 2, "gg_ttxgg": 3}
+PROCESS_IDS = {"gg_ttx": 1, "gg_ttxg": 2, "gg_ttxgg": 3, "uux_ttxgg": 4}
 
 WORKLOADS = {
     # g g -> t tbar at fixed sqrt(s) = 1 TeV: closed-form target, FP64
@@ -20,13 +20,16 @@ WORKLOADS = {
     # g g -> t tbar g g, Gamma_t = 1.5 GeV, pT_g > 30 GeV and Delta R_gg > 0.4
     "gg_ttxgg_13tev": dict(process="gg_ttxgg", mt=173.0, wt=1.5, gs=1.2177, sqrt_s=13000.0, lumi=True,
                            pt_cut=30.0, dr_cut=0.4, events=2 ** 22, iterations=5, seed=3),
+    # u u~ -> t t~ g g with the g g -> t t~ g g set-up (the luminosity serves u and u~)
+    "uux_ttxgg_13tev": dict(process="uux_ttxgg", mt=173.0, wt=1.5, gs=1.2177, sqrt_s=13000.0, lumi=True,
+                            pt_cut=30.0, dr_cut=0.4, events=10_000, iterations=5, seed=5),
 }
 
 
-# the batched mixed launch: three gluon-initiated processes together, each with
-# its own Vegas grid (the processes' own set-ups above), FP32 amplitudes
-MIXED = {"workloads": ["gg_ttx_1tev", "gg_ttxg_13tev", "gg_ttxgg_13tev"],
-         "events": [4_000_000, 1_000_000, 250_000], "seed": 4}
+# the batched mixed launch: four processes together, each with its own Vegas
+# grid (the processes' own set-ups above), FP32 amplitudes
+MIXED = {"workloads": ["gg_ttx_1tev", "gg_ttxg_13tev", "gg_ttxgg_13tev", "uux_ttxgg_13tev"],
+         "events": [4_000_000, 1_000_000, 250_000, 10_000], "seed": 4}
 
 
 def oracle_cfg(w):
