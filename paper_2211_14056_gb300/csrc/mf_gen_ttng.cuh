@@ -193,6 +193,8 @@ static __constant__ uint8_t kPathFirst4_2[4] = {0, 3, 6, 9};
 static __constant__ uint8_t kPathMask4_3[24] = {7, 11, 7, 13, 11, 13, 7, 11, 7, 14, 11, 14, 7, 13, 7, 14, 13, 14, 11, 13, 11, 14, 13, 14};
 static __constant__ uint16_t kPathBlk4_3[72] = {2052, 11284, 3616, 4102, 13336, 5672, 1026, 3092, 3632, 4102, 14364, 6712, 1026, 5144, 5696, 2052, 6172, 6728, 2052, 10764, 3664, 4102, 12816, 5720, 512, 2572, 3632, 4102, 14364, 7264, 512, 4624, 5696, 2052, 6172, 7272, 1026, 9736, 3664, 4102, 12816, 6768, 512, 1544, 3616, 4102, 13336, 7288, 512, 4624, 6728, 1026, 5144, 7272, 1026, 9736, 5720, 2052, 10764, 6768, 512, 1544, 5672, 2052, 11284, 7288, 512, 2572, 6712, 1026, 3092, 7264};
 static __constant__ uint8_t kPathFirst4_3[12] = {0, 2, 4, 6, 8, 10, 12, 14, 16, 18, 20, 22};
+static __constant__ uint8_t kL3Pair4[24] = {3, 5, 1, 4, 0, 2, 9, 11, 7, 10, 6, 8, 15, 17, 13, 16, 12, 14, 21, 23, 19, 22, 18, 20};
+static __constant__ uint8_t kL3Miss4[12] = {1, 2, 3, 0, 2, 3, 0, 1, 3, 0, 1, 2};
 static __constant__ uint8_t kFinalSigma4[24] = {23, 17, 21, 11, 15, 9, 22, 16, 19, 5, 13, 3, 20, 10, 18, 4, 7, 1, 14, 8, 12, 2, 6, 0};
 static __constant__ uint16_t kFinalBlk4[96] = {4102, 14364, 7264, 16000, 2052, 6172, 7272, 16016, 4102, 13336, 7288, 16032, 1026, 5144, 7272, 16048, 2052, 11284, 7288, 16064, 1026, 3092, 7264, 16080, 4102, 14364, 6712, 16096, 2052, 6172, 6728, 16112, 4102, 12816, 6768, 16128, 512, 4624, 6728, 7888, 2052, 10764, 6768, 16144, 512, 2572, 6712, 7856, 4102, 13336, 5672, 16160, 1026, 5144, 5696, 7952, 4102, 12816, 5720, 16176, 512, 4624, 5696, 7872, 1026, 9736, 5720, 7920, 512, 1544, 5672, 7824, 2052, 11284, 3616, 7984, 1026, 3092, 3632, 7936, 2052, 10764, 3664, 7968, 512, 2572, 3632, 7840, 1026, 9736, 3664, 7904, 512, 1544, 3616, 7808};
 template <> struct Paths<4> {

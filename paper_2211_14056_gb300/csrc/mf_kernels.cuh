@@ -397,6 +397,73 @@ __device__ __forceinline__ float colour_sum_tc(const float* J, int group) {
   return mine;
 }
 
+// The last level of the quark line for one completion: J_sigma for both top
+// helicities of the level-(NG-1) path `path`, R[l] the path's level-l currents.
+template <int NG, typename T>
+__device__ __forceinline__ void final_amplitudes(int path, const S4<T> (&R)[NG], const LaneCtx<T>& cx) {
+  using PT = Paths<NG>;
+  S4<T> W = apply(make_slash(lane_block<NG, T>(cx, PT::final_blk(path, 0))), R[NG - 1]);
+#pragma unroll
+  for (int m = 1; m < NG; ++m)
+    apply_acc(make_slash(lane_block<NG, T>(cx, PT::final_blk(path, m))), R[NG - 1 - m], W);
+  const int sig = PT::final_sigma(path);
+  const cplx<T> j0 = rowdot(cx.ub0, W), j1 = rowdot(cx.ub1, W);
+  cx.J[(sig * 2 + 0) * kJStride<T>] = j0.r;
+  cx.J[(sig * 2 + 0) * kJStride<T> + kJPlane<NG, T>] = j0.i;
+  cx.J[(sig * 2 + 1) * kJStride<T>] = j1.r;
+  cx.J[(sig * 2 + 1) * kJStride<T> + kJPlane<NG, T>] = j1.i;
+}
+
+// The quark line of four gluons with the three-gluon currents shared by lane
+// pairs.  R(S) for S = (a, b, c) does not depend on the helicity of the gluon g
+// missing from S, so lanes l and l ^ (1 << g) need the same R(S) for both
+// paths (a, b, c) and (b, a, c): each computes one, the partner's arrives by a
+// shuffle.  Order: last gluon c (its level-1 current in registers), then the
+// missing gluon g; the two-gluon currents come from the shared store.
+template <typename T>
+__device__ __forceinline__ void quark_walk_paired4(const S4<T>& v, const LaneCtx<T>& cx, unsigned H) {
+  using PT = Paths<4>;
+  constexpr int NR2 = WarpMem<4, T>::NR2;
+  auto load_r2 = [&](int p2) {
+    const uint8_t m2 = PT::template mask<2>(p2);
+    const int idx = p2 * 8 + int((unsigned(cx.pk >> (4 * m2)) & 15u) | (cx.ltb << 2));
+    S4<T> r;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.c[k] = cx.R2[k * NR2 + idx];
+    return r;
+  };
+#pragma unroll 1
+  for (int c = 0; c < 4; ++c) {
+    S4<T> R[4];
+    R[0] = v;
+    const uint8_t m1 = PT::template mask<1>(c);
+    R[1] = quark_prop_f(cx.Ptab[m1], cx.m, cx.qf[m1],
+                        apply(make_slash(lane_block<4, T>(cx, PT::template blk<1>(c, 0))), v));
+#pragma unroll 1
+    for (int gi = 0; gi < 3; ++gi) {
+      const int g = kL3Miss4[c * 3 + gi];
+      const unsigned bit = (H >> g) & 1u;
+      const int mine = kL3Pair4[(c * 3 + gi) * 2 + bit], other = kL3Pair4[(c * 3 + gi) * 2 + (bit ^ 1u)];
+      R[2] = load_r2(mine >> 1);
+      S4<T> X = apply(make_slash(lane_block<4, T>(cx, PT::template blk<3>(mine, 0))), R[2]);
+      apply_acc(make_slash(lane_block<4, T>(cx, PT::template blk<3>(mine, 1))), R[1], X);
+      apply_acc(make_slash(lane_block<4, T>(cx, PT::template blk<3>(mine, 2))), v, X);
+      const uint8_t m3 = PT::template mask<3>(mine);
+      R[3] = quark_prop_f(cx.Ptab[m3], cx.m, cx.qf[m3], X);
+      S4<T> Ro;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        Ro.c[k].r = __shfl_xor_sync(0xffffffffu, R[3].c[k].r, 1 << g);
+        Ro.c[k].i = __shfl_xor_sync(0xffffffffu, R[3].c[k].i, 1 << g);
+      }
+      final_amplitudes<4, T>(mine, R, cx);
+      R[2] = load_r2(other >> 1);
+      R[3] = Ro;
+      final_amplitudes<4, T>(other, R, cx);
+    }
+  }
+}
+
 // |M|^2 (without the normalisation MeParams::norm) of one event, computed by
 // its lane group; p: physical momenta in MadGraph order; wm: this warp's
 // shared memory (WarpMem layout); tc: colour sum on the tensor cores (FP32
@@ -492,7 +559,11 @@ __device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* w
   cx.ltb = unsigned((gl >> NG) & 1);
   S4<T> R[NG];
   R[0] = v_out(qtb, mt, ltb);
-  quark_walk<NG, 1, T>(0, R, cx);
+  if constexpr (NG == 4 && kShareSuffixes<T>) {
+    quark_walk_paired4<T>(R[0], cx, H);
+  } else {
+    quark_walk<NG, 1, T>(0, R, cx);
+  }
   if constexpr (std::is_same<T, float>::value) {
     if (tc) {
       __syncwarp();   // every lane's J is in shared memory

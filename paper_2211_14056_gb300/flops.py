@@ -78,6 +78,8 @@ def lane_flops(ng):
         if l == 2 and ng >= 3:
             continue
         count = math.factorial(ng) // math.factorial(ng - l)
+        if ng == 4 and l == 3:
+            count //= 2      # shared by the lane pair that differs in the missing gluon's helicity
         total += count * (APPLY + (l - 1) * APPLY_ACC + l * SLASH + 4 * l + QPROP)
     # colour-ordered amplitudes, both top helicities
     total += math.factorial(ng) * (APPLY + (ng - 1) * APPLY_ACC + ng * SLASH + 2 * ROWDOT)

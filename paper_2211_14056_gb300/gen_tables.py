@@ -212,6 +212,21 @@ def emit_lane(n, lines, colour):
         lines.append(f"static __constant__ uint8_t kPathFirst{n}_{l}[{len(firsts)}] = {{{', '.join(map(str, firsts))}}};")
     fsig = [o for (o, _) in final]
     frefs = [_pack(i, sg, bl, off) for (_, r) in final for (i, sg) in r]
+    if n == 4:
+        # level-3 paths (a, b, c) paired by their missing gluon g: for every last
+        # gluon c and every g != c, the two paths over {a, b} = rest \ {c, g};
+        # lanes that differ only in g's helicity share both currents
+        pair, miss = [], []
+        for c in range(n):
+            for g in range(n):
+                if g == c:
+                    continue
+                two = [k for k, (T, _, _) in enumerate(levels[3]) if T[-1] == c and g not in T]
+                assert len(two) == 2
+                pair += two
+                miss.append(g)
+        lines.append(f"static __constant__ uint8_t kL3Pair{n}[{len(pair)}] = {{{', '.join(map(str, pair))}}};")
+        lines.append(f"static __constant__ uint8_t kL3Miss{n}[{len(miss)}] = {{{', '.join(map(str, miss))}}};")
     lines.append(f"static __constant__ uint8_t kFinalSigma{n}[{len(fsig)}] = {{{', '.join(map(str, fsig))}}};")
     lines.append(f"static __constant__ uint16_t kFinalBlk{n}[{len(frefs)}] = {{{', '.join(map(str, frefs))}}};")
     lines.append(f"template <> struct Paths<{n}> {{")
