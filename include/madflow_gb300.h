@@ -60,6 +60,12 @@ typedef int mf_status;
  * ubar); average 1/36.  Not covered: MF_FP32_TC, mf_grad and
  * mf_vegas_accumulate_static (MF_ERR_UNSUPPORTED). */
 #define MF_PROC_UUX_TTXGG 4
+/* e+ e- -> mu+ mu-: QED, one s-channel photon diagram (Feynman gauge),
+ * massless leptons, 16 helicities, average 1/4, no colour (n_flow = 1, the
+ * 1 x 1 matrix 1).  Fixed partonic energy only (lumi = 0), no cuts apply (no
+ * final gluons); coupling e_qed.  Not covered: MF_FP32_TC, mf_grad and
+ * mf_vegas_accumulate_static (MF_ERR_UNSUPPORTED). */
+#define MF_PROC_EE_MUMU 5
 
 /* arithmetic of the matrix element */
 #define MF_FP64 0      /* everything in FP64 */
@@ -75,7 +81,8 @@ typedef struct mf_grid mf_grid;
 typedef struct {
   int process_id;              /* MF_PROC_* */
   int n_ext;                   /* external particles: 4, 5 or 6, must match the process */
-  const double* masses;        /* host [n_ext] GeV: 0, 0, m_t, m_t, 0...; the two top masses must agree */
+  const double* masses;        /* host [n_ext] GeV: 0, 0, m_t, m_t, 0...; the two top masses must agree;
+                                  all 0 for MF_PROC_EE_MUMU */
   double top_width;            /* Gamma_t >= 0 in the internal top propagators */
   double g_s;                  /* strong coupling (fixed, no running) */
   int n_flow;                  /* colour flows: (n_ext-2)! for g g processes, 12 for u ubar -> t tbar g g */
@@ -87,6 +94,7 @@ typedef struct {
   double pt_cut_g;             /* final-gluon pT threshold (0 disables) */
   double dr_cut_gg;            /* final-gluon pair Delta R threshold (0 disables) */
   int precision;               /* MF_FP64, MF_FP32 or MF_FP32_TC */
+  double e_qed;                /* electromagnetic coupling e = sqrt(4 pi alpha) (MF_PROC_EE_MUMU only) */
 } mf_process_desc;
 
 /* Result of one Vegas iteration and of the combination of every iteration

@@ -6,6 +6,7 @@ ctypes (PyTorch tensors supply device memory and streams).  There is no CPU
 fallback: importing the binding without the built library raises.
 """
 from .binding import (  # noqa: F401
-    MF_FP32, MF_FP32_TC, MF_FP64, MF_PROC_GG_TTX, MF_PROC_GG_TTXG, MF_PROC_GG_TTXGG, MF_PROC_UUX_TTXGG,
+    MF_FP32, MF_FP32_TC, MF_FP64, MF_PROC_EE_MUMU, MF_PROC_GG_TTX, MF_PROC_GG_TTXG, MF_PROC_GG_TTXGG,
+    MF_PROC_UUX_TTXGG,
     Grid, MFError, Mixed, Process, fma_throughput, kernel_launches, library_path, load_library,
 )

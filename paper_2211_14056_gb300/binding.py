@@ -16,10 +16,11 @@ _LIB_PATH = os.path.join(HERE, "lib", "libmadflow_gb300.so")
 
 MF_OK, MF_ERR_ARG, MF_ERR_CUDA, MF_ERR_UNSUPPORTED, MF_ERR_COLOUR, MF_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 MF_WARN_NEWTON = 1
-MF_PROC_GG_TTX, MF_PROC_GG_TTXG, MF_PROC_GG_TTXGG, MF_PROC_UUX_TTXGG = 1, 2, 3, 4
+MF_PROC_GG_TTX, MF_PROC_GG_TTXG, MF_PROC_GG_TTXGG, MF_PROC_UUX_TTXGG, MF_PROC_EE_MUMU = 1, 2, 3, 4, 5
 MF_FP64, MF_FP32, MF_FP32_TC = 0, 1, 2
 
-_NGLUON = {MF_PROC_GG_TTX: 2, MF_PROC_GG_TTXG: 3, MF_PROC_GG_TTXGG: 4, MF_PROC_UUX_TTXGG: 4}
+_NGLUON = {MF_PROC_GG_TTX: 2, MF_PROC_GG_TTXG: 3, MF_PROC_GG_TTXGG: 4, MF_PROC_UUX_TTXGG: 4, MF_PROC_EE_MUMU: 2}
+ALPHA_EM = 1.0 / 137.035999     # Thomson limit; e = sqrt(4 pi alpha)
 
 
 class MFError(RuntimeError):
@@ -35,6 +36,7 @@ class ProcessDesc(C.Structure):
         ("colour_num", C.POINTER(C.c_int64)), ("colour_den", C.c_int64), ("sqrt_s", C.c_double),
         ("lumi", C.c_int), ("lumi_N", C.c_double), ("lumi_a", C.c_double), ("lumi_b", C.c_double),
         ("pt_cut_g", C.c_double), ("dr_cut_gg", C.c_double), ("precision", C.c_int),
+        ("e_qed", C.c_double),
     ]
 
 
@@ -161,14 +163,21 @@ class Process:
 
     def __init__(self, process_id, mt=173.0, wt=0.0, gs=1.2177, sqrt_s=1000.0, lumi=False,
                  lumi_N=1.0, lumi_a=-1.1, lumi_b=5.0, pt_cut=0.0, dr_cut=0.0, precision=MF_FP64,
-                 colour=None):
+                 colour=None, e_qed=None, masses=None):
         lib = load_library()
         ng = _NGLUON.get(process_id)
         if ng is None:
             raise MFError(MF_ERR_UNSUPPORTED, "unknown process id")
         self.ngluons, self.n_ext = ng, ng + 2
-        masses = (C.c_double * self.n_ext)(*([0.0, 0.0, mt, mt] + [0.0] * (ng - 2)))
-        if process_id == MF_PROC_UUX_TTXGG:
+        if masses is None:
+            masses = [0.0] * 4 if process_id == MF_PROC_EE_MUMU else [0.0, 0.0, mt, mt] + [0.0] * (ng - 2)
+        masses = (C.c_double * self.n_ext)(*masses)
+        if e_qed is None:
+            e_qed = math.sqrt(4 * math.pi * ALPHA_EM)
+        if process_id == MF_PROC_EE_MUMU:
+            num, den = colour if colour is not None else ([1], 1)
+            nflow = 1
+        elif process_id == MF_PROC_UUX_TTXGG:
             num, den = colour if colour is not None else colour_matrix_uux()
             nflow = 12
         else:
@@ -176,7 +185,7 @@ class Process:
             nflow = math.factorial(ng)
         cnum = (C.c_int64 * len(num))(*num)
         d = ProcessDesc(process_id, self.n_ext, masses, wt, gs, nflow, cnum, den, sqrt_s,
-                        1 if lumi else 0, lumi_N, lumi_a, lumi_b, pt_cut, dr_cut, precision)
+                        1 if lumi else 0, lumi_N, lumi_a, lumi_b, pt_cut, dr_cut, precision, e_qed)
         h = C.c_void_p()
         _check(lib.mf_init_process(C.byref(d), C.byref(h)))
         self._h = h

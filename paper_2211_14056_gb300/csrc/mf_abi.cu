@@ -46,12 +46,16 @@ int factorial(int n) { return n <= 1 ? 1 : n * factorial(n - 1); }
 // in FP32, ~160 B/event in FP64)
 constexpr int64_t kRecordChunk = int64_t(1) << 20;
 
+// colourless process: the 1 x 1 matrix 1
+const int kNoColour[1] = {1};
+
 const int* lib_colour(int key, int* den) {
   switch (key) {
     case 2: *den = kColourDen2; return kColourNum2;
     case 3: *den = kColourDen3; return kColourNum3;
     case 4: *den = kColourDen4; return kColourNum4;
     case mf::detail::kUuxKey: *den = kUuxColourDen; return kUuxColourNum;
+    case mf::detail::kEeKey: *den = 1; return kNoColour;
   }
   return nullptr;
 }
@@ -67,6 +71,7 @@ cudaError_t dispatch_acc_config(int ng, int prec, int ndim, int nbins, size_t* s
     case 3: return me_acc_config<3>(p, ndim, nbins, smem, ctas);
     case 4: return me_acc_config<4>(p, ndim, nbins, smem, ctas);
     case kUuxKey: return uux_acc_config(p, ndim, nbins, smem, ctas);
+    case kEeKey: return ee_acc_config(p, ndim, nbins, smem, ctas);
   }
   return cudaErrorInvalidValue;
 }
@@ -97,6 +102,7 @@ cudaError_t dispatch_me_config(int ng, int prec, size_t* smem, int* ctas) {
     case 3: return me_config<3>(p, smem, ctas);
     case 4: return me_config<4>(p, smem, ctas);
     case mf::detail::kUuxKey: return uux_me_config(p, smem, ctas);
+    case mf::detail::kEeKey: return ee_me_config(p, smem, ctas);
   }
   return cudaErrorInvalidValue;
 }
@@ -161,25 +167,33 @@ mf_status mf_init_process(const mf_process_desc* d, mf_process** out) {
     case MF_PROC_GG_TTXG: ng = 3; break;
     case MF_PROC_GG_TTXGG: ng = 4; break;
     case MF_PROC_UUX_TTXGG: ng = 4; kind = 1; break;
+    case MF_PROC_EE_MUMU: ng = 2; kind = 2; break;
     default: return fail(MF_ERR_UNSUPPORTED, "mf_init_process: unknown process_id");
   }
-  const int key = kind == 1 ? kUuxKey : ng;
-  const int nflow = kind == 1 ? kUuxFlows : factorial(ng);
+  const bool qed = kind == 2;
+  const int key = kind == 1 ? kUuxKey : qed ? kEeKey : ng;
+  const int nflow = kind == 1 ? kUuxFlows : qed ? 1 : factorial(ng);
   if (d->n_ext != ng + 2) return fail(MF_ERR_ARG, "mf_init_process: n_ext does not match the process");
   if (d->masses == nullptr) return fail(MF_ERR_ARG, "mf_init_process: masses is null");
-  const double mt = d->masses[2];
+  const double mt = qed ? 0.0 : d->masses[2];
   for (int i = 0; i < d->n_ext; ++i) {
-    const bool top = (i == 2 || i == 3);
+    const bool top = !qed && (i == 2 || i == 3);
     if (!std::isfinite(d->masses[i]) || (top ? !(d->masses[i] > 0) : d->masses[i] != 0.0))
-      return fail(MF_ERR_ARG, "mf_init_process: masses must be (0, 0, m_t, m_t, 0, ...) with m_t > 0");
+      return fail(MF_ERR_ARG, qed ? "mf_init_process: the leptons of e+ e- -> mu+ mu- are massless"
+                                  : "mf_init_process: masses must be (0, 0, m_t, m_t, 0, ...) with m_t > 0");
   }
-  if (d->masses[3] != mt) return fail(MF_ERR_ARG, "mf_init_process: top and antitop masses differ");
+  if (d->masses[3] != d->masses[2]) return fail(MF_ERR_ARG, "mf_init_process: top and antitop masses differ");
   if (!(d->top_width >= 0) || !std::isfinite(d->top_width)) return fail(MF_ERR_ARG, "mf_init_process: bad top_width");
-  if (!(d->g_s > 0) || !std::isfinite(d->g_s)) return fail(MF_ERR_ARG, "mf_init_process: bad g_s");
+  if (qed) {
+    if (!(d->e_qed > 0) || !std::isfinite(d->e_qed)) return fail(MF_ERR_ARG, "mf_init_process: bad e_qed");
+    if (d->lumi != 0) return fail(MF_ERR_ARG, "mf_init_process: e+ e- -> mu+ mu- runs at a fixed energy (lumi = 0)");
+  } else if (!(d->g_s > 0) || !std::isfinite(d->g_s)) {
+    return fail(MF_ERR_ARG, "mf_init_process: bad g_s");
+  }
   if (d->precision != MF_FP64 && d->precision != MF_FP32 && d->precision != MF_FP32_TC)
     return fail(MF_ERR_ARG, "mf_init_process: bad precision");
   // colour matrix: must be the library's exact trace-basis matrix
-  if (kind == 1 && d->precision == MF_FP32_TC)
+  if (kind != 0 && d->precision == MF_FP32_TC)
     return fail(MF_ERR_UNSUPPORTED, "mf_init_process: the tensor-core colour sum covers the gluon-initiated processes");
   if (d->n_flow != nflow) return fail(MF_ERR_COLOUR, "mf_init_process: n_flow does not match the process's colour basis");
   if (d->colour_num == nullptr || d->colour_den <= 0) return fail(MF_ERR_COLOUR, "mf_init_process: colour matrix missing");
@@ -196,7 +210,8 @@ mf_status mf_init_process(const mf_process_desc* d, mf_process** out) {
       if (std::abs(lnum[a * nf + b]) > 2048)
         return fail(MF_ERR_COLOUR, "mf_init_process: scaled colour matrix is not TF32-exact");
     }
-  if (!(d->sqrt_s > 2 * mt) || !std::isfinite(d->sqrt_s)) return fail(MF_ERR_ARG, "mf_init_process: sqrt_s must exceed 2 m_t");
+  if (!(d->sqrt_s > 2 * mt) || !std::isfinite(d->sqrt_s))
+    return fail(MF_ERR_ARG, qed ? "mf_init_process: sqrt_s must be > 0" : "mf_init_process: sqrt_s must exceed 2 m_t");
   if (d->lumi != 0 && d->lumi != 1) return fail(MF_ERR_ARG, "mf_init_process: lumi must be 0 or 1");
   if (d->lumi && !(d->lumi_N > 0 && d->lumi_b >= 0 && std::isfinite(d->lumi_a)))
     return fail(MF_ERR_ARG, "mf_init_process: bad luminosity parameters");
@@ -206,7 +221,7 @@ mf_status mf_init_process(const mf_process_desc* d, mf_process** out) {
   p->ng = ng;
   p->kind = kind;
   p->precision = d->precision;
-  const int n = ng;   // final-state particles: t, tbar and ng - 2 gluons
+  const int n = ng;   // final-state particles: t, tbar and ng - 2 gluons (mu-, mu+ for e+ e-)
   p->ndim = 3 * n - 4 + (d->lumi ? 2 : 0);
   SampleParams& sp = p->sp;
   sp.n_final = n;
@@ -226,13 +241,13 @@ mf_status mf_init_process(const mf_process_desc* d, mf_process** out) {
   sp.phi_const = std::pow(2 * pi, 4 - 3 * n) * std::pow(pi / 2, n - 1) / (factorial(n - 1) * factorial(n - 2));
   MeParams& mp = p->mp;
   mp.mt = mt;
-  mp.mw = mt * d->top_width;
+  mp.mw = qed ? 0.0 : mt * d->top_width;
   mp.colour_tc = d->precision == MF_FP32_TC ? 1 : 0;
   p->g_s = d->g_s;
   p->width = d->top_width;
   const int sid = factorial(ng - 2);        // identical final-state gluons
-  const double average = kind == 1 ? 36.0 : 256.0;   // spin x colour states of u u~ or g g
-  mp.norm = std::pow(d->g_s, 2 * ng) / (average * sid * lden);
+  const double average = kind == 1 ? 36.0 : qed ? 4.0 : 256.0;   // spin x colour states of u u~, e+ e- or g g
+  mp.norm = qed ? std::pow(d->e_qed, 4) / average : std::pow(d->g_s, 2 * ng) / (average * sid * lden);
 
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -364,13 +379,14 @@ mf_status mf_matrix_element(mf_process* p, int64_t n, const double* momenta, dou
   if (p == nullptr || n < 0) return fail(MF_ERR_ARG, "mf_matrix_element: bad argument");
   if (n == 0) return MF_OK;
   if (momenta == nullptr || me2 == nullptr) return fail(MF_ERR_ARG, "mf_matrix_element: null buffer");
-  const int epb = p->kind == 1 ? kWarps : kWarps * (32 / (2 << p->ng));   // events per CTA pass
+  const int epb = p->kind == 1 ? kWarps : p->kind == 2 ? kThreads : kWarps * (32 / (2 << p->ng));   // events per CTA pass
   const int64_t need = (n + epb - 1) / epb;
   const int64_t cap = int64_t(p->sms) * effective_ctas(p, p->me_ctas);
   const int grid = int(need < cap ? need : cap);
   cudaError_t e;
   switch (proc_key(p)) {
     case kUuxKey: e = launch_matrix_element_uux(p->precision == MF_FP64 ? 0 : 1, p->mp, n, momenta, me2, grid, (cudaStream_t)stream); break;
+    case kEeKey: e = launch_matrix_element_ee(p->precision == MF_FP64 ? 0 : 1, p->mp, n, momenta, me2, grid, (cudaStream_t)stream); break;
     case 2: e = launch_matrix_element<2>(p->precision == MF_FP64 ? 0 : 1, p->mp, n, momenta, me2, grid, (cudaStream_t)stream); break;
     case 3: e = launch_matrix_element<3>(p->precision == MF_FP64 ? 0 : 1, p->mp, n, momenta, me2, grid, (cudaStream_t)stream); break;
     default: e = launch_matrix_element<4>(p->precision == MF_FP64 ? 0 : 1, p->mp, n, momenta, me2, grid, (cudaStream_t)stream); break;
@@ -412,6 +428,7 @@ mf_status mf_vegas_accumulate(mf_process* p, mf_grid* g, uint64_t seed, int iter
     cudaError_t e;
     switch (proc_key(p)) {
       case kUuxKey: e = launch_chunk_uux(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
+      case kEeKey: e = launch_chunk_ee(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
       case 2: e = launch_chunk<2>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
       case 3: e = launch_chunk<3>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
       default: e = launch_chunk<4>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;

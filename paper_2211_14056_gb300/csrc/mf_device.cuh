@@ -200,8 +200,10 @@ __device__ __forceinline__ void o4_add(const V4<T>& GL, const V4<T>& GM, const V
 template <typename T>
 __device__ __forceinline__ void helicity_chi(const R4<T>& p, int lam, cplx<T>& c0, cplx<T>& c1) {
   const T px = p.v[1], py = p.v[2], pz = p.v[3];
-  const T pa = sqrt(fma(px, px, fma(py, py, pz * pz)));
-  const T s = pa + pz;
+  const T pt2 = fma(px, px, py * py);
+  const T pa = sqrt(fma(pz, pz, pt2));
+  // |p| + pz, free of cancellation for pz < 0: pt^2 / (|p| - pz)
+  const T s = pz >= T(0) ? pa + pz : pt2 / (pa - pz);
   if (pa == T(0)) {
     c0 = {lam > 0 ? T(1) : T(0), T(0)};
     c1 = {lam > 0 ? T(0) : T(1), T(0)};

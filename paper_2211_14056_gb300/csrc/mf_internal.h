@@ -32,7 +32,8 @@ struct mf_process {
   size_t me_smem = 0;
   int ctas_override = 0;
   double g_s = 0.0, width = 0.0;   // strong coupling and top width of the descriptor
-  int kind = 0;                    // 0: g g -> t t~ + gluons (ng = n_final), 1: u u~ -> t t~ g g
+  int kind = 0;                    // 0: g g -> t t~ + gluons (ng = n_final), 1: u u~ -> t t~ g g,
+                                   // 2: e+ e- -> mu+ mu- (ng = n_final = 2)
 };
 
 struct mf_grid {
@@ -70,11 +71,24 @@ cudaError_t launch_chunk_uux(int precision, const SampleParams& sp, const MePara
                              int64_t first_event, int64_t n, int64_t C, void* rec_base, uint64_t seed, int iter,
                              int accumulate, double* partials, unsigned long long* counters, double* w_out, int grid,
                              cudaStream_t s, cudaEvent_t* ev);
+// e+ e- -> mu+ mu- (mf_kernels_ee.cu)
+cudaError_t ee_me_config(int precision, size_t* smem, int* ctas);
+cudaError_t ee_acc_config(int precision, int ndim, int nbins, size_t* smem, int* ctas);
+cudaError_t launch_matrix_element_ee(int precision, const MeParams& mp, int64_t n, const double* mom, double* out,
+                                     int grid, cudaStream_t s);
+cudaError_t launch_me_acc_ee(int precision, const MeParams& mp, int n_final, int ndim, int nbins, void* rec_base,
+                             int64_t C, int accumulate, double* partials, unsigned long long* counters, double* w_out,
+                             int grid, cudaStream_t s);
+cudaError_t launch_chunk_ee(int precision, const SampleParams& sp, const MeParams& mp, const double* edges,
+                            int64_t first_event, int64_t n, int64_t C, void* rec_base, uint64_t seed, int iter,
+                            int accumulate, double* partials, unsigned long long* counters, double* w_out, int grid,
+                            cudaStream_t s, cudaEvent_t* ev);
 namespace detail {
 // Kernel-selection key of a process: the gluon count of the gluon-initiated
-// processes, kUuxKey for u u~ -> t t~ g g.
+// processes, kUuxKey for u u~ -> t t~ g g, kEeKey for e+ e- -> mu+ mu-.
 constexpr int kUuxKey = 100;
-inline int proc_key(const mf_process* p) { return p->kind == 1 ? kUuxKey : p->ng; }
+constexpr int kEeKey = 200;
+inline int proc_key(const mf_process* p) { return p->kind == 1 ? kUuxKey : p->kind == 2 ? kEeKey : p->ng; }
 // Record one iteration's device result (sum w, sum w^2, I_k, sigma_k^2, passing
 // events, Newton misses) on the grid and fill *out with it and the running
 // inverse-variance combination.

@@ -251,6 +251,8 @@ cudaError_t launch_acc_dispatch(int key, int prec, const MeParams& mp, int n_fin
                                 cudaStream_t s) {
   if (key == kUuxKey)
     return launch_me_acc_uux(prec, mp, n_final, ndim, nbins, rec, C, accumulate, partials, counters, nullptr, grid, s);
+  if (key == kEeKey)
+    return launch_me_acc_ee(prec, mp, n_final, ndim, nbins, rec, C, accumulate, partials, counters, nullptr, grid, s);
   switch (key) {
     case 2: return launch_me_acc<2>(prec, mp, n_final, ndim, nbins, rec, C, accumulate, partials, counters, nullptr, grid, s);
     case 3: return launch_me_acc<3>(prec, mp, n_final, ndim, nbins, rec, C, accumulate, partials, counters, nullptr, grid, s);
@@ -330,15 +332,15 @@ mf_status enqueue(mf_mixed* m, int refine, cudaStream_t s) {
     }
   } else {
     // the shared queue covers the gluon-initiated processes; u u~ -> t t~ g g
-    // runs its own kernel on the queue's CTA count, adding to the partials
-    // the queue kernel zeroed
+    // and e+ e- -> mu+ mu- run their own kernels on the queue's CTA count,
+    // adding to the partials the queue kernel zeroed
     for (int k = 0; k < m->nproc; ++k) {
       const mf_process* p = m->procs[k];
       if (p->kind == 0) continue;
       mf_grid* g = m->grids[k];
       MF_CUDA(launch_acc_dispatch(proc_key(p), m->precision, p->mp, p->sp.n_final, g->ndim, g->nbins, g->d_records,
                                   g->chunk, 1, g->d_partials, g->d_counters, grid, s),
-              "mf_mixed (u u~ kernel)");
+              "mf_mixed (own kernel)");
       count_launches(1);
     }
   }

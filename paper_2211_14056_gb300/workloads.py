@@ -8,7 +8,7 @@ luminosity f(x) = x^-1.1 (1-x)^5 at sqrt(S) = 13 TeV for the 2 -> 3 and
 luminosity uniforms (if any), then the RAMBO uniforms.
 """
 
-PROCESS_IDS = {"gg_ttx": 1, "gg_ttxg": 2, "gg_ttxgg": 3, "uux_ttxgg": 4}
+PROCESS_IDS = {"gg_ttx": 1, "gg_ttxg": 2, "gg_ttxgg": 3, "uux_ttxgg": 4, "epem_mupmum": 5}
 
 WORKLOADS = {
     # g g -> t tbar at fixed sqrt(s) = 1 TeV: closed-form target, FP64
@@ -23,6 +23,10 @@ WORKLOADS = {
     # u u~ -> t t~ g g with the g g -> t t~ g g set-up (the luminosity serves u and u~)
     "uux_ttxgg_13tev": dict(process="uux_ttxgg", mt=173.0, wt=1.5, gs=1.2177, sqrt_s=13000.0, lumi=True,
                             pt_cut=30.0, dr_cut=0.4, events=10_000, iterations=5, seed=5),
+    # e+ e- -> mu+ mu- (QED, photon exchange) at a fixed sqrt(s) = 100 GeV: closed-form
+    # |M|^2 = e^4 (1 + cos^2 theta) and sigma = 4 pi alpha^2 / (3 s); mt and gs are unused
+    "epem_mupmum_100gev": dict(process="epem_mupmum", mt=0.0, wt=0.0, gs=1.2177, sqrt_s=100.0, lumi=False,
+                               pt_cut=0.0, dr_cut=0.0, events=2 ** 20, iterations=5, seed=6),
 }
 
 

@@ -145,3 +145,25 @@ def test_uux_colour_matrix_against_oracle_brute_force():
             tens.append(t)
     ref = np.array([[np.vdot(a, b).real for b in tens] for a in tens])
     np.testing.assert_allclose(np.array(M) / D, ref, atol=1e-12)
+
+
+def test_ee_description_checks_without_device(lib):
+    from paper_2211_14056_gb300 import binding as B
+    h = C.c_void_p()
+    masses = (C.c_double * 4)(0, 0, 0, 0)
+    one = (C.c_int64 * 1)(1)
+    base = dict(process_id=B.MF_PROC_EE_MUMU, n_ext=4, masses=masses, top_width=0.0, g_s=1.2, n_flow=1,
+                colour_num=one, colour_den=1, sqrt_s=100.0, lumi=0, lumi_N=1, lumi_a=-1.1, lumi_b=5,
+                pt_cut_g=0, dr_cut_gg=0, precision=0, e_qed=0.3)
+    two = (C.c_int64 * 1)(2)
+    massive = (C.c_double * 4)(0, 0, 0.105, 0.105)
+    for change, status in [(dict(masses=massive), B.MF_ERR_ARG),
+                           (dict(lumi=1), B.MF_ERR_ARG),
+                           (dict(e_qed=0.0), B.MF_ERR_ARG),
+                           (dict(sqrt_s=0.0), B.MF_ERR_ARG),
+                           (dict(n_ext=5), B.MF_ERR_ARG),
+                           (dict(precision=2), B.MF_ERR_UNSUPPORTED),
+                           (dict(n_flow=2), B.MF_ERR_COLOUR),
+                           (dict(colour_num=two), B.MF_ERR_COLOUR)]:
+        d = B.ProcessDesc(**{**base, **change})
+        assert lib.mf_init_process(C.byref(d), C.byref(h)) == status, change
