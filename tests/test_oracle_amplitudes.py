@@ -11,6 +11,8 @@
 * massless limit: the helicity configurations that must vanish do, and the
   MHV partial amplitudes follow the Parke-Taylor form |<f- j>^3 <f+ j>|^2 / prod|s|;
 * |M|^2 scales as g_s^(2 (n_ext - 2)).
+* helicity-flip symmetry at Gamma_t = 0: |M_h|^2 = |M_-h|^2 per helicity
+  configuration, and the per-helicity values of the two algorithms agree.
 """
 import itertools
 import math
@@ -182,3 +184,38 @@ def test_massless_helicity_selection_and_parke_taylor(name, nfin):
                 ratios.append(np.abs(Jh[si]) ** 2 / pt)
     ratios = np.array(ratios)
     np.testing.assert_allclose(ratios, ratios.flat[0], rtol=1e-10)
+
+
+def _per_helicity(proc, p):
+    """Colour-summed |M_h|^2 for every helicity configuration h, shape
+    (2,) * n_ext + (N,), from the Feynman-diagram terms with explicit colour."""
+    ext, q = proc.external(p)
+    K = proc.amp.amplitude_terms(ext, q)
+    c = proc.amp.colour_terms()
+    M = np.einsum("tc,th->ch", c, K.reshape(K.shape[0], -1))
+    per = np.sum(np.abs(M) ** 2, axis=0)
+    return per.reshape((2,) * len(proc.particles) + (p.shape[0],))
+
+
+@pytest.mark.parametrize("name,nfin,masses", [("gg_ttxg", 3, None), ("gg_ttxgg", 4, None),
+                                              ("uux_ttxgg", 4, None), ("epem_mupmum", 2, [0.0, 0.0])])
+def test_helicity_flip_symmetry(name, nfin, masses):
+    """At Gamma_t = 0 every tree amplitude here is built from real momenta,
+    real couplings and helicity states whose flipped counterparts are their
+    conjugates up to phases (parity followed by complex conjugation), so the
+    colour-summed |M|^2 of each helicity configuration equals that of the
+    configuration with every helicity reversed, event by event, also for the
+    non-planar 2 -> 3 and 2 -> 4 kinematics.  A phase or sign slip between the
+    two helicity states of any external wavefunction breaks it."""
+    proc = Process(name, wt=0.0)
+    p = points(nfin, 5, masses=masses, seed=8)
+    per = _per_helicity(proc, p)
+    flip = per[(slice(None, None, -1),) * len(proc.particles)]
+    scale = np.max(per.reshape(-1, p.shape[0]), axis=0)
+    assert np.max(np.abs(flip - per) / scale) < 1e-12
+    if name.startswith("gg"):
+        bg = QQbarGluons(proc)
+        J = bg.partial_amplitudes(p)
+        Jf = J.reshape(J.shape[0], -1, J.shape[-1])
+        perbg = np.real(np.einsum("shn,st,thn->hn", np.conj(Jf), bg.C, Jf)).reshape(per.shape)
+        np.testing.assert_allclose(perbg, per, rtol=0, atol=1e-12 * scale.max())
