@@ -211,9 +211,12 @@ mf_status mf_vegas_accumulate_static(mf_process* proc, const double* edges, int 
  *   dw_dy           device [ndim][n] FP64 or NULL: per-event dw/dy_j, the
  *                   derivative with respect to the Vegas uniform of
  *                   dimension j inside its bin.
- * Forward mode: every pass recomputes the kinematics and |M|^2 with two
- * tangent directions (dual numbers); pass 0 carries m_t and Gamma_t, each
- * further pass (only with dw_dy) two uniforms.  dI/dg_s is exact:
+ * Reverse mode: per chunk of events, the sampler runs with two tangents (m_t
+ * and y_0) and writes per-event records; the adjoint kernel recomputes every
+ * wavefunction, current and amplitude of |M|^2 and sweeps back once to
+ * d|M|^2/d(momenta, m_t, Gamma_t), which it contracts with the records'
+ * tangents and keeps per event; with dw_dy, further sampler-only passes
+ * carry two uniforms each and reuse the stored adjoint.  dI/dg_s is exact:
  * |M|^2 is proportional to g_s^(2 n_gluons).  Bins, cuts and the Newton
  * decision are piecewise constant and give no derivative, so dI/dtheta is
  * the derivative of the estimator at fixed uniforms, not of the integral
@@ -222,6 +225,13 @@ mf_status mf_vegas_accumulate_static(mf_process* proc, const double* edges, int 
  * the grid's scratch; synchronises the stream. */
 mf_status mf_grad(mf_process* proc, const mf_grid* grid, uint64_t seed, int iter, int64_t n, double* sigma,
                   double* dsigma, double* dw_dtheta, double* dw_dy, void* stream);
+
+/* The same derivatives in forward mode (the cross-check of mf_grad): every
+ * pass recomputes the kinematics and |M|^2 with dual numbers carrying two
+ * tangent directions; pass 0 carries m_t and Gamma_t, each further pass (only
+ * with dw_dy) two uniforms.  Same arguments, outputs and errors as mf_grad. */
+mf_status mf_grad_forward(mf_process* proc, const mf_grid* grid, uint64_t seed, int iter, int64_t n, double* sigma,
+                          double* dsigma, double* dw_dtheta, double* dw_dy, void* stream);
 
 /* Measurement utility: when enabled, mf_vegas_accumulate records CUDA events
  * around its per-chunk kernels (the iteration runs in chunks of 2^20 events:

@@ -85,6 +85,8 @@ EXPORTS = {
                                     C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p]),
     "mf_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_int64, C.POINTER(C.c_double),
                           C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mf_grad_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_int64, C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_void_p]),
     "mf_last_error": (C.c_char_p, []),
     "mf_kernel_launches": (C.c_int64, []),
 }
@@ -248,14 +250,16 @@ class Process:
             _ptr(totals, torch.float64, 2 + self.ndim * nbins + 2, "totals"),
             _ptr(weights, torch.float64, n, "weights"), _stream(stream)))
 
-    def grad(self, grid, seed, it, n, dw_dtheta=None, dw_dy=None, stream=None):
+    def grad(self, grid, seed, it, n, dw_dtheta=None, dw_dy=None, stream=None, forward=False):
         """sigma and [dsigma/dg_s, dsigma/dm_t, dsigma/dGamma_t] of iteration `it`
-        over events 0..n-1 (mf_grad); the optional device tensors receive the
-        per-event derivatives ([3, n] and [ndim, n], float64)."""
+        over events 0..n-1 (mf_grad, reverse mode; mf_grad_forward with
+        forward=True); the optional device tensors receive the per-event
+        derivatives ([3, n] and [ndim, n], float64)."""
         import torch
         sig = C.c_double()
         ds = (C.c_double * 3)()
-        _check(load_library().mf_grad(
+        fn = load_library().mf_grad_forward if forward else load_library().mf_grad
+        _check(fn(
             self._h, grid._h, seed, it, n, C.byref(sig), ds,
             _ptr(dw_dtheta, torch.float64, 3 * n, "dw_dtheta"), _ptr(dw_dy, torch.float64, self.ndim * n, "dw_dy"),
             _stream(stream)))

@@ -1,0 +1,563 @@
+// Reverse-mode derivative (adjoint) of one event's |M|^2 with respect to the
+// momenta, m_t and Gamma_t (arXiv:2211.14056, Sec. 2 notes that the device
+// operator has no derivative and that adding one is straightforward).
+//
+// One reverse sweep per event, recomputing instead of storing: the lane group
+// rebuilds the mask table and the gluon sub-currents G(B), every lane walks
+// its quark line to get its colour-ordered amplitudes J, the colour form gives
+// Jb = 2 norm C J, and the lanes walk the quark line again, depth first,
+// propagating adjoints from every amplitude back through the suffix currents
+// R(S) on the current path (held in registers with their adjoints) into the
+// adjoints of the sub-currents (accumulated in shared memory), of the
+// propagator momenta, m_t, Gamma_t and the external spinors.  The gluon
+// levels are then reversed from the longest blocks down to the polarisation
+// vectors.  Derivatives of the external wavefunctions and of the propagator
+// factors are taken locally (dual numbers over the few inputs of each) and
+// contracted with their adjoints.
+//
+// Convention: for the real result f and a complex intermediate z = x + i y,
+// zb = df/dx + i df/dy; then z = a w gives wb += conj(a) zb, and a real
+// parameter t with dz/dt = z' gets tb += Re(conj(z') zb).
+#pragma once
+#include "mf_kernels.cuh"
+
+namespace mf {
+
+// conj(a) * b and acc + conj(a) * b
+template <typename T> __device__ __forceinline__ cplx<T> cmulc(cplx<T> a, cplx<T> b) {
+  return {fma(a.r, b.r, a.i * b.i), fma(a.r, b.i, -(a.i * b.r))};
+}
+template <typename T> __device__ __forceinline__ cplx<T> cfmac(cplx<T> a, cplx<T> b, cplx<T> acc) {
+  return {fma(a.r, b.r, fma(a.i, b.i, acc.r)), fma(a.r, b.i, fma(-a.i, b.r, acc.i))};
+}
+// Re(conj(a) b)
+template <typename T> __device__ __forceinline__ T redot(cplx<T> a, cplx<T> b) { return fma(a.r, b.r, a.i * b.i); }
+
+// o = (G-slash) R: accumulate Gb and Rb from ob
+template <typename T>
+__device__ __forceinline__ void adj_apply(const V4<T>& G, const S4<T>& R, const S4<T>& ob, V4<T>& Gb, S4<T>& Rb) {
+  const Slash<T> s = make_slash(G);
+  Rb.c[0] = cfmac(s.a, ob.c[2], cfmac(s.c, ob.c[3], Rb.c[0]));
+  Rb.c[1] = cfmac(s.d, ob.c[2], cfmac(s.b, ob.c[3], Rb.c[1]));
+  Rb.c[2] = cfmac(s.b, ob.c[0], cfmac(-s.c, ob.c[1], Rb.c[2]));
+  Rb.c[3] = cfmac(-s.d, ob.c[0], cfmac(s.a, ob.c[1], Rb.c[3]));
+  const cplx<T> ab = cfmac(R.c[3], ob.c[1], cmulc(R.c[0], ob.c[2]));
+  const cplx<T> bb = cfmac(R.c[2], ob.c[0], cmulc(R.c[1], ob.c[3]));
+  const cplx<T> cb = cfmac(R.c[0], ob.c[3], -cmulc(R.c[2], ob.c[1]));
+  const cplx<T> db = cfmac(R.c[1], ob.c[2], -cmulc(R.c[3], ob.c[0]));
+  Gb.c[0] = Gb.c[0] + ab + bb;
+  Gb.c[3] = Gb.c[3] + ab - bb;
+  Gb.c[1] = Gb.c[1] + cb + db;
+  Gb.c[2] = Gb.c[2] + times_i(db - cb);
+}
+
+// o = f (P-slash + m) X (quark_prop_f): Xb, Pb, mb and fb from ob
+template <typename T>
+__device__ __forceinline__ void adj_prop(const R4<T>& P, T m, cplx<T> f, const S4<T>& X, const S4<T>& ob, S4<T>& Xb,
+                                         R4<T>& Pb, T& mb, cplx<T>& fb) {
+  const T a = P.v[0] + P.v[3], b = P.v[0] - P.v[3];
+  const cplx<T> c = {P.v[1], P.v[2]}, d = {P.v[1], -P.v[2]};
+  S4<T> y;
+  y.c[0] = rfma(b, X.c[2], rfma(m, X.c[0], -(d * X.c[3])));
+  y.c[1] = rfma(a, X.c[3], rfma(m, X.c[1], -(c * X.c[2])));
+  y.c[2] = rfma(a, X.c[0], rfma(m, X.c[2], d * X.c[1]));
+  y.c[3] = rfma(b, X.c[1], rfma(m, X.c[3], c * X.c[0]));
+  cplx<T> yb[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    yb[k] = cmulc(f, ob.c[k]);
+    fb = cfmac(y.c[k], ob.c[k], fb);
+  }
+  Xb.c[0] = rfma(m, yb[0], rfma(a, yb[2], cmulc(c, yb[3])));
+  Xb.c[1] = rfma(m, yb[1], rfma(b, yb[3], cmulc(d, yb[2])));
+  Xb.c[2] = rfma(b, yb[0], rfma(m, yb[2], -cmulc(c, yb[1])));
+  Xb.c[3] = rfma(a, yb[1], rfma(m, yb[3], -cmulc(d, yb[0])));
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s += redot(X.c[k], yb[k]);
+  mb += s;
+  const T ab = redot(X.c[3], yb[1]) + redot(X.c[0], yb[2]);
+  const T bb = redot(X.c[2], yb[0]) + redot(X.c[1], yb[3]);
+  const cplx<T> cb = cmulc(X.c[0], yb[3]) - cmulc(X.c[2], yb[1]);
+  const cplx<T> db = cmulc(X.c[1], yb[2]) - cmulc(X.c[3], yb[0]);
+  Pb.v[0] += ab + bb;
+  Pb.v[3] += ab - bb;
+  Pb.v[1] += cb.r + db.r;
+  Pb.v[2] += cb.i - db.i;
+}
+
+// acc -= sg O3(GL, GR, PL, PR) (o3_sub) with accb given: GLb, GRb, PLb, PRb
+template <typename T>
+__device__ __forceinline__ void adj_o3(const V4<T>& GL, const V4<T>& GR, const R4<T>& PL, const R4<T>& PR, T sg,
+                                       const V4<T>& accb, V4<T>& GLb, V4<T>& GRb, R4<T>& PLb, R4<T>& PRb) {
+  R4<T> a, b, c;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    a.v[k] = PR.v[k] - PL.v[k];
+    b.v[k] = fma(T(2), PR.v[k], PL.v[k]);
+    c.v[k] = fma(T(2), PL.v[k], PR.v[k]);
+  }
+  const cplx<T> s0 = mdot(GL, GR), s1 = mdot(b, GL), s2 = mdot(c, GR);
+  cplx<T> s0b = {T(0), T(0)}, s1b = {T(0), T(0)}, s2b = {T(0), T(0)};
+  R4<T> ab;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const cplx<T> ob = -sg * accb.c[k];     // adjoint of O3 component k
+    s0b = rfma(a.v[k], ob, s0b);
+    ab.v[k] = redot(s0, ob);
+    GRb.c[k] = GRb.c[k] - cmulc(s1, ob);
+    s1b = s1b - cmulc(GR.c[k], ob);
+    GLb.c[k] = cfmac(s2, ob, GLb.c[k]);
+    s2b = cfmac(GL.c[k], ob, s2b);
+  }
+  R4<T> bb, cbr;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const T g = k == 0 ? T(1) : T(-1);
+    GLb.c[k] = cfmac(GR.c[k], g * s0b, GLb.c[k]);
+    GRb.c[k] = cfmac(GL.c[k], g * s0b, GRb.c[k]);
+    GLb.c[k] = rfma(g * b.v[k], s1b, GLb.c[k]);
+    bb.v[k] = g * redot(GL.c[k], s1b);
+    GRb.c[k] = rfma(g * c.v[k], s2b, GRb.c[k]);
+    cbr.v[k] = g * redot(GR.c[k], s2b);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    PLb.v[k] += -ab.v[k] + bb.v[k] + T(2) * cbr.v[k];
+    PRb.v[k] += ab.v[k] + T(2) * bb.v[k] + cbr.v[k];
+  }
+}
+
+// acc += sg [2 (L.R) M - (L.M) R - (M.R) L] (o4_add) with accb given
+template <typename T>
+__device__ __forceinline__ void adj_o4(const V4<T>& GL, const V4<T>& GM, const V4<T>& GR, T sg, const V4<T>& accb,
+                                       V4<T>& GLb, V4<T>& GMb, V4<T>& GRb) {
+  const cplx<T> lr = mdot(GL, GR), lm = mdot(GL, GM), mr = mdot(GM, GR);
+  cplx<T> lrb = {T(0), T(0)}, lmb = {T(0), T(0)}, mrb = {T(0), T(0)};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const cplx<T> ob = sg * accb.c[k];
+    GMb.c[k] = cfmac(T(2) * lr, ob, GMb.c[k]);
+    lrb = cfmac(T(2) * GM.c[k], ob, lrb);
+    GRb.c[k] = GRb.c[k] - cmulc(lm, ob);
+    lmb = lmb - cmulc(GR.c[k], ob);
+    GLb.c[k] = GLb.c[k] - cmulc(mr, ob);
+    mrb = mrb - cmulc(GL.c[k], ob);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const T g = k == 0 ? T(1) : T(-1);
+    GLb.c[k] = cfmac(GR.c[k], g * lrb, cfmac(GM.c[k], g * lmb, GLb.c[k]));
+    GRb.c[k] = cfmac(GL.c[k], g * lrb, cfmac(GM.c[k], g * mrb, GRb.c[k]));
+    GMb.c[k] = cfmac(GL.c[k], g * lmb, cfmac(GR.c[k], g * mrb, GMb.c[k]));
+  }
+}
+
+// amplitude planes of the adjoint kernel: [re/im][sigma * 2 + top helicity][32 lanes]
+template <int NG> constexpr int kAdjPlane = TTNG<NG>::NPERM * 2 * 32;
+
+// Per-lane accumulators of the momentum adjoints (shared memory, one column
+// per lane of the warp): row i*4 + c holds d|M|^2/dp[i][c] for the momenta
+// in MadGraph order, then the explicit d/dm_t and d/d(m_t Gamma_t).
+template <int NG> struct AdjRows {
+  static constexpr int NEXT = NG + 2;
+  static constexpr int MB = 4 * NEXT, MWB = 4 * NEXT + 1, N = 4 * NEXT + 2;
+};
+
+template <int NG, typename T> __device__ __forceinline__ void acc_row(T* pb, int row, T x) { pb[row * 32] += x; }
+
+// Kb for K = sum of the outgoing-convention gluon momenta q_g (g in msk),
+// q_g = -p for the incoming gluons g = 0, 1 (legs 0, 1), +p for legs 4..
+template <int NG, typename T> __device__ __forceinline__ void add_mask(T* pb, unsigned msk, const R4<T>& Kb) {
+#pragma unroll
+  for (int g = 0; g < NG; ++g)
+    if ((msk >> g) & 1u) {
+      const int leg = g < 2 ? g : g + 2;
+      const T s = g < 2 ? T(-1) : T(1);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc_row<NG, T>(pb, leg * 4 + c, s * Kb.v[c]);
+    }
+}
+
+// adjoint of the propagator factor f = -1/(den + i m Gamma), den = P^2 - m^2
+// with P = q_tbar + K(msk) (= -Ptab[msk]); a Ptab adjoint Ptb is folded in
+template <int NG, typename T>
+__device__ __forceinline__ void chain_prop(T* pb, unsigned msk, const R4<T>& Ptab, cplx<T> f, cplx<T> fb,
+                                           const R4<T>& Ptb, T m) {
+  const cplx<T> f2 = f * f;                  // d f / d z = 1 / z^2 = f^2
+  const cplx<T> zb = cmulc(f2, fb);
+  const T denb = zb.r, mwb = zb.i;
+  R4<T> Pb;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const T g = c == 0 ? T(1) : T(-1);
+    Pb.v[c] = T(2) * g * (-Ptab.v[c]) * denb - Ptb.v[c];
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) acc_row<NG, T>(pb, 3 * 4 + c, Pb.v[c]);   // q_tbar = p[3]
+  add_mask<NG, T>(pb, msk, Pb);
+  acc_row<NG, T>(pb, AdjRows<NG>::MB, T(-2) * m * denb);
+  acc_row<NG, T>(pb, AdjRows<NG>::MWB, mwb);
+}
+
+// d(spinor)/d(E, px, py, pz, m) contracted with the spinor's adjoint
+template <int NG, typename T, typename F>
+__device__ __forceinline__ void chain_spinor(T* pb, int leg, const T (&p)[4], T m, const S4<T>& sb, F&& fn) {
+  using D = Dual<T, 5>;
+  R4<D> pd;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    pd.v[c] = D(p[c]);
+    pd.v[c].d[c] = T(1);
+  }
+  D md = D(m);
+  md.d[4] = T(1);
+  const S4<D> s = fn(pd, md);
+  T g[5] = {T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) g[j] += s.c[k].r.d[j] * sb.c[k].r + s.c[k].i.d[j] * sb.c[k].i;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) acc_row<NG, T>(pb, leg * 4 + c, g[c]);
+  acc_row<NG, T>(pb, AdjRows<NG>::MB, g[4]);
+}
+
+// Reverse depth-first walk (see quark_walk for the forward recursion).  The
+// forward pass (ADJ = false) stores the amplitudes J; the reverse pass
+// (ADJ = true) reads Jb in their place, recomputes every R(S) on the way down
+// and, after a node's subtree, propagates the node's adjoint Rb[LV] into the
+// sub-currents (atomically into Gb), the propagator inputs and Rb of its
+// ancestors.
+template <typename T> struct AdjCtx {
+  const cplx<T>* Gs;
+  cplx<T>* Gb;
+  const R4<T>* Ptab;
+  const cplx<T>* qf;
+  uint64_t pk;
+  S4<T> ub0, ub1, ubb0, ubb1;
+  T m;
+  T* J;          // this lane's column of the J (or Jb) planes
+  T* pb;         // this lane's column of the momentum-adjoint rows
+};
+
+template <int NG, typename T>
+__device__ __forceinline__ void gb_add(const AdjCtx<T>& cx, uint16_t ref, const V4<T>& g) {
+  const unsigned idx = unsigned(cx.pk >> (4 * ref_mask(ref))) & 15u;
+  const int pos = ref_off(ref) + int(idx);
+  const T s = ref_neg(ref) ? T(-1) : T(1);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    atomicAdd(&cx.Gb[k * TTNG<NG>::NSTORE + pos].r, s * g.c[k].r);
+    atomicAdd(&cx.Gb[k * TTNG<NG>::NSTORE + pos].i, s * g.c[k].i);
+  }
+}
+
+template <int NG, typename T>
+__device__ __forceinline__ V4<T> adj_block(const AdjCtx<T>& cx, uint16_t ref) {
+  const unsigned idx = unsigned(cx.pk >> (4 * ref_mask(ref))) & 15u;
+  V4<T> g = gs_load<NG, T>(cx.Gs, ref_off(ref) + int(idx));
+  if (ref_neg(ref)) g = neg(g);
+  return g;
+}
+
+template <int NG, int LV, bool ADJ, typename T>
+__device__ __forceinline__ void adj_walk(int parent, S4<T> (&R)[NG], S4<T> (&Rb)[NG], AdjCtx<T>& cx) {
+  using PT = Paths<NG>;
+  const int first = PT::template first<LV>(parent);
+#pragma unroll 1
+  for (int k = 0; k <= NG - LV; ++k) {
+    const int path = first + k;
+    const uint8_t msk = PT::template mask<LV>(path);
+    {
+      S4<T> X = apply(make_slash(adj_block<NG, T>(cx, PT::template blk<LV>(path, 0))), R[LV - 1]);
+#pragma unroll
+      for (int m = 1; m < LV; ++m)
+        apply_acc(make_slash(adj_block<NG, T>(cx, PT::template blk<LV>(path, m))), R[LV - 1 - m], X);
+      R[LV] = quark_prop_f(cx.Ptab[msk], cx.m, cx.qf[msk], X);
+    }
+    if constexpr (ADJ) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) Rb[LV].c[c] = {T(0), T(0)};
+    }
+    if constexpr (LV < NG - 1) {
+      adj_walk<NG, LV + 1, ADJ, T>(path, R, Rb, cx);
+    } else {
+      {
+        S4<T> W = apply(make_slash(adj_block<NG, T>(cx, PT::final_blk(path, 0))), R[NG - 1]);
+#pragma unroll
+        for (int m = 1; m < NG; ++m)
+          apply_acc(make_slash(adj_block<NG, T>(cx, PT::final_blk(path, m))), R[NG - 1 - m], W);
+        const int sig = PT::final_sigma(path);
+        T* j = cx.J + (sig * 2) * 32;
+        if constexpr (!ADJ) {
+          const cplx<T> j0 = rowdot(cx.ub0, W), j1 = rowdot(cx.ub1, W);
+          j[0] = j0.r;
+          j[kAdjPlane<NG>] = j0.i;
+          j[32] = j1.r;
+          j[32 + kAdjPlane<NG>] = j1.i;
+        } else {
+          const cplx<T> jb0 = {j[0], j[kAdjPlane<NG>]}, jb1 = {j[32], j[32 + kAdjPlane<NG>]};
+          S4<T> Wb;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            Wb.c[c] = cfmac(cx.ub1.c[c], jb1, cmulc(cx.ub0.c[c], jb0));
+            cx.ubb0.c[c] = cfmac(W.c[c], jb0, cx.ubb0.c[c]);
+            cx.ubb1.c[c] = cfmac(W.c[c], jb1, cx.ubb1.c[c]);
+          }
+#pragma unroll
+          for (int m = 0; m < NG; ++m) {
+            const uint16_t ref = PT::final_blk(path, m);
+            V4<T> gb;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) gb.c[c] = {T(0), T(0)};
+            adj_apply(adj_block<NG, T>(cx, ref), R[NG - 1 - m], Wb, gb, Rb[NG - 1 - m]);
+            gb_add<NG, T>(cx, ref, gb);
+          }
+        }
+      }
+    }
+    if constexpr (ADJ) {
+      // node adjoint: R[LV] = f (P-slash + m) X, X = sum_m G_m-slash R[LV-1-m]
+      S4<T> X = apply(make_slash(adj_block<NG, T>(cx, PT::template blk<LV>(path, 0))), R[LV - 1]);
+#pragma unroll
+      for (int m = 1; m < LV; ++m)
+        apply_acc(make_slash(adj_block<NG, T>(cx, PT::template blk<LV>(path, m))), R[LV - 1 - m], X);
+      S4<T> Xb;
+      R4<T> Ptb = {{T(0), T(0), T(0), T(0)}};
+      T mb = T(0);
+      cplx<T> fb = {T(0), T(0)};
+      const R4<T> Pt = cx.Ptab[msk];
+      const cplx<T> f = cx.qf[msk];
+      adj_prop(Pt, cx.m, f, X, Rb[LV], Xb, Ptb, mb, fb);
+      acc_row<NG, T>(cx.pb, AdjRows<NG>::MB, mb);
+      chain_prop<NG, T>(cx.pb, msk, Pt, f, fb, Ptb, cx.m);
+#pragma unroll
+      for (int m = 0; m < LV; ++m) {
+        const uint16_t ref = PT::template blk<LV>(path, m);
+        V4<T> gb;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) gb.c[c] = {T(0), T(0)};
+        adj_apply(adj_block<NG, T>(cx, ref), R[LV - 1 - m], Xb, gb, Rb[LV - 1 - m]);
+        gb_add<NG, T>(cx, ref, gb);
+      }
+    }
+  }
+}
+
+
+template <int NG, typename T> __device__ __forceinline__ void gb_atomic(cplx<T>* Gb, int pos, const V4<T>& g) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    atomicAdd(&Gb[k * TTNG<NG>::NSTORE + pos].r, g.c[k].r);
+    atomicAdd(&Gb[k * TTNG<NG>::NSTORE + pos].i, g.c[k].i);
+  }
+}
+
+// Reverse of gluon_level<NG, K>: every item's adjoint Gb is complete (all its
+// users, longer blocks and quark lines, are done); propagate it into the
+// sub-blocks' adjoints, the momentum sums and 1/K^2.
+template <int NG, int K, typename T>
+__device__ __forceinline__ void adj_gluon_level(const MaskTab<NG, T>& mt, const cplx<T>* Gs, cplx<T>* Gb, int gl, T* pb) {
+  constexpr int L = Lanes<NG>::L;
+  constexpr int nblk = TTNG<NG>::FIRST[K + 1] - TTNG<NG>::FIRST[K];
+  constexpr int items = nblk << K;
+  constexpr int n3 = K - 1;
+  constexpr int n4 = (K - 1) * (K - 2) / 2;
+#pragma unroll 1
+  for (int it = gl; it < items; it += L) {
+    const int bl = it >> K;
+    const unsigned c = unsigned(it) & ((1u << K) - 1u);
+    const int b = TTNG<NG>::FIRST[K] + bl;
+    const unsigned mb = blk_mask<NG>()[b];
+    const unsigned H = pdep_mask<NG>(c, mb);
+    const int pos = blk_off<NG>()[b] + int(c);
+    const V4<T> G = gs_load<NG, T>(Gs, pos), Gbar = gs_load<NG, T>(Gb, pos);
+    const T ginv = mt.ginv[mb];
+    // G = ginv acc: d/d(ginv) = Re(conj(acc) Gb) = Re(conj(G) Gb) / ginv, ginv = 1/K^2
+    T gib = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gib += redot(G.c[k], Gbar.c[k]);
+    const T k2b = -ginv * gib;
+    const R4<T> Kv = mt.qsum[mb];
+    R4<T> Kb;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Kb.v[k] = T(2) * (k == 0 ? T(1) : T(-1)) * Kv.v[k] * k2b;
+    add_mask<NG, T>(pb, mb, Kb);
+    V4<T> accb;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) accb.c[k] = ginv * Gbar.c[k];
+    const uint16_t* t3 = o3_table<NG, K>() + bl * n3 * 2;
+#pragma unroll 1
+    for (int s = 0; s < n3; ++s) {
+      const uint16_t rl = t3[2 * s], rr = t3[2 * s + 1];
+      const V4<T> GL = load_block<NG, T>(Gs, rl, H), GR = load_block<NG, T>(Gs, rr, H);
+      const R4<T> PL = mt.qsum[ref_mask(rl)], PR = mt.qsum[ref_mask(rr)];
+      V4<T> GLb, GRb;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) GLb.c[k] = GRb.c[k] = {T(0), T(0)};
+      R4<T> PLb = {{T(0), T(0), T(0), T(0)}}, PRb = {{T(0), T(0), T(0), T(0)}};
+      adj_o3(GL, GR, PL, PR, (ref_neg(rl) != ref_neg(rr)) ? T(-1) : T(1), accb, GLb, GRb, PLb, PRb);
+      gb_atomic<NG, T>(Gb, ref_off(rl) + int(pext_mask<NG>(H, ref_mask(rl))), GLb);
+      gb_atomic<NG, T>(Gb, ref_off(rr) + int(pext_mask<NG>(H, ref_mask(rr))), GRb);
+      add_mask<NG, T>(pb, ref_mask(rl), PLb);
+      add_mask<NG, T>(pb, ref_mask(rr), PRb);
+    }
+    if constexpr (K >= 3) {
+      const uint16_t* t4 = o4_table<NG, K>() + bl * n4 * 3;
+#pragma unroll 1
+      for (int s = 0; s < n4; ++s) {
+        const uint16_t r0 = t4[3 * s], r1 = t4[3 * s + 1], r2 = t4[3 * s + 2];
+        const V4<T> GL = load_block<NG, T>(Gs, r0, H), GM = load_block<NG, T>(Gs, r1, H),
+                    GR = load_block<NG, T>(Gs, r2, H);
+        V4<T> GLb, GMb, GRb;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) GLb.c[k] = GMb.c[k] = GRb.c[k] = {T(0), T(0)};
+        adj_o4(GL, GM, GR, (ref_neg(r0) ^ ref_neg(r1) ^ ref_neg(r2)) ? T(-1) : T(1), accb, GLb, GMb, GRb);
+        gb_atomic<NG, T>(Gb, ref_off(r0) + int(pext_mask<NG>(H, ref_mask(r0))), GLb);
+        gb_atomic<NG, T>(Gb, ref_off(r1) + int(pext_mask<NG>(H, ref_mask(r1))), GMb);
+        gb_atomic<NG, T>(Gb, ref_off(r2) + int(pext_mask<NG>(H, ref_mask(r2))), GRb);
+      }
+    }
+  }
+}
+
+// Shared memory of one warp of the adjoint kernel: per event of the warp the
+// sub-currents, their adjoints and the mask table; per lane the amplitude
+// planes (J, then Jb) and the momentum-adjoint rows.
+template <int NG, typename T> struct AdjMem {
+  static constexpr int EPW = Lanes<NG>::EPW;
+  static constexpr size_t gs_bytes = sizeof(cplx<T>) * 4 * TTNG<NG>::NSTORE * EPW;
+  static constexpr size_t gb_off = gs_bytes;
+  static constexpr size_t pt_off = gb_off + gs_bytes;
+  static constexpr size_t j_off = (pt_off + MaskTab<NG, T>::bytes * EPW + 15) & ~size_t(15);
+  static constexpr size_t pb_off = j_off + sizeof(T) * 2 * kAdjPlane<NG>;
+  static constexpr size_t bytes = (pb_off + sizeof(T) * AdjRows<NG>::N * 32 + 15) & ~size_t(15);
+};
+
+// |M|^2 of the group's event (every lane returns it) and, on return, the
+// group-summed adjoint rows d|M|^2/dp[i][c], d/dm_t, d/d(m_t Gamma_t) in out[]
+// (all lanes).  norm includes 1/D of the colour matrix C = num / D.
+template <int NG, typename T>
+__device__ __forceinline__ T adj_group_me2(const T (&p)[NG + 2][4], unsigned char* wm, int group, int gl, T mt, T mw,
+                                           T norm, T (&out)[AdjRows<NG>::N]) {
+  using AM = AdjMem<NG, T>;
+  constexpr int L = Lanes<NG>::L, NP = TTNG<NG>::NPERM, NS = TTNG<NG>::NSTORE, NR = AdjRows<NG>::N;
+  const int lane = threadIdx.x & 31;
+  cplx<T>* Gs = reinterpret_cast<cplx<T>*>(wm) + group * 4 * NS;
+  cplx<T>* Gb = reinterpret_cast<cplx<T>*>(wm + AM::gb_off) + group * 4 * NS;
+  const MaskTab<NG, T> mtab(wm + AM::pt_off + group * MaskTab<NG, T>::bytes);
+  T* Jw = reinterpret_cast<T*>(wm + AM::j_off) + lane;
+  T* pb = reinterpret_cast<T*>(wm + AM::pb_off) + lane;
+  for (int i = gl; i < 4 * NS; i += L) Gb[i] = {T(0), T(0)};
+#pragma unroll 1
+  for (int r = 0; r < NR; ++r) pb[r * 32] = T(0);
+  R4<T> qtb;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) qtb.v[c] = p[3][c];
+  event_tables<NG, T>(p, mtab, Gs, gl, mt, mw);
+  __syncwarp();
+  gluon_level<NG, 2, T>(mtab, Gs, gl);
+  if constexpr (NG >= 3) { __syncwarp(); gluon_level<NG, 3, T>(mtab, Gs, gl); }
+  if constexpr (NG >= 4) { __syncwarp(); gluon_level<NG, 4, T>(mtab, Gs, gl); }
+  __syncwarp();
+  // this lane's quark line: amplitudes J
+  const unsigned H = unsigned(gl) & ((1u << NG) - 1u);
+  const int ltb = ((gl >> NG) & 1) ? 1 : -1;
+  AdjCtx<T> cx;
+  cx.Gs = Gs;
+  cx.Gb = Gb;
+  cx.Ptab = mtab.ptab;
+  cx.qf = mtab.qf;
+  cx.pk = 0;
+#pragma unroll
+  for (unsigned msk = 1; msk < (1u << NG); ++msk) cx.pk |= uint64_t(pext_mask<NG>(H, msk)) << (4 * msk);
+  R4<T> pt;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) pt.v[c] = p[2][c];
+  cx.ub0 = ubar_out(pt, mt, -1);
+  cx.ub1 = ubar_out(pt, mt, 1);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) cx.ubb0.c[c] = cx.ubb1.c[c] = {T(0), T(0)};
+  cx.m = mt;
+  cx.J = Jw;
+  cx.pb = pb;
+  S4<T> R[NG], Rb[NG];
+  R[0] = v_out(qtb, mt, ltb);
+  adj_walk<NG, 1, false, T>(0, R, Rb, cx);
+  // colour form and its adjoint Jb = 2 norm C J (in place), per top helicity
+  const int* num = colour_num_dev<NG>();
+  const T js = T(2) * norm;     // norm carries the colour matrix's 1/D
+  T me = T(0);
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    cplx<T> Y[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) Y[a] = {T(0), T(0)};
+#pragma unroll 1
+    for (int b = 0; b < NP; ++b) {
+      const cplx<T> jb = {Jw[(b * 2 + h) * 32], Jw[(b * 2 + h) * 32 + kAdjPlane<NG>]};
+#pragma unroll
+      for (int a = 0; a < NP; ++a) Y[a] = rfma(T(num[a * NP + b]), jb, Y[a]);
+    }
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      T* j = Jw + (a * 2 + h) * 32;
+      me += redot(cplx<T>{j[0], j[kAdjPlane<NG>]}, Y[a]);
+      j[0] = js * Y[a].r;
+      j[kAdjPlane<NG>] = js * Y[a].i;
+    }
+  }
+  me *= T(0.5) * js;
+  // reverse walk, then the external spinors
+#pragma unroll
+  for (int c = 0; c < 4; ++c) Rb[0].c[c] = {T(0), T(0)};
+  adj_walk<NG, 1, true, T>(0, R, Rb, cx);
+  chain_spinor<NG, T>(pb, 3, p[3], mt, Rb[0], [&](const R4<Dual<T, 5>>& q, Dual<T, 5> m) { return v_out(q, m, ltb); });
+  chain_spinor<NG, T>(pb, 2, p[2], mt, cx.ubb0, [&](const R4<Dual<T, 5>>& q, Dual<T, 5> m) { return ubar_out(q, m, -1); });
+  chain_spinor<NG, T>(pb, 2, p[2], mt, cx.ubb1, [&](const R4<Dual<T, 5>>& q, Dual<T, 5> m) { return ubar_out(q, m, 1); });
+  __syncwarp();
+  // gluon levels in reverse
+  if constexpr (NG >= 4) { adj_gluon_level<NG, 4, T>(mtab, Gs, Gb, gl, pb); __syncwarp(); }
+  if constexpr (NG >= 3) { adj_gluon_level<NG, 3, T>(mtab, Gs, Gb, gl, pb); __syncwarp(); }
+  adj_gluon_level<NG, 2, T>(mtab, Gs, Gb, gl, pb);
+  __syncwarp();
+  // polarisation vectors of the outgoing gluons (the incoming ones lie on the
+  // beam axis, where eps does not depend on the momentum)
+  for (int it = gl; it < 2 * NG; it += L) {
+    const int g = it >> 1;
+    if (g < 2) continue;
+    const V4<T> eb = gs_load<NG, T>(Gb, 2 * g + (it & 1));
+    using D = Dual<T, 3>;
+    R4<D> kd;
+    kd.v[0] = D(p[g + 2][0]);
+#pragma unroll
+    for (int c = 1; c < 4; ++c) {
+      kd.v[c] = D(p[g + 2][c]);
+      kd.v[c].d[c - 1] = T(1);
+    }
+    const V4<D> e = polarisation(kd, (it & 1) ? 1 : -1, true);
+#pragma unroll
+    for (int c = 1; c < 4; ++c) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) s += e.c[k].r.d[c - 1] * eb.c[k].r + e.c[k].i.d[c - 1] * eb.c[k].i;
+      acc_row<NG, T>(pb, (g + 2) * 4 + c, s);
+    }
+  }
+  __syncwarp();
+  // sum the group's lanes
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    T x = pb[r * 32];
+#pragma unroll
+    for (int off = L / 2; off > 0; off >>= 1) x += shfl_xor_any(0xffffffffu, x, off);
+    out[r] = x;
+  }
+#pragma unroll
+  for (int off = L / 2; off > 0; off >>= 1) me += shfl_xor_any(0xffffffffu, me, off);
+  __syncwarp();
+  return me;
+}
+
+}  // namespace mf

@@ -464,22 +464,13 @@ __device__ __forceinline__ void quark_walk_paired4(const S4<T>& v, const LaneCtx
   }
 }
 
-// |M|^2 (without the normalisation MeParams::norm) of one event, computed by
-// its lane group; p: physical momenta in MadGraph order; wm: this warp's
-// shared memory (WarpMem layout); tc: colour sum on the tensor cores (FP32
-// only).  Every lane of the warp must call this (the group synchronises with
-// __syncwarp).
+// Per event, helicity independent: the mask table (momentum sum K, -(q_tbar + K),
+// 1/K^2 and the top-propagator factor of every gluon subset, one subset per
+// lane) and the polarisation vectors (level-1 sub-currents).
 template <int NG, typename T>
-__device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* wm, int group, int gl, T mt, T mw,
-                                       int tc = 0) {
-  using WM = WarpMem<NG, T>;
+__device__ __forceinline__ void event_tables(const T (&p)[NG + 2][4], const MaskTab<NG, T>& mtab, cplx<T>* Gs, int gl,
+                                             T mt, T mw) {
   constexpr int L = Lanes<NG>::L;
-  constexpr int NP = TTNG<NG>::NPERM;
-  cplx<T>* Gs = reinterpret_cast<cplx<T>*>(wm) + group * 4 * TTNG<NG>::NSTORE;
-  const MaskTab<NG, T> mtab(wm + WM::pt_off + group * MaskTab<NG, T>::bytes);
-  T* Jw = reinterpret_cast<T*>(wm + WM::j_off);
-  cplx<T>* R2 = reinterpret_cast<cplx<T>*>(wm + WM::r2_off) + group * 4 * WM::NR2;
-  const int lane = threadIdx.x & 31;
   R4<T> q[NG];
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
@@ -488,9 +479,9 @@ __device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* w
 #pragma unroll
     for (int c = 0; c < 4; ++c) q[g].v[c] = s * p[leg][c];
   }
-  R4<T> qtb, pt;
+  R4<T> qtb;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) { qtb.v[c] = p[3][c]; pt.v[c] = p[2][c]; }
+  for (int c = 0; c < 4; ++c) qtb.v[c] = p[3][c];
   // the mask table (one mask per lane), and the polarisation vectors (level 1)
   if (gl < (1 << NG)) {
     R4<T> K = {{T(0), T(0), T(0), T(0)}};
@@ -531,6 +522,28 @@ __device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* w
     for (int c = 0; c < 4; ++c) k.v[c] = p[leg][c];
     gs_store<NG, T>(Gs, 2 * g + (it & 1), polarisation(k, (it & 1) ? 1 : -1, g >= 2));
   }
+}
+
+// |M|^2 (without the normalisation MeParams::norm) of one event, computed by
+// its lane group; p: physical momenta in MadGraph order; wm: this warp's
+// shared memory (WarpMem layout); tc: colour sum on the tensor cores (FP32
+// only).  Every lane of the warp must call this (the group synchronises with
+// __syncwarp).
+template <int NG, typename T>
+__device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* wm, int group, int gl, T mt, T mw,
+                                       int tc = 0) {
+  using WM = WarpMem<NG, T>;
+  constexpr int L = Lanes<NG>::L;
+  constexpr int NP = TTNG<NG>::NPERM;
+  cplx<T>* Gs = reinterpret_cast<cplx<T>*>(wm) + group * 4 * TTNG<NG>::NSTORE;
+  const MaskTab<NG, T> mtab(wm + WM::pt_off + group * MaskTab<NG, T>::bytes);
+  T* Jw = reinterpret_cast<T*>(wm + WM::j_off);
+  cplx<T>* R2 = reinterpret_cast<cplx<T>*>(wm + WM::r2_off) + group * 4 * WM::NR2;
+  const int lane = threadIdx.x & 31;
+  R4<T> qtb, pt;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) { qtb.v[c] = p[3][c]; pt.v[c] = p[2][c]; }
+  event_tables<NG, T>(p, mtab, Gs, gl, mt, mw);
   __syncwarp();
   gluon_level<NG, 2, T>(mtab, Gs, gl);
   if constexpr (NG >= 3) { __syncwarp(); gluon_level<NG, 3, T>(mtab, Gs, gl); }

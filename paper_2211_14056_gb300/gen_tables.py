@@ -325,6 +325,7 @@ def render():
         "template <int NG> struct Paths;",
         "template <int NG> struct ColourTC;",
         "template <int NG> __device__ __forceinline__ const float* colour_frag_a();",
+        "template <int NG> __device__ __forceinline__ const int* colour_num_dev();",
         "template <typename T> __device__ __forceinline__ V4<T> neg(const V4<T>& a) {",
         "  V4<T> o;",
         "#pragma unroll",
@@ -341,6 +342,8 @@ def render():
         lines.append(f"// colour matrix, {n} gluons: C = M / {D}; orderings lexicographic")
         lines.append(f"static constexpr int kColourDen{n} = {D};")
         lines.append(f"static const int kColourNum{n}[{P * P}] = {{{', '.join(map(str, flat))}}};")
+        lines.append(f"static __constant__ int kColourNumD{n}[{P * P}] = {{{', '.join(map(str, flat))}}};")
+        lines.append(f"template <> __device__ __forceinline__ const int* colour_num_dev<{n}>() {{ return kColourNumD{n}; }}")
         emit_tables(n, lines)
         emit_lane(n, lines, colours[n])
         emit_colour_tc(n, lines, colours[n])

@@ -57,6 +57,51 @@ def _grad(p, edges, seed, it, n):
     return sigma, ds, th.view(3, n).cpu().numpy(), dy.view(p.ndim, n).cpu().numpy()
 
 
+def _grad_both(p, edges, seed, it, n):
+    """(reverse, forward) results of the same derivative request."""
+    out = []
+    for forward in (False, True):
+        g = p.grid()
+        g.set(edges)
+        th = torch.full((3 * n,), float("nan"), dtype=torch.float64, device="cuda")
+        dy = torch.full((p.ndim * n,), float("nan"), dtype=torch.float64, device="cuda")
+        sigma, ds = p.grad(g, seed, it, n, dw_dtheta=th, dw_dy=dy, forward=forward)
+        torch.cuda.synchronize()
+        out.append((sigma, ds, th.view(3, n).cpu().numpy(), dy.view(p.ndim, n).cpu().numpy()))
+    return out
+
+
+@pytest.mark.parametrize("precision,bar", [("MF_FP64", 1e-9), ("MF_FP32", 2e-3)])
+@pytest.mark.parametrize("name", NAMES)
+def test_reverse_mode_matches_forward_mode(mf, name, precision, bar):
+    """The adjoint sweep (mf_grad) and the dual-number passes
+    (mf_grad_forward) compute the same derivatives by different algorithms:
+    per event and per output row they agree to rounding (relative to the
+    row's largest entry; FP32 rounding of two different operation orders)."""
+    p, w = _proc(mf, name, getattr(mf, precision))
+    n = 3001
+    edges = random_grid(p.ndim, seed=31)
+    (sr, dr, tr, yr), (sf, df, tf, yf) = _grad_both(p, edges, 17, 2, n)
+    assert np.isfinite(tr).all() and np.isfinite(yr).all()
+    rows = [("w", tr[0], tf[0]), ("dm_t", tr[1], tf[1]), ("dGamma_t", tr[2], tf[2])]
+    rows += [(f"dy{j}", yr[j], yf[j]) for j in range(p.ndim)]
+    # rows whose exact value vanishes (d/dGamma_t at Gamma_t = 0, d/dphi of a
+    # 2 -> 2 process) hold rounding noise in both modes: each row is measured
+    # against max(its largest entry, floor * the largest weight)
+    floor = 1e-5 if precision == "MF_FP64" else 1e-3
+    wmax = np.max(np.abs(tf[0]))           # dw/dg_s = (2 n_gluons / g_s) w: the weights' scale
+    worst = 0.0
+    for label, a, b in rows:
+        scale = max(np.max(np.abs(b)), floor * wmax)
+        err = np.max(np.abs(a - b)) / scale
+        print(f"{name} {precision} {label}: max |rev - fwd| / scale = {err:.2e}")
+        worst = max(worst, err)
+    assert worst < bar
+    assert sr == pytest.approx(sf, rel=1e-12 if precision == "MF_FP64" else 1e-6)
+    for k in range(3):
+        assert dr[k] == pytest.approx(df[k], rel=10 * bar, abs=floor * abs(df[0]))
+
+
 def _weights(mf, name, edges, seed, it, n, **over):
     p, _ = _proc(mf, name, mf.MF_FP64, **over)
     g = p.grid()
