@@ -419,8 +419,8 @@ def main():
 
 
 def _grad_leg(p32, p64, g32, g64, w, torch):
-    """mf_grad on the frozen grid: d sigma/d(g_s, m_t, Gamma_t) and the
-    per-event derivatives with respect to every uniform; events/s."""
+    """mf_grad (reverse mode) on the frozen grid: d sigma/d(g_s, m_t, Gamma_t)
+    and the per-event derivatives with respect to every uniform; events/s."""
     out = {}
     for name, p, g, n, reps in (("fp32", p32, g32, 2 ** 20, 2), ("fp64", p64, g64, 2 ** 18, 1)):
         th = torch.empty(3 * n, dtype=torch.float64, device="cuda")
@@ -435,7 +435,8 @@ def _grad_leg(p32, p64, g32, g64, w, torch):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         out[name] = {"events": n, "ms": ms, "events_per_s": n / (ms * 1e-3), "sigma_pb": sigma,
-                     "dsigma_dgs_dmt_dwt": ds, "tangent_passes": 1 + (p.ndim + 1) // 2,
+                     "dsigma_dgs_dmt_dwt": ds, "mode": "reverse: one adjoint sweep of |M|^2 per event",
+                     "sampler_tangent_passes": 1 + p.ndim // 2,
                      "per_event_outputs": "dw/d(g_s, m_t, Gamma_t) [3, n], dw/dy [ndim, n]"}
         del th, dy
     return out

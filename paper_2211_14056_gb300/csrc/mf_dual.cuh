@@ -19,6 +19,7 @@ using ::acos;
 using ::atan2;
 using ::cos;
 using ::exp;
+using ::expm1;
 using ::fabs;
 using ::fma;
 using ::fmax;
@@ -156,6 +157,9 @@ template <typename B, int N> __host__ __device__ __forceinline__ Dual<B, N> exp(
 }
 template <typename B, int N> __host__ __device__ __forceinline__ Dual<B, N> log(const Dual<B, N>& a) {
   return chain(a, log(a.v), B(1) / a.v);
+}
+template <typename B, int N> __host__ __device__ __forceinline__ Dual<B, N> expm1(const Dual<B, N>& a) {
+  return chain(a, expm1(a.v), exp(a.v));
 }
 template <typename B, int N> __host__ __device__ __forceinline__ Dual<B, N> log1p(const Dual<B, N>& a) {
   return chain(a, log1p(a.v), B(1) / (B(1) + a.v));

@@ -175,9 +175,11 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
     else log_tau0 = sp.log_tau0;
     const K lt = K(log_tau0);
     const K lx[2] = {K(x[0]) * lt, K(x[1]) * (K(1) - K(x[0])) * lt};
+    // ln(1 - x) = ln(-expm1(ln x)): accurate also for x within an ulp of 1
+    // (where 1 - exp(ln x) would round to 0 in FP32)
     K l1m = K(0);
 #pragma unroll 1
-    for (int j = 0; j < 2; ++j) l1m += log1p(-exp(lx[j]));
+    for (int j = 0; j < 2; ++j) l1m += log(-expm1(lx[j]));
     const K lsum = lx[0] + lx[1];
     shat = D(exp(lsum)) * (sp.sqrt_s * sp.sqrt_s);
     const K ff = exp(K(sp.lumi_a + 1.0) * lsum + K(sp.lumi_b) * l1m);

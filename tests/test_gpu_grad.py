@@ -347,3 +347,18 @@ def test_autograd_cross_section(mf):
     pred = float((theta.grad * step).sum())
     assert (I2.item() - sigma) == pytest.approx(pred, rel=1e-2)
     assert math.isfinite(I2.item())
+
+
+def test_fp32_derivatives_finite_near_the_luminosity_edge(mf):
+    """2^20 events on the uniform grid include one with x_1 within an FP32 ulp
+    of 1 (its weight is ~1e-33 pb): ln(1 - x_1) comes from expm1, so the
+    FP32 weight and every derivative stay finite."""
+    p, w = _proc(mf, "gg_ttxgg_13tev", mf.MF_FP32)
+    g = p.grid()
+    n = 2 ** 20
+    th = torch.empty(3 * n, dtype=torch.float64, device="cuda")
+    dy = torch.empty(p.ndim * n, dtype=torch.float64, device="cuda")
+    sigma, ds = p.grad(g, w["seed"], 5001, n, th, dy)
+    torch.cuda.synchronize()
+    assert math.isfinite(sigma) and all(math.isfinite(x) for x in ds)
+    assert torch.isfinite(th).all().item() and torch.isfinite(dy).all().item()
