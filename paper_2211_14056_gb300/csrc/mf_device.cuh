@@ -193,6 +193,11 @@ __device__ __forceinline__ void o4_add(const V4<T>& GL, const V4<T>& GM, const V
   }
 }
 
+// a / b; in FP32 with the fast reciprocal (2 ulp), which is all the
+// wavefunctions need
+template <typename T> __device__ __forceinline__ T quot(T a, T b) { return a / b; }
+template <> __device__ __forceinline__ float quot<float>(float a, float b) { return __fdividef(a, b); }
+
 // ---------------------------------------------------------------------------
 // External states.  Two-component helicity eigenstates of p/|p|:
 //   chi_+ = (|p|+pz, px+i py)/sqrt(2|p|(|p|+pz)), chi_- = (-px+i py, |p|+pz)/(same),
@@ -203,12 +208,12 @@ __device__ __forceinline__ void helicity_chi(const R4<T>& p, int lam, cplx<T>& c
   const T pt2 = fma(px, px, py * py);
   const T pa = sqrt(fma(pz, pz, pt2));
   // |p| + pz, free of cancellation for pz < 0: pt^2 / (|p| - pz)
-  const T s = pz >= T(0) ? pa + pz : pt2 / (pa - pz);
+  const T s = pz >= T(0) ? pa + pz : quot(pt2, pa - pz);
   if (pa == T(0)) {
     c0 = {lam > 0 ? T(1) : T(0), T(0)};
     c1 = {lam > 0 ? T(0) : T(1), T(0)};
   } else if (s > T(0)) {
-    const T inv = T(1) / sqrt(T(2) * pa * s);
+    const T inv = rsqrt(T(2) * pa * s);
     if (lam > 0) { c0 = {s * inv, T(0)}; c1 = {px * inv, py * inv}; }
     else         { c0 = {-px * inv, py * inv}; c1 = {s * inv, T(0)}; }
   } else {
@@ -222,7 +227,7 @@ template <typename T>
 __device__ __forceinline__ void omegas(const R4<T>& p, T m, T& wp, T& wm) {
   const T pa = sqrt(fma(p.v[1], p.v[1], fma(p.v[2], p.v[2], p.v[3] * p.v[3])));
   wp = sqrt(p.v[0] + pa);
-  wm = (m == T(0)) ? T(0) : m / wp;
+  wm = (m == T(0)) ? T(0) : m * rsqrt(p.v[0] + pa);
 }
 
 // ubar(p, l) for an outgoing quark: u = (w_{-l} chi_l, w_l chi_l), ubar = (u2*, u3*, u0*, u1*)
