@@ -156,19 +156,20 @@ __device__ __forceinline__ void adj_o4(const V4<T>& GL, const V4<T>& GM, const V
 // amplitude planes of the adjoint kernel: [re/im][sigma * 2 + top helicity][32 lanes]
 template <int NG> constexpr int kAdjPlane = TTNG<NG>::NPERM * 2 * 32;
 
-// Per-lane accumulators of the momentum adjoints (shared memory, one column
-// per lane of the warp): row i*4 + c holds d|M|^2/dp[i][c] for the momenta
-// in MadGraph order, then the explicit d/dm_t and d/d(m_t Gamma_t).
+// Per-lane accumulators of the momentum adjoints (registers; every index is
+// a compile-time constant): row i*4 + c holds d|M|^2/dp[i][c] for the
+// momenta in MadGraph order, then the explicit d/dm_t and d/d(m_t Gamma_t).
 template <int NG> struct AdjRows {
   static constexpr int NEXT = NG + 2;
   static constexpr int MB = 4 * NEXT, MWB = 4 * NEXT + 1, N = 4 * NEXT + 2;
 };
+template <int NG, typename T> struct AdjAcc { T r[AdjRows<NG>::N]; };
 
-template <int NG, typename T> __device__ __forceinline__ void acc_row(T* pb, int row, T x) { pb[row * 32] += x; }
+template <int NG, typename T> __device__ __forceinline__ void acc_row(AdjAcc<NG, T>& pb, int row, T x) { pb.r[row] += x; }
 
 // Kb for K = sum of the outgoing-convention gluon momenta q_g (g in msk),
 // q_g = -p for the incoming gluons g = 0, 1 (legs 0, 1), +p for legs 4..
-template <int NG, typename T> __device__ __forceinline__ void add_mask(T* pb, unsigned msk, const R4<T>& Kb) {
+template <int NG, typename T> __device__ __forceinline__ void add_mask(AdjAcc<NG, T>& pb, unsigned msk, const R4<T>& Kb) {
 #pragma unroll
   for (int g = 0; g < NG; ++g)
     if ((msk >> g) & 1u) {
@@ -182,7 +183,7 @@ template <int NG, typename T> __device__ __forceinline__ void add_mask(T* pb, un
 // adjoint of the propagator factor f = -1/(den + i m Gamma), den = P^2 - m^2
 // with P = q_tbar + K(msk) (= -Ptab[msk]); a Ptab adjoint Ptb is folded in
 template <int NG, typename T>
-__device__ __forceinline__ void chain_prop(T* pb, unsigned msk, const R4<T>& Ptab, cplx<T> f, cplx<T> fb,
+__device__ __forceinline__ void chain_prop(AdjAcc<NG, T>& pb, unsigned msk, const R4<T>& Ptab, cplx<T> f, cplx<T> fb,
                                            const R4<T>& Ptb, T m) {
   const cplx<T> f2 = f * f;                  // d f / d z = 1 / z^2 = f^2
   const cplx<T> zb = cmulc(f2, fb);
@@ -202,7 +203,7 @@ __device__ __forceinline__ void chain_prop(T* pb, unsigned msk, const R4<T>& Pta
 
 // d(spinor)/d(E, px, py, pz, m) contracted with the spinor's adjoint
 template <int NG, typename T, typename F>
-__device__ __forceinline__ void chain_spinor(T* pb, int leg, const T (&p)[4], T m, const S4<T>& sb, F&& fn) {
+__device__ __forceinline__ void chain_spinor(AdjAcc<NG, T>& pb, int leg, const T (&p)[4], T m, const S4<T>& sb, F&& fn) {
   using D = Dual<T, 5>;
   R4<D> pd;
 #pragma unroll
@@ -238,12 +239,28 @@ template <typename T> struct AdjCtx {
   S4<T> ub0, ub1, ubb0, ubb1;
   T m;
   T* J;          // this lane's column of the J (or Jb) planes
-  T* pb;         // this lane's column of the momentum-adjoint rows
+  unsigned gl;   // lane within the event's group
 };
 
+// Add a lane's adjoint of a sub-current it used.  The stored position depends
+// only on the helicities of the block's own gluons, so the lanes that differ
+// in the other gluons' or the antitop's helicity add to the same entry: they
+// are summed by xor shuffles first and one lane per entry adds the sum.
 template <int NG, typename T>
-__device__ __forceinline__ void gb_add(const AdjCtx<T>& cx, uint16_t ref, const V4<T>& g) {
-  const unsigned idx = unsigned(cx.pk >> (4 * ref_mask(ref))) & 15u;
+__device__ __forceinline__ void gb_add(const AdjCtx<T>& cx, uint16_t ref, V4<T> g) {
+  const unsigned mb = ref_mask(ref);
+  const unsigned other = ((2u << NG) - 1u) & ~mb;
+#pragma unroll
+  for (int b = 0; b <= NG; ++b)
+    if ((other >> b) & 1u) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        g.c[k].r += shfl_xor_any(0xffffffffu, g.c[k].r, 1 << b);
+        g.c[k].i += shfl_xor_any(0xffffffffu, g.c[k].i, 1 << b);
+      }
+    }
+  if ((cx.gl & other) != 0u) return;
+  const unsigned idx = unsigned(cx.pk >> (4 * mb)) & 15u;
   const int pos = ref_off(ref) + int(idx);
   const T s = ref_neg(ref) ? T(-1) : T(1);
 #pragma unroll
@@ -262,7 +279,8 @@ __device__ __forceinline__ V4<T> adj_block(const AdjCtx<T>& cx, uint16_t ref) {
 }
 
 template <int NG, int LV, bool ADJ, typename T>
-__device__ __forceinline__ void adj_walk(int parent, S4<T> (&R)[NG], S4<T> (&Rb)[NG], AdjCtx<T>& cx) {
+__device__ __forceinline__ void adj_walk(int parent, S4<T> (&R)[NG], S4<T> (&Rb)[NG], AdjCtx<T>& cx,
+                                         AdjAcc<NG, T>& pb) {
   using PT = Paths<NG>;
   const int first = PT::template first<LV>(parent);
 #pragma unroll 1
@@ -281,7 +299,7 @@ __device__ __forceinline__ void adj_walk(int parent, S4<T> (&R)[NG], S4<T> (&Rb)
       for (int c = 0; c < 4; ++c) Rb[LV].c[c] = {T(0), T(0)};
     }
     if constexpr (LV < NG - 1) {
-      adj_walk<NG, LV + 1, ADJ, T>(path, R, Rb, cx);
+      adj_walk<NG, LV + 1, ADJ, T>(path, R, Rb, cx, pb);
     } else {
       {
         S4<T> W = apply(make_slash(adj_block<NG, T>(cx, PT::final_blk(path, 0))), R[NG - 1]);
@@ -330,8 +348,8 @@ __device__ __forceinline__ void adj_walk(int parent, S4<T> (&R)[NG], S4<T> (&Rb)
       const R4<T> Pt = cx.Ptab[msk];
       const cplx<T> f = cx.qf[msk];
       adj_prop(Pt, cx.m, f, X, Rb[LV], Xb, Ptb, mb, fb);
-      acc_row<NG, T>(cx.pb, AdjRows<NG>::MB, mb);
-      chain_prop<NG, T>(cx.pb, msk, Pt, f, fb, Ptb, cx.m);
+      acc_row<NG, T>(pb, AdjRows<NG>::MB, mb);
+      chain_prop<NG, T>(pb, msk, Pt, f, fb, Ptb, cx.m);
 #pragma unroll
       for (int m = 0; m < LV; ++m) {
         const uint16_t ref = PT::template blk<LV>(path, m);
@@ -358,7 +376,8 @@ template <int NG, typename T> __device__ __forceinline__ void gb_atomic(cplx<T>*
 // users, longer blocks and quark lines, are done); propagate it into the
 // sub-blocks' adjoints, the momentum sums and 1/K^2.
 template <int NG, int K, typename T>
-__device__ __forceinline__ void adj_gluon_level(const MaskTab<NG, T>& mt, const cplx<T>* Gs, cplx<T>* Gb, int gl, T* pb) {
+__device__ __forceinline__ void adj_gluon_level(const MaskTab<NG, T>& mt, const cplx<T>* Gs, cplx<T>* Gb, int gl,
+                                                AdjAcc<NG, T>& pb) {
   constexpr int L = Lanes<NG>::L;
   constexpr int nblk = TTNG<NG>::FIRST[K + 1] - TTNG<NG>::FIRST[K];
   constexpr int items = nblk << K;
@@ -424,15 +443,14 @@ __device__ __forceinline__ void adj_gluon_level(const MaskTab<NG, T>& mt, const 
 
 // Shared memory of one warp of the adjoint kernel: per event of the warp the
 // sub-currents, their adjoints and the mask table; per lane the amplitude
-// planes (J, then Jb) and the momentum-adjoint rows.
+// planes (J, then Jb).
 template <int NG, typename T> struct AdjMem {
   static constexpr int EPW = Lanes<NG>::EPW;
   static constexpr size_t gs_bytes = sizeof(cplx<T>) * 4 * TTNG<NG>::NSTORE * EPW;
   static constexpr size_t gb_off = gs_bytes;
   static constexpr size_t pt_off = gb_off + gs_bytes;
   static constexpr size_t j_off = (pt_off + MaskTab<NG, T>::bytes * EPW + 15) & ~size_t(15);
-  static constexpr size_t pb_off = j_off + sizeof(T) * 2 * kAdjPlane<NG>;
-  static constexpr size_t bytes = (pb_off + sizeof(T) * AdjRows<NG>::N * 32 + 15) & ~size_t(15);
+  static constexpr size_t bytes = (j_off + sizeof(T) * 2 * kAdjPlane<NG> + 15) & ~size_t(15);
 };
 
 // |M|^2 of the group's event (every lane returns it) and, on return, the
@@ -448,10 +466,10 @@ __device__ __forceinline__ T adj_group_me2(const T (&p)[NG + 2][4], unsigned cha
   cplx<T>* Gb = reinterpret_cast<cplx<T>*>(wm + AM::gb_off) + group * 4 * NS;
   const MaskTab<NG, T> mtab(wm + AM::pt_off + group * MaskTab<NG, T>::bytes);
   T* Jw = reinterpret_cast<T*>(wm + AM::j_off) + lane;
-  T* pb = reinterpret_cast<T*>(wm + AM::pb_off) + lane;
   for (int i = gl; i < 4 * NS; i += L) Gb[i] = {T(0), T(0)};
-#pragma unroll 1
-  for (int r = 0; r < NR; ++r) pb[r * 32] = T(0);
+  AdjAcc<NG, T> pb;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) pb.r[r] = T(0);
   R4<T> qtb;
 #pragma unroll
   for (int c = 0; c < 4; ++c) qtb.v[c] = p[3][c];
@@ -481,10 +499,10 @@ __device__ __forceinline__ T adj_group_me2(const T (&p)[NG + 2][4], unsigned cha
   for (int c = 0; c < 4; ++c) cx.ubb0.c[c] = cx.ubb1.c[c] = {T(0), T(0)};
   cx.m = mt;
   cx.J = Jw;
-  cx.pb = pb;
+  cx.gl = unsigned(gl);
   S4<T> R[NG], Rb[NG];
   R[0] = v_out(qtb, mt, ltb);
-  adj_walk<NG, 1, false, T>(0, R, Rb, cx);
+  adj_walk<NG, 1, false, T>(0, R, Rb, cx, pb);
   // colour form and its adjoint Jb = 2 norm C J (in place), per top helicity
   const int* num = colour_num_dev<NG>();
   const T js = T(2) * norm;     // norm carries the colour matrix's 1/D
@@ -512,7 +530,7 @@ __device__ __forceinline__ T adj_group_me2(const T (&p)[NG + 2][4], unsigned cha
   // reverse walk, then the external spinors
 #pragma unroll
   for (int c = 0; c < 4; ++c) Rb[0].c[c] = {T(0), T(0)};
-  adj_walk<NG, 1, true, T>(0, R, Rb, cx);
+  adj_walk<NG, 1, true, T>(0, R, Rb, cx, pb);
   chain_spinor<NG, T>(pb, 3, p[3], mt, Rb[0], [&](const R4<Dual<T, 5>>& q, Dual<T, 5> m) { return v_out(q, m, ltb); });
   chain_spinor<NG, T>(pb, 2, p[2], mt, cx.ubb0, [&](const R4<Dual<T, 5>>& q, Dual<T, 5> m) { return ubar_out(q, m, -1); });
   chain_spinor<NG, T>(pb, 2, p[2], mt, cx.ubb1, [&](const R4<Dual<T, 5>>& q, Dual<T, 5> m) { return ubar_out(q, m, 1); });
@@ -524,32 +542,35 @@ __device__ __forceinline__ T adj_group_me2(const T (&p)[NG + 2][4], unsigned cha
   __syncwarp();
   // polarisation vectors of the outgoing gluons (the incoming ones lie on the
   // beam axis, where eps does not depend on the momentum)
-  for (int it = gl; it < 2 * NG; it += L) {
-    const int g = it >> 1;
-    if (g < 2) continue;
-    const V4<T> eb = gs_load<NG, T>(Gb, 2 * g + (it & 1));
-    using D = Dual<T, 3>;
-    R4<D> kd;
-    kd.v[0] = D(p[g + 2][0]);
 #pragma unroll
-    for (int c = 1; c < 4; ++c) {
-      kd.v[c] = D(p[g + 2][c]);
-      kd.v[c].d[c - 1] = T(1);
-    }
-    const V4<D> e = polarisation(kd, (it & 1) ? 1 : -1, true);
+  for (int g = 2; g < NG; ++g) {
 #pragma unroll
-    for (int c = 1; c < 4; ++c) {
-      T s = T(0);
+    for (int bit = 0; bit < 2; ++bit) {
+      if (gl != (2 * g + bit) % L) continue;
+      const V4<T> eb = gs_load<NG, T>(Gb, 2 * g + bit);
+      using D = Dual<T, 3>;
+      R4<D> kd;
+      kd.v[0] = D(p[g + 2][0]);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) s += e.c[k].r.d[c - 1] * eb.c[k].r + e.c[k].i.d[c - 1] * eb.c[k].i;
-      acc_row<NG, T>(pb, (g + 2) * 4 + c, s);
+      for (int c = 1; c < 4; ++c) {
+        kd.v[c] = D(p[g + 2][c]);
+        kd.v[c].d[c - 1] = T(1);
+      }
+      const V4<D> e = polarisation(kd, bit ? 1 : -1, true);
+#pragma unroll
+      for (int c = 1; c < 4; ++c) {
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s += e.c[k].r.d[c - 1] * eb.c[k].r + e.c[k].i.d[c - 1] * eb.c[k].i;
+        acc_row<NG, T>(pb, (g + 2) * 4 + c, s);
+      }
     }
   }
   __syncwarp();
   // sum the group's lanes
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
-    T x = pb[r * 32];
+    T x = pb.r[r];
 #pragma unroll
     for (int off = L / 2; off > 0; off >>= 1) x += shfl_xor_any(0xffffffffu, x, off);
     out[r] = x;
