@@ -364,7 +364,26 @@ __device__ __forceinline__ void adj_walk(int parent, S4<T> (&R)[NG], S4<T> (&Rb)
 }
 
 
-template <int NG, typename T> __device__ __forceinline__ void gb_atomic(cplx<T>* Gb, int pos, const V4<T>& g) {
+// Add an item's adjoint of one of its sub-blocks.  The items of a round sit on
+// consecutive lanes with the helicity index c in the low K lane bits; the
+// items of one block whose helicities differ only in gluons outside the
+// sub-block (bits red of c) hit the same entry, so they are summed by xor
+// shuffles first and one of them adds.  Every lane of the group calls this.
+template <int NG, int K, typename T>
+__device__ __forceinline__ void gb_item_add(cplx<T>* Gb, int pos, V4<T> g, unsigned red, unsigned c, bool act) {
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const T r = shfl_xor_any(0xffffffffu, g.c[k].r, 1 << j);
+      const T i = shfl_xor_any(0xffffffffu, g.c[k].i, 1 << j);
+      if ((red >> j) & 1u) {
+        g.c[k].r += r;
+        g.c[k].i += i;
+      }
+    }
+  }
+  if (!act || (c & red) != 0u) return;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     atomicAdd(&Gb[k * TTNG<NG>::NSTORE + pos].r, g.c[k].r);
@@ -374,7 +393,8 @@ template <int NG, typename T> __device__ __forceinline__ void gb_atomic(cplx<T>*
 
 // Reverse of gluon_level<NG, K>: every item's adjoint Gb is complete (all its
 // users, longer blocks and quark lines, are done); propagate it into the
-// sub-blocks' adjoints, the momentum sums and 1/K^2.
+// sub-blocks' adjoints, the momentum sums and 1/K^2.  Rounds of L items run
+// on all lanes (idle lanes carry zero adjoints through the shuffles).
 template <int NG, int K, typename T>
 __device__ __forceinline__ void adj_gluon_level(const MaskTab<NG, T>& mt, const cplx<T>* Gs, cplx<T>* Gb, int gl,
                                                 AdjAcc<NG, T>& pb) {
@@ -384,14 +404,21 @@ __device__ __forceinline__ void adj_gluon_level(const MaskTab<NG, T>& mt, const 
   constexpr int n3 = K - 1;
   constexpr int n4 = (K - 1) * (K - 2) / 2;
 #pragma unroll 1
-  for (int it = gl; it < items; it += L) {
-    const int bl = it >> K;
+  for (int base = 0; base < items; base += L) {
+    const int it = base + gl;
+    const bool act = it < items;
+    const int bl = act ? it >> K : 0;
     const unsigned c = unsigned(it) & ((1u << K) - 1u);
     const int b = TTNG<NG>::FIRST[K] + bl;
     const unsigned mb = blk_mask<NG>()[b];
     const unsigned H = pdep_mask<NG>(c, mb);
     const int pos = blk_off<NG>()[b] + int(c);
-    const V4<T> G = gs_load<NG, T>(Gs, pos), Gbar = gs_load<NG, T>(Gb, pos);
+    const V4<T> G = gs_load<NG, T>(Gs, pos);
+    V4<T> Gbar = gs_load<NG, T>(Gb, pos);
+    if (!act) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) Gbar.c[k] = {T(0), T(0)};
+    }
     const T ginv = mt.ginv[mb];
     // G = ginv acc: d/d(ginv) = Re(conj(acc) Gb) = Re(conj(G) Gb) / ginv, ginv = 1/K^2
     T gib = T(0);
@@ -417,8 +444,10 @@ __device__ __forceinline__ void adj_gluon_level(const MaskTab<NG, T>& mt, const 
       for (int k = 0; k < 4; ++k) GLb.c[k] = GRb.c[k] = {T(0), T(0)};
       R4<T> PLb = {{T(0), T(0), T(0), T(0)}}, PRb = {{T(0), T(0), T(0), T(0)}};
       adj_o3(GL, GR, PL, PR, (ref_neg(rl) != ref_neg(rr)) ? T(-1) : T(1), accb, GLb, GRb, PLb, PRb);
-      gb_atomic<NG, T>(Gb, ref_off(rl) + int(pext_mask<NG>(H, ref_mask(rl))), GLb);
-      gb_atomic<NG, T>(Gb, ref_off(rr) + int(pext_mask<NG>(H, ref_mask(rr))), GRb);
+      gb_item_add<NG, K, T>(Gb, ref_off(rl) + int(pext_mask<NG>(H, ref_mask(rl))), GLb,
+                            pext_mask<NG>(mb & ~ref_mask(rl), mb), c, act);
+      gb_item_add<NG, K, T>(Gb, ref_off(rr) + int(pext_mask<NG>(H, ref_mask(rr))), GRb,
+                            pext_mask<NG>(mb & ~ref_mask(rr), mb), c, act);
       add_mask<NG, T>(pb, ref_mask(rl), PLb);
       add_mask<NG, T>(pb, ref_mask(rr), PRb);
     }
@@ -433,9 +462,12 @@ __device__ __forceinline__ void adj_gluon_level(const MaskTab<NG, T>& mt, const 
 #pragma unroll
         for (int k = 0; k < 4; ++k) GLb.c[k] = GMb.c[k] = GRb.c[k] = {T(0), T(0)};
         adj_o4(GL, GM, GR, (ref_neg(r0) ^ ref_neg(r1) ^ ref_neg(r2)) ? T(-1) : T(1), accb, GLb, GMb, GRb);
-        gb_atomic<NG, T>(Gb, ref_off(r0) + int(pext_mask<NG>(H, ref_mask(r0))), GLb);
-        gb_atomic<NG, T>(Gb, ref_off(r1) + int(pext_mask<NG>(H, ref_mask(r1))), GMb);
-        gb_atomic<NG, T>(Gb, ref_off(r2) + int(pext_mask<NG>(H, ref_mask(r2))), GRb);
+        gb_item_add<NG, K, T>(Gb, ref_off(r0) + int(pext_mask<NG>(H, ref_mask(r0))), GLb,
+                              pext_mask<NG>(mb & ~ref_mask(r0), mb), c, act);
+        gb_item_add<NG, K, T>(Gb, ref_off(r1) + int(pext_mask<NG>(H, ref_mask(r1))), GMb,
+                              pext_mask<NG>(mb & ~ref_mask(r1), mb), c, act);
+        gb_item_add<NG, K, T>(Gb, ref_off(r2) + int(pext_mask<NG>(H, ref_mask(r2))), GRb,
+                              pext_mask<NG>(mb & ~ref_mask(r2), mb), c, act);
       }
     }
   }
