@@ -206,8 +206,9 @@ def main():
                     help="only run 3 iterations of EVENTS events each (small case for ncu captures)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="arithmetic of --profile-case")
-    ap.add_argument("--profile-kernel", default="iterate", choices=["iterate", "me"],
-                    help="--profile-case target: whole iterations, or sampling + the |M|^2 kernel alone")
+    ap.add_argument("--profile-kernel", default="iterate", choices=["iterate", "me", "grad"],
+                    help="--profile-case target: whole iterations, sampling + the |M|^2 kernel alone, or "
+                         "two reverse-mode derivative calls (mf_grad with every per-event output)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -239,6 +240,15 @@ def main():
             torch.cuda.synchronize()
             print(json.dumps({"profile_case": args.workload, "kernel": "me", "events": ne,
                               "precision": args.precision, "mean_me2": float(me.mean())}))
+            return 0
+        if args.profile_kernel == "grad":
+            ne = args.profile_case
+            th = torch.empty(3 * ne, dtype=torch.float64, device="cuda")
+            dy = torch.empty(p.ndim * ne, dtype=torch.float64, device="cuda")
+            for it in range(2):
+                sigma, ds = p.grad(g, w["seed"], it, ne, th, dy)
+            print(json.dumps({"profile_case": args.workload, "kernel": "grad", "events": ne,
+                              "precision": args.precision, "sigma": sigma, "dsigma": ds}))
             return 0
         for it in range(3):
             r = p.vegas_iterate(g, w["seed"], it, args.profile_case, refine=True)
