@@ -204,8 +204,8 @@ def main():
     ap.add_argument("--adapt-events", type=int, default=2 ** 20)
     ap.add_argument("--profile-case", type=int, default=0, metavar="EVENTS",
                     help="only run 3 iterations of EVENTS events each (small case for ncu captures)")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
-                    help="arithmetic of --profile-case")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32tc", "fp64"],
+                    help="arithmetic of --profile-case (fp32tc: FP32 with the tensor-core colour sum)")
     ap.add_argument("--profile-kernel", default="iterate", choices=["iterate", "me", "grad"],
                     help="--profile-case target: whole iterations, sampling + the |M|^2 kernel alone, or "
                          "two reverse-mode derivative calls (mf_grad with every per-event output)")
@@ -227,7 +227,7 @@ def main():
     torch.cuda.set_device(local)
     if args.profile_case:
         w = WORKLOADS[args.workload]
-        prec = mf.MF_FP32 if args.precision == "fp32" else mf.MF_FP64
+        prec = {"fp32": mf.MF_FP32, "fp32tc": mf.MF_FP32_TC, "fp64": mf.MF_FP64}[args.precision]
         p = mf.Process(PROCESS_IDS[w["process"]], **process_kwargs(w, prec))
         g = p.grid()
         if args.profile_kernel == "me":
