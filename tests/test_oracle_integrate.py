@@ -4,6 +4,8 @@
   form sigma = (pi alpha_s^2 / 3s)[(1 + rho + rho^2/16) ln((1+beta)/(1-beta))
   - beta (7/4 + 31 rho/16)] (Combridge 1979) within 3 sigma, and that closed
   form equals Gauss-Legendre quadrature of the differential closed form;
+* e+ e- -> mu+ mu- at sqrt(s) = 100 GeV: the estimate agrees with
+  4 pi alpha^2 / (3 s) within 3 sigma;
 * the hadronic chain (luminosity map, flux, Vegas Jacobian, massive two-body
   phase space) integrates a constant |M|^2 to the 2-D quadrature of
   f(x1) f(x2) beta(s_hat) / (16 pi s_hat);
@@ -50,6 +52,19 @@ def test_gg_ttx_vegas_matches_closed_form():
     ref = sigma_gg_ttx(1000.0, 173.0, 1.2177)
     assert abs(I - ref) < 3 * sig
     assert sig / I < 5e-4
+
+
+def test_ee_mumu_vegas_matches_closed_form():
+    """e+ e- -> mu+ mu- (photon exchange, massless): sigma = 4 pi alpha^2 / (3 s)
+    (Peskin-Schroeder Eq. 5.13); the massless two-body phase space (the
+    rescaling is the identity) and the flux enter unchanged."""
+    cfg = dict(process="epem_mupmum", sqrt_s=100.0, lumi=False)
+    st = integrate.Setup(cfg)
+    res, edges, (I, sig, chi2) = integrate.integrate(st, seed=2, iterations=4, nev=20000)
+    alpha = 1.0 / 137.035999
+    ref = 4 * math.pi * alpha ** 2 / (3 * 100.0 ** 2) * ps.GEV2_TO_PB
+    assert abs(I - ref) < 3 * sig
+    assert sig / I < 2e-4
 
 
 def test_hadronic_chain_with_constant_matrix_element():
