@@ -46,7 +46,8 @@ typedef int mf_status;
 #define MF_ERR_CUDA (-2)        /* a CUDA runtime call failed (message has the CUDA error) */
 #define MF_ERR_UNSUPPORTED (-3) /* process / precision not built */
 #define MF_ERR_COLOUR (-4)      /* colour matrix: wrong size, not symmetric, not the process's, not TF32-exact */
-#define MF_ERR_TIMEOUT (-5)     /* a bounded device wait gave up */
+#define MF_ERR_TIMEOUT (-5)     /* reserved for a bounded device wait that gives up; no kernel of this
+                                   library spins on a flag, so no entry point returns it */
 #define MF_WARN_NEWTON 1        /* some events missed the massive-rescaling Newton tolerance; their weight is 0 */
 
 /* processes (gluon count of the colour-ordered recursion in brackets) */
