@@ -1,4 +1,4 @@
-// Several processes in one iteration (SURVEY config "batched mixed launch";
+// Several processes in one iteration (the batched mixed launch;
 // arXiv:2211.14056 Sec. 3, Fig. 3: how the work is spread over blocks and
 // threads decides the run time, so the launch shape is tuned, not fixed).
 //
