@@ -26,7 +26,6 @@ all-reduced once per step before the refinement.
 """
 import argparse
 import json
-import math
 import multiprocessing as mp
 import os
 import statistics
