@@ -265,8 +265,12 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
     for (int it = 0; it < 50; ++it) {
       const double u0 = xi * e0, u1 = xi * e1;
       const double r0 = sqrt(fma(u0, u0, m2v)), r1 = sqrt(fma(u1, u1, m2v));
-      const double f = u0 * u0 / (r0 + mv) + u1 * u1 / (r1 + mv) + xi * er - exv;
-      const double fp = xi * (e0 * e0 / r0 + e1 * e1 / r1) + er;
+      // the four fractions over one common denominator (one division; every
+      // term is positive, so nothing cancels)
+      const double A = r0 + mv, B = r1 + mv, rr = r0 * r1, ab = A * B;
+      const double iden = 1.0 / (ab * rr);
+      const double f = fma(u0 * u0, B, u1 * u1 * A) * rr * iden + fma(xi, er, -exv);
+      const double fp = fma(xi * fma(e0 * e0, r1, e1 * e1 * r0), ab * iden, er);
       const double dxi = f / fp;
       xi -= dxi;
       const double ad = fabs(dxi);
@@ -283,19 +287,27 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
     const D fp = xi * (E[0] * E[0] / r0 + E[1] * E[1] / r1) + Erest;
     xi = xi - f / fp;
   }
-  D ksum = D(0.0), kprod = D(1.0), k2sum = D(0.0);
+  // |k| = xi |p| = xi E for massless p; the massless final particles have
+  // |k| / k0 = 1, so only the two massive ones enter the product, over one
+  // common denominator
+  const D ka0 = xi * E[0], ka1 = xi * E[1];
+  const D k00 = sqrt(ka0 * ka0 + m2), k01 = sqrt(ka1 * ka1 + m2);
+  const D ik = D(1.0) / (k00 * k01);
+  const D kprod = ka0 * ka1 * ik;
+  D ksum = ka0 + ka1, k2sum = (ka0 * ka0 * k01 + ka1 * ka1 * k00) * ik;
+  out.p[2][0] = K(k00);
+  out.p[3][0] = K(k01);
 #pragma unroll 1
   for (int i = 0; i < n; ++i) {
-    const D ka = xi * E[i];      // |k| = xi |p| = xi E for massless p
-    const D k0 = (i < 2) ? sqrt(ka * ka + m2) : ka;
-    const D ik0 = D(1.0) / k0;
-    out.p[2 + i][0] = K(k0);
+    if (i >= 2) {
+      const D ka = xi * E[i];
+      out.p[2 + i][0] = K(ka);
+      ksum = ksum + ka;
+      k2sum = k2sum + ka;
+    }
     out.p[2 + i][1] = K(xi * D(pm[i][1]));
     out.p[2 + i][2] = K(xi * D(pm[i][2]));
     out.p[2 + i][3] = K(xi * D(pm[i][3]));
-    ksum = ksum + ka;
-    kprod = kprod * (ka * ik0);
-    k2sum = k2sum + ka * ka * ik0;
   }
   D wm = D(1.0);
   {
