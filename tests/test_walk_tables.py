@@ -1,0 +1,69 @@
+"""Host-side properties of the generated quark-line walk tables (gen_tables).
+
+The four-gluon amplitude kernel shares three-gluon quark currents between
+lane pairs: lanes l and l ^ (1 << g) differ only in the helicity of gluon g,
+and a current R(S) with g not in S is the same for both.  For every last
+gluon c and missing gluon g the table kL3Pair4 lists the two level-3 paths
+(a, b, c), (b, a, c); the lane whose g-helicity bit is `bit` computes entry
+`bit` and receives entry `bit ^ 1` from its partner.  These tests check, on
+the emitted tables, that the exchange is consistent and that every lane ends
+up with every level-3 current exactly once, and the depth-first layout the
+kernels rely on.
+"""
+import itertools
+import re
+
+from paper_2211_14056_gb300 import gen_tables
+
+
+def _array(src, name):
+    m = re.search(r"%s\[\d+\] = \{([^}]*)\}" % re.escape(name), src)
+    return [int(x) for x in m.group(1).split(",")]
+
+
+def test_level3_pairs_share_their_current():
+    src = gen_tables.render()
+    pair, miss = _array(src, "kL3Pair4"), _array(src, "kL3Miss4")
+    levels, _ = gen_tables.lane_paths(4)
+    l3 = [T for (T, _, _) in levels[3]]
+    assert len(pair) == 24 and len(miss) == 12
+    for c in range(4):
+        gs = miss[3 * c:3 * c + 3]
+        assert sorted(gs) == sorted(g for g in range(4) if g != c)
+        for gi, g in enumerate(gs):
+            p0, p1 = pair[(3 * c + gi) * 2], pair[(3 * c + gi) * 2 + 1]
+            S0, S1 = l3[p0], l3[p1]
+            # both end with c, neither contains g, and they are the two orders of the rest
+            assert S0[-1] == c and S1[-1] == c and g not in S0 and g not in S1
+            assert S0[:2] == S1[:2][::-1] and set(S0) == set(S1)
+
+
+def test_every_lane_gets_every_level3_current_once():
+    src = gen_tables.render()
+    pair, miss = _array(src, "kL3Pair4"), _array(src, "kL3Miss4")
+    for H in range(16):
+        got = []
+        for c in range(4):
+            for gi in range(3):
+                g = miss[c * 3 + gi]
+                bit = (H >> g) & 1
+                mine, other = pair[(c * 3 + gi) * 2 + bit], pair[(c * 3 + gi) * 2 + (bit ^ 1)]
+                # the partner lane (g's helicity flipped) computes exactly what this lane receives
+                partner_bit = ((H ^ (1 << g)) >> g) & 1
+                assert pair[(c * 3 + gi) * 2 + partner_bit] == other
+                got += [mine, other]
+        assert sorted(got) == list(range(24))
+
+
+def test_depth_first_layout():
+    for n in (2, 3, 4):
+        levels, final = gen_tables.lane_paths(n)
+        for l in range(1, n):
+            # children of one parent are contiguous, n - l + 1 of them, in parent order
+            parents = [p for (_, p, _) in levels[l]]
+            assert parents == sorted(parents)
+            assert all(parents.count(p) == n - l + 1 for p in set(parents))
+            for (T, p, _) in levels[l]:
+                assert T[1:] == levels[l - 1][p][0]
+        # the completions are the n! orderings, each once
+        assert sorted(o for (o, _) in final) == list(range(len(list(itertools.permutations(range(n))))))
