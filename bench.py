@@ -509,7 +509,8 @@ def _mixed_leg(mf, torch, iters=5):
 
 def _ncu_traffic(name):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
+    the current kernel sources (else None): the summary lists the source files
+    the kernel is compiled from (`kernel_sources`) and their SHA-256."""
     import hashlib
     path = os.path.join(ROOT, "profiles", name + ".md")
     if not os.path.exists(path):
@@ -517,13 +518,14 @@ def _ncu_traffic(name):
     rec = {}
     for line in open(path):
         k, _, v = line.strip().partition(":")
-        if k in ("dram_bytes_per_launch", "sources_sha256"):
+        if k in ("dram_bytes_per_launch", "sources_sha256", "kernel_sources"):
             rec[k] = v.strip()
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2211_14056_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    files = rec["kernel_sources"].split() if "kernel_sources" in rec else \
+        sorted(f for f in os.listdir(csrc) if f.endswith((".cu", ".cuh")))
+    for f in files:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     if rec.get("sources_sha256") != h.hexdigest() or "dram_bytes_per_launch" not in rec:
         return None
     return int(rec["dram_bytes_per_launch"])
