@@ -138,6 +138,16 @@ mf_status mf_grid_get(const mf_grid* grid, double* edges_host);
 mf_status mf_grid_set(mf_grid* grid, const double* edges_host);
 /* Forget the recorded iterations (the combination starts again). */
 mf_status mf_grid_reset(mf_grid* grid);
+/* The recorded iterations (checkpoint / resume of the combination): with
+ * I_k and var_k NULL, *count receives the number recorded; otherwise the
+ * first *count estimates I_k and variances sigma_k^2 are copied to the host
+ * arrays (*count must be >= the number recorded).  mf_grid_set_history
+ * replaces the record with `count` iterations (every var_k > 0).  Together
+ * with mf_grid_get/set and the counter-based random numbers, a restored grid
+ * continues like the original: the same events and per-event weights; the
+ * iteration sums differ only in summation order (~1e-16 relative). */
+mf_status mf_grid_history(const mf_grid* grid, int* count, double* I_k, double* var_k);
+mf_status mf_grid_set_history(mf_grid* grid, int count, const double* I_k, const double* var_k);
 
 /* Per-event kinematics of global events 0..n-1 of iteration `iter`:
  * Philox4x32-10 uniforms, Vegas map, luminosity map, RAMBO on diet, massive

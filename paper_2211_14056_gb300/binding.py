@@ -61,6 +61,8 @@ EXPORTS = {
     "mf_grid_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mf_grid_set": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mf_grid_reset": (C.c_int, [C.c_void_p]),
+    "mf_grid_history": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_void_p, C.c_void_p]),
+    "mf_grid_set_history": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "mf_sample": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_int64, C.c_void_p, C.c_void_p,
                             C.c_void_p, C.c_void_p]),
     "mf_matrix_element": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -309,6 +311,31 @@ class Grid:
 
     def reset(self):
         _check(load_library().mf_grid_reset(self._h))
+
+    def history(self):
+        """(I_k, sigma_k^2) of the recorded iterations, as numpy arrays."""
+        import numpy as np
+        n = C.c_int(0)
+        _check(load_library().mf_grid_history(self._h, C.byref(n), None, None))
+        I = np.zeros(max(n.value, 1))
+        v = np.zeros(max(n.value, 1))
+        _check(load_library().mf_grid_history(self._h, C.byref(n), I.ctypes.data, v.ctypes.data))
+        return I[:n.value], v[:n.value]
+
+    def checkpoint(self):
+        """The grid's whole state: edges and the recorded iterations."""
+        I, v = self.history()
+        return {"edges": self.get(), "I_k": I, "var_k": v}
+
+    def restore(self, state):
+        import numpy as np
+        self.set(state["edges"])
+        I = np.ascontiguousarray(state["I_k"], dtype=np.float64)
+        v = np.ascontiguousarray(state["var_k"], dtype=np.float64)
+        if I.shape != v.shape or I.ndim != 1:
+            raise ValueError("I_k and var_k must be 1-D arrays of one length")
+        _check(load_library().mf_grid_set_history(self._h, int(I.size), I.ctypes.data if I.size else None,
+                                                  v.ctypes.data if v.size else None))
 
     def profile(self, enable=True):
         _check(load_library().mf_grid_profile(self._h, 1 if enable else 0))

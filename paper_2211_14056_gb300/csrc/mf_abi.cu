@@ -363,6 +363,34 @@ mf_status mf_grid_reset(mf_grid* g) {
   return MF_OK;
 }
 
+mf_status mf_grid_history(const mf_grid* g, int* count, double* I_k, double* var_k) {
+  if (g == nullptr || count == nullptr) return fail(MF_ERR_ARG, "mf_grid_history: null argument");
+  const int have = int(g->Ik.size());
+  if (I_k == nullptr && var_k == nullptr) {
+    *count = have;
+    return MF_OK;
+  }
+  if (I_k == nullptr || var_k == nullptr) return fail(MF_ERR_ARG, "mf_grid_history: need both arrays or neither");
+  if (*count < have) return fail(MF_ERR_ARG, "mf_grid_history: arrays shorter than the record");
+  for (int k = 0; k < have; ++k) {
+    I_k[k] = g->Ik[size_t(k)];
+    var_k[k] = g->vark[size_t(k)];
+  }
+  *count = have;
+  return MF_OK;
+}
+
+mf_status mf_grid_set_history(mf_grid* g, int count, const double* I_k, const double* var_k) {
+  if (g == nullptr || count < 0 || (count > 0 && (I_k == nullptr || var_k == nullptr)))
+    return fail(MF_ERR_ARG, "mf_grid_set_history: bad argument");
+  for (int k = 0; k < count; ++k)
+    if (!std::isfinite(I_k[k]) || !(var_k[k] > 0) || !std::isfinite(var_k[k]))
+      return fail(MF_ERR_ARG, "mf_grid_set_history: estimates must be finite and variances > 0");
+  g->Ik.assign(I_k, I_k + count);
+  g->vark.assign(var_k, var_k + count);
+  return MF_OK;
+}
+
 mf_status mf_sample(mf_process* p, const mf_grid* g, uint64_t seed, int iter, int64_t n, double* momenta,
                     double* weight_ps, uint8_t* bins, void* stream) {
   if (p == nullptr || g == nullptr || n < 0) return fail(MF_ERR_ARG, "mf_sample: bad argument");

@@ -167,3 +167,10 @@ def test_ee_description_checks_without_device(lib):
                            (dict(colour_num=two), B.MF_ERR_COLOUR)]:
         d = B.ProcessDesc(**{**base, **change})
         assert lib.mf_init_process(C.byref(d), C.byref(h)) == status, change
+
+
+def test_grid_history_null_arguments(lib):
+    from paper_2211_14056_gb300 import binding as B
+    n = C.c_int(0)
+    assert lib.mf_grid_history(None, C.byref(n), None, None) == B.MF_ERR_ARG
+    assert lib.mf_grid_set_history(None, 0, None, None) == B.MF_ERR_ARG
