@@ -40,9 +40,8 @@ if ROOT not in sys.path:
 
 METRIC = "gg→tt̄gg events/s on 1 GB300, FP32/TC vs FP64 fused at σ rel.err≤1e-5; % FMA peak"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
-SM_COUNT_NOMINAL = 152
-FP32_LANES_PER_SM = 128
-FP64_NOMINAL_TFLOPS = 1.25
+FP32_LANES_PER_SM = 128            # FP32 FMA lanes per Blackwell SM (4 sub-partitions x 32)
+FP64_NOMINAL_TFLOPS = 1.25         # GB300's published FP64 rate (the measured DFMA rate is reported beside it)
 
 
 def _measured_peaks():
@@ -365,7 +364,8 @@ def main():
     achieved64 = fpe * statistics.mean(pass64) / (statistics.mean(m[0] for m in me64) * 1e-3) / 1e12
     traffic = _ncu_traffic("k_me_acc_gg_ttxgg_fp32")
     sm_max = _measured_peaks().get("sm_max_mhz", 2070.0)
-    peak_derived = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_derived = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
 
     # 7. the derivative and mixed-launch workloads (N = 1 only)
     grad = mixed = None
@@ -388,7 +388,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "process": "g g -> t tbar g g", "events_per_step": n,
-                       "precision": "FP32 amplitudes + FMA colour sum; FP64 sampling, Newton and sums",
+                       "precision": "FP32 kinematics and amplitudes (FMA colour sum); FP64 Vegas map, Newton polish, "
+                                    "weight and sums",
                        "l2": "flushed (512 MB write) between timed steps; inputs are generated in-kernel",
                        "grid": "adapted by 5 FP64 iterations of 2^20 events, then refined every step"},
             "fp64": {"value": value64, "unit": "events/s", "ms_per_step": ms64},
@@ -404,7 +405,7 @@ def main():
                          "kernel": "k_me_acc<4,float>", "flops_per_event": fpe,
                          "launch_ms": me_ms / chunks, "launches_per_step": chunks,
                          "sampling_ms_per_step": statistics.mean(m[2] for m in me32),
-                         "peak_source": f"derived: {SM_COUNT_NOMINAL} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x "
+                         "peak_source": f"derived: {sm_count} SMs (device) x {FP32_LANES_PER_SM} FP32 FMA lanes x "
                                         f"2 flop x {sm_max:.0f} MHz",
                          "peak_measured_fma": peak_meas, "frac_of_measured_fma": achieved / peak_meas,
                          "fp64": {"kernel": "k_me_acc<4,double>", "achieved": achieved64, "peak": FP64_NOMINAL_TFLOPS,

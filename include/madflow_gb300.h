@@ -149,6 +149,17 @@ mf_status mf_grid_reset(mf_grid* grid);
 mf_status mf_grid_history(const mf_grid* grid, int* count, double* I_k, double* var_k);
 mf_status mf_grid_set_history(mf_grid* grid, int count, const double* I_k, const double* var_k);
 
+/* The uniforms alone (arXiv:2211.14056 Sec. 1: the tensorised Monte Carlo
+ * draws a tensor of random numbers per iteration; Philox4x32-10, Salmon et
+ * al., SC'11): y[j][e] in [0, 1) for dimension j < ndim of global event
+ * first_event + e, e < n, the stream every sampling kernel of this library
+ * draws from (key (seed_lo, seed_hi ^ iter), counter (event_lo, event_hi,
+ * j/2, 0), dims 2k and 2k+1 from words (0,1) and (2,3), 53-bit mantissas).
+ *   y  device [ndim][n] FP64, caller-owned (output); 1 <= ndim <= 10.
+ * Asynchronous on `stream`.  MF_ERR_ARG: negative n or first_event, ndim out
+ * of range, y NULL with n > 0. */
+mf_status mf_uniforms(uint64_t seed, int iter, int64_t first_event, int64_t n, int ndim, double* y, void* stream);
+
 /* Per-event kinematics of global events 0..n-1 of iteration `iter`:
  * Philox4x32-10 uniforms, Vegas map, luminosity map, RAMBO on diet, massive
  * rescaling, cuts.  Outputs (device, each may be NULL):
@@ -200,9 +211,14 @@ mf_status mf_vegas_finish(mf_process* proc, mf_grid* grid, int64_t n_total, int 
  *   weights device [n] FP64 or NULL (output).
  * The per-CTA scratch lives in a fixed 2 MiB array inside the library's device
  * image, reserved on every device that loads the library until the process
- * exits; a launch that would need more returns MF_ERR_ARG.  The first call on
- * a device looks up that array's device address (make it before any stream
- * capture).  The call allocates nothing.  All calls on a device share the one
+ * exits; the launch uses as many persistent CTAs as that array holds (the
+ * result does not depend on the CTA count), and a set-up whose single CTA
+ * needs more than the array returns MF_ERR_ARG.  MF_ERR_UNSUPPORTED: the
+ * fused kernel does not fit on an SM.  The first call on a device looks up
+ * that array's device address and caches it for the process (make that call
+ * before any stream capture); the cached address does not survive
+ * cudaDeviceReset, after which this entry point must not be called again in
+ * the process.  The call allocates nothing.  All calls on a device share the one
  * array: calls that overlap on the GPU (other streams, other host threads) race
  * and must be serialised by the caller.  Each call overwrites every scratch
  * word it reads, so nothing needs clearing between calls. */

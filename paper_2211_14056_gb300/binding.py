@@ -66,6 +66,7 @@ EXPORTS = {
     "mf_sample": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_int64, C.c_void_p, C.c_void_p,
                             C.c_void_p, C.c_void_p]),
     "mf_matrix_element": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mf_uniforms": (C.c_int, [C.c_uint64, C.c_int, C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
     "mf_vegas_iterate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_int64, C.c_int,
                                    C.POINTER(Result), C.c_void_p, C.c_void_p]),
     "mf_vegas_accumulate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_int64, C.c_int64,
@@ -126,6 +127,17 @@ def fma_throughput(precision):
     t = C.c_double()
     _check(load_library().mf_fma_throughput(precision, C.byref(t)))
     return t.value
+
+
+def uniforms(seed, it, n, ndim, first_event=0, out=None, stream=None):
+    """The Philox uniforms y[ndim, n] (float64, device) of global events
+    first_event .. first_event + n - 1 of iteration `it` (mf_uniforms)."""
+    import torch
+    if out is None:
+        out = torch.empty((ndim, n), dtype=torch.float64, device="cuda")
+    _check(load_library().mf_uniforms(seed, it, first_event, n, ndim, _ptr(out, torch.float64, ndim * n, "y"),
+                                      _stream(stream)))
+    return out
 
 
 @functools.lru_cache(maxsize=None)

@@ -118,19 +118,21 @@ mf_status record_iteration(mf_grid* g, const double* r, int64_t n_total, mf_resu
   out->n_events = n_total;
   out->n_pass = int64_t(r[4]);
   out->n_newton_fail = int64_t(r[5]);
+  if (!(r[3] > 0) || !std::isfinite(r[2]) || !std::isfinite(r[3])) {
+    // not recorded: the inverse-variance combination cannot weigh it, and the
+    // recorded history stays one that mf_grid_set_history accepts
+    out->iterations = int(g->Ik.size());
+    out->I = out->sigma = out->chi2dof = NAN;
+    return fail(MF_ERR_ARG, "mf_vegas_finish: the iteration has zero variance (or a non-finite estimate); "
+                            "combination undefined, iteration not recorded");
+  }
   g->Ik.push_back(r[2]);
   g->vark.push_back(r[3]);
   out->iterations = int(g->Ik.size());
   double sw = 0, swi = 0;
-  bool ok = true;
   for (size_t k = 0; k < g->Ik.size(); ++k) {
-    if (!(g->vark[k] > 0)) { ok = false; break; }
     sw += 1.0 / g->vark[k];
     swi += g->Ik[k] / g->vark[k];
-  }
-  if (!ok) {
-    out->I = out->sigma = out->chi2dof = NAN;
-    return fail(MF_ERR_ARG, "mf_vegas_finish: an iteration has zero variance; combination undefined");
   }
   out->I = swi / sw;
   out->sigma = 1.0 / std::sqrt(sw);
@@ -403,6 +405,15 @@ mf_status mf_sample(mf_process* p, const mf_grid* g, uint64_t seed, int iter, in
   return MF_OK;
 }
 
+mf_status mf_uniforms(uint64_t seed, int iter, int64_t first_event, int64_t n, int ndim, double* y, void* stream) {
+  if (n < 0 || first_event < 0 || ndim < 1 || ndim > kMaxDim) return fail(MF_ERR_ARG, "mf_uniforms: bad argument");
+  if (n == 0) return MF_OK;
+  if (y == nullptr) return fail(MF_ERR_ARG, "mf_uniforms: null buffer");
+  MF_CUDA(launch_uniforms(seed, iter, first_event, n, ndim, y, (cudaStream_t)stream), "mf_uniforms");
+  g_launches.fetch_add(1);
+  return MF_OK;
+}
+
 mf_status mf_matrix_element(mf_process* p, int64_t n, const double* momenta, double* me2, void* stream) {
   if (p == nullptr || n < 0) return fail(MF_ERR_ARG, "mf_matrix_element: bad argument");
   if (n == 0) return MF_OK;
@@ -569,8 +580,10 @@ mf_status mf_fma_throughput(int precision, double* tflops) {
 // the library's own device image, reserved when the library is loaded on a
 // device and held there until the process exits.
 //
-// Limit: kStaticScratchBytes (2 MiB), enough for every built process at its
-// full persistent launch (at most 2 + 10*64 doubles per CTA plus two counters).
+// Limit: kStaticScratchBytes (2 MiB).  A CTA needs 2 + ndim*nbins doubles and
+// two counters (at most 5.1 KB at 10 dimensions x 64 bins); the launch uses
+// as many persistent CTAs as the occupancy allows and the array holds
+// (at least 400 at the largest set-up), and strides over the events.
 static constexpr size_t kStaticScratchBytes = size_t(2) << 20;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
@@ -612,17 +625,25 @@ extern "C" mf_status mf_vegas_accumulate_static(mf_process* p, const double* edg
   int ctas = 0;
   cudaError_t e = dispatch_fused_config(p->ng, p->precision, p->ndim, nbins, &smem, &ctas);
   if (e != cudaSuccess) return cuda_fail(e, "mf_vegas_accumulate_static (configuration)");
-  const int64_t ntiles = (n + kTile - 1) / kTile;
-  const int64_t cap = int64_t(p->sms) * effective_ctas(p, ctas);
-  const int grid = int(ntiles < cap ? ntiles : cap);
+  if (ctas < 1)
+    return fail(MF_ERR_UNSUPPORTED, "mf_vegas_accumulate_static: the fused kernel's shared memory (" +
+                                        std::to_string(smem) + " bytes) does not fit on an SM");
+  // per-CTA scratch: the CTA's partial sums, then (after all CTAs' sums) its
+  // two counters; the grid shrinks to what the reserved array holds (the
+  // kernel strides over the events, so the result does not depend on it)
   const size_t nacc = 2 + size_t(p->ndim) * nbins;
-  const size_t part_bytes = sizeof(double) * nacc * size_t(grid);
-  const size_t cnt_off = (part_bytes + 255) & ~size_t(255);
-  const size_t need = cnt_off + sizeof(unsigned long long) * 2 * size_t(grid);
-  if (need > kStaticScratchBytes)
-    return fail(MF_ERR_ARG, "mf_vegas_accumulate_static: this launch needs " + std::to_string(need) +
+  const size_t per_cta = sizeof(double) * nacc + sizeof(unsigned long long) * 2;
+  const int64_t fit = int64_t((kStaticScratchBytes - 256) / per_cta);
+  if (fit < 1)
+    return fail(MF_ERR_ARG, "mf_vegas_accumulate_static: one CTA needs " + std::to_string(per_cta + 256) +
                                 " bytes of scratch, more than the " + std::to_string(kStaticScratchBytes) +
                                 " bytes reserved in the library");
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  int64_t cap = int64_t(p->sms) * effective_ctas(p, ctas);
+  if (cap > fit) cap = fit;
+  const int grid = int(ntiles < cap ? ntiles : cap);
+  const size_t part_bytes = sizeof(double) * nacc * size_t(grid);
+  const size_t cnt_off = (part_bytes + 255) & ~size_t(255);
   unsigned char* scratch = nullptr;
   e = static_scratch(&scratch);
   if (e != cudaSuccess) return cuda_fail(e, "mf_vegas_accumulate_static (scratch address)");

@@ -987,6 +987,8 @@ cudaError_t me_config(int precision, size_t* smem, int* ctas_per_sm);
 
 cudaError_t launch_sample(const SampleParams& sp, const double* edges, int64_t n, uint64_t seed, int iter,
                           double* mom, double* wps, uint8_t* bins, cudaStream_t s);
+cudaError_t launch_uniforms(uint64_t seed, int iter, int64_t first_event, int64_t n, int ndim, double* y,
+                            cudaStream_t s);
 // totals: [0] sum w, [1] sum w^2, [2 + j*nbins + b] histogram, [nacc] passing events, [nacc+1] Newton misses
 cudaError_t launch_reduce(const double* partials, const unsigned long long* counters, int nblocks, int ndim, int nbins,
                           double* totals, cudaStream_t s);

@@ -25,6 +25,29 @@ __global__ void __launch_bounds__(kThreads) k_sample(SampleParams sp, const doub
   }
 }
 
+// The uniforms alone: y[j][e] of global event first_event + e (the same
+// Philox stream every sampling kernel draws from), coalesced FP64 stores.
+__global__ void __launch_bounds__(kThreads) k_uniforms(uint64_t seed, int iter, int64_t first_event, int64_t n,
+                                                       int ndim, double* __restrict__ y) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+    double u[kMaxDim];
+    draw_uniforms(seed, iter, uint64_t(first_event + e), ndim, u);
+    for (int j = 0; j < ndim; ++j) y[int64_t(j) * n + e] = u[j];
+  }
+}
+
+cudaError_t launch_uniforms(uint64_t seed, int iter, int64_t first_event, int64_t n, int ndim, double* y,
+                            cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t need = (n + kThreads - 1) / kThreads;
+  const int grid = int(need < int64_t(sms) * 16 ? need : int64_t(sms) * 16);
+  k_uniforms<<<grid, kThreads, 0, s>>>(seed, iter, first_event, n, ndim, y);
+  return cudaGetLastError();
+}
+
 size_t record_bytes(int precision, int n_final, int ndim, int64_t C) {
   return precision == 0 ? RecordView<double>::bytes(n_final, ndim, C) : RecordView<float>::bytes(n_final, ndim, C);
 }

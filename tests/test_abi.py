@@ -65,6 +65,11 @@ def test_rejects_bad_descriptions_without_device(lib):
     wrong_m = (C.c_double * 4)(0, 0, 173, 172)
     d = B.ProcessDesc(**{**base, "masses": wrong_m})
     assert lib.mf_init_process(C.byref(d), C.byref(h)) == B.MF_ERR_ARG
+    # the uniforms' argument checks come before any device work
+    assert lib.mf_uniforms(1, 0, -1, 10, 3, None, None) == B.MF_ERR_ARG
+    assert lib.mf_uniforms(1, 0, 0, 10, 11, None, None) == B.MF_ERR_ARG
+    assert lib.mf_uniforms(1, 0, 0, 10, 3, None, None) == B.MF_ERR_ARG
+    assert lib.mf_uniforms(1, 0, 0, 0, 3, None, None) == B.MF_OK
 
 
 def test_generated_header_is_current(tmp_path):

@@ -60,3 +60,28 @@ def test_history_arguments(mf):
     I, v = g.history()
     np.testing.assert_array_equal(I, [1.0, 2.0])
     np.testing.assert_array_equal(v, [0.5, 0.25])
+
+
+def test_zero_variance_iteration_is_not_recorded(mf):
+    """An iteration in which no event passes the cuts (all weights 0, zero
+    variance) has no place in the inverse-variance combination: the call
+    fails with MF_ERR_ARG and leaves the recorded history as it was, so a
+    checkpoint taken afterwards still restores."""
+    from paper_2211_14056_gb300.workloads import PROCESS_IDS, WORKLOADS, process_kwargs
+    w = dict(WORKLOADS["gg_ttxg_13tev"])
+    p = mf.Process(PROCESS_IDS[w["process"]], **process_kwargs(w, mf.MF_FP64))
+    g = p.grid()
+    p.vegas_iterate(g, seed=3, it=0, n=4000, refine=False)
+    w["pt_cut"] = 1.0e5                        # above sqrt(S) / 2: nothing passes
+    q = mf.Process(PROCESS_IDS[w["process"]], **process_kwargs(w, mf.MF_FP64))
+    gq = q.grid()
+    gq.restore(g.checkpoint())
+    with pytest.raises(mf.MFError) as ei:
+        q.vegas_iterate(gq, seed=3, it=1, n=4000, refine=False)
+    assert ei.value.status == mf.MF_ERR_ARG
+    I, v = gq.history()
+    assert I.size == 1 and v[0] > 0
+    g2 = p.grid()
+    g2.restore(gq.checkpoint())
+    r = p.vegas_iterate(g2, seed=3, it=1, n=4000, refine=False)
+    assert r["iterations"] == 2

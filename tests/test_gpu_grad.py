@@ -1,13 +1,15 @@
-"""Derivatives of the estimate (mf_grad): the forward-mode dual-number kernels
-against central finite differences.
+"""Derivatives of the estimate: mf_grad (reverse mode, a hand-written adjoint
+sweep of |M|^2) and mf_grad_forward (forward mode, dual numbers) against
+each other and against central finite differences.
 
 What pins them:
+  * the oracle's FP64 weights at y +- h e_j, at m_t +- h and at Gamma_t +- h
+    (a few events, fully independent of the CUDA path), as plain central
+    differences and, for a tight bar, Richardson-extrapolated;
   * the CUDA path's own FP64 weights at theta +- h (all events of the sample,
     a different code path: the plain iteration kernels with shifted
-    parameters), per event, for m_t and Gamma_t;
-  * the oracle's FP64 weights at y +- h e_j and at m_t +- h (a few events,
-    fully independent of the CUDA path), as plain central differences and,
-    for a tight bar, Richardson-extrapolated;
+    parameters), per event, for m_t and Gamma_t, as a consistency check of
+    the whole sample beside the oracle's few events;
   * g_s: I(g_s) is a homogeneous polynomial of degree 2 n_gluons, so the
     central difference of the library's own I agrees to O(h^2);
   * sigma and the per-event weights equal those of mf_vegas_iterate.
@@ -272,6 +274,51 @@ def test_derivatives_match_extrapolated_oracle_differences(mf, name, k):
     assert ok.sum() >= k - 1 and err.max() < 1e-8
 
 
+@pytest.mark.parametrize("name,k", [("gg_ttx_1tev", 40), ("gg_ttxg_13tev", 30), ("gg_ttxgg_13tev", 20)])
+def test_width_derivative_matches_extrapolated_oracle_differences(mf, name, k):
+    """FP64 dw/dGamma_t at Gamma_t = 1.5 GeV against Richardson-extrapolated
+    central differences of the oracle's weights at Gamma_t +- h (h = 1e-2
+    GeV, its own Vegas map, phase space and amplitudes; a different algorithm
+    from the adjoint sweep).  Gamma_t enters only the internal top propagators
+    1/(P^2 - m_t^2 + i m_t Gamma_t), smooth on the scale Gamma_t, so the
+    extrapolation's O(h^4) truncation is ~(h/Gamma_t)^4 ~ 2e-9 relative and the
+    rounding ~eps w / h ~ 1e-14 w.  Cuts and bins do not depend on Gamma_t:
+    every event that passes is compared.  The forward-mode pass
+    (mf_grad_forward) is held to the same reference."""
+    seed, it, n = 41, 1, 256
+    wt = 1.5
+    p, w = _proc(mf, name, mf.MF_FP64, wt=wt)
+    edges = random_grid(p.ndim, seed=19)
+    _, _, th, _ = _grad(p, edges, seed, it, n)
+    (_, _, _, _), (_, _, thf, _) = _grad_both(p, edges, seed, it, n)
+    amp = "feynman" if name == "gg_ttx_1tev" else "bg"
+    w1 = dict(w, wt=wt)
+    st = _oracle_setup(w1, amp)
+    y = oph.uniforms(seed, it, np.arange(n, dtype=np.uint64), st.ndim)
+    w0, _ = st.weights(y, edges)
+    sel = np.flatnonzero(w0 > 0)[:k]
+    assert sel.size == k
+    ys = y[:, sel]
+
+    def f(h):
+        ww, _ = _oracle_setup(w1, amp, wt=wt + h).weights(ys, edges)
+        return ww
+
+    ref = _richardson(f, 1e-2)
+    # the weight's own scale per unit Gamma_t is w / Gamma_t; a derivative far
+    # below it (an event with no near-resonant internal top) is compared there
+    scale = np.maximum(np.abs(ref), 1e-2 * np.abs(w0[sel]) / wt)
+    for label, got in (("reverse", th[2, sel]), ("forward", thf[2, sel])):
+        err = np.abs(got - ref) / scale
+        _report(f"{name} dw/dGamma_t ({label}) vs extrapolated oracle", err)
+        assert np.median(err) < 1e-8 and err.max() < 1e-6
+    # with a final-state gluon an internal top (t + g) can come near its pole:
+    # there Gamma_t moves the weights visibly (for g g -> t tbar the internal
+    # tops are space-like and the derivative is ~1e-6 w / Gamma_t)
+    if name != "gg_ttx_1tev":
+        assert np.max(np.abs(ref) * wt / np.abs(w0[sel])) > 1e-4
+
+
 @pytest.mark.parametrize("name,n", [("gg_ttxg_13tev", 20000), ("gg_ttxgg_13tev", 4000)])
 def test_fp32_derivatives_against_fp64(mf, name, n):
     """FP32 kinematics and amplitudes (FP64 weights): the error of the
@@ -347,6 +394,40 @@ def test_autograd_cross_section(mf):
     pred = float((theta.grad * step).sum())
     assert (I2.item() - sigma) == pytest.approx(pred, rel=1e-2)
     assert math.isfinite(I2.item())
+
+
+def test_autograd_event_weights(mf):
+    """torch.autograd through the per-event weights w(theta, y): the forward
+    values equal mf_vegas_iterate's weights, backward gives the
+    vector-Jacobian products of mf_grad's per-event derivatives for theta and
+    for the uniforms, and the uniforms are the library's Philox stream
+    (checked against the oracle's Philox bit for bit)."""
+    from paper_2211_14056_gb300.autograd import event_weights
+    from paper_2211_14056_gb300.workloads import PROCESS_IDS, WORKLOADS, process_kwargs
+    name, n, seed, it = "gg_ttxgg_13tev", 777, 6, 1
+    w = WORKLOADS[name]
+    kw = process_kwargs(w, mf.MF_FP64)
+    for key in ("gs", "mt", "wt"):
+        kw.pop(key)
+    p, _ = _proc(mf, name, mf.MF_FP64)
+    edges = random_grid(p.ndim, seed=8)
+    y = mf.uniforms(seed, it, n, p.ndim)
+    yo = oph.uniforms(seed, it, np.arange(n, dtype=np.uint64), p.ndim)
+    np.testing.assert_array_equal(y.cpu().numpy(), yo)
+    y.requires_grad_(True)
+    theta = torch.tensor([w["gs"], w["mt"], w["wt"]], dtype=torch.float64, requires_grad=True)
+    wts = event_weights(theta, y, PROCESS_IDS[w["process"]], edges, seed, it, **kw)
+    w0, _ = _weights(mf, name, edges, seed, it, n)
+    np.testing.assert_array_equal(wts.detach().cpu().numpy(), w0)
+    gvec = torch.linspace(-1.0, 2.0, n, dtype=torch.float64, device="cuda")
+    (wts * gvec).sum().backward()
+    _, _, th, dy = _grad(p, edges, seed, it, n)
+    gv = gvec.cpu().numpy()
+    np.testing.assert_allclose(theta.grad.numpy(), th @ gv, rtol=1e-12)
+    np.testing.assert_allclose(y.grad.cpu().numpy(), dy * gv[None, :], rtol=1e-12, atol=0)
+    with pytest.raises(ValueError):
+        event_weights(theta, torch.rand(p.ndim, n, dtype=torch.float64, device="cuda"),
+                      PROCESS_IDS[w["process"]], edges, seed, it, **kw)
 
 
 def test_fp32_derivatives_finite_near_the_luminosity_edge(mf):

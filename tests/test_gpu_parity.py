@@ -2,19 +2,21 @@
 
 Bars (FP64 path): bins bit-exact; momenta and phase-space weights within
 1e-12 relative; I_k, sigma_k and refined edges within 1e-12 relative; per-event
-|M|^2 and event weights within 1e-12 relative for at least 99% of events and
-within 1e-10 for every event (``assert_fp64_parity``; g g -> t tbar g g: 95%,
-its 123 diagrams accumulate rounding to ~1e-12 on a few percent of events).  FP32 path: per-event
-|M|^2 within 2e-4 relative, its error statistics printed.
+|M|^2 and event weights within 1e-12 relative, except events on which the
+oracle's own FP64 algorithms disagree (``assert_fp64_parity``): there the
+GPU value must lie within four times that disagreement of the reference, and
+every event within 1e-10.  FP32 path: per-event |M|^2 within 2e-4 relative,
+its error statistics printed.
 
 Why the per-event |M|^2 bar has a tail: input momenta conserve momentum only
 to ~1e-14 relative (rounding in the phase-space map), and a propagator whose
 invariant is small against the energies (a top nearly collinear with a gluon,
 E^2 / (P^2 - m^2) ~ 10^2..10^3) turns the routing-dependent part of that
-violation into ~1e-11 of |M|^2.  The oracle's own two FP64 algorithms (Feynman
-diagrams vs colour-ordered recursion) disagree by the same 1e-11 on exactly
-those events, and perturbing the momenta by 1e-15 moves either by ~1e-12..1e-11,
-so no FP64 evaluation can be held to 1e-12 there.  A wrong term would show at
+violation into ~1e-11 of |M|^2: the value of |M|^2 on such inputs is only
+defined to that level.  The oracle's algorithms (Feynman diagrams with the
+internal momenta summed from the tree's root, the same diagrams re-rooted at
+the antitop, and the colour-ordered recursion) measure that ambiguity event
+by event, and each tail event is held to it.  A wrong term would show at
 O(1), far above 1e-10.
 """
 import math
@@ -39,13 +41,53 @@ def mf():
     return mf
 
 
-def assert_fp64_parity(got, ref, core=1e-12, tail=1e-10, frac=0.99):
+def oracle_spread(setup, p):
+    """Relative spread of |M|^2 over the oracle's independent FP64 evaluations
+    of the same events: Feynman diagrams routed from the last leg (the
+    reference), Feynman diagrams re-rooted at the antitop (every internal
+    momentum summed from the other side of the tree), and, for a heavy quark
+    pair plus gluons, the colour-ordered recursion."""
+    from oracle.berends_giele import QQbarGluons
+    from oracle.feynman import Amplitude, DiagramSet
+    from oracle.processes import outgoing_flavours
+    proc = setup.proc
+    p = np.asarray(p)
+    vals = [proc.me2(p)]
+    ds = DiagramSet(outgoing_flavours(proc.name), root=list(proc.particles).index("t~"))
+    amp = Amplitude(ds, proc.mass, proc.amp.widths, {"gs": proc.gs, "e": proc.ee})
+    ext, q = proc.external(p)
+    vals.append(amp.summed_squared(ext, q) / proc.average)
+    if all(x in ("g", "t", "t~") for x in proc.particles):
+        vals.append(QQbarGluons(proc).me2(p))
+    v = np.stack(vals)
+    return (v.max(axis=0) - v.min(axis=0)) / np.abs(v[0])
+
+
+def assert_fp64_parity(got, ref, core=1e-12, tail=1e-10, frac=0.99, momenta=None, setup=None):
+    """Per-event FP64 parity.  With the events' momenta and oracle set-up
+    given, every event outside ``core`` is arbitrated: the oracle evaluates it
+    with each of its algorithms (``oracle_spread``), and the GPU value must
+    lie within core |ref| + 4 * (their spread) of the reference (relative
+    deviations of weights equal those of |M|^2 up to the weight factor's own
+    rounding, ~1e-15).  Without momenta the blanket fraction ``frac`` applies
+    instead."""
     got, ref = np.asarray(got), np.asarray(ref)
     assert got.shape == ref.shape
     rel = np.abs(got - ref) / np.abs(ref)
-    print(f"FP64 parity: {np.mean(rel <= core):.4f} of {rel.size} within {core:g}, max {rel.max():.2e}")
-    assert np.mean(rel <= core) >= frac
+    inside = rel <= core
+    print(f"FP64 parity: {np.mean(inside):.4f} of {rel.size} within {core:g}, max {rel.max():.2e}")
     assert rel.max() <= tail
+    if momenta is None:
+        assert np.mean(inside) >= frac
+        return
+    out = np.flatnonzero(~inside)
+    if out.size == 0:
+        return
+    spread = oracle_spread(setup, np.asarray(momenta)[out])
+    ratio = rel[out] / np.maximum(spread, core)
+    print(f"  {out.size} tail events: GPU deviation / oracle spread: median {np.median(ratio):.2f}, "
+          f"max {ratio.max():.2f}; spread median {np.median(spread):.1e}, max {spread.max():.1e}")
+    assert np.all(rel[out] <= core + 4 * spread)
 
 
 def _proc(mf, name, precision, **over):
@@ -103,9 +145,8 @@ def _cut_events(st, seed, nev):
     return po[cut][:nev]
 
 
-@pytest.mark.parametrize("name,nev,frac", [("gg_ttx_1tev", 1000, 0.99), ("gg_ttxg_13tev", 500, 0.99),
-                                           ("gg_ttxgg_13tev", 200, 0.95)])
-def test_matrix_element_fp64_matches_feynman_oracle(mf, name, nev, frac):
+@pytest.mark.parametrize("name,nev", [("gg_ttx_1tev", 1000), ("gg_ttxg_13tev", 500), ("gg_ttxgg_13tev", 200)])
+def test_matrix_element_fp64_matches_feynman_oracle(mf, name, nev):
     p, w = _proc(mf, name, mf.MF_FP64)
     st = _oracle_setup(w)
     po = _cut_events(st, 5, nev)
@@ -113,7 +154,7 @@ def test_matrix_element_fp64_matches_feynman_oracle(mf, name, nev, frac):
     out = torch.empty(len(po), dtype=torch.float64, device="cuda")
     p.matrix_element(len(po), _aos_to_soa(po), out)
     torch.cuda.synchronize()
-    assert_fp64_parity(out.cpu().numpy(), ref, frac=frac)
+    assert_fp64_parity(out.cpu().numpy(), ref, momenta=po, setup=st)
 
 
 @pytest.mark.parametrize("tc", [False, True])
@@ -205,10 +246,9 @@ def test_matrix_element_edge_cases(mf):
     assert_fp64_parity(one.cpu().numpy(), ref[:1])
 
 
-@pytest.mark.parametrize("name,n,amp,frac", [("gg_ttx_1tev", 20000, "feynman", 0.99),
-                                             ("gg_ttxg_13tev", 4000, "bg", 0.99),
-                                             ("gg_ttxgg_13tev", 700, "bg", 0.95)])
-def test_vegas_iterations_match_oracle(mf, name, n, amp, frac):
+@pytest.mark.parametrize("name,n,amp", [("gg_ttx_1tev", 20000, "feynman"), ("gg_ttxg_13tev", 4000, "bg"),
+                                        ("gg_ttxgg_13tev", 700, "bg")])
+def test_vegas_iterations_match_oracle(mf, name, n, amp):
     """Two iterations with refinement: weights, I_k, sigma_k and the refined
     grid against the oracle's (colour-ordered recursion for the big processes,
     itself pinned to the Feynman-diagram oracle)."""
@@ -223,7 +263,8 @@ def test_vegas_iterations_match_oracle(mf, name, n, amp, frac):
         wg = wt.cpu().numpy()
         np.testing.assert_array_equal(wg > 0, ro["w"] > 0)
         nz = ro["w"] > 0
-        assert_fp64_parity(wg[nz], ro["w"][nz], frac=frac)
+        pk = st.kinematics(oph.uniforms(9, it, np.arange(n, dtype=np.uint64), st.ndim), edges)[0]
+        assert_fp64_parity(wg[nz], ro["w"][nz], momenta=pk[nz], setup=st)
         assert r["I_k"] == pytest.approx(ro["I"], rel=1e-12)
         assert r["sigma_k"] == pytest.approx(math.sqrt(ro["var"]), rel=1e-11)
         assert r["n_pass"] == int(nz.sum())
@@ -249,7 +290,8 @@ def test_full_size_sampled_weights_and_determinism(mf):
     wo, _ = st.weights(y, ov.uniform_grid(st.ndim))
     nz = wo > 0
     np.testing.assert_array_equal(wall[idx.astype(np.int64)] > 0, nz)
-    assert_fp64_parity(wall[idx.astype(np.int64)][nz], wo[nz], frac=0.95)
+    pk = st.kinematics(y, ov.uniform_grid(st.ndim))[0]
+    assert_fp64_parity(wall[idx.astype(np.int64)][nz], wo[nz], momenta=pk[nz], setup=st)
     g2 = p.grid()
     wt2 = torch.empty(n, dtype=torch.float64, device="cuda")
     p.vegas_iterate(g2, seed=w["seed"], it=0, n=n, refine=False, weights=wt2)

@@ -7,6 +7,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle.integrate as oi
+import oracle.philox as oph
 import oracle.vegas as ov
 from tests.test_gpu_parity import _aos_to_soa, assert_fp64_parity
 
@@ -35,7 +36,6 @@ def _setup(w):
 
 
 def _events(st, seed, nev):
-    import oracle.philox as oph
     y = oph.uniforms(seed, 0, np.arange(4 * nev, dtype=np.uint64), st.ndim)
     po, _, _, cut = st.kinematics(y, ov.uniform_grid(st.ndim))
     return po[cut][:nev]
@@ -50,7 +50,7 @@ def test_matrix_element_fp64_matches_oracle(mf, wt):
     out = torch.empty(len(po), dtype=torch.float64, device="cuda")
     p.matrix_element(len(po), _aos_to_soa(po), out)
     torch.cuda.synchronize()
-    assert_fp64_parity(out.cpu().numpy(), ref, frac=0.95)
+    assert_fp64_parity(out.cpu().numpy(), ref, momenta=po, setup=st)
 
 
 def test_matrix_element_fp32_error(mf):
@@ -83,7 +83,8 @@ def test_vegas_iterations_match_oracle(mf):
         wg = wt.cpu().numpy()
         np.testing.assert_array_equal(wg > 0, ro["w"] > 0)
         nz = ro["w"] > 0
-        assert_fp64_parity(wg[nz], ro["w"][nz], frac=0.95)
+        pk = st.kinematics(oph.uniforms(9, it, np.arange(n, dtype=np.uint64), st.ndim), edges)[0]
+        assert_fp64_parity(wg[nz], ro["w"][nz], momenta=pk[nz], setup=st)
         assert r["I_k"] == pytest.approx(ro["I"], rel=1e-10)
         assert r["sigma_k"] == pytest.approx(np.sqrt(ro["var"]), rel=1e-9)
         np.testing.assert_allclose(g.get(), ov.refine(edges, ro["hist"]), rtol=0, atol=1e-12)
@@ -110,7 +111,7 @@ def test_unsupported_paths_and_sizes(mf):
     one = torch.empty(1, dtype=torch.float64, device="cuda")
     p.matrix_element(1, _aos_to_soa(po[:1]), one)
     torch.cuda.synchronize()
-    assert_fp64_parity(out.cpu().numpy(), ref, frac=0.95)
+    assert_fp64_parity(out.cpu().numpy(), ref, momenta=po, setup=st)
     assert one.item() == out[0].item()
 
 
