@@ -204,6 +204,9 @@ def main():
                     help="only run 3 iterations of EVENTS events each (small case for ncu captures)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32tc", "fp64"],
                     help="arithmetic of --profile-case (fp32tc: FP32 with the tensor-core colour sum)")
+    ap.add_argument("--launch-shapes", action="store_true",
+                    help="only run the full launch-shape sweep of the |M|^2 kernel (10^6 g g -> t tbar g g events "
+                         "per shape) and print it as one JSON line")
     ap.add_argument("--profile-kernel", default="iterate", choices=["iterate", "me", "grad"],
                     help="--profile-case target: whole iterations, sampling + the |M|^2 kernel alone, or "
                          "two reverse-mode derivative calls (mf_grad with every per-event output)")
@@ -223,6 +226,9 @@ def main():
     from paper_2211_14056_gb300.workloads import PROCESS_IDS, WORKLOADS, oracle_cfg, process_kwargs
 
     torch.cuda.set_device(local)
+    if args.launch_shapes:
+        print(json.dumps({"launch_shapes": _launch_shape_leg(mf, torch, full=True)}), flush=True)
+        return 0
     if args.profile_case:
         w = WORKLOADS[args.workload]
         prec = {"fp32": mf.MF_FP32, "fp32tc": mf.MF_FP32_TC, "fp64": mf.MF_FP64}[args.precision]
@@ -363,15 +369,22 @@ def main():
     peak64_meas = mf.fma_throughput(mf.MF_FP64)
     achieved64 = fpe * statistics.mean(pass64) / (statistics.mean(m[0] for m in me64) * 1e-3) / 1e12
     traffic = _ncu_traffic("k_me_acc_gg_ttxgg_fp32")
+    # the sampling kernel's HBM roofline: record bytes written per event over
+    # its CUDA-event time (it is bound by the FP64 pipe, not by HBM)
+    hbm_peak = _measured_peaks().get("hbm_gbs")
+    spe = mflops.sampler_bytes_per_event(ng, p32.ndim, statistics.mean(pass32) / n, 4)
+    smp_ms = statistics.mean(m[2] for m in me32)
+    smp_gbs = spe * n / (smp_ms * 1e-3) / 1e9
     sm_max = _measured_peaks().get("sm_max_mhz", 2070.0)
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     peak_derived = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
 
     # 7. the derivative and mixed-launch workloads (N = 1 only)
-    grad = mixed = None
+    grad = mixed = shapes = None
     if world == 1 and not args.no_extras:
         grad = _grad_leg(p32, p64, g32, g64, w, torch)
         mixed = _mixed_leg(mf, torch)
+        shapes = _launch_shape_leg(mf, torch)
 
     # 8. CPU baseline: the oracle on the host cores (rank 0 only, N = 1 only)
     cpu = None
@@ -404,7 +417,12 @@ def main():
                          "frac": achieved / peak_derived, "traffic": traffic,
                          "kernel": "k_me_acc<4,float>", "flops_per_event": fpe,
                          "launch_ms": me_ms / chunks, "launches_per_step": chunks,
-                         "sampling_ms_per_step": statistics.mean(m[2] for m in me32),
+                         "sampling_ms_per_step": smp_ms,
+                         "sampling": {"kernel": "k_sample_rec<float>", "bound": "FP64 pipe (Vegas map, Newton "
+                                      "polish, weight), not HBM", "bytes_per_event": spe, "achieved": smp_gbs,
+                                      "peak": hbm_peak, "unit": "GB/s",
+                                      "frac": (smp_gbs / hbm_peak) if hbm_peak else None,
+                                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
                          "peak_source": f"derived: {sm_count} SMs (device) x {FP32_LANES_PER_SM} FP32 FMA lanes x "
                                         f"2 flop x {sm_max:.0f} MHz",
                          "peak_measured_fma": peak_meas, "frac_of_measured_fma": achieved / peak_meas,
@@ -420,6 +438,8 @@ def main():
             line["grad"] = grad
         if mixed is not None:
             line["mixed"] = mixed
+        if shapes is not None:
+            line["launch_shape"] = shapes
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -506,6 +526,50 @@ def _mixed_leg(mf, torch, iters=5):
             "speedup_vs_separate": ms_sep / ms_mixed,
             "autotune": {"candidates": cands, "ms": times, "best": cands[best]},
             "graph": True, "I_pb": [r["I"] for r in res]}
+
+
+def _launch_shape_leg(mf, torch, full=False, n=10 ** 6, reps=3):
+    """The launch-shape study (arXiv:2211.14056 Sec. 3, Fig. 3: run time of
+    10^6 g g -> t tbar g g events against threads per block): one Vegas
+    accumulation of n FP32 events (sampling + |M|^2 + accumulation) per launch
+    shape of the |M|^2 kernel, warps per CTA 1..7 (32..224 threads) at the
+    most CTAs per SM that fit (``full``: every CTA count up to that), on the
+    uniform grid.  Times are CUDA events on the stream, mean of `reps` calls
+    after one warm-up call."""
+    import statistics as stats
+    from paper_2211_14056_gb300.workloads import PROCESS_IDS, WORKLOADS, process_kwargs
+    w = WORKLOADS["gg_ttxgg_13tev"]
+    p = mf.Process(PROCESS_IDS[w["process"]], **process_kwargs(w, mf.MF_FP32))
+    g = p.grid()
+    pts = []
+    for W in range(1, 8):
+        cmax = p.set_launch_shape(W)
+        cs = list(range(1, cmax + 1)) if full else sorted({cmax, 1} if W == 4 else {cmax})
+        for c in cs:
+            p.set_ctas_per_sm(c)
+            p.vegas_accumulate(g, w["seed"], 0, 0, n)
+            g.profile(True)
+            tt, tm = [], []
+            for r in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                p.vegas_accumulate(g, w["seed"], 1 + r, 0, n)
+                e1.record()
+                torch.cuda.synchronize()
+                tt.append(e0.elapsed_time(e1))
+                tm.append(g.profile_read()[1])
+            g.profile(False)
+            ms = stats.mean(tt)
+            pts.append({"threads_per_block": 32 * W, "warps_per_cta": W, "ctas_per_sm": c, "warps_per_sm": W * c,
+                        "ms": ms, "me_ms": stats.mean(tm), "events_per_s": n / (ms * 1e-3)})
+    p.set_launch_shape(0)
+    p.set_ctas_per_sm(0)
+    best = min(pts, key=lambda x: x["ms"])
+    default = [x for x in pts if x["warps_per_cta"] == 4 and x["ctas_per_sm"] == max(
+        y["ctas_per_sm"] for y in pts if y["warps_per_cta"] == 4)][0]
+    return {"workload": "gg_ttxgg_13tev (uniform grid), FP32", "events": n, "points": pts, "best": best,
+            "default": default}
 
 
 def _ncu_traffic(name):

@@ -124,6 +124,19 @@ mf_status mf_process_ndim(const mf_process* proc, int* ndim);
  * (arXiv:2211.14056 Sec. 3, Fig. 3: the block configuration matters). */
 mf_status mf_set_ctas_per_sm(mf_process* proc, int ctas_per_sm);
 
+/* Launch shape of the |M|^2 kernel of the iteration (arXiv:2211.14056 Sec. 3,
+ * Fig. 3: the run time of 10^6 g g -> t t~ g g events depends on the threads
+ * per block): warps_per_cta in 1..7 (32 to 224 threads per block; every warp
+ * holds ~29 KB of shared memory, so 7 warps is the largest CTA that fits an
+ * SM), 0 restores the default of 4.  Together with mf_set_ctas_per_sm it
+ * spans the launch shapes of the launch-shape study; results do not depend on
+ * it (the same per-warp code; only the order of the CTA partial sums).
+ * *max_ctas_per_sm (host, may be NULL) receives how many such CTAs fit on
+ * one SM at 50 bins per dimension (the occupancy limit of mf_set_ctas_per_sm).
+ * Covers MF_PROC_GG_TTXGG with MF_FP32 or MF_FP32_TC (else
+ * MF_ERR_UNSUPPORTED); MF_ERR_ARG outside [0, 7]. */
+mf_status mf_set_launch_shape(mf_process* proc, int warps_per_cta, int* max_ctas_per_sm);
+
 /* Vegas grid (Lepage 1978, the integrator named in Sec. 1): nbins equal bins
  * per dimension (2 <= nbins <= 64), device edges [ndim][nbins+1], device
  * scratch for per-CTA partial sums sized for the process's largest launch,

@@ -56,6 +56,7 @@ EXPORTS = {
     "mf_destroy_process": (C.c_int, [C.c_void_p]),
     "mf_process_ndim": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "mf_set_ctas_per_sm": (C.c_int, [C.c_void_p, C.c_int]),
+    "mf_set_launch_shape": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "mf_grid_create": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     "mf_grid_destroy": (C.c_int, [C.c_void_p]),
     "mf_grid_get": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -223,6 +224,13 @@ class Process:
 
     def set_ctas_per_sm(self, c):
         _check(load_library().mf_set_ctas_per_sm(self._h, int(c)))
+
+    def set_launch_shape(self, warps_per_cta):
+        """Warps per CTA of the iteration's |M|^2 kernel (0: default); returns
+        how many such CTAs fit on one SM."""
+        c = C.c_int()
+        _check(load_library().mf_set_launch_shape(self._h, int(warps_per_cta), C.byref(c)))
+        return c.value
 
     def grid(self, nbins=50):
         return Grid(self, nbins)

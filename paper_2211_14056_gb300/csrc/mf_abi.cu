@@ -284,6 +284,27 @@ mf_status mf_set_ctas_per_sm(mf_process* p, int c) {
   return MF_OK;
 }
 
+mf_status mf_set_launch_shape(mf_process* p, int warps_per_cta, int* max_ctas_per_sm) {
+  if (p == nullptr || warps_per_cta < 0 || warps_per_cta > 7)
+    return fail(MF_ERR_ARG, "mf_set_launch_shape: warps_per_cta must be in [0, 7]");
+  if (warps_per_cta > 0 && (p->kind != 0 || p->ng != 4 || p->precision == MF_FP64))
+    return fail(MF_ERR_UNSUPPORTED, "mf_set_launch_shape: launch shapes exist for g g -> t t~ g g in FP32");
+  if (warps_per_cta > 0) {
+    size_t smem = 0;
+    int ctas = 0;
+    MF_CUDA(me_acc_shape_config(warps_per_cta, p->ndim, 50, &smem, &ctas), "mf_set_launch_shape");
+    if (ctas < 1)
+      return fail(MF_ERR_UNSUPPORTED, "mf_set_launch_shape: " + std::to_string(warps_per_cta) + " warps (" +
+                                          std::to_string(smem) + " bytes of shared memory) do not fit on an SM");
+    if (max_ctas_per_sm != nullptr) *max_ctas_per_sm = ctas;
+  } else if (max_ctas_per_sm != nullptr) {
+    size_t smem = 0;
+    MF_CUDA(dispatch_acc_config(proc_key(p), p->precision, p->ndim, 50, &smem, max_ctas_per_sm), "mf_set_launch_shape");
+  }
+  p->me_warps = warps_per_cta;
+  return MF_OK;
+}
+
 mf_status mf_grid_create(const mf_process* p, int nbins, mf_grid** out) {
   if (p == nullptr || out == nullptr) return fail(MF_ERR_ARG, "mf_grid_create: null argument");
   if (nbins < 2 || nbins > 64) return fail(MF_ERR_ARG, "mf_grid_create: nbins must be in [2, 64]");
@@ -302,8 +323,10 @@ mf_status mf_grid_create(const mf_process* p, int nbins, mf_grid** out) {
   }
   if (e == cudaSuccess) e = dispatch_acc_config(proc_key(p), p->precision, g->ndim, nbins, &g->acc_smem, &g->acc_ctas);
   if (e == cudaSuccess && g->acc_ctas < 1) e = cudaErrorInvalidConfiguration;
-  const int most = std::max(g->fused_ctas, g->acc_ctas);
-  g->max_blocks = p->sms * (most < 1 ? 1 : most);
+  // CTA partials: room for the largest persistent grid any launch shape uses
+  // (at most 8 resident warps per SM, one warp per CTA)
+  const int most = std::max(std::max(g->fused_ctas, g->acc_ctas), 8);
+  g->max_blocks = p->sms * most;
   g->chunk = kRecordChunk;
   std::vector<double> edges(size_t(g->ndim) * (nbins + 1));
   for (int j = 0; j < g->ndim; ++j)
@@ -444,7 +467,20 @@ mf_status mf_vegas_accumulate(mf_process* p, mf_grid* g, uint64_t seed, int iter
   SampleParams sp = p->sp;
   sp.nbins = g->nbins;
   const int prec = p->precision == MF_FP64 ? 0 : 1;
-  const int64_t cap = int64_t(p->sms) * effective_ctas(p, g->acc_ctas);
+  const int warps = p->me_warps > 0 ? p->me_warps : kWarps;
+  int acc_ctas = g->acc_ctas;
+  if (p->me_warps > 0) {
+    if (g->shape_warps != p->me_warps) {
+      size_t smem = 0;
+      int ctas = 0;
+      MF_CUDA(me_acc_shape_config(p->me_warps, g->ndim, g->nbins, &smem, &ctas), "mf_vegas_accumulate (launch shape)");
+      if (ctas < 1) return fail(MF_ERR_UNSUPPORTED, "mf_vegas_accumulate: the launch shape does not fit on an SM");
+      g->shape_warps = p->me_warps;
+      g->shape_ctas = ctas;
+    }
+    acc_ctas = g->shape_ctas;
+  }
+  const int64_t cap = std::min<int64_t>(int64_t(p->sms) * effective_ctas(p, acc_ctas), g->max_blocks);
   int grid = 0;
   if (g->profile) {
     const size_t need = size_t(3) * size_t((n + g->chunk - 1) / g->chunk);
@@ -460,7 +496,7 @@ mf_status mf_vegas_accumulate(mf_process* p, mf_grid* g, uint64_t seed, int iter
   for (int64_t done = 0, k = 0; done < n; done += g->chunk, ++k) {
     const int64_t m = std::min(g->chunk, n - done);
     const int64_t warps_needed = (m + 31) / 32;
-    const int64_t ctas_needed = (warps_needed + kWarps - 1) / kWarps;
+    const int64_t ctas_needed = (warps_needed + warps - 1) / warps;
     if (k == 0) grid = int(std::min(cap, std::max<int64_t>(ctas_needed, 1)));
     double* w = weights ? weights + done : nullptr;
     cudaEvent_t* evk = g->profile ? &g->ev[size_t(3) * k] : nullptr;
@@ -470,7 +506,7 @@ mf_status mf_vegas_accumulate(mf_process* p, mf_grid* g, uint64_t seed, int iter
       case kEeKey: e = launch_chunk_ee(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
       case 2: e = launch_chunk<2>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
       case 3: e = launch_chunk<3>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
-      default: e = launch_chunk<4>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
+      default: e = launch_chunk<4>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk, p->me_warps); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "mf_vegas_accumulate (chunk kernels)");
     g_launches.fetch_add(2);

@@ -31,6 +31,7 @@ struct mf_process {
   int me_ctas = 1;
   size_t me_smem = 0;
   int ctas_override = 0;
+  int me_warps = 0;                // warps per CTA of the |M|^2 kernel (0: the default 4; mf_set_launch_shape)
   double g_s = 0.0, width = 0.0;   // strong coupling and top width of the descriptor
   int kind = 0;                    // 0: g g -> t t~ + gluons (ng = n_final), 1: u u~ -> t t~ g g,
                                    // 2: e+ e- -> mu+ mu- (ng = n_final = 2)
@@ -43,6 +44,8 @@ struct mf_grid {
   int fused_ctas = 1;
   size_t fused_smem = 0;
   int acc_ctas = 1;            // CTAs per SM of the |M|^2-and-accumulate kernel
+  int shape_warps = 0;         // launch shape whose occupancy shape_ctas holds (0: none yet)
+  int shape_ctas = 0;
   size_t acc_smem = 0;
   int64_t chunk = 0;           // events per record chunk
   void* d_records = nullptr;   // per-event records of one chunk

@@ -861,12 +861,16 @@ __global__ void __launch_bounds__(kThreads) k_sample_rec(SampleParams sp, const 
     if (e < n) {
       EventKin<K> k;
       sample_event(sp, edges, seed, iter, uint64_t(first_event + e), k);
-      for (int i = 0; i < nf; ++i)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) rec.mom[int64_t(i * 4 + c) * rec.C + e] = k.p[2 + i][c];
+      for (int i = 0; i < kMaxExt - 2; ++i)
+        if (i < nf)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) rec.mom[int64_t(i * 4 + c) * rec.C + e] = k.p[2 + i][c];
       rec.rs[e] = k.p[0][0] + k.p[1][0];
       rec.pref[e] = k.prefactor;
-      for (int j = 0; j < sp.ndim; ++j) rec.flag[int64_t(j) * rec.C + e] = k.bins[j];
+#pragma unroll
+      for (int j = 0; j < kMaxDim; ++j)
+        if (j < sp.ndim) rec.flag[int64_t(j) * rec.C + e] = k.bins[j];
       pass = k.pass;
       fail = k.newton_fail;
       if (!pass && w_out != nullptr) w_out[e] = 0.0;
@@ -883,23 +887,24 @@ __global__ void __launch_bounds__(kThreads) k_sample_rec(SampleParams sp, const 
   }
 }
 
-template <int NG, typename T> struct MeAccLayout {
+// W: warps per CTA (the launch shape; 4 by default)
+template <int NG, typename T, int W = kWarps> struct MeAccLayout {
   __host__ __device__ static size_t al(size_t x) { return (x + 15) & ~size_t(15); }
   __host__ __device__ static size_t hist(int) { return 0; }
   __host__ __device__ static size_t sums(int nacc) { return al(sizeof(double) * (nacc - 2)); }
   __host__ __device__ static size_t warps(int nacc) { return al(sums(nacc) + sizeof(double) * 2); }
-  __host__ __device__ static size_t total(int nacc) { return al(warps(nacc) + WarpMem<NG, T>::bytes * kWarps); }
+  __host__ __device__ static size_t total(int nacc) { return al(warps(nacc) + WarpMem<NG, T>::bytes * W); }
 };
 
 // |M|^2 of the listed events, weights, Vegas sums.  partials[blockIdx.x * nacc + k]
 // receive (accumulate = 0) or add (accumulate = 1) the CTA's sums; block 0
-// also carries the chunk's counters.
-template <int NG, typename T>
-__global__ void __launch_bounds__(kThreads, 2) k_me_acc(MeParams mp, int ndim, int nbins, RecordView<T> rec,
-                                                        int accumulate, double* __restrict__ partials,
-                                                        unsigned long long* __restrict__ counters,
-                                                        double* __restrict__ w_out) {
-  using LY = MeAccLayout<NG, T>;
+// also carries the chunk's counters.  W warps per CTA (32 W threads).
+template <int NG, typename T, int W = kWarps>
+__global__ void __launch_bounds__(32 * W, (8 / W) > 0 ? 8 / W : 1)
+    k_me_acc(MeParams mp, int ndim, int nbins, RecordView<T> rec, int accumulate, double* __restrict__ partials,
+             unsigned long long* __restrict__ counters, double* __restrict__ w_out) {
+  using LY = MeAccLayout<NG, T, W>;
+  constexpr int kThr = 32 * W;
   constexpr int EPW = Lanes<NG>::EPW, L = Lanes<NG>::L, NEXT = Lanes<NG>::NEXT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nacc = 2 + ndim * nbins;
@@ -908,7 +913,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_me_acc(MeParams mp, int ndim, i
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int group = lane / L, gl = lane % L;
   unsigned char* wm = smem_raw + LY::warps(nacc) + warp * WarpMem<NG, T>::bytes;
-  for (int i = t; i < ndim * nbins; i += kThreads) hist[i] = 0.0;
+  for (int i = t; i < ndim * nbins; i += kThr) hist[i] = 0.0;
   if (t < 2) sums[t] = 0.0;
   const T mt = T(mp.mt), mw = T(mp.mw);
   const unsigned full = 0xffffffffu;
@@ -916,8 +921,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_me_acc(MeParams mp, int ndim, i
   double s1 = 0.0, s2 = 0.0;
   __syncthreads();
 
-  const int64_t stride = int64_t(gridDim.x) * kWarps * EPW;
-  for (int64_t base = (int64_t(blockIdx.x) * kWarps + warp) * EPW; base < npass; base += stride) {
+  const int64_t stride = int64_t(gridDim.x) * W * EPW;
+  for (int64_t base = (int64_t(blockIdx.x) * W + warp) * EPW; base < npass; base += stride) {
     const int64_t k = base + group;
     const bool ok = k < npass;
     const int64_t e = rec.list[ok ? k : base];
@@ -950,7 +955,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_me_acc(MeParams mp, int ndim, i
   }
   __syncthreads();
   double* dst = partials + int64_t(blockIdx.x) * nacc;
-  for (int i = t; i < ndim * nbins; i += kThreads) dst[2 + i] = (accumulate ? dst[2 + i] : 0.0) + hist[i];
+  for (int i = t; i < ndim * nbins; i += kThr) dst[2 + i] = (accumulate ? dst[2 + i] : 0.0) + hist[i];
   if (t < 2) dst[t] = (accumulate ? dst[t] : 0.0) + sums[t];
   if (t < 2) {
     const unsigned long long c = blockIdx.x == 0 ? (unsigned long long)rec.count[t] : 0ull;
@@ -973,12 +978,20 @@ template <int NG>
 cudaError_t launch_me_acc(int precision, const MeParams& mp, int n_final, int ndim, int nbins, void* rec_base,
                           int64_t C, int accumulate, double* partials, unsigned long long* counters, double* w_out,
                           int grid, cudaStream_t s);
-// two-kernel iteration over one chunk of records (rec_base: RecordView of chunk capacity C)
+// two-kernel iteration over one chunk of records (rec_base: RecordView of chunk capacity C);
+// me_warps > 0 selects the |M|^2 kernel with that many warps per CTA (g g -> t t~ g g, FP32 only)
 template <int NG>
 cudaError_t launch_chunk(int precision, const SampleParams& sp, const MeParams& mp, const double* edges,
                          int64_t first_event, int64_t n, int64_t C, void* rec_base, uint64_t seed, int iter,
                          int accumulate, double* partials, unsigned long long* counters, double* w_out, int grid,
-                         cudaStream_t s, cudaEvent_t* ev = nullptr);
+                         cudaStream_t s, cudaEvent_t* ev = nullptr, int me_warps = 0);
+// The FP32 g g -> t t~ g g |M|^2-and-accumulate kernel with `warps` (1..8) warps per
+// CTA (mf_launch_shape.cu): its shared memory and occupancy, and a launch over
+// the records of one chunk.
+cudaError_t me_acc_shape_config(int warps, int ndim, int nbins, size_t* smem, int* ctas);
+cudaError_t launch_me_acc_shape(int warps, const MeParams& mp, int n_final, int ndim, int nbins, void* rec_base,
+                                int64_t C, int accumulate, double* partials, unsigned long long* counters,
+                                double* w_out, int grid, cudaStream_t s);
 template <int NG>
 cudaError_t me_acc_config(int precision, int ndim, int nbins, size_t* smem, int* ctas_per_sm);
 size_t record_bytes(int precision, int n_final, int ndim, int64_t C);
@@ -1060,7 +1073,7 @@ cudaError_t launch_fma_peak(int precision, int blocks, int iters, float* sink, c
   cudaError_t launch_chunk<NG>(int precision, const SampleParams& sp, const MeParams& mp, const double* edges,    \
                                int64_t first_event, int64_t n, int64_t C, void* rec_base, uint64_t seed, int iter, \
                                int accumulate, double* partials, unsigned long long* counters, double* w_out,     \
-                               int grid, cudaStream_t s, cudaEvent_t* ev) {                                       \
+                               int grid, cudaStream_t s, cudaEvent_t* ev, int me_warps) {                         \
     const int nacc = 2 + sp.ndim * sp.nbins;                                                                      \
     const size_t esm = sizeof(double) * sp.ndim * (sp.nbins + 1);                                                 \
     int dev = 0, sms = 0;                                                                                         \
@@ -1085,8 +1098,14 @@ cudaError_t launch_fma_peak(int precision, int blocks, int iters, float* sink, c
       if (ev) cudaEventRecord(ev[0], s);                                                                          \
       k_sample_rec<float><<<sgrid, kThreads, esm, s>>>(sp, edges, first_event, n, seed, iter, rec, w_out);        \
       if (ev) cudaEventRecord(ev[1], s);                                                                          \
-      k_me_acc<NG, float><<<grid, kThreads, MeAccLayout<NG, float>::total(nacc), s>>>(                            \
-          mp, sp.ndim, sp.nbins, rec, accumulate, partials, counters, w_out);                                     \
+      if (me_warps > 0) {                                                                                         \
+        e = launch_me_acc_shape(me_warps, mp, sp.n_final, sp.ndim, sp.nbins, rec_base, C, accumulate, partials,  \
+                                counters, w_out, grid, s);                                                        \
+        if (e != cudaSuccess) return e;                                                                           \
+      } else {                                                                                                    \
+        k_me_acc<NG, float><<<grid, kThreads, MeAccLayout<NG, float>::total(nacc), s>>>(                          \
+            mp, sp.ndim, sp.nbins, rec, accumulate, partials, counters, w_out);                                   \
+      }                                                                                                           \
       if (ev) cudaEventRecord(ev[2], s);                                                                          \
     }                                                                                                             \
     return cudaGetLastError();                                                                                    \

@@ -17,11 +17,16 @@ __global__ void __launch_bounds__(kThreads) k_sample(SampleParams sp, const doub
     EventKin<double> k;
     sample_event(sp, edges, seed, iter, uint64_t(ev), k);
     if (mom != nullptr)
-      for (int i = 0; i < next; ++i)
-        for (int c = 0; c < 4; ++c) mom[int64_t(i * 4 + c) * n + ev] = k.p[i][c];
+#pragma unroll
+      for (int i = 0; i < kMaxExt; ++i)
+        if (i < next)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) mom[int64_t(i * 4 + c) * n + ev] = k.p[i][c];
     if (wps != nullptr) wps[ev] = k.prefactor;
     if (bins != nullptr)
-      for (int j = 0; j < sp.ndim; ++j) bins[int64_t(j) * n + ev] = k.bins[j];
+#pragma unroll
+      for (int j = 0; j < kMaxDim; ++j)
+        if (j < sp.ndim) bins[int64_t(j) * n + ev] = k.bins[j];
   }
 }
 
@@ -32,7 +37,9 @@ __global__ void __launch_bounds__(kThreads) k_uniforms(uint64_t seed, int iter, 
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
     double u[kMaxDim];
     draw_uniforms(seed, iter, uint64_t(first_event + e), ndim, u);
-    for (int j = 0; j < ndim; ++j) y[int64_t(j) * n + e] = u[j];
+#pragma unroll
+    for (int j = 0; j < kMaxDim; ++j)
+      if (j < ndim) y[int64_t(j) * n + e] = u[j];
   }
 }
 

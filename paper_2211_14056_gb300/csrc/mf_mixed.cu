@@ -66,11 +66,16 @@ __global__ void __launch_bounds__(kThreads) k_sample_mixed(MixedArgs<K> a) {
       EventKin<K> k;
       sample_event(a.sp[p], edges + eoff[p], seed, iter, uint64_t(e), k);
       const RecordView<K>& r = a.rec[p];
-      for (int i = 0; i < a.sp[p].n_final; ++i)
-        for (int c = 0; c < 4; ++c) r.mom[int64_t(i * 4 + c) * r.C + e] = k.p[2 + i][c];
+#pragma unroll
+      for (int i = 0; i < kMaxExt - 2; ++i)
+        if (i < a.sp[p].n_final)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) r.mom[int64_t(i * 4 + c) * r.C + e] = k.p[2 + i][c];
       r.rs[e] = k.p[0][0] + k.p[1][0];
       r.pref[e] = k.prefactor;
-      for (int j = 0; j < a.ndim[p]; ++j) r.flag[int64_t(j) * r.C + e] = k.bins[j];
+#pragma unroll
+      for (int j = 0; j < kMaxDim; ++j)
+        if (j < a.ndim[p]) r.flag[int64_t(j) * r.C + e] = k.bins[j];
       pass = k.pass;
       fail = k.newton_fail;
       if (!pass && a.w_out[p] != nullptr) a.w_out[p][e] = 0.0;

@@ -136,37 +136,46 @@ template <typename B, int N> __device__ __forceinline__ void seed_tangent(Dual<B
 // K = double: every step in FP64.  K = float: luminosity, RAMBO and cuts in
 // FP32; bins, map, Jacobian, Newton (polished to 1e-15 in FP64) and weight in
 // FP64.  D = dual numbers: the same steps carry tangents seeded by ts.
+// Every loop over dimensions or particles runs to the compile-time maximum
+// (kMaxDim, kMaxExt) behind a guard on the runtime count, fully unrolled, so
+// that every per-particle and per-dimension array is indexed by constants and
+// lives in registers (a runtime index would put them in local memory).
 template <typename K, typename D = double>
 __device__ __forceinline__ void sample_event(const SampleParams& sp, const double* edges, uint64_t seed, int iter,
                                              uint64_t ev, EventKin<K, D>& out, const TangentSeeds* ts = nullptr) {
   double y[kMaxDim];
   D x[kMaxDim];
-  draw_uniforms(seed, iter, ev, sp.ndim, y);
+  const int ndim = sp.ndim;
+  draw_uniforms(seed, iter, ev, ndim, y);
   double jac = 1.0;
   const double nb = double(sp.nbins);
-#pragma unroll 1
-  for (int j = 0; j < sp.ndim; ++j) {
-    const double t = __dmul_rn(y[j], nb);
-    int b = int(t);
-    if (b > sp.nbins - 1) b = sp.nbins - 1;
-    const double e0 = edges[j * (sp.nbins + 1) + b], e1 = edges[j * (sp.nbins + 1) + b + 1];
-    const double w = e1 - e0;
-    if constexpr (is_dual<D>::value) {
-      D yd = D(y[j]);
-      if (ts) seed_tangent(yd, ts->y_slot[j]);
-      x[j] = (yd * nb - double(b)) * w + e0;
+#pragma unroll
+  for (int j = 0; j < kMaxDim; ++j) {
+    if (j < ndim) {
+      const double t = __dmul_rn(y[j], nb);
+      int b = int(t);
+      if (b > sp.nbins - 1) b = sp.nbins - 1;
+      const double e0 = edges[j * (sp.nbins + 1) + b], e1 = edges[j * (sp.nbins + 1) + b + 1];
+      const double w = e1 - e0;
+      if constexpr (is_dual<D>::value) {
+        D yd = D(y[j]);
+        if (ts) seed_tangent(yd, ts->y_slot[j]);
+        x[j] = (yd * nb - double(b)) * w + e0;
+      } else {
+        x[j] = fma(t - double(b), w, e0);
+      }
+      jac *= nb * w;
+      out.bins[j] = uint8_t(b);
     } else {
-      x[j] = fma(t - double(b), w, e0);
+      x[j] = D(0.0);
+      out.bins[j] = 0;
     }
-    jac *= nb * w;
-    out.bins[j] = uint8_t(b);
   }
   D mtd = D(sp.mt);
   if (ts) seed_tangent(mtd, ts->mt_slot);
   // partonic energy and luminosity
   D shat, lum = D(1.0), excess;
   const D thr = D(2.0) * mtd;
-  int off = 0;
   if (sp.lumi) {
     // ln x1 = u ln tau0, ln x2 = v (1 - u) ln tau0 (= v ln(tau0/x1));
     // f(x1) f(x2) x1 x2 = N^2 exp((a + 1)(ln x1 + ln x2) + b (ln(1-x1) + ln(1-x2)))
@@ -177,48 +186,69 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
     const K lx[2] = {K(x[0]) * lt, K(x[1]) * (K(1) - K(x[0])) * lt};
     // ln(1 - x) = ln(-expm1(ln x)): accurate also for x within an ulp of 1
     // (where 1 - exp(ln x) would round to 0 in FP32)
-    K l1m = K(0);
-#pragma unroll 1
-    for (int j = 0; j < 2; ++j) l1m += log(-expm1(lx[j]));
+    const K l1m = log(-expm1(lx[0])) + log(-expm1(lx[1]));
     const K lsum = lx[0] + lx[1];
     shat = D(exp(lsum)) * (sp.sqrt_s * sp.sqrt_s);
     const K ff = exp(K(sp.lumi_a + 1.0) * lsum + K(sp.lumi_b) * l1m);
     lum = D(ff) * (D(1.0) - x[0]) * log_tau0 * log_tau0 * (sp.lumi_N * sp.lumi_N);
-    off = 2;
   } else {
     shat = D(sp.sqrt_s * sp.sqrt_s);
   }
+  // the phase-space uniforms: the dimensions after the luminosity's two
+  D xr[kMaxDim - 2];
+#pragma unroll
+  for (int j = 0; j < kMaxDim - 2; ++j) xr[j] = sp.lumi ? x[j + 2] : x[j];
   const D rs = sqrt(shat);
   const K rsk = K(rs);
   const int n = sp.n_final;
-  // RAMBO on diet: intermediate masses
+  // RAMBO on diet: intermediate masses M[i - 1] of Q_i (M[0] = sqrt(s_hat), M[n - 1] = 0)
   K M[kMaxExt];
   M[0] = rsk;
-#pragma unroll 1
-  for (int i = 2; i <= n - 1; ++i) M[i - 1] = M[i - 2] * sqrt(mass_ratio(K(x[off + i - 2]), n - i));
-  M[n - 1] = K(0);
+#pragma unroll
+  for (int i = 2; i <= kMaxExt; ++i) {
+    if (i <= n - 1) M[i - 1] = M[i - 2] * sqrt(mass_ratio(K(xr[i - 2]), n - i));
+    else M[i - 1] = K(0);
+  }
+  // the angle uniforms xa: the phase-space uniforms after the n - 2 mass
+  // ones, shifted one place per mass uniform (a runtime offset into xr would
+  // be a runtime index)
+  D xa[kMaxDim - 2];
+#pragma unroll
+  for (int j = 0; j < kMaxDim - 2; ++j) xa[j] = xr[j];
+#pragma unroll
+  for (int s = 0; s < kMaxExt - 2; ++s)
+    if (s < n - 2)
+#pragma unroll
+      for (int j = 0; j < kMaxDim - 3; ++j) xa[j] = xa[j + 1];
   K pm[kMaxExt][4];
   K Q[4] = {rsk, K(0), K(0), K(0)};
   K MQ = rsk;
-#pragma unroll 1
-  for (int i = 1; i <= n - 1; ++i) {
-    const K Mi = M[i - 1], Mn = M[i];
-    const K q = (Mi - Mn) * (Mi + Mn) / (K(2) * Mi);
-    const K rc = K(x[off + n - 2 + 2 * (i - 1)]);
-    const K rp = K(x[off + n - 2 + 2 * (i - 1) + 1]);
-    const K cth = K(2) * rc - K(1);
-    const K sth = K(2) * sqrt(rc * (K(1) - rc));
-    K sph, cph;
-    sincos_turns(rp, &sph, &cph);
-    const K pr[4] = {q, q * sth * cph, q * sth * sph, q * cth};
-    const K Qr[4] = {Mi - q, -pr[1], -pr[2], -pr[3]};
-    K Qn[4];
-    boost_from_rest(Q, MQ, pr, pm[i - 1]);
-    boost_from_rest(Q, MQ, Qr, Qn);
-    for (int c = 0; c < 4; ++c) Q[c] = Qn[c];
-    MQ = Mn;
+#pragma unroll
+  for (int i = 1; i <= kMaxExt - 1; ++i) {
+    if (i <= n - 1) {
+      const K Mi = M[i - 1], Mn = M[i];
+      const K q = (Mi - Mn) * (Mi + Mn) / (K(2) * Mi);
+      // (cos theta, phi) uniforms of this step: after the n - 2 mass uniforms
+      const K rc = K(xa[2 * (i - 1)]), rp = K(xa[2 * (i - 1) + 1]);
+      const K cth = K(2) * rc - K(1);
+      const K sth = K(2) * sqrt(rc * (K(1) - rc));
+      K sph, cph;
+      sincos_turns(rp, &sph, &cph);
+      const K pr[4] = {q, q * sth * cph, q * sth * sph, q * cth};
+      const K Qr[4] = {Mi - q, -pr[1], -pr[2], -pr[3]};
+      K Qn[4];
+      boost_from_rest(Q, MQ, pr, pm[i - 1]);
+      boost_from_rest(Q, MQ, Qr, Qn);
+      // Q_{i+1}; after the last step it is the last massless momentum (a
+      // later step, if any, overwrites pm[i] with its own decay product)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        Q[c] = Qn[c];
+        pm[i][c] = Qn[c];
+      }
+      MQ = Mn;
+    }
   }
-  for (int c = 0; c < 4; ++c) pm[n - 1][c] = Q[c];
   // Phi_n(s_hat)
   D phi = D(sp.phi_const);
   for (int i = 0; i < n - 2; ++i) phi = phi * shat;
@@ -232,10 +262,14 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
   const D m2 = mtd * mtd;
   D E[kMaxExt];
   D Erest = D(0.0);
-#pragma unroll 1
-  for (int i = 0; i < n; ++i) {
-    E[i] = D(pm[i][0]);
-    if (i >= 2) Erest = Erest + E[i];
+#pragma unroll
+  for (int i = 0; i < kMaxExt; ++i) {
+    if (i < n) {
+      E[i] = D(pm[i][0]);
+      if (i >= 2) Erest = Erest + E[i];
+    } else {
+      E[i] = D(0.0);
+    }
   }
   excess = (shat - thr * thr) / (rs + thr);     // sqrt(s) - 2m
   double xi0 = sqrt(fmax(value_of(excess) * value_of(rs + thr), 0.0)) / value_of(rs);
@@ -297,17 +331,19 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
   D ksum = ka0 + ka1, k2sum = (ka0 * ka0 * k01 + ka1 * ka1 * k00) * ik;
   out.p[2][0] = K(k00);
   out.p[3][0] = K(k01);
-#pragma unroll 1
-  for (int i = 0; i < n; ++i) {
-    if (i >= 2) {
-      const D ka = xi * E[i];
-      out.p[2 + i][0] = K(ka);
-      ksum = ksum + ka;
-      k2sum = k2sum + ka;
+#pragma unroll
+  for (int i = 0; i < kMaxExt - 2; ++i) {
+    if (i < n) {
+      if (i >= 2) {
+        const D ka = xi * E[i];
+        out.p[2 + i][0] = K(ka);
+        ksum = ksum + ka;
+        k2sum = k2sum + ka;
+      }
+      out.p[2 + i][1] = K(xi * D(pm[i][1]));
+      out.p[2 + i][2] = K(xi * D(pm[i][2]));
+      out.p[2 + i][3] = K(xi * D(pm[i][3]));
     }
-    out.p[2 + i][1] = K(xi * D(pm[i][1]));
-    out.p[2 + i][2] = K(xi * D(pm[i][2]));
-    out.p[2 + i][3] = K(xi * D(pm[i][3]));
   }
   D wm = D(1.0);
   {
@@ -321,24 +357,29 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
   // cuts on the final gluons (particles 4..)
   int pass = converged;
   if (sp.pt_cut2 > 0.0) {
-    for (int g = 4; g < 2 + n; ++g) {
-      const K pt2 = out.p[g][1] * out.p[g][1] + out.p[g][2] * out.p[g][2];
-      pass &= (pt2 > K(sp.pt_cut2)) ? 1 : 0;
+#pragma unroll
+    for (int g = 4; g < kMaxExt; ++g) {
+      if (g < 2 + n) {
+        const K pt2 = out.p[g][1] * out.p[g][1] + out.p[g][2] * out.p[g][2];
+        pass &= (pt2 > K(sp.pt_cut2)) ? 1 : 0;
+      }
     }
   }
   if (sp.dr_cut2 > 0.0) {
     // Delta y = ln[(E_g + z_g)(E_h - z_h) / ((E_g - z_g)(E_h + z_h))] / 2,
     // Delta phi = atan2(cross, dot) of the transverse momenta (in [-pi, pi])
-#pragma unroll 1
-    for (int g = 4; g < 2 + n; ++g) {
-#pragma unroll 1
-      for (int h = g + 1; h < 2 + n; ++h) {
-        const K dy = K(0.5) * log(((out.p[g][0] + out.p[g][3]) * (out.p[h][0] - out.p[h][3])) /
-                                  ((out.p[g][0] - out.p[g][3]) * (out.p[h][0] + out.p[h][3])));
-        const K cr = out.p[g][1] * out.p[h][2] - out.p[g][2] * out.p[h][1];
-        const K dt = out.p[g][1] * out.p[h][1] + out.p[g][2] * out.p[h][2];
-        const K dphi = atan2(cr, dt);
-        pass &= (dy * dy + dphi * dphi > K(sp.dr_cut2)) ? 1 : 0;
+#pragma unroll
+    for (int g = 4; g < kMaxExt; ++g) {
+#pragma unroll
+      for (int h = g + 1; h < kMaxExt; ++h) {
+        if (h < 2 + n) {
+          const K dy = K(0.5) * log(((out.p[g][0] + out.p[g][3]) * (out.p[h][0] - out.p[h][3])) /
+                                    ((out.p[g][0] - out.p[g][3]) * (out.p[h][0] + out.p[h][3])));
+          const K cr = out.p[g][1] * out.p[h][2] - out.p[g][2] * out.p[h][1];
+          const K dt = out.p[g][1] * out.p[h][1] + out.p[g][2] * out.p[h][2];
+          const K dphi = atan2(cr, dt);
+          pass &= (dy * dy + dphi * dphi > K(sp.dr_cut2)) ? 1 : 0;
+        }
       }
     }
   }

@@ -101,6 +101,15 @@ def me2_flops_per_event(ng):
     return gluon_current_flops(ng) + shared_suffix_flops(ng) + lanes * (lane_flops(ng) + int(math.log2(lanes)))
 
 
+def sampler_bytes_per_event(n_final, ndim, pass_fraction, kin_bytes):
+    """Algorithmic HBM bytes the sampling kernel (k_sample_rec) writes per
+    event: the record (final-state momenta and sqrt(s_hat) in the kinematics
+    type, the FP64 weight prefactor, one byte per Vegas bin) plus the 4-byte
+    entry of the pass list for the events that pass.  It reads only the Vegas
+    edges (shared memory, once per CTA)."""
+    return (4 * n_final + 1) * kin_bytes + 8 + ndim + 4 * pass_fraction
+
+
 if __name__ == "__main__":
     for ng in (2, 3, 4):
         print(ng, gluon_current_flops(ng), lane_flops(ng), me2_flops_per_event(ng))

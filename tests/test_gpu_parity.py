@@ -251,13 +251,19 @@ def test_matrix_element_edge_cases(mf):
 def test_vegas_iterations_match_oracle(mf, name, n, amp):
     """Two iterations with refinement: weights, I_k, sigma_k and the refined
     grid against the oracle's (colour-ordered recursion for the big processes,
-    itself pinned to the Feynman-diagram oracle)."""
+    itself pinned to the Feynman-diagram oracle).  Each iteration is compared
+    on the GPU's own current edges: the refined edges agree with the oracle's
+    refinement to 1e-12 absolute, and a narrow bin would turn that rounding
+    into ~1e-11 of an event's Vegas Jacobian, which is not the arithmetic
+    under test."""
     p, w = _proc(mf, name, mf.MF_FP64)
     g = p.grid()
     st = _oracle_setup(w, amplitude=amp)
     edges = ov.uniform_grid(st.ndim)
     wt = torch.empty(n, dtype=torch.float64, device="cuda")
     for it in range(2):
+        np.testing.assert_allclose(g.get(), edges, rtol=0, atol=1e-12)
+        edges = g.get()
         r = p.vegas_iterate(g, seed=9, it=it, n=n, refine=True, weights=wt)
         ro = oi.iteration(st, 9, it, n, edges)
         wg = wt.cpu().numpy()
@@ -269,7 +275,7 @@ def test_vegas_iterations_match_oracle(mf, name, n, amp):
         assert r["sigma_k"] == pytest.approx(math.sqrt(ro["var"]), rel=1e-11)
         assert r["n_pass"] == int(nz.sum())
         edges = ov.refine(edges, ro["hist"])
-        np.testing.assert_allclose(g.get(), edges, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(g.get(), edges, rtol=0, atol=1e-12)
     assert r["iterations"] == 2
 
 
