@@ -13,9 +13,12 @@ to ~1e-14 relative (rounding in the phase-space map), and a propagator whose
 invariant is small against the energies (a top nearly collinear with a gluon,
 E^2 / (P^2 - m^2) ~ 10^2..10^3) turns the routing-dependent part of that
 violation into ~1e-11 of |M|^2: the value of |M|^2 on such inputs is only
-defined to that level.  The oracle's algorithms (Feynman diagrams with the
-internal momenta summed from the tree's root, the same diagrams re-rooted at
-the antitop, and the colour-ordered recursion) measure that ambiguity event
+defined to that level.  Likewise a helicity spinor of a momentum within a
+degree of the -z axis forms |p| + p_z with a cancellation (the oracle writes it
+as such; the GPU uses the cancellation-free form), worth ~1e-12 of |M|^2.  The
+oracle's evaluations (Feynman diagrams with the internal momenta summed from
+the tree's root, the same diagrams re-rooted at the antitop, the same in a
+rotated frame, and the colour-ordered recursion) measure that ambiguity event
 by event, and each tail event is held to it.  A wrong term would show at
 O(1), far above 1e-10.
 """
@@ -41,12 +44,25 @@ def mf():
     return mf
 
 
+def _rotated(p, axis=(1.0, 1.0, 1.0), angle=1.0):
+    """All momenta rotated by `angle` about `axis` (|M|^2 is invariant)."""
+    a = np.asarray(axis) / np.linalg.norm(axis)
+    K = np.array([[0.0, -a[2], a[1]], [a[2], 0.0, -a[0]], [-a[1], a[0], 0.0]])
+    R = np.eye(3) + np.sin(angle) * K + (1.0 - np.cos(angle)) * (K @ K)
+    q = np.array(p, dtype=np.float64, copy=True)
+    q[..., 1:] = q[..., 1:] @ R.T
+    return q
+
+
 def oracle_spread(setup, p):
     """Relative spread of |M|^2 over the oracle's independent FP64 evaluations
     of the same events: Feynman diagrams routed from the last leg (the
     reference), Feynman diagrams re-rooted at the antitop (every internal
-    momentum summed from the other side of the tree), and, for a heavy quark
-    pair plus gluons, the colour-ordered recursion."""
+    momentum summed from the other side of the tree), the reference in a
+    rotated frame (helicity spinors of a momentum near the -z axis cancel in
+    |p| + p_z, by ~1e-12 for a top within a degree of the beam; a rotation
+    moves every momentum off the axis) and, for a heavy quark pair plus
+    gluons, the colour-ordered recursion."""
     from oracle.berends_giele import QQbarGluons
     from oracle.feynman import Amplitude, DiagramSet
     from oracle.processes import outgoing_flavours
@@ -57,6 +73,7 @@ def oracle_spread(setup, p):
     amp = Amplitude(ds, proc.mass, proc.amp.widths, {"gs": proc.gs, "e": proc.ee})
     ext, q = proc.external(p)
     vals.append(amp.summed_squared(ext, q) / proc.average)
+    vals.append(proc.me2(_rotated(p)))
     if all(x in ("g", "t", "t~") for x in proc.particles):
         vals.append(QQbarGluons(proc).me2(p))
     v = np.stack(vals)
