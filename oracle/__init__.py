@@ -22,6 +22,7 @@ colour          SU(3) generators and brute-force colour sums.
 feynman         Tree-diagram enumeration and evaluation with explicit colour.
 berends_giele   Colour-ordered recursion for a heavy quark pair plus gluons.
 processes       Process definitions (externals, masses, couplings, averages).
+pdf             Log-bicubic (Hermite) interpolation of tabulated parton densities.
 integrate       Event weights and Vegas iterations built from the above.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test except the

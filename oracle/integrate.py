@@ -6,7 +6,9 @@ For one event with uniforms y[d] (arXiv:2211.14056, Sec. 1: tensorised Vegas
 over events; the steps below follow the order in which the weight is built):
 
   1. x, J_vegas, bins = Vegas map of y                         (``vegas``)
-  2. hadronic set-up: (x1, x2, s_hat, L) = luminosity map of x[0], x[1];
+  2. hadronic set-up: (x1, x2, s_hat, L) = luminosity map of x[0], x[1]
+     (a synthetic gluon density, or tabulated densities summed over the
+     channel's parton pairs, ``pdf``);
      fixed partonic set-up: s_hat = s, L = 1                   (``phase_space``)
   3. massless momenta and Phi_n from the remaining x           (RAMBO on diet)
   4. massive momenta and weight factor W                       (rescaling)
@@ -21,7 +23,8 @@ import math
 import numpy as np
 
 from . import philox, vegas, phase_space as ps
-from .processes import Process, final_gluons
+from .processes import Process, final_jets
+from .pdf import PDFGrid
 from .berends_giele import QQbarGluons
 
 
@@ -47,14 +50,23 @@ class Setup:
         self.ndim = ndim(cfg)
         self.lumi = cfg.get("lumi", False)
         self.masses = [self.proc.mass.get(x, 0.0) for x in self.proc.particles[2:]]
-        self.gluons = final_gluons(self.name)
+        self.gluons = final_jets(self.name)       # the cuts' partons: final gluons and light quarks
+        self.pdf = None
+        if self.lumi == "pdf":
+            d = cfg["pdf"]
+            self.pdf = PDFGrid(d["x_min"], d["x_max"], d["q2_min"], d["q2_max"], d["xf"])
         self.bg = QQbarGluons(self.proc) if amplitude == "bg" else None
 
     def kinematics(self, y, edges):
         """Steps 1-5: (momenta [N, n+2, 4], weight without |M|^2 [N], bins, cut)."""
         c = self.cfg
         x, jac, bins = vegas.vegas_map(y, edges)
-        if self.lumi:
+        if self.lumi == "pdf":
+            S = c["sqrt_s"] ** 2
+            tau0 = (sum(self.masses)) ** 2 / S
+            x1, x2, shat, L = ps.pdf_luminosity_map(x[0], x[1], tau0, S, self.pdf, c["pairs"], c.get("mu_f", 0.5))
+            xr = x[2:]
+        elif self.lumi:
             S = c["sqrt_s"] ** 2
             tau0 = (sum(self.masses)) ** 2 / S
             x1, x2, shat, L = ps.luminosity_map(x[0], x[1], tau0, S,

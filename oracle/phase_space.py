@@ -173,6 +173,22 @@ def luminosity_map(ua, ub, tau0, S, N=1.0, a=-1.1, b=5.0):
     return x1, x2, x1 * x2 * S, f(x1) * f(x2) * jac
 
 
+def pdf_luminosity_map(ua, ub, tau0, S, pdf, pairs, mu_f):
+    """(x1, x2, s_hat, factor) with tabulated parton densities: the same map
+    as ``luminosity_map``; the factor is sum over the parton pairs (a, b) of
+    x1 f_a(x1, Q^2) x2 f_b(x2, Q^2) (the map's x1 x2 absorbed into the
+    tabulated x f) times ln(1/tau0) ln(x1/tau0), at the factorisation scale
+    Q = mu_f sqrt(s_hat).  pdf: an ``oracle.pdf.PDFGrid``."""
+    x1 = tau0 ** ua
+    x2 = (tau0 / x1) ** ub
+    shat = x1 * x2 * S
+    q2 = mu_f * mu_f * shat
+    lum = 0.0
+    for a, b in pairs:
+        lum = lum + pdf.xfx(a, x1, q2) * pdf.xfx(b, x2, q2)
+    return x1, x2, shat, lum * math.log(1.0 / tau0) * np.log(x1 / tau0)
+
+
 def pt(p):
     return np.sqrt(p[..., 1] ** 2 + p[..., 2] ** 2)
 

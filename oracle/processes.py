@@ -28,6 +28,20 @@ PROCESSES = {
     "uux_ttxgg":  (("u", "u~", "t", "t~", "g", "g"), (True, True, False, False, False, False), 36, 2),
     "uux_ttx":    (("u", "u~", "t", "t~"), (True, True, False, False), 36, 1),
     "epem_mupmum": (("e-", "e+", "mu-", "mu+"), (True, True, False, False), 4, 1),
+    # the other subprocesses of p p -> t tbar g g (the antiquark or a quark from
+    # either beam; other light flavours have the same |M|^2): average over the
+    # spins and colours of q g = 2*3 x 2*8 = 96; one final gluon, so S_id = 1
+    "uxu_ttxgg":  (("u~", "u", "t", "t~", "g", "g"), (True, True, False, False, False, False), 36, 2),
+    "ug_ttxgu":   (("u", "g", "t", "t~", "g", "u"), (True, True, False, False, False, False), 96, 1),
+    "gu_ttxgu":   (("g", "u", "t", "t~", "g", "u"), (True, True, False, False, False, False), 96, 1),
+    "uxg_ttxgux": (("u~", "g", "t", "t~", "g", "u~"), (True, True, False, False, False, False), 96, 1),
+    "gux_ttxgux": (("g", "u~", "t", "t~", "g", "u~"), (True, True, False, False, False, False), 96, 1),
+    # massless 2 -> 2 processes with textbook closed forms (pins of the
+    # external states the crossed processes use: incoming antiquark, incoming
+    # gluon with an outgoing quark)
+    "ug_ug":      (("u", "g", "u", "g"), (True, True, False, False), 96, 1),
+    "uux_gg":     (("u", "u~", "g", "g"), (True, True, False, False), 36, 2),
+    "gg_uux":     (("g", "g", "u", "u~"), (True, True, False, False), 256, 1),
 }
 
 _ANTI = {"t": "t~", "t~": "t", "u": "u~", "u~": "u", "g": "g", "a": "a",
@@ -44,6 +58,14 @@ def outgoing_flavours(name):
 def final_gluons(name):
     parts, incoming, _, _ = PROCESSES[name]
     return [i for i, (p, inc) in enumerate(zip(parts, incoming)) if p == "g" and not inc]
+
+
+def final_jets(name):
+    """Final-state light partons (gluons and light quarks): the cuts apply to
+    each of them (for processes whose only light final partons are gluons,
+    the same as ``final_gluons``)."""
+    parts, incoming, _, _ = PROCESSES[name]
+    return [i for i, (p, inc) in enumerate(zip(parts, incoming)) if p in ("g", "u", "u~") and not inc]
 
 
 class Process:

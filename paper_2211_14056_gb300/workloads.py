@@ -8,7 +8,8 @@ luminosity f(x) = x^-1.1 (1-x)^5 at sqrt(S) = 13 TeV for the 2 -> 3 and
 luminosity uniforms (if any), then the RAMBO uniforms.
 """
 
-PROCESS_IDS = {"gg_ttx": 1, "gg_ttxg": 2, "gg_ttxgg": 3, "uux_ttxgg": 4, "epem_mupmum": 5}
+PROCESS_IDS = {"gg_ttx": 1, "gg_ttxg": 2, "gg_ttxgg": 3, "uux_ttxgg": 4, "epem_mupmum": 5,
+               "uxu_ttxgg": 6, "ug_ttxgu": 7, "gu_ttxgu": 8, "uxg_ttxgux": 9, "gux_ttxgux": 10}
 
 WORKLOADS = {
     # g g -> t tbar at fixed sqrt(s) = 1 TeV: closed-form target, FP64
@@ -30,6 +31,27 @@ WORKLOADS = {
 }
 
 
+# p p -> t t~ g g as the sum of its subprocesses (arXiv:2211.14056 Table 1),
+# each channel a two-quark-line or gluon amplitude with its own Vegas grid and
+# its parton pairs in the luminosity, from the synthetic tabulated set of
+# ``pdfgrid`` (flavour index = PDG code + 4, gluon 4) at Q = sqrt(s_hat) / 2:
+#   gg; q q~ and q~ q (q = d, u, s, c from beam 1 or 2); q g, g q, q~ g, g q~.
+# Same energy, width and cuts as g g -> t t~ g g; the cuts apply to every final
+# light parton (the gluon and the quark of the q g channels).
+_PP = dict(mt=173.0, wt=1.5, gs=1.2177, sqrt_s=13000.0, lumi="pdf", mu_f=0.5, pt_cut=30.0, dr_cut=0.4,
+           iterations=5)
+PP_CHANNELS = {
+    "pp_ttxgg_gg": dict(_PP, process="gg_ttxgg", pairs=[(4, 4)], events=2 ** 21, seed=11),
+    "pp_ttxgg_qqx": dict(_PP, process="uux_ttxgg", pairs=[(5, 3), (6, 2), (7, 1), (8, 0)], events=2 ** 18, seed=12),
+    "pp_ttxgg_qxq": dict(_PP, process="uxu_ttxgg", pairs=[(3, 5), (2, 6), (1, 7), (0, 8)], events=2 ** 18, seed=13),
+    "pp_ttxgg_qg": dict(_PP, process="ug_ttxgu", pairs=[(5, 4), (6, 4), (7, 4), (8, 4)], events=2 ** 19, seed=14),
+    "pp_ttxgg_gq": dict(_PP, process="gu_ttxgu", pairs=[(4, 5), (4, 6), (4, 7), (4, 8)], events=2 ** 19, seed=15),
+    "pp_ttxgg_qxg": dict(_PP, process="uxg_ttxgux", pairs=[(3, 4), (2, 4), (1, 4), (0, 4)], events=2 ** 19, seed=16),
+    "pp_ttxgg_gqx": dict(_PP, process="gux_ttxgux", pairs=[(4, 3), (4, 2), (4, 1), (4, 0)], events=2 ** 19, seed=17),
+}
+WORKLOADS.update(PP_CHANNELS)
+
+
 # the batched mixed launch: four processes together, each with its own Vegas
 # grid (the processes' own set-ups above), FP32 amplitudes
 MIXED = {"workloads": ["gg_ttx_1tev", "gg_ttxg_13tev", "gg_ttxgg_13tev", "uux_ttxgg_13tev"],
@@ -37,12 +59,23 @@ MIXED = {"workloads": ["gg_ttx_1tev", "gg_ttxg_13tev", "gg_ttxgg_13tev", "uux_tt
 
 
 def oracle_cfg(w):
-    """The same workload as the keyword dict oracle.integrate.Setup takes."""
+    """The same workload as the keyword dict oracle.integrate.Setup takes
+    (with tabulated densities: the synthetic set itself, the pairs, mu_f)."""
     keys = ("process", "mt", "wt", "gs", "sqrt_s", "lumi", "pt_cut", "dr_cut")
-    return {k: w[k] for k in keys}
+    cfg = {k: w[k] for k in keys}
+    if w["lumi"] == "pdf":
+        from .pdfgrid import synthetic_set
+        cfg.update(pdf=synthetic_set(), pairs=list(w["pairs"]), mu_f=w["mu_f"])
+    return cfg
 
 
-def process_kwargs(w, precision):
-    """Keyword arguments of binding.Process for a workload."""
-    return dict(mt=w["mt"], wt=w["wt"], gs=w["gs"], sqrt_s=w["sqrt_s"], lumi=w["lumi"],
-                pt_cut=w["pt_cut"], dr_cut=w["dr_cut"], precision=precision)
+def process_kwargs(w, precision, pdf=None):
+    """Keyword arguments of binding.Process for a workload (pdf: the loaded
+    set, a binding.PDFSet, for the tabulated-density workloads)."""
+    kw = dict(mt=w["mt"], wt=w["wt"], gs=w["gs"], sqrt_s=w["sqrt_s"], lumi=w["lumi"],
+              pt_cut=w["pt_cut"], dr_cut=w["dr_cut"], precision=precision)
+    if w["lumi"] == "pdf":
+        if pdf is None:
+            raise ValueError("this workload needs a loaded parton-density set (pdf=)")
+        kw.update(pdf=pdf, pairs=list(w["pairs"]), mu_f=w["mu_f"])
+    return kw

@@ -13,6 +13,13 @@
 * |M|^2 scales as g_s^(2 (n_ext - 2)).
 * helicity-flip symmetry at Gamma_t = 0: |M_h|^2 = |M_-h|^2 per helicity
   configuration, and the per-helicity values of the two algorithms agree.
+* the other subprocesses of p p -> t tbar g g (incoming antiquark, incoming
+  gluon with an outgoing quark): massless 2 -> 2 closed forms with the same
+  external states (q g -> q g, q qbar -> g g, g g -> q qbar; Ellis-Stirling-
+  Webber Table 7.1), crossing keeps the diagram count, gauge and Lorentz
+  invariance, and the relations between channels: exchanging the beams, and
+  charge conjugation (q~ g -> t t~ g q~ equals q g -> t~ t g q with the top
+  and antitop momenta exchanged).
 """
 import itertools
 import math
@@ -88,7 +95,8 @@ def _gauge_ratio(proc, p, leg):
     return np.max(np.abs(M)) / single
 
 
-@pytest.mark.parametrize("name,nfin", [("gg_ttxg", 3), ("gg_ttxgg", 4), ("uux_ttxgg", 4)])
+@pytest.mark.parametrize("name,nfin", [("gg_ttxg", 3), ("gg_ttxgg", 4), ("uux_ttxgg", 4), ("ug_ttxgu", 4),
+                                       ("gux_ttxgux", 4)])
 def test_gauge_invariance(name, nfin):
     proc = Process(name, wt=0.0)
     p = points(nfin, 6, seed=4)
@@ -114,7 +122,8 @@ def _random_lorentz(rng):
     return B @ R
 
 
-@pytest.mark.parametrize("name,nfin", [("gg_ttxg", 3), ("gg_ttxgg", 4), ("uux_ttxgg", 4)])
+@pytest.mark.parametrize("name,nfin", [("gg_ttxg", 3), ("gg_ttxgg", 4), ("uux_ttxgg", 4), ("ug_ttxgu", 4),
+                                       ("uxg_ttxgux", 4)])
 def test_lorentz_invariance(name, nfin):
     # Gamma_t = 0: a fixed-width propagator breaks gauge invariance at
     # O(Gamma/m), and with it the frame independence of the physical-
@@ -219,3 +228,46 @@ def test_helicity_flip_symmetry(name, nfin, masses):
         Jf = J.reshape(J.shape[0], -1, J.shape[-1])
         perbg = np.real(np.einsum("shn,st,thn->hn", np.conj(Jf), bg.C, Jf)).reshape(per.shape)
         np.testing.assert_allclose(perbg, per, rtol=0, atol=1e-12 * scale.max())
+
+
+def _mandelstam(p):
+    s = mdot(p[:, 0] + p[:, 1], p[:, 0] + p[:, 1])
+    t = mdot(p[:, 0] - p[:, 2], p[:, 0] - p[:, 2])
+    u = mdot(p[:, 0] - p[:, 3], p[:, 0] - p[:, 3])
+    return s, t, u
+
+
+@pytest.mark.parametrize("name", ["ug_ug", "uux_gg", "gg_uux"])
+def test_massless_two_to_two_closed_forms(name):
+    """Spin- and colour-averaged |M|^2 / g^4 of Ellis-Stirling-Webber Table 7.1
+    (massless, t = (p1 - p3)^2, u = (p1 - p4)^2); the process's 1/2! for two
+    final gluons is part of the oracle's |M|^2."""
+    p = points(2, 40, 700.0, masses=[0.0, 0.0], seed=11)
+    proc = Process(name)
+    s, t, u = _mandelstam(p)
+    if name == "ug_ug":
+        ref = -(4 / 9) * (s * s + u * u) / (s * u) + (u * u + s * s) / (t * t)
+    elif name == "uux_gg":
+        ref = ((32 / 27) * (t * t + u * u) / (t * u) - (8 / 3) * (t * t + u * u) / (s * s)) / 2
+    else:
+        ref = (1 / 6) * (t * t + u * u) / (t * u) - (3 / 8) * (t * t + u * u) / (s * s)
+    np.testing.assert_allclose(proc.me2(p), proc.gs ** 4 * ref, rtol=1e-12)
+
+
+def test_crossing_keeps_the_diagram_count():
+    n = len(DiagramSet(outgoing_flavours("uux_ttxgg")).diagrams)
+    for name in ("uxu_ttxgg", "ug_ttxgu", "gu_ttxgu", "uxg_ttxgux", "gux_ttxgux"):
+        assert len(DiagramSet(outgoing_flavours(name)).diagrams) == n
+
+
+@pytest.mark.parametrize("wt", [0.0, 1.5])
+def test_beam_exchange_and_charge_conjugation(wt):
+    p = points(4, 8, seed=12)
+    beams = p[:, [1, 0, 2, 3, 4, 5]]
+    tops = p[:, [0, 1, 3, 2, 4, 5]]
+    me = lambda name, q: Process(name, wt=wt).me2(q)
+    np.testing.assert_allclose(me("uxu_ttxgg", p), me("uux_ttxgg", beams), rtol=1e-12)
+    np.testing.assert_allclose(me("gu_ttxgu", p), me("ug_ttxgu", beams), rtol=1e-12)
+    np.testing.assert_allclose(me("gux_ttxgux", p), me("uxg_ttxgux", beams), rtol=1e-12)
+    np.testing.assert_allclose(me("uxg_ttxgux", p), me("ug_ttxgu", tops), rtol=1e-12)
+    np.testing.assert_allclose(me("gux_ttxgux", p), me("gu_ttxgu", tops), rtol=1e-12)
