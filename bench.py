@@ -207,7 +207,7 @@ def main():
     ap.add_argument("--launch-shapes", action="store_true",
                     help="only run the full launch-shape sweep of the |M|^2 kernel (10^6 g g -> t tbar g g events "
                          "per shape) and print it as one JSON line")
-    ap.add_argument("--profile-kernel", default="iterate", choices=["iterate", "me", "grad"],
+    ap.add_argument("--profile-kernel", default="iterate", choices=["iterate", "me", "grad", "pdf"],
                     help="--profile-case target: whole iterations, sampling + the |M|^2 kernel alone, or "
                          "two reverse-mode derivative calls (mf_grad with every per-event output)")
     args = ap.parse_args()
@@ -244,6 +244,10 @@ def main():
             torch.cuda.synchronize()
             print(json.dumps({"profile_case": args.workload, "kernel": "me", "events": ne,
                               "precision": args.precision, "mean_me2": float(me.mean())}))
+            return 0
+        if args.profile_kernel == "pdf":
+            r = _pdf_leg(mf, torch, n=args.profile_case, reps=2)
+            print(json.dumps({"profile_case": "pdf", "points": args.profile_case, "result": r}))
             return 0
         if args.profile_kernel == "grad":
             ne = args.profile_case
@@ -380,11 +384,13 @@ def main():
     peak_derived = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
 
     # 7. the derivative and mixed-launch workloads (N = 1 only)
-    grad = mixed = shapes = None
+    grad = mixed = shapes = pp = pdfk = None
     if world == 1 and not args.no_extras:
         grad = _grad_leg(p32, p64, g32, g64, w, torch)
         mixed = _mixed_leg(mf, torch)
         shapes = _launch_shape_leg(mf, torch)
+        pp = _pp_leg(mf, torch)
+        pdfk = _pdf_leg(mf, torch)
 
     # 8. CPU baseline: the oracle on the host cores (rank 0 only, N = 1 only)
     cpu = None
@@ -440,6 +446,10 @@ def main():
             line["mixed"] = mixed
         if shapes is not None:
             line["launch_shape"] = shapes
+        if pp is not None:
+            line["pp_ttxgg"] = pp
+        if pdfk is not None:
+            line["pdf_interpolation"] = pdfk
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -526,6 +536,82 @@ def _mixed_leg(mf, torch, iters=5):
             "speedup_vs_separate": ms_sep / ms_mixed,
             "autotune": {"candidates": cands, "ms": times, "best": cands[best]},
             "graph": True, "I_pb": [r["I"] for r in res]}
+
+
+def _pp_leg(mf, torch, iters=5):
+    """p p -> t tbar g g as the sum of its seven subprocess channels (gg, q q~,
+    q~ q, q g, g q, q~ g, g q~; each its own grid, tabulated densities), in one
+    mixed plan (FP32): three adaptation iterations, the autotuner's choice of
+    launch form, then graph-replayed iterations.  sigma is the sum of the
+    channels' estimates, its error their errors in quadrature."""
+    from paper_2211_14056_gb300.pdfgrid import synthetic_set
+    from paper_2211_14056_gb300.workloads import PP_CHANNELS, PROCESS_IDS, process_kwargs
+    pdf = mf.PDFSet.from_dict(synthetic_set())
+    names = list(PP_CHANNELS)
+    procs = [mf.Process(PROCESS_IDS[PP_CHANNELS[k]["process"]], **process_kwargs(PP_CHANNELS[k], mf.MF_FP32, pdf=pdf))
+             for k in names]
+    grids = [p.grid() for p in procs]
+    n = [PP_CHANNELS[k]["events"] for k in names]
+    m = mf.Mixed(procs, grids, n)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        for it in range(3):
+            m.run(11, it, refine=True, stream=side)
+        cands = [(0, 32), (0, 128), (0, 0)]
+        times, best = m.autotune(11, cands, stream=side)
+        m.use_graph(True)
+        m.run(11, 3, refine=True, stream=side)
+        side.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(side)
+        for i in range(iters):
+            res = m.run(11, 4 + i, refine=True, stream=side)
+        e1.record(side)
+        side.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    total = sum(n)
+    sig = sum(r["I_k"] for r in res)
+    err = sum(r["sigma_k"] ** 2 for r in res) ** 0.5
+    return {"channels": names, "events": n, "ms_per_iteration": ms, "events_per_s": total / (ms * 1e-3),
+            "sigma_pb": sig, "sigma_err_pb": err,
+            "channel_sigma_pb": {k: r["I_k"] for k, r in zip(names, res)},
+            "autotune": {"candidates": cands, "ms": times, "best": cands[best]}, "precision": "FP32",
+            "pdf": "synthetic tabulated set (9 flavours, 97 x 41 nodes), log-bicubic interpolation, "
+                   "Q = sqrt(s_hat)/2"}
+
+
+def _pdf_leg(mf, torch, n=2 ** 26, reps=5):
+    """The interpolation kernel alone (mf_pdf_eval, FP32 arithmetic): x and Q^2
+    read, x f written (24 bytes per point of HBM traffic, 1.5 GB per launch,
+    inputs larger than L2); GB/s against the measured copy bandwidth."""
+    import statistics as stats
+    from paper_2211_14056_gb300 import pdfgrid
+    pdf = mf.PDFSet.from_dict(pdfgrid.synthetic_set())
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    x = torch.exp(torch.empty(n, dtype=torch.float64, device="cuda").uniform_(-9.0, 0.0, generator=g))
+    q2 = torch.exp(torch.empty(n, dtype=torch.float64, device="cuda").uniform_(2.0, 18.0, generator=g))
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    res = {}
+    for name, prec in (("fp32", mf.MF_FP32), ("fp64", mf.MF_FP64)):
+        pdf.eval(pdfgrid.GLUON, n, x, q2, out, precision=prec)
+        ts = []
+        for r in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            pdf.eval(pdfgrid.GLUON, n, x, q2, out, precision=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = stats.mean(ts)
+        gbs = 24.0 * n / (ms * 1e-3) / 1e9
+        peak = _measured_peaks().get("hbm_gbs")
+        res[name] = {"points": n, "ms": ms, "points_per_s": n / (ms * 1e-3), "achieved": gbs, "unit": "GB/s",
+                     "peak": peak, "frac": gbs / peak if peak else None}
+    res["kernel"] = "k_pdf_eval (flavour table staged in shared memory)"
+    res["bytes_per_point"] = 24
+    return res
 
 
 def _launch_shape_leg(mf, torch, full=False, n=10 ** 6, reps=3):

@@ -15,7 +15,8 @@
  *
  * Conventions shared by every call:
  *   - units GeV, cross sections in pb;
- *   - particle order: the two incoming partons, t, tbar, then final gluons;
+ *   - particle order: the two incoming partons, t, tbar, then the final light
+ *     partons (gluons first);
  *   - momenta arrays are structure-of-arrays FP64: element (particle i,
  *     component c, event e) at [(i*4 + c)*n + e], components (E, px, py, pz),
  *     partonic centre-of-mass frame, beam 1 along +z;
@@ -67,6 +68,22 @@ typedef int mf_status;
  * final gluons); coupling e_qed.  Not covered: MF_FP32_TC, mf_grad and
  * mf_vegas_accumulate_static (MF_ERR_UNSUPPORTED). */
 #define MF_PROC_EE_MUMU 5
+/* The other subprocesses of p p -> t tbar g g (arXiv:2211.14056 Table 1:
+ * pp -> t tbar g g sums them), crossings of the u ubar -> t tbar g g amplitude
+ * (same 12-structure colour matrix, same restrictions; the u quark stands for
+ * any light flavour, whose |M|^2 is the same: the channel's parton pairs in
+ * the luminosity sum the flavours).  Final light partons: the gluon first,
+ * then the (anti)quark; the cuts apply to both.
+ *   MF_PROC_UXU_TTXGG   ubar u -> t tbar g g   (quark from beam 2; average 1/36, 1/2!)
+ *   MF_PROC_UG_TTXGU    u g -> t tbar g u      (average 1/96)
+ *   MF_PROC_GU_TTXGU    g u -> t tbar g u
+ *   MF_PROC_UXG_TTXGUX  ubar g -> t tbar g ubar
+ *   MF_PROC_GUX_TTXGUX  g ubar -> t tbar g ubar */
+#define MF_PROC_UXU_TTXGG 6
+#define MF_PROC_UG_TTXGU 7
+#define MF_PROC_GU_TTXGU 8
+#define MF_PROC_UXG_TTXGUX 9
+#define MF_PROC_GUX_TTXGUX 10
 
 /* arithmetic of the matrix element */
 #define MF_FP64 0      /* everything in FP64 */
@@ -76,6 +93,7 @@ typedef int mf_status;
 
 typedef struct mf_process mf_process;
 typedef struct mf_grid mf_grid;
+typedef struct mf_pdf mf_pdf;
 
 /* Process description (arXiv:2211.14056 Sec. 2: the process-dependent
  * functions a generator produces; here the parameters of a built kernel). */
@@ -90,12 +108,18 @@ typedef struct {
   const int64_t* colour_num;   /* host [n_flow*n_flow] integer numerators of the process's colour matrix */
   int64_t colour_den;          /* common denominator; C = colour_num / colour_den */
   double sqrt_s;               /* hadronic sqrt(S) if lumi = 1, else the fixed partonic sqrt(s) */
-  int lumi;                    /* 0: fixed partonic energy; 1: synthetic gluon luminosity */
+  int lumi;                    /* 0: fixed partonic energy; 1: synthetic gluon luminosity;
+                                  2: tabulated parton densities (pdf, pairs, mu_f below) */
   double lumi_N, lumi_a, lumi_b;  /* f(x) = N x^a (1-x)^b per gluon */
   double pt_cut_g;             /* final-gluon pT threshold (0 disables) */
   double dr_cut_gg;            /* final-gluon pair Delta R threshold (0 disables) */
   int precision;               /* MF_FP64, MF_FP32 or MF_FP32_TC */
   double e_qed;                /* electromagnetic coupling e = sqrt(4 pi alpha) (MF_PROC_EE_MUMU only) */
+  /* lumi = 2 (tabulated parton densities): */
+  const mf_pdf* pdf;           /* the set (mf_pdf_create); must outlive the process */
+  int n_pairs;                 /* 1..8 parton pairs of the channel */
+  const int* pairs;            /* host [n_pairs][2]: flavour indices (beam 1, beam 2) into the set */
+  double mu_f;                 /* factorisation scale Q = mu_f * sqrt(s_hat) (> 0) */
 } mf_process_desc;
 
 /* Result of one Vegas iteration and of the combination of every iteration
@@ -136,6 +160,27 @@ mf_status mf_set_ctas_per_sm(mf_process* proc, int ctas_per_sm);
  * Covers MF_PROC_GG_TTXGG with MF_FP32 or MF_FP32_TC (else
  * MF_ERR_UNSUPPORTED); MF_ERR_ARG outside [0, 7]. */
 mf_status mf_set_launch_shape(mf_process* proc, int warps_per_cta, int* max_ctas_per_sm);
+
+/* Tabulated parton densities (arXiv:2211.14056 Sec. 1: the integrand's
+ * densities come from PDFFlow, a GPU interpolation of tabulated LHAPDF sets).
+ * mf_pdf_create loads a set: xf host [nflav][nq][nx] = x f(x, Q^2) of each
+ * flavour on nodes uniform in ln x (x_min .. x_max <= 1, nx nodes) and in
+ * ln Q^2 (q2_min .. q2_max, nq nodes), 4 <= nq, nx <= 4096, 1 <= nflav <= 64.
+ * The interpolation is log-bicubic Hermite: node slopes in ln x from finite
+ * differences (mean of the neighbouring quotients, one-sided at the ends),
+ * cubic Hermite in ln x on the rows around Q^2, then cubic Hermite in ln Q^2
+ * with slopes from the same finite differences of those rows; queries outside
+ * the table are clamped to its edge.  The set is copied to the device in FP64
+ * and FP32 (allocated here, owned by the handle); MF_ERR_ARG on bad sizes,
+ * ranges or non-finite values.
+ * mf_pdf_eval: x f of flavour `flavour` at n points, x and q2 device [n] FP64
+ * (inputs), xf device [n] FP64 (output), arithmetic in MF_FP64 or MF_FP32;
+ * asynchronous on `stream`. */
+mf_status mf_pdf_create(int nflav, int nq, int nx, double x_min, double x_max, double q2_min, double q2_max,
+                        const double* xf, mf_pdf** out);
+mf_status mf_pdf_destroy(mf_pdf* pdf);
+mf_status mf_pdf_eval(const mf_pdf* pdf, int precision, int flavour, int64_t n, const double* x, const double* q2,
+                      double* xf, void* stream);
 
 /* Vegas grid (Lepage 1978, the integrator named in Sec. 1): nbins equal bins
  * per dimension (2 <= nbins <= 64), device edges [ndim][nbins+1], device
@@ -288,7 +333,7 @@ mf_status mf_grid_profile_read(mf_grid* grid, double* sample_ms, double* me_ms, 
  * the denominator of the amplitude kernel's roofline.  Synchronises the device. */
 mf_status mf_fma_throughput(int precision, double* tflops);
 
-/* Mixed launch: up to 4 processes integrated together, each with its own
+/* Mixed launch: up to 8 processes integrated together, each with its own
  * grid and event count (arXiv:2211.14056 Sec. 3, Fig. 3: how the work is
  * spread over blocks and threads sets the run time).  One sampling launch
  * for every process, one persistent |M|^2 launch whose warps take tiles of
@@ -312,7 +357,11 @@ mf_status mf_fma_throughput(int precision, double* tflops);
  *   mf_mixed_autotune times each candidate (ctas_per_sm, tile), tile = 0
  *                     being the per-process form, on one unrefined iteration
  *                     (results not recorded), writes the times (ms) and the
- *                     index of the fastest, and keeps it. */
+ *                     index of the fastest, and keeps it.
+ * When the shared-queue kernel cannot fit on an SM (its shared memory holds
+ * every process's Vegas sums beside the warps' g g -> t t~ g g stores: e.g.
+ * seven FP64 processes), the plan runs the per-process form only: tile > 0
+ * in mf_mixed_set_launch or in an autotune candidate is MF_ERR_UNSUPPORTED. */
 typedef struct mf_mixed mf_mixed;
 mf_status mf_mixed_create(mf_process* const* procs, mf_grid* const* grids, const int64_t* n, int nproc,
                           mf_mixed** out);

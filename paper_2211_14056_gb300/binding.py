@@ -17,9 +17,14 @@ _LIB_PATH = os.path.join(HERE, "lib", "libmadflow_gb300.so")
 MF_OK, MF_ERR_ARG, MF_ERR_CUDA, MF_ERR_UNSUPPORTED, MF_ERR_COLOUR, MF_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 MF_WARN_NEWTON = 1
 MF_PROC_GG_TTX, MF_PROC_GG_TTXG, MF_PROC_GG_TTXGG, MF_PROC_UUX_TTXGG, MF_PROC_EE_MUMU = 1, 2, 3, 4, 5
+MF_PROC_UXU_TTXGG, MF_PROC_UG_TTXGU, MF_PROC_GU_TTXGU, MF_PROC_UXG_TTXGUX, MF_PROC_GUX_TTXGUX = 6, 7, 8, 9, 10
 MF_FP64, MF_FP32, MF_FP32_TC = 0, 1, 2
 
-_NGLUON = {MF_PROC_GG_TTX: 2, MF_PROC_GG_TTXG: 3, MF_PROC_GG_TTXGG: 4, MF_PROC_UUX_TTXGG: 4, MF_PROC_EE_MUMU: 2}
+_NGLUON = {MF_PROC_GG_TTX: 2, MF_PROC_GG_TTXG: 3, MF_PROC_GG_TTXGG: 4, MF_PROC_UUX_TTXGG: 4, MF_PROC_EE_MUMU: 2,
+           MF_PROC_UXU_TTXGG: 4, MF_PROC_UG_TTXGU: 4, MF_PROC_GU_TTXGU: 4, MF_PROC_UXG_TTXGUX: 4,
+           MF_PROC_GUX_TTXGUX: 4}
+_TWO_QUARK_LINES = {MF_PROC_UUX_TTXGG, MF_PROC_UXU_TTXGG, MF_PROC_UG_TTXGU, MF_PROC_GU_TTXGU, MF_PROC_UXG_TTXGUX,
+                    MF_PROC_GUX_TTXGUX}
 ALPHA_EM = 1.0 / 137.035999     # Thomson limit; e = sqrt(4 pi alpha)
 
 
@@ -36,7 +41,8 @@ class ProcessDesc(C.Structure):
         ("colour_num", C.POINTER(C.c_int64)), ("colour_den", C.c_int64), ("sqrt_s", C.c_double),
         ("lumi", C.c_int), ("lumi_N", C.c_double), ("lumi_a", C.c_double), ("lumi_b", C.c_double),
         ("pt_cut_g", C.c_double), ("dr_cut_gg", C.c_double), ("precision", C.c_int),
-        ("e_qed", C.c_double),
+        ("e_qed", C.c_double), ("pdf", C.c_void_p), ("n_pairs", C.c_int), ("pairs", C.POINTER(C.c_int)),
+        ("mu_f", C.c_double),
     ]
 
 
@@ -91,6 +97,11 @@ EXPORTS = {
                           C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_void_p]),
     "mf_grad_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_int64, C.POINTER(C.c_double),
                                   C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mf_pdf_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                C.POINTER(C.c_double), C.POINTER(C.c_void_p)]),
+    "mf_pdf_destroy": (C.c_int, [C.c_void_p]),
+    "mf_pdf_eval": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                              C.c_void_p]),
     "mf_last_error": (C.c_char_p, []),
     "mf_kernel_launches": (C.c_int64, []),
 }
@@ -175,12 +186,53 @@ def _stream(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
+class PDFSet:
+    """A tabulated parton-density set loaded on the device (mf_pdf_create):
+    xf [nflav][nq][nx] = x f(x, Q^2) on nodes uniform in ln x and ln Q^2."""
+
+    def __init__(self, x_min, x_max, q2_min, q2_max, xf):
+        import numpy as np
+        t = np.ascontiguousarray(xf, dtype=np.float64)
+        if t.ndim != 3:
+            raise ValueError("xf must be [nflav][nq][nx]")
+        self.nflav, self.nq, self.nx = t.shape
+        h = C.c_void_p()
+        _check(load_library().mf_pdf_create(self.nflav, self.nq, self.nx, x_min, x_max, q2_min, q2_max,
+                                            t.ctypes.data_as(C.POINTER(C.c_double)), C.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_dict(cls, d):
+        return cls(d["x_min"], d["x_max"], d["q2_min"], d["q2_max"], d["xf"])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().mf_pdf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def eval(self, flavour, n, x, q2, out, precision=MF_FP64, stream=None):
+        """out[e] = x f(x[e], q2[e]) of one flavour (device float64 tensors)."""
+        import torch
+        _check(load_library().mf_pdf_eval(self._h, precision, flavour, n, _ptr(x, torch.float64, n, "x"),
+                                          _ptr(q2, torch.float64, n, "q2"), _ptr(out, torch.float64, n, "xf"),
+                                          _stream(stream)))
+
+
 class Process:
-    """A configured process (mf_init_process) and its launches."""
+    """A configured process (mf_init_process) and its launches.  lumi: False
+    (fixed partonic energy), True (synthetic gluon luminosity) or "pdf"
+    (tabulated densities: pdf = a PDFSet, pairs = [(flavour a, flavour b)...],
+    mu_f = factorisation scale over sqrt(s_hat))."""
 
     def __init__(self, process_id, mt=173.0, wt=0.0, gs=1.2177, sqrt_s=1000.0, lumi=False,
                  lumi_N=1.0, lumi_a=-1.1, lumi_b=5.0, pt_cut=0.0, dr_cut=0.0, precision=MF_FP64,
-                 colour=None, e_qed=None, masses=None):
+                 colour=None, e_qed=None, masses=None, pdf=None, pairs=None, mu_f=0.5):
         lib = load_library()
         ng = _NGLUON.get(process_id)
         if ng is None:
@@ -194,15 +246,25 @@ class Process:
         if process_id == MF_PROC_EE_MUMU:
             num, den = colour if colour is not None else ([1], 1)
             nflow = 1
-        elif process_id == MF_PROC_UUX_TTXGG:
+        elif process_id in _TWO_QUARK_LINES:
             num, den = colour if colour is not None else colour_matrix_uux()
             nflow = 12
         else:
             num, den = colour if colour is not None else colour_matrix(ng)
             nflow = math.factorial(ng)
         cnum = (C.c_int64 * len(num))(*num)
+        lumi_code = 2 if lumi == "pdf" else (1 if lumi else 0)
+        pdf_h, npairs, cpairs = None, 0, None
+        if lumi_code == 2:
+            if pdf is None or not pairs:
+                raise ValueError('lumi="pdf" needs pdf (a PDFSet) and pairs')
+            flat = [int(f) for ab in pairs for f in ab]
+            npairs, cpairs = len(pairs), (C.c_int * len(flat))(*flat)
+            pdf_h = pdf._h
+            self._pdf = pdf                    # the set must outlive the process
         d = ProcessDesc(process_id, self.n_ext, masses, wt, gs, nflow, cnum, den, sqrt_s,
-                        1 if lumi else 0, lumi_N, lumi_a, lumi_b, pt_cut, dr_cut, precision, e_qed)
+                        lumi_code, lumi_N, lumi_a, lumi_b, pt_cut, dr_cut, precision, e_qed, pdf_h, npairs,
+                        cpairs, mu_f)
         h = C.c_void_p()
         _check(lib.mf_init_process(C.byref(d), C.byref(h)))
         self._h = h

@@ -163,15 +163,21 @@ int64_t mf_kernel_launches(void) { return g_launches.load(); }
 mf_status mf_init_process(const mf_process_desc* d, mf_process** out) {
   if (d == nullptr || out == nullptr) return fail(MF_ERR_ARG, "mf_init_process: null argument");
   *out = nullptr;
-  int ng = 0, kind = 0;
+  int ng = 0, kind = 0, chan = 0;
   switch (d->process_id) {
     case MF_PROC_GG_TTX: ng = 2; break;
     case MF_PROC_GG_TTXG: ng = 3; break;
     case MF_PROC_GG_TTXGG: ng = 4; break;
-    case MF_PROC_UUX_TTXGG: ng = 4; kind = 1; break;
+    case MF_PROC_UUX_TTXGG: ng = 4; kind = 1; chan = kChanQQB; break;
     case MF_PROC_EE_MUMU: ng = 2; kind = 2; break;
+    case MF_PROC_UXU_TTXGG: ng = 4; kind = 1; chan = kChanQBQ; break;
+    case MF_PROC_UG_TTXGU: ng = 4; kind = 1; chan = kChanQG; break;
+    case MF_PROC_GU_TTXGU: ng = 4; kind = 1; chan = kChanGQ; break;
+    case MF_PROC_UXG_TTXGUX: ng = 4; kind = 1; chan = kChanQBG; break;
+    case MF_PROC_GUX_TTXGUX: ng = 4; kind = 1; chan = kChanGQB; break;
     default: return fail(MF_ERR_UNSUPPORTED, "mf_init_process: unknown process_id");
   }
+  const bool quark_gluon = kind == 1 && chan >= kChanQG;   // one final gluon and a final quark
   const bool qed = kind == 2;
   const int key = kind == 1 ? kUuxKey : qed ? kEeKey : ng;
   const int nflow = kind == 1 ? kUuxFlows : qed ? 1 : factorial(ng);
@@ -214,9 +220,23 @@ mf_status mf_init_process(const mf_process_desc* d, mf_process** out) {
     }
   if (!(d->sqrt_s > 2 * mt) || !std::isfinite(d->sqrt_s))
     return fail(MF_ERR_ARG, qed ? "mf_init_process: sqrt_s must be > 0" : "mf_init_process: sqrt_s must exceed 2 m_t");
-  if (d->lumi != 0 && d->lumi != 1) return fail(MF_ERR_ARG, "mf_init_process: lumi must be 0 or 1");
-  if (d->lumi && !(d->lumi_N > 0 && d->lumi_b >= 0 && std::isfinite(d->lumi_a)))
+  if (d->lumi != 0 && d->lumi != 1 && d->lumi != 2) return fail(MF_ERR_ARG, "mf_init_process: lumi must be 0, 1 or 2");
+  if (d->lumi == 1 && !(d->lumi_N > 0 && d->lumi_b >= 0 && std::isfinite(d->lumi_a)))
     return fail(MF_ERR_ARG, "mf_init_process: bad luminosity parameters");
+  PdfView pview{};
+  if (d->lumi == 2) {
+    if (d->pdf == nullptr || d->pairs == nullptr || d->n_pairs < 1 || d->n_pairs > kMaxPdfPairs)
+      return fail(MF_ERR_ARG, "mf_init_process: lumi = 2 needs a parton-density set and 1..8 parton pairs");
+    if (!(d->mu_f > 0) || !std::isfinite(d->mu_f)) return fail(MF_ERR_ARG, "mf_init_process: mu_f must be > 0");
+    pview = pdf_view(d->pdf);
+    for (int k = 0; k < 2 * d->n_pairs; ++k)
+      if (d->pairs[k] < 0 || d->pairs[k] >= pview.nflav)
+        return fail(MF_ERR_ARG, "mf_init_process: a parton pair names a flavour outside the set");
+    int dev = 0;
+    cudaError_t ed = cudaGetDevice(&dev);
+    if (ed != cudaSuccess) return cuda_fail(ed, "mf_init_process");
+    if (dev != pdf_device(d->pdf)) return fail(MF_ERR_ARG, "mf_init_process: the set lives on another device");
+  }
   if (!(d->pt_cut_g >= 0) || !(d->dr_cut_gg >= 0)) return fail(MF_ERR_ARG, "mf_init_process: cuts must be >= 0");
 
   mf_process* p = new mf_process();
@@ -241,14 +261,25 @@ mf_status mf_init_process(const mf_process_desc* d, mf_process** out) {
   sp.dr_cut2 = d->dr_cut_gg * d->dr_cut_gg;
   const double pi = 3.14159265358979323846;
   sp.phi_const = std::pow(2 * pi, 4 - 3 * n) * std::pow(pi / 2, n - 1) / (factorial(n - 1) * factorial(n - 2));
+  if (d->lumi == 2) {
+    sp.pdf = pview;
+    sp.npairs = d->n_pairs;
+    for (int k = 0; k < d->n_pairs; ++k) {
+      sp.pairs[k][0] = uint8_t(d->pairs[2 * k]);
+      sp.pairs[k][1] = uint8_t(d->pairs[2 * k + 1]);
+    }
+    sp.ln_muf2 = 2.0 * std::log(d->mu_f);
+  }
   MeParams& mp = p->mp;
   mp.mt = mt;
   mp.mw = qed ? 0.0 : mt * d->top_width;
   mp.colour_tc = d->precision == MF_FP32_TC ? 1 : 0;
+  mp.chan = chan;
   p->g_s = d->g_s;
   p->width = d->top_width;
-  const int sid = factorial(ng - 2);        // identical final-state gluons
-  const double average = kind == 1 ? 36.0 : qed ? 4.0 : 256.0;   // spin x colour states of u u~, e+ e- or g g
+  const int sid = quark_gluon ? 1 : factorial(ng - 2);   // identical final-state gluons
+  // spin x colour states of the initial partons: q q~ 4*9, q g 4*24, e+ e- 4, g g 4*64
+  const double average = quark_gluon ? 96.0 : kind == 1 ? 36.0 : qed ? 4.0 : 256.0;
   mp.norm = qed ? std::pow(d->e_qed, 4) / average : std::pow(d->g_s, 2 * ng) / (average * sid * lden);
 
   cudaError_t e = cudaGetDevice(&p->device);

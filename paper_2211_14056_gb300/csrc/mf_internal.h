@@ -99,6 +99,9 @@ mf_status record_iteration(mf_grid* g, const double* r, int64_t n_total, mf_resu
 // Grow the grid's per-event record buffer to hold `events` (a configuration call).
 mf_status grid_reserve(mf_grid* g, int64_t events);
 int effective_ctas(const mf_process* p, int occupancy);
+// the device view and device of a loaded parton-density set (mf_pdf.cu)
+PdfView pdf_view(const mf_pdf* p);
+int pdf_device(const mf_pdf* p);
 cudaError_t dispatch_acc_config(int ng, int prec, int ndim, int nbins, size_t* smem, int* ctas);
 }  // namespace detail
 }  // namespace mf

@@ -30,7 +30,12 @@ struct MeParams {
   double mt, mw;     // top mass, mass * width
   double norm;       // g^(2 NG) / (spin-colour average * identical-particle factor * colour denominator)
   int colour_tc;     // 1: FP32 colour sum on the tensor cores (MF_FP32_TC)
+  int chan;          // two-quark-line processes: which subprocess (beams, crossing) the amplitude serves
 };
+
+// MeParams::chan of the two-quark-line amplitude (mf_kernels_uux.cu): u u~, u~ u,
+// u g, g u, u~ g, g u~ initial states
+constexpr int kChanQQB = 0, kChanQBQ = 1, kChanQG = 2, kChanGQ = 3, kChanQBG = 4, kChanGQB = 5;
 
 template <int NG> struct Lanes {
   static constexpr int L = 2 << NG;        // lanes per event

@@ -9,22 +9,66 @@
 
 namespace mf {
 
-// |M|^2 (without MeParams::norm) of one event: every lane of the warp calls it
+// |M|^2 (without MeParams::norm) of one event: every lane of the warp calls it.
+// p: physical momenta, p[0] beam 1 (+z), p[1] beam 2 (-z), p[2] t, p[3] tbar,
+// p[4], p[5] the final light partons (a final gluon first).  The generated
+// amplitude is that of u(P0) u~(P1) -> t(P2) t~(P3) g(P4) g(P5) with every
+// momentum entering only through sums; the other subprocesses of p p -> t t~
+// g g are its crossings, evaluated by filling its external slots (chan):
+//   kChanQQB  u u~ -> t t~ g g        beams as they are
+//   kChanQBQ  u~ u -> t t~ g g        the quark from beam 2
+//   kChanQG   u g  -> t t~ g u        the u~ slot takes the outgoing quark,
+//                                      ubar(p5) at momentum -p5; the first gluon
+//                                      slot the incoming gluon, eps(p1) at -p1
+//   kChanGQ   g u  -> t t~ g u        the same with the beams exchanged
+//   kChanQBG  u~ g -> t t~ g u~       charge conjugate of u g -> t~ t g u: the
+//   kChanGQB  g u~ -> t t~ g u~       quark slots take the antiquarks' momenta,
+//                                      the top slots exchange t and t~
+// (a crossed fermion flips the amplitude's sign, which |M|^2 does not see;
+// the colour decomposition is over index slots and does not change).
+// (the kChan* codes are declared beside MeParams)
+
 template <typename T>
-__device__ __forceinline__ T uux_warp_me2(const T (&p)[6][4], T mt, T mw) {
+__device__ __forceinline__ T uux_warp_me2(const T (&p)[6][4], T mt, T mw, int chan) {
   const int lane = threadIdx.x & 31;
-  R4<T> P[6];
+  R4<T> Q[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) P[i].v[c] = p[i][c];
+    for (int c = 0; c < 4; ++c) Q[i].v[c] = p[i][c];
   const int l1 = (lane & 1) ? 1 : -1, l2 = (lane & 2) ? 1 : -1, l4 = (lane & 4) ? 1 : -1;
   const int l5 = (lane & 8) ? 1 : -1, l6 = (lane & 16) ? 1 : -1;
-  const S4<T> U1 = u_in(P[0], T(0), l1);
-  const S4<T> V2 = vbar_in(P[1], T(0), l2);
-  const S4<T> VTB = v_out(P[3], mt, l4);
-  const S4<T> UB3[2] = {ubar_out(P[2], mt, -1), ubar_out(P[2], mt, 1)};
-  const V4<T> E5 = polarisation(P[4], l5, true), E6 = polarisation(P[5], l6, true);
+  const bool swap_beams = chan == kChanQBQ || chan == kChanGQ || chan == kChanGQB;
+  const bool crossed = chan >= kChanQG;
+  const bool conj_tops = chan == kChanQBG || chan == kChanGQB;
+  const R4<T>& qin = swap_beams ? Q[1] : Q[0];      // the incoming (anti)quark on the amplitude's quark line
+  const R4<T>& other = swap_beams ? Q[0] : Q[1];    // the other beam parton
+  const R4<T>& top = conj_tops ? Q[3] : Q[2];
+  const R4<T>& atop = conj_tops ? Q[2] : Q[3];
+  R4<T> P[6];
+  P[0] = qin;
+  P[2] = top;
+  P[3] = atop;
+  S4<T> V2;
+  V4<T> E5, E6;
+  if (crossed) {
+    P[1] = -Q[5];
+    P[4] = -other;
+    P[5] = Q[4];
+    V2 = ubar_out(Q[5], T(0), l2);
+    E5 = polarisation(other, l5, false);
+    E6 = polarisation(Q[4], l6, true);
+  } else {
+    P[1] = other;
+    P[4] = Q[4];
+    P[5] = Q[5];
+    V2 = vbar_in(other, T(0), l2);
+    E5 = polarisation(Q[4], l5, true);
+    E6 = polarisation(Q[5], l6, true);
+  }
+  const S4<T> U1 = u_in(qin, T(0), l1);
+  const S4<T> VTB = v_out(atop, mt, l4);
+  const S4<T> UB3[2] = {ubar_out(top, mt, -1), ubar_out(top, mt, 1)};
   cplx<T> J[2][kUuxFlows];
   uux_amplitudes<T>(P, mt, mw, U1, V2, VTB, UB3, E5, E6, J);
   T part = uux_colour_form<T>(J[0]) + uux_colour_form<T>(J[1]);
@@ -44,7 +88,7 @@ __global__ void __launch_bounds__(kThreads) k_matrix_element_uux(MeParams mp, in
     for (int i = 0; i < 6; ++i)
 #pragma unroll
       for (int c = 0; c < 4; ++c) p[i][c] = T(mom[int64_t(i * 4 + c) * n + e]);
-    const T v = uux_warp_me2<T>(p, mt, mw);
+    const T v = uux_warp_me2<T>(p, mt, mw, mp.chan);
     if (lane == 0) out[e] = double(v) * mp.norm;
   }
 }
@@ -75,7 +119,7 @@ __global__ void __launch_bounds__(kThreads) k_me_acc_uux(MeParams mp, int ndim, 
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int c = 0; c < 4; ++c) p[2 + i][c] = rec.mom[int64_t(i * 4 + c) * rec.C + e];
-    const T v = uux_warp_me2<T>(p, mt, mw);
+    const T v = uux_warp_me2<T>(p, mt, mw, mp.chan);
     const double w = double(v) * mp.norm * rec.pref[e];
     if (lane == 0) {
       s1 += w;

@@ -20,7 +20,7 @@
 
 namespace mf {
 
-constexpr int kMaxProc = 4;
+constexpr int kMaxProc = 8;
 
 template <typename K> struct MixedArgs {
   int nproc;
@@ -226,6 +226,8 @@ struct mf_mixed {
   int ctas_per_sm = 0;               // 0 = occupancy
   int occupancy = 1;
   int tile = 32;                     // listed events per work item; 0: per-process kernels
+  bool queue_fits = true;            // the shared-queue kernel fits on an SM (its shared memory holds
+                                     // every process's sums beside the warps' 2->4 stores)
   int acc_occ[kMaxProc] = {};        // occupancy of each process's own |M|^2 kernel
   size_t me_smem = 0, sample_smem = 0;
   unsigned* d_queue = nullptr;
@@ -375,7 +377,7 @@ mf_status mf_mixed_create(mf_process* const* procs, mf_grid* const* grids, const
                           mf_mixed** out) {
   if (procs == nullptr || grids == nullptr || n == nullptr || out == nullptr)
     return fail(MF_ERR_ARG, "mf_mixed_create: null argument");
-  if (nproc < 1 || nproc > kMaxProc) return fail(MF_ERR_ARG, "mf_mixed_create: 1 to 4 processes");
+  if (nproc < 1 || nproc > kMaxProc) return fail(MF_ERR_ARG, "mf_mixed_create: 1 to 8 processes");
   *out = nullptr;
   mf_mixed* m = new mf_mixed();
   m->nproc = nproc;
@@ -420,7 +422,13 @@ mf_status mf_mixed_create(mf_process* const* procs, mf_grid* const* grids, const
     e = cudaFuncSetAttribute(k_me_mixed<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(m->me_smem));
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m->occupancy, k_me_mixed<float>, kThreads, m->me_smem);
   }
-  if (e == cudaSuccess && m->occupancy < 1) e = cudaErrorInvalidConfiguration;
+  if (e == cudaSuccess && m->occupancy < 1) {
+    // too many processes' sums for the shared queue: the plan runs the
+    // per-process form only
+    m->queue_fits = false;
+    m->occupancy = 0;
+    m->tile = 0;
+  }
   for (int k = 0; k < nproc && e == cudaSuccess; ++k) {
     size_t asm_ = 0;
     e = dispatch_acc_config(proc_key(procs[k]), m->precision, grids[k]->ndim, grids[k]->nbins, &asm_, &m->acc_occ[k]);
@@ -461,6 +469,9 @@ mf_status mf_mixed_destroy(mf_mixed* m) {
 
 mf_status mf_mixed_set_launch(mf_mixed* m, int ctas_per_sm, int tile) {
   if (m == nullptr || ctas_per_sm < 0 || tile < 0) return fail(MF_ERR_ARG, "mf_mixed_set_launch: bad argument");
+  if (tile > 0 && !m->queue_fits)
+    return fail(MF_ERR_UNSUPPORTED, "mf_mixed_set_launch: the shared-queue kernel does not fit on an SM for this "
+                                    "plan (per-process form only, tile = 0)");
   m->ctas_per_sm = ctas_per_sm;
   m->tile = tile;
   drop_graphs(m);
@@ -521,6 +532,10 @@ mf_status mf_mixed_autotune(mf_mixed* m, uint64_t seed, int ncand, const int* ca
     return fail(MF_ERR_ARG, "mf_mixed_autotune: bad argument");
   for (int c = 0; c < ncand; ++c)
     if (cand_ctas[c] < 0 || cand_tile[c] < 0) return fail(MF_ERR_ARG, "mf_mixed_autotune: bad candidate");
+  for (int c = 0; c < ncand; ++c)
+    if (cand_tile[c] > 0 && !m->queue_fits)
+      return fail(MF_ERR_UNSUPPORTED, "mf_mixed_autotune: a shared-queue candidate for a plan that runs the "
+                                      "per-process form only");
   cudaStream_t s = (cudaStream_t)stream;
   const int keep_c = m->ctas_per_sm, keep_t = m->tile;
   const bool keep_g = m->use_graph;

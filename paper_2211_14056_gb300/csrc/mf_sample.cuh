@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include "mf_dual.cuh"
+#include "mf_pdf.cuh"
 
 namespace mf {
 
@@ -34,13 +35,19 @@ struct SampleParams {
   int n_final;          // final-state particles (2..4)
   int ndim;             // Vegas dimensions
   int nbins;            // bins per dimension
-  int lumi;             // 0: fixed partonic sqrt(s); 1: synthetic gluon luminosity
+  int lumi;             // 0: fixed partonic sqrt(s); 1: synthetic gluon luminosity; 2: tabulated densities
   double sqrt_s;        // hadronic sqrt(S) (lumi) or partonic sqrt(s)
   double tau0, log_tau0;
   double lumi_N, lumi_a, lumi_b;
-  double mt;            // top mass (final particles 0, 1 massive; gluons massless)
+  double mt;            // top mass (final particles 0, 1 massive; gluons and light quarks massless)
   double pt_cut2, dr_cut2;   // squared thresholds (0 disables)
   double phi_const;     // (2 pi)^(4-3n) (pi/2)^(n-1) / ((n-1)! (n-2)!)
+  // lumi = 2: the set, the channel's parton pairs (flavour indices of beam 1,
+  // beam 2) and ln(mu_f^2) (factorisation scale Q = mu_f sqrt(s_hat))
+  PdfView pdf;
+  int npairs;
+  uint8_t pairs[kMaxPdfPairs][2];
+  double ln_muf2;
 };
 
 // K: arithmetic of the kinematics (momenta, luminosity, cuts); D: that of the
@@ -186,11 +193,27 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
     const K lx[2] = {K(x[0]) * lt, K(x[1]) * (K(1) - K(x[0])) * lt};
     // ln(1 - x) = ln(-expm1(ln x)): accurate also for x within an ulp of 1
     // (where 1 - exp(ln x) would round to 0 in FP32)
-    const K l1m = log(-expm1(lx[0])) + log(-expm1(lx[1]));
     const K lsum = lx[0] + lx[1];
     shat = D(exp(lsum)) * (sp.sqrt_s * sp.sqrt_s);
-    const K ff = exp(K(sp.lumi_a + 1.0) * lsum + K(sp.lumi_b) * l1m);
-    lum = D(ff) * (D(1.0) - x[0]) * log_tau0 * log_tau0 * (sp.lumi_N * sp.lumi_N);
+    if (sp.lumi == 2) {
+      // tabulated densities: sum over the channel's parton pairs of
+      // x1 f_a(x1, Q^2) x2 f_b(x2, Q^2) (the map's x1 x2 is in the table's x f),
+      // ln Q^2 = ln mu_f^2 + ln x1 + ln x2 + ln S
+      // (the derivative pass does not cover tabulated densities: no tangents here)
+      K L = K(0);
+      if constexpr (!is_dual<K>::value) {
+        const K lq2 = K(sp.ln_muf2 + 2.0 * log(sp.sqrt_s)) + lsum;
+        const PdfCell<K> c1 = pdf_cell(sp.pdf, lx[0], lq2), c2 = pdf_cell(sp.pdf, lx[1], lq2);
+#pragma unroll 1
+        for (int k = 0; k < sp.npairs; ++k)
+          L += pdf_xfx(sp.pdf, sp.pairs[k][0], c1) * pdf_xfx(sp.pdf, sp.pairs[k][1], c2);
+      }
+      lum = D(L) * (D(1.0) - x[0]) * log_tau0 * log_tau0;
+    } else {
+      const K l1m = log(-expm1(lx[0])) + log(-expm1(lx[1]));
+      const K ff = exp(K(sp.lumi_a + 1.0) * lsum + K(sp.lumi_b) * l1m);
+      lum = D(ff) * (D(1.0) - x[0]) * log_tau0 * log_tau0 * (sp.lumi_N * sp.lumi_N);
+    }
   } else {
     shat = D(sp.sqrt_s * sp.sqrt_s);
   }

@@ -47,7 +47,7 @@ def test_rejects_bad_descriptions_without_device(lib):
                 colour_den=den, sqrt_s=1000.0, lumi=0, lumi_N=1, lumi_a=-1.1, lumi_b=5, pt_cut_g=0,
                 dr_cut_gg=0, precision=0)
     cases = [
-        (dict(process_id=9), B.MF_ERR_UNSUPPORTED),
+        (dict(process_id=99), B.MF_ERR_UNSUPPORTED),
         (dict(n_ext=5), B.MF_ERR_ARG),
         (dict(g_s=-1.0), B.MF_ERR_ARG),
         (dict(sqrt_s=300.0), B.MF_ERR_ARG),
