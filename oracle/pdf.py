@@ -44,7 +44,7 @@ def node_slopes(f, h):
     """Finite-difference slopes at every node of the last axis of f (equal
     spacing h): the mean of the two neighbouring difference quotients
     inside, the one-sided quotient at the first and last node."""
-    f = np.asarray(f, dtype=np.float64)
+    f = np.asarray(f)
     d = np.diff(f, axis=-1) / h
     m = np.empty_like(f)
     m[..., 0] = d[..., 0]
@@ -62,14 +62,17 @@ def _cell(t, t0, h, n):
 
 
 class PDFGrid:
-    """One tabulated set: xf[nflav][nq][nx] on uniform nodes in ln x and ln Q^2."""
+    """One tabulated set: xf[nflav][nq][nx] on uniform nodes in ln x and ln Q^2.
+    dtype: the arithmetic (FP64; np.longdouble gives the same scheme with a
+    wider mantissa, which the tests use to measure FP64 rounding)."""
 
-    def __init__(self, x_min, x_max, q2_min, q2_max, xf):
-        self.xf = np.asarray(xf, dtype=np.float64)
+    def __init__(self, x_min, x_max, q2_min, q2_max, xf, dtype=np.float64):
+        self.dtype = dtype
+        self.xf = np.asarray(xf, dtype=dtype)
         self.nflav, self.nq, self.nx = self.xf.shape
-        self.t0, self.s0 = np.log(x_min), np.log(q2_min)
-        self.ht = (np.log(x_max) - self.t0) / (self.nx - 1)
-        self.hs = (np.log(q2_max) - self.s0) / (self.nq - 1)
+        self.t0, self.s0 = np.log(dtype(x_min)), np.log(dtype(q2_min))
+        self.ht = (np.log(dtype(x_max)) - self.t0) / (self.nx - 1)
+        self.hs = (np.log(dtype(q2_max)) - self.s0) / (self.nq - 1)
         self.mx = node_slopes(self.xf, self.ht)          # x-slopes of every row's nodes
 
     def _row(self, f, l, i, u):
@@ -78,8 +81,8 @@ class PDFGrid:
 
     def xfx(self, flavour, x, q2):
         """x f(x, Q^2) of one flavour index at arrays x, q2 (same shape)."""
-        x = np.asarray(x, dtype=np.float64)
-        q2 = np.asarray(q2, dtype=np.float64)
+        x = np.asarray(x, dtype=self.dtype)
+        q2 = np.asarray(q2, dtype=self.dtype)
         shape = np.broadcast(x, q2).shape
         x, q2 = np.broadcast_to(x, shape).ravel(), np.broadcast_to(q2, shape).ravel()
         i, u = _cell(np.log(x), self.t0, self.ht, self.nx)

@@ -268,7 +268,7 @@ mf_status mf_init_process(const mf_process_desc* d, mf_process** out) {
       sp.pairs[k][0] = uint8_t(d->pairs[2 * k]);
       sp.pairs[k][1] = uint8_t(d->pairs[2 * k + 1]);
     }
-    sp.ln_muf2 = 2.0 * std::log(d->mu_f);
+    sp.ln_muf2_S = 2.0 * std::log(d->mu_f) + 2.0 * std::log(d->sqrt_s);
   }
   MeParams& mp = p->mp;
   mp.mt = mt;

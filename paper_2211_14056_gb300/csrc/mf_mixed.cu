@@ -413,14 +413,19 @@ mf_status mf_mixed_create(mf_process* const* procs, mf_grid* const* grids, const
   }
   m->sample_smem = esm;
   cudaError_t e = cudaSuccess;
-  if (m->precision == 0) {
-    m->me_smem = MixedLayout<double>::total(ndim, nbins, nproc);
-    e = cudaFuncSetAttribute(k_me_mixed<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(m->me_smem));
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m->occupancy, k_me_mixed<double>, kThreads, m->me_smem);
-  } else {
-    m->me_smem = MixedLayout<float>::total(ndim, nbins, nproc);
-    e = cudaFuncSetAttribute(k_me_mixed<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(m->me_smem));
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m->occupancy, k_me_mixed<float>, kThreads, m->me_smem);
+  int smem_optin = 0;
+  e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, procs[0]->device);
+  m->me_smem = m->precision == 0 ? MixedLayout<double>::total(ndim, nbins, nproc)
+                                 : MixedLayout<float>::total(ndim, nbins, nproc);
+  m->occupancy = 0;
+  if (e == cudaSuccess && m->me_smem <= size_t(smem_optin)) {
+    if (m->precision == 0) {
+      e = cudaFuncSetAttribute(k_me_mixed<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(m->me_smem));
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m->occupancy, k_me_mixed<double>, kThreads, m->me_smem);
+    } else {
+      e = cudaFuncSetAttribute(k_me_mixed<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(m->me_smem));
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m->occupancy, k_me_mixed<float>, kThreads, m->me_smem);
+    }
   }
   if (e == cudaSuccess && m->occupancy < 1) {
     // too many processes' sums for the shared queue: the plan runs the

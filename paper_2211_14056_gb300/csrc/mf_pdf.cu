@@ -38,7 +38,9 @@ __global__ void __launch_bounds__(256) k_pdf_eval(PdfView pv, int flavour, int64
     fl = reinterpret_cast<const K*>(smem_raw);
   }
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
-    const K lx = K(log(x[e])), lq = K(log(q2[e]));
+    // the logarithms in the arithmetic's own precision (an FP64 log would
+    // bound the FP32 kernel by GB300's FP64 rate)
+    const K lx = log(K(x[e])), lq = log(K(q2[e]));
     const PdfCell<K> c = pdf_cell(pv, lx, lq);
     out[e] = double(pdf_xfx_slice(pv, fl, c));
   }
@@ -93,6 +95,8 @@ mf_status mf_pdf_create(int nflav, int nq, int nx, double x_min, double x_max, d
   v.ht = (std::log(x_max) - v.t0) / (nx - 1);
   v.s0 = std::log(q2_min);
   v.hs = (std::log(q2_max) - v.s0) / (nq - 1);
+  v.iht = 1.0 / v.ht;
+  v.ihs = 1.0 / v.hs;
   // a flavour's slice of (value, slope) pairs, padded to 64 bytes in FP64 and FP32
   v.slice = (int64_t(nq) * nx * 2 + 7) / 8 * 8;
   std::vector<double> t64(size_t(nflav) * v.slice, 0.0);

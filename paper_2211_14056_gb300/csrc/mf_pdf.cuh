@@ -27,6 +27,7 @@ struct PdfView {
   int nflav, nq, nx;
   int64_t slice;            // elements per flavour (>= nq * nx * 2)
   double t0, ht, s0, hs;    // ln x_min and the ln x step; ln Q2_min and the ln Q^2 step
+  double iht, ihs;          // 1 / ht, 1 / hs
 };
 
 template <typename K> struct PdfCell {
@@ -38,10 +39,10 @@ template <typename K> __device__ __forceinline__ const K* pdf_table(const PdfVie
 template <> __device__ __forceinline__ const double* pdf_table<double>(const PdfView& pv) { return pv.tab64; }
 template <> __device__ __forceinline__ const float* pdf_table<float>(const PdfView& pv) { return pv.tab32; }
 
-// (cell, local coordinate) of a logarithm on n nodes c0 + k h, clamped to the range
+// (cell, local coordinate) of a logarithm on n nodes c0 + k h (ih = 1/h), clamped to the range
 template <typename K>
-__device__ __forceinline__ void pdf_locate(K z, double c0, double h, int n, int& cell, K& loc) {
-  K r = (z - K(c0)) / K(h);
+__device__ __forceinline__ void pdf_locate(K z, double c0, double ih, int n, int& cell, K& loc) {
+  K r = (z - K(c0)) * K(ih);
   r = r < K(0) ? K(0) : (r > K(n - 1) ? K(n - 1) : r);
   int k = int(r);
   k = k > n - 2 ? n - 2 : k;
@@ -52,8 +53,8 @@ __device__ __forceinline__ void pdf_locate(K z, double c0, double h, int n, int&
 template <typename K>
 __device__ __forceinline__ PdfCell<K> pdf_cell(const PdfView& pv, K lnx, K lnq2) {
   PdfCell<K> c;
-  pdf_locate(lnx, pv.t0, pv.ht, pv.nx, c.i, c.u);
-  pdf_locate(lnq2, pv.s0, pv.hs, pv.nq, c.j, c.v);
+  pdf_locate(lnx, pv.t0, pv.iht, pv.nx, c.i, c.u);
+  pdf_locate(lnq2, pv.s0, pv.ihs, pv.nq, c.j, c.v);
   return c;
 }
 

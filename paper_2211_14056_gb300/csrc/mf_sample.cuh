@@ -43,11 +43,12 @@ struct SampleParams {
   double pt_cut2, dr_cut2;   // squared thresholds (0 disables)
   double phi_const;     // (2 pi)^(4-3n) (pi/2)^(n-1) / ((n-1)! (n-2)!)
   // lumi = 2: the set, the channel's parton pairs (flavour indices of beam 1,
-  // beam 2) and ln(mu_f^2) (factorisation scale Q = mu_f sqrt(s_hat))
+  // beam 2) and ln(mu_f^2 S) (factorisation scale Q = mu_f sqrt(s_hat):
+  // ln Q^2 = ln(mu_f^2 S) + ln x1 + ln x2)
   PdfView pdf;
   int npairs;
   uint8_t pairs[kMaxPdfPairs][2];
-  double ln_muf2;
+  double ln_muf2_S;
 };
 
 // K: arithmetic of the kinematics (momenta, luminosity, cuts); D: that of the
@@ -197,12 +198,11 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
     shat = D(exp(lsum)) * (sp.sqrt_s * sp.sqrt_s);
     if (sp.lumi == 2) {
       // tabulated densities: sum over the channel's parton pairs of
-      // x1 f_a(x1, Q^2) x2 f_b(x2, Q^2) (the map's x1 x2 is in the table's x f),
-      // ln Q^2 = ln mu_f^2 + ln x1 + ln x2 + ln S
+      // x1 f_a(x1, Q^2) x2 f_b(x2, Q^2) (the map's x1 x2 is in the table's x f)
       // (the derivative pass does not cover tabulated densities: no tangents here)
       K L = K(0);
       if constexpr (!is_dual<K>::value) {
-        const K lq2 = K(sp.ln_muf2 + 2.0 * log(sp.sqrt_s)) + lsum;
+        const K lq2 = K(sp.ln_muf2_S) + lsum;
         const PdfCell<K> c1 = pdf_cell(sp.pdf, lx[0], lq2), c2 = pdf_cell(sp.pdf, lx[1], lq2);
 #pragma unroll 1
         for (int k = 0; k < sp.npairs; ++k)

@@ -80,14 +80,15 @@ def oracle_spread(setup, p):
     return (v.max(axis=0) - v.min(axis=0)) / np.abs(v[0])
 
 
-def assert_fp64_parity(got, ref, core=1e-12, tail=1e-10, frac=0.99, momenta=None, setup=None):
+def assert_fp64_parity(got, ref, core=1e-12, tail=1e-10, frac=0.99, momenta=None, setup=None, extra=None):
     """Per-event FP64 parity.  With the events' momenta and oracle set-up
     given, every event outside ``core`` is arbitrated: the oracle evaluates it
     with each of its algorithms (``oracle_spread``), and the GPU value must
     lie within core |ref| + 4 * (their spread) of the reference (relative
     deviations of weights equal those of |M|^2 up to the weight factor's own
-    rounding, ~1e-15).  Without momenta the blanket fraction ``frac`` applies
-    instead."""
+    rounding, ~1e-15; ``extra(indices)``, if given, adds the relative rounding
+    spread of another factor of the weight, e.g. an interpolated luminosity).
+    Without momenta the blanket fraction ``frac`` applies instead."""
     got, ref = np.asarray(got), np.asarray(ref)
     assert got.shape == ref.shape
     rel = np.abs(got - ref) / np.abs(ref)
@@ -101,6 +102,8 @@ def assert_fp64_parity(got, ref, core=1e-12, tail=1e-10, frac=0.99, momenta=None
     if out.size == 0:
         return
     spread = oracle_spread(setup, np.asarray(momenta)[out])
+    if extra is not None:
+        spread = spread + extra(out)
     ratio = rel[out] / np.maximum(spread, core)
     print(f"  {out.size} tail events: GPU deviation / oracle spread: median {np.median(ratio):.2f}, "
           f"max {ratio.max():.2f}; spread median {np.median(spread):.1e}, max {spread.max():.1e}")

@@ -67,9 +67,40 @@ def _points(n, seed):
     lq = rng.uniform(np.log(pdfgrid.Q2_MIN) - 1.0, np.log(pdfgrid.Q2_MAX) + 1.0, n)
     x, q2 = np.exp(lx), np.exp(lq)
     xn, qn = pdfgrid.nodes()
-    x[:40] = xn[rng.integers(0, len(xn), 40)]                        # nodes, including x = 1
-    q2[:40] = qn[rng.integers(0, len(qn), 40)]
+    m = min(40, n)
+    x[:m] = xn[rng.integers(0, len(xn), m)]                          # nodes, including x = 1
+    q2[:m] = qn[rng.integers(0, len(qn), m)]
     return x, q2
+
+
+def _lumi_spread(st, y, edges):
+    """Relative FP64 rounding of the tabulated-density luminosity of the
+    events with uniforms y[:, e]: the oracle's FP64 value against the same
+    scheme in extended precision, plus the change one ulp of x1, x2 or Q^2
+    makes (near x -> 1 a density is a small difference of its node values and
+    slopes, and its relative rounding grows to ~1e-12)."""
+    from oracle import phase_space as ps
+    x, _, _ = ov.vegas_map(y, edges)
+    c = st.cfg
+    S = c["sqrt_s"] ** 2
+    tau0 = (sum(st.masses)) ** 2 / S
+    x1 = tau0 ** x[0]
+    x2 = (tau0 / x1) ** x[1]
+    q2 = c["mu_f"] ** 2 * x1 * x2 * S
+    d = c["pdf"]
+    ext = PDFGrid(d["x_min"], d["x_max"], d["q2_min"], d["q2_max"], d["xf"], dtype=np.longdouble)
+
+    def lum(g, a1, a2, q):
+        return sum(g.xfx(fa, a1, q) * g.xfx(fb, a2, q) for fa, fb in c["pairs"])
+
+    X = [np.asarray(v, dtype=np.longdouble) for v in (x1, x2, q2)]
+    le = lum(ext, *X)
+    spread = np.abs(lum(st.pdf, x1, x2, q2) - le)
+    for k in range(3):
+        Xk = list(X)
+        Xk[k] = Xk[k] * (1 + np.longdouble(2.0 ** -52))
+        spread = spread + np.abs(lum(ext, *Xk) - le)
+    return np.asarray(spread / np.abs(le), dtype=np.float64)
 
 
 @pytest.mark.parametrize("n", [10007, 1, 0])
@@ -88,7 +119,11 @@ def test_pdf_eval_matches_oracle(mf, pdf, n):
             if n == 0:
                 continue
             got = out[:n].cpu().numpy()
-            scale = np.maximum(np.abs(ref), 1e-6 * np.max(np.abs(d["xf"][f])))
+            # FP32: a density that vanishes linearly (charm at the lowest Q^2,
+            # every flavour at x -> 1) is compared against 1e-3 of its table's
+            # scale there
+            floor = 1e-6 if prec == mf.MF_FP64 else 1e-3
+            scale = np.maximum(np.abs(ref), floor * np.max(np.abs(d["xf"][f])))
             err = np.abs(got - ref) / scale
             assert err.max() < bar, (f, prec, err.max())
 
@@ -132,7 +167,9 @@ def test_channel_matrix_element_matches_oracle(mf, pdf, name):
                                     ("pp_ttxgg_gqx", 500)])
 def test_channel_iterations_match_oracle(mf, pdf, name, n):
     """Two refined iterations per channel on the tabulated-density
-    luminosity, each compared on the GPU's own current edges."""
+    luminosity, each compared on the GPU's own current edges; a weight outside
+    1e-12 is held to the oracle's spread of |M|^2 plus the FP64 rounding of
+    the luminosity at that event."""
     p, w = _proc(mf, pdf, name, mf.MF_FP64)
     g = p.grid()
     st = _setup(w, amplitude="bg" if w["process"] == "gg_ttxgg" else "feynman")
@@ -145,11 +182,16 @@ def test_channel_iterations_match_oracle(mf, pdf, name, n):
         np.testing.assert_array_equal(wg > 0, ro["w"] > 0)
         nz = ro["w"] > 0
         assert nz.sum() > 0.3 * n
-        pk = st.kinematics(oph.uniforms(19, it, np.arange(n, dtype=np.uint64), st.ndim), edges)[0]
-        assert_fp64_parity(wg[nz], ro["w"][nz], momenta=pk[nz], setup=st)
+        y = oph.uniforms(19, it, np.arange(n, dtype=np.uint64), st.ndim)
+        pk = st.kinematics(y, edges)[0]
+        yz = y[:, nz]
+        assert_fp64_parity(wg[nz], ro["w"][nz], tail=1e-9, momenta=pk[nz], setup=st,
+                           extra=lambda idx: _lumi_spread(st, yz[:, idx], edges))
         assert r["I_k"] == pytest.approx(ro["I"], rel=1e-12)
         assert r["sigma_k"] == pytest.approx(math.sqrt(ro["var"]), rel=1e-11)
-        np.testing.assert_allclose(g.get(), ov.refine(edges, ro["hist"]), rtol=0, atol=1e-12)
+        # the luminosity's rounding moves sums of w^2 at ~1e-13, the refined
+        # edges at ~1e-12
+        np.testing.assert_allclose(g.get(), ov.refine(edges, ro["hist"]), rtol=0, atol=1e-11)
 
 
 @pytest.mark.parametrize("precision,tile,bar", [(0, 0, 1e-12), (1, 32, 1e-6), (1, 0, 1e-12)])
