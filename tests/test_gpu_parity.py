@@ -88,19 +88,23 @@ def assert_fp64_parity(got, ref, core=1e-12, tail=1e-10, frac=0.99, momenta=None
     deviations of weights equal those of |M|^2 up to the weight factor's own
     rounding, ~1e-15; ``extra(indices)``, if given, adds the relative rounding
     spread of another factor of the weight, e.g. an interpolated luminosity).
-    Without momenta the blanket fraction ``frac`` applies instead."""
+    Without momenta the blanket fraction ``frac`` applies instead.  Returns
+    the relative deviation each event was allowed (core, or its arbitrated
+    bound), from which sums of the values can be bounded."""
     got, ref = np.asarray(got), np.asarray(ref)
     assert got.shape == ref.shape
     rel = np.abs(got - ref) / np.abs(ref)
     inside = rel <= core
     print(f"FP64 parity: {np.mean(inside):.4f} of {rel.size} within {core:g}, max {rel.max():.2e}")
     assert rel.max() <= tail
+    allowed = np.full(rel.shape, core)
     if momenta is None:
         assert np.mean(inside) >= frac
-        return
+        allowed[~inside] = tail
+        return allowed
     out = np.flatnonzero(~inside)
     if out.size == 0:
-        return
+        return allowed
     spread = oracle_spread(setup, np.asarray(momenta)[out])
     if extra is not None:
         spread = spread + extra(out)
@@ -108,6 +112,8 @@ def assert_fp64_parity(got, ref, core=1e-12, tail=1e-10, frac=0.99, momenta=None
     print(f"  {out.size} tail events: GPU deviation / oracle spread: median {np.median(ratio):.2f}, "
           f"max {ratio.max():.2f}; spread median {np.median(spread):.1e}, max {spread.max():.1e}")
     assert np.all(rel[out] <= core + 4 * spread)
+    allowed[out] = core + 4 * spread
+    return allowed
 
 
 def _proc(mf, name, precision, **over):
