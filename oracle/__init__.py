@@ -24,6 +24,7 @@ berends_giele   Colour-ordered recursion for a heavy quark pair plus gluons.
 processes       Process definitions (externals, masses, couplings, averages).
 pdf             Log-bicubic (Hermite) interpolation of tabulated parton densities.
 integrate       Event weights and Vegas iterations built from the above.
+unweight        Hit-or-miss unweighting of weighted events.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test except the
 absolute cross sections of the 2->3 and 2->4 processes, which the paper never

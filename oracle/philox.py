@@ -16,6 +16,10 @@ Stream layout (both sides implement this independently):
     words (w0, w1, w2, w3) = Philox4x32-10(counter, key)
     dim 2j   uses (w0, w1);  dim 2j+1 uses (w2, w3)
     y = ((w_a << 21) | (w_b >> 11)) * 2**-53      in [0, 1), exact in FP64
+A second stream, for decisions taken after the weight (the hit-or-miss
+unweighting), uses the same key and counter (event & 0xffffffff, event >> 32,
+0, 1): its words (w0, w1) give one uniform per event, independent of the
+Vegas uniforms (whose counters end in 0).
 """
 import numpy as np
 
@@ -80,3 +84,14 @@ def uniforms(seed, iteration, events, ndim):
         if 2 * j + 1 < ndim:
             out[2 * j + 1] = words_to_unit(w2, w3)
     return out
+
+
+def unweight_uniforms(seed, iteration, events):
+    """r[len(events)]: the unweighting stream's uniform of each listed event."""
+    ev = np.asarray(events, dtype=np.uint64)
+    seed = int(seed)
+    k0 = seed & MASK32
+    k1 = ((seed >> 32) ^ int(iteration)) & MASK32
+    w0, w1, _, _ = philox4x32_10(ev & np.uint64(MASK32), ev >> np.uint64(32), np.zeros_like(ev),
+                                 np.ones_like(ev), k0, k1)
+    return words_to_unit(w0, w1)
