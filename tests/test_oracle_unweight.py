@@ -70,7 +70,7 @@ def test_unbiased_with_and_without_overweights(w_max):
 
 def test_limits():
     w = np.array([-1.0, 0.0, 1e-3, 0.2, 5.0])
-    r = np.array([0.0, 0.5, 0.0, 0.99, 0.5])
+    r = np.array([0.1, 0.5, 0.3, 0.99, 0.5])
     kept, _ = unweight(w, r, 1e300)
     assert kept.tolist() == [False, False, False, False, False]
     kept, weight = unweight(w, r, 1e-10)
