@@ -304,6 +304,7 @@ def main():
     both = (w64 != 0) & (w32 != 0)
     flips = int(((w64 != 0) ^ (w32 != 0)).sum())      # cut / threshold decisions taken differently
     relw = ((w32[both] - w64[both]).abs() / w64[both].abs()).double()
+    w_max_fp32 = float(w32.max())                     # the unweighting's maximum weight (this frozen grid)
     ev_err = {"max": float(relw.max()), "median": float(relw.median()),
               "p999": float(torch.quantile(relw[: 2 ** 24].float(), 0.999)),
               "decision_flips": flips, "events_compared": int(both.sum())}
@@ -384,13 +385,14 @@ def main():
     peak_derived = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
 
     # 7. the derivative and mixed-launch workloads (N = 1 only)
-    grad = mixed = shapes = pp = pdfk = None
+    grad = mixed = shapes = pp = pdfk = unw = None
     if world == 1 and not args.no_extras:
         grad = _grad_leg(p32, p64, g32, g64, w, torch)
         mixed = _mixed_leg(mf, torch)
         shapes = _launch_shape_leg(mf, torch)
         pp = _pp_leg(mf, torch)
         pdfk = _pdf_leg(mf, torch)
+        unw = _unweight_leg(p32, g32, w, torch, n, w_max_fp32)
 
     # 8. CPU baseline: the oracle on the host cores (rank 0 only, N = 1 only)
     cpu = None
@@ -450,6 +452,8 @@ def main():
             line["pp_ttxgg"] = pp
         if pdfk is not None:
             line["pdf_interpolation"] = pdfk
+        if unw is not None:
+            line["unweighting"] = unw
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -612,6 +616,33 @@ def _pdf_leg(mf, torch, n=2 ** 26, reps=5):
     res["kernel"] = "k_pdf_eval (flavour table staged in shared memory)"
     res["bytes_per_point"] = 24
     return res
+
+
+def _unweight_leg(p, g, w, torch, n, w_max, reps=3):
+    """Hit-or-miss unweighting (mf_unweight) of n FP32 g g -> t tbar g g events
+    on the frozen grid with w_max = the largest weight of one iteration: the
+    same kernels as an iteration plus the hit-or-miss pass; unweighted events
+    per second and the unweighting efficiency."""
+    import statistics as stats
+    cap = n // 8
+    mom = torch.empty(p.n_ext * 4 * cap, dtype=torch.float64, device="cuda")
+    wt = torch.empty(cap, dtype=torch.float64, device="cuda")
+    ev = torch.empty(cap, dtype=torch.int64, device="cuda")
+    p.unweight(g, w["seed"], 6000, 0, n, w_max, cap, mom, wt, ev)
+    ts, kept = [], []
+    for r in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        k, o, st = p.unweight(g, w["seed"], 6001 + r, 0, n, w_max, cap, mom, wt, ev)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        kept.append(k)
+    ms = stats.mean(ts)
+    return {"events": n, "w_max": w_max, "ms": ms, "weighted_events_per_s": n / (ms * 1e-3),
+            "kept_per_call": stats.mean(kept), "unweighted_events_per_s": stats.mean(kept) / (ms * 1e-3),
+            "efficiency": stats.mean(kept) / n}
 
 
 def _launch_shape_leg(mf, torch, full=False, n=10 ** 6, reps=3):

@@ -50,6 +50,7 @@ typedef int mf_status;
 #define MF_ERR_TIMEOUT (-5)     /* reserved for a bounded device wait that gives up; no kernel of this
                                    library spins on a flag, so no entry point returns it */
 #define MF_WARN_NEWTON 1        /* some events missed the massive-rescaling Newton tolerance; their weight is 0 */
+#define MF_WARN_CAPACITY 2      /* more events were kept than the output buffers hold (mf_unweight) */
 
 /* processes (gluon count of the colour-ordered recursion in brackets) */
 #define MF_PROC_GG_TTX 1   /* g g -> t tbar        [2 gluons; 3 diagrams, 2 colour flows, 16 helicities]  */
@@ -282,6 +283,28 @@ mf_status mf_vegas_finish(mf_process* proc, mf_grid* grid, int64_t n_total, int 
  * word it reads, so nothing needs clearing between calls. */
 mf_status mf_vegas_accumulate_static(mf_process* proc, const double* edges, int nbins, uint64_t seed, int iter,
                                      int64_t first_event, int64_t n, double* totals, double* weights, void* stream);
+
+/* Unweighted events by hit-or-miss (the event-generation step that follows
+ * the weighted integration of arXiv:2211.14056 Sec. 1; the paper states no
+ * algorithm, this is the practice of MadEvent/MadFlow): the events
+ * first_event .. first_event + n - 1 of iteration `iter` are evaluated on the
+ * grid's current edges exactly as by mf_vegas_iterate (same weights w; the
+ * grid records nothing), and event e is kept if r_e w_max < w_e, with r_e the
+ * uniform of a second Philox stream (same key, counter (e_lo, e_hi, 0, 1),
+ * words (0, 1)).  A kept event carries weight max(1, w_e / w_max) (> 1 for an
+ * overweight event), so that w_max * (sum of kept weights) / n estimates the
+ * integral without bias.  Outputs (device, caller-owned, `capacity` entries
+ * each): momenta [n_ext][4][capacity] FP64 (the event's momenta in the layout
+ * of the conventions, from the kinematics the weight was computed with),
+ * weight [capacity] FP64, event [capacity] int64 (global event index).  The
+ * kept events are written in an unspecified order (their set is fixed).
+ * *n_kept, *n_over (host): events kept, of which overweight.  More kept
+ * events than `capacity`: only `capacity` are written and the call returns
+ * MF_WARN_CAPACITY.  MF_ERR_ARG: w_max not finite and > 0, bad sizes.
+ * Synchronises the stream. */
+mf_status mf_unweight(mf_process* proc, mf_grid* grid, uint64_t seed, int iter, int64_t first_event, int64_t n,
+                      double w_max, int64_t capacity, double* momenta, double* weight, int64_t* event,
+                      int64_t* n_kept, int64_t* n_over, void* stream);
 
 /* Derivatives of one iteration's estimate (arXiv:2211.14056 Sec. 2: the
  * device operator is differentiable in principle; the paper leaves its

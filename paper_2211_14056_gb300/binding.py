@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(HERE, "lib", "libmadflow_gb300.so")
 
 MF_OK, MF_ERR_ARG, MF_ERR_CUDA, MF_ERR_UNSUPPORTED, MF_ERR_COLOUR, MF_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
-MF_WARN_NEWTON = 1
+MF_WARN_NEWTON, MF_WARN_CAPACITY = 1, 2
 MF_PROC_GG_TTX, MF_PROC_GG_TTXG, MF_PROC_GG_TTXGG, MF_PROC_UUX_TTXGG, MF_PROC_EE_MUMU = 1, 2, 3, 4, 5
 MF_PROC_UXU_TTXGG, MF_PROC_UG_TTXGU, MF_PROC_GU_TTXGU, MF_PROC_UXG_TTXGUX, MF_PROC_GUX_TTXGUX = 6, 7, 8, 9, 10
 MF_FP64, MF_FP32, MF_FP32_TC = 0, 1, 2
@@ -81,6 +81,9 @@ EXPORTS = {
     "mf_grid_totals": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int)]),
     "mf_vegas_finish": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.POINTER(Result), C.c_void_p]),
     "mf_fma_throughput": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "mf_unweight": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_int64, C.c_int64, C.c_double,
+                              C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64),
+                              C.POINTER(C.c_int64), C.c_void_p]),
     "mf_grid_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "mf_grid_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "mf_vegas_accumulate_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_uint64, C.c_int, C.c_int64,
@@ -333,6 +336,21 @@ class Process:
             self._h, _ptr(edges, torch.float64, self.ndim * (nbins + 1), "edges"), nbins, seed, it, first_event, n,
             _ptr(totals, torch.float64, 2 + self.ndim * nbins + 2, "totals"),
             _ptr(weights, torch.float64, n, "weights"), _stream(stream)))
+
+    def unweight(self, grid, seed, it, first_event, n, w_max, capacity, momenta=None, weight=None, event=None,
+                 stream=None):
+        """Hit-or-miss unweighting (mf_unweight) of events first_event ..
+        first_event + n - 1 into caller-owned device buffers (momenta float64
+        [n_ext*4*capacity], weight float64 [capacity], event int64
+        [capacity]); returns (kept, overweight, status)."""
+        import torch
+        k, o = C.c_int64(), C.c_int64()
+        st = _check(load_library().mf_unweight(
+            self._h, grid._h, seed, it, first_event, n, w_max, capacity,
+            _ptr(momenta, torch.float64, self.n_ext * 4 * capacity, "momenta"),
+            _ptr(weight, torch.float64, capacity, "weight"), _ptr(event, torch.int64, capacity, "event"),
+            C.byref(k), C.byref(o), _stream(stream)))
+        return k.value, o.value, st
 
     def grad(self, grid, seed, it, n, dw_dtheta=None, dw_dy=None, stream=None, forward=False):
         """sigma and [dsigma/dg_s, dsigma/dm_t, dsigma/dGamma_t] of iteration `it`

@@ -144,10 +144,18 @@ mf_status record_iteration(mf_grid* g, const double* r, int64_t n_total, mf_resu
 mf_status grid_reserve(mf_grid* g, int64_t events) {
   if (events <= g->chunk) return MF_OK;
   void* buf = nullptr;
+  double* wbuf = nullptr;
   MF_CUDA(cudaMalloc(&buf, record_bytes(g->proc->precision == MF_FP64 ? 0 : 1, g->proc->sp.n_final, g->ndim, events)),
           "grid_reserve");
+  cudaError_t e = cudaMalloc(&wbuf, sizeof(double) * events);
+  if (e != cudaSuccess) {
+    cudaFree(buf);
+    return cuda_fail(e, "grid_reserve");
+  }
   cudaFree(g->d_records);
+  cudaFree(g->d_wchunk);
   g->d_records = buf;
+  g->d_wchunk = wbuf;
   g->chunk = events;
   return MF_OK;
 }
@@ -370,6 +378,8 @@ mf_status mf_grid_create(const mf_process* p, int nbins, mf_grid** out) {
   if (e == cudaSuccess)
     e = cudaMalloc(&g->d_records, record_bytes(p->precision == MF_FP64 ? 0 : 1, p->sp.n_final, g->ndim, g->chunk));
   if (e == cudaSuccess) e = cudaMalloc(&g->d_result, sizeof(double) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_wchunk, sizeof(double) * g->chunk);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_ucount, sizeof(unsigned long long) * 2);
   if (e == cudaSuccess) e = cudaMallocHost(&g->h_result, sizeof(double) * 8);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_edges, edges.data(), sizeof(double) * edges.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
@@ -389,6 +399,8 @@ mf_status mf_grid_destroy(mf_grid* g) {
   cudaFree(g->d_counters);
   cudaFree(g->d_totals);
   cudaFree(g->d_result);
+  cudaFree(g->d_wchunk);
+  cudaFree(g->d_ucount);
   cudaFreeHost(g->h_result);
   delete g;
   return MF_OK;
@@ -599,6 +611,49 @@ mf_status mf_vegas_iterate(mf_process* p, mf_grid* g, uint64_t seed, int iter, i
   mf_status st = mf_vegas_accumulate(p, g, seed, iter, 0, n, weights, stream);
   if (st < 0) return st;
   return mf_vegas_finish(p, g, n, refine, out, stream);
+}
+
+mf_status mf_unweight(mf_process* p, mf_grid* g, uint64_t seed, int iter, int64_t first_event, int64_t n,
+                      double w_max, int64_t capacity, double* momenta, double* weight, int64_t* event,
+                      int64_t* n_kept, int64_t* n_over, void* stream) {
+  if (p == nullptr || g == nullptr || n_kept == nullptr || n_over == nullptr)
+    return fail(MF_ERR_ARG, "mf_unweight: null argument");
+  if (g->proc != p) return fail(MF_ERR_ARG, "mf_unweight: grid belongs to another process");
+  if (n < 1 || first_event < 0 || capacity < 0) return fail(MF_ERR_ARG, "mf_unweight: need n >= 1, first_event >= 0, capacity >= 0");
+  if (!(w_max > 0) || !std::isfinite(w_max)) return fail(MF_ERR_ARG, "mf_unweight: w_max must be finite and > 0");
+  if (capacity > 0 && (momenta == nullptr || weight == nullptr || event == nullptr))
+    return fail(MF_ERR_ARG, "mf_unweight: null output buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  SampleParams sp = p->sp;
+  sp.nbins = g->nbins;
+  const int prec = p->precision == MF_FP64 ? 0 : 1;
+  const int64_t cap = int64_t(p->sms) * effective_ctas(p, g->acc_ctas);
+  MF_CUDA(cudaMemsetAsync(g->d_ucount, 0, 2 * sizeof(unsigned long long), s), "mf_unweight (counts)");
+  for (int64_t done = 0; done < n; done += g->chunk) {
+    const int64_t m = std::min(g->chunk, n - done);
+    const int64_t ctas_needed = ((m + 31) / 32 + kWarps - 1) / kWarps;
+    const int grid = int(std::min(std::min(cap, std::max<int64_t>(ctas_needed, 1)), int64_t(g->max_blocks)));
+    // the chunk's weights: the iteration's kernels (their Vegas sums are not recorded)
+    cudaError_t e;
+    switch (proc_key(p)) {
+      case kUuxKey: e = launch_chunk_uux(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s, nullptr); break;
+      case kEeKey: e = launch_chunk_ee(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s, nullptr); break;
+      case 2: e = launch_chunk<2>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s); break;
+      case 3: e = launch_chunk<3>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s); break;
+      default: e = launch_chunk<4>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s, nullptr, p->me_warps); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "mf_unweight (chunk kernels)");
+    MF_CUDA(launch_unweight(prec, g->d_records, sp.n_final, g->ndim, g->chunk, g->d_wchunk, m, seed, iter,
+                            first_event + done, w_max, capacity, momenta, weight, event, g->d_ucount, s),
+            "mf_unweight (hit or miss)");
+    g_launches.fetch_add(3);
+  }
+  unsigned long long h[2] = {0, 0};
+  MF_CUDA(cudaMemcpyAsync(h, g->d_ucount, sizeof(h), cudaMemcpyDeviceToHost, s), "mf_unweight (counts)");
+  MF_CUDA(cudaStreamSynchronize(s), "mf_unweight (sync)");
+  *n_kept = int64_t(h[0]);
+  *n_over = int64_t(h[1]);
+  return *n_kept > capacity ? MF_WARN_CAPACITY : MF_OK;
 }
 
 mf_status mf_fma_throughput(int precision, double* tflops) {

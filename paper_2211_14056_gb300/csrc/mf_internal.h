@@ -58,6 +58,8 @@ struct mf_grid {
   double* d_totals = nullptr;   // [2 + ndim*nbins + 2]: sums, histogram, passing events, Newton misses
   double* d_result = nullptr;
   double* h_result = nullptr;
+  double* d_wchunk = nullptr;               // [chunk] weights of one record chunk (unweighting)
+  unsigned long long* d_ucount = nullptr;   // [2] kept and overweight events (unweighting)
   std::vector<double> Ik, vark;
 };
 

@@ -1007,6 +1007,11 @@ cudaError_t launch_sample(const SampleParams& sp, const double* edges, int64_t n
                           double* mom, double* wps, uint8_t* bins, cudaStream_t s);
 cudaError_t launch_uniforms(uint64_t seed, int iter, int64_t first_event, int64_t n, int ndim, double* y,
                             cudaStream_t s);
+// hit-or-miss unweighting of one chunk of evaluated records (weights w[n])
+cudaError_t launch_unweight(int precision, void* rec_base, int n_final, int ndim, int64_t C, const double* w,
+                            int64_t n, uint64_t seed, int iter, int64_t first_event, double w_max, int64_t cap,
+                            double* mom_out, double* weight_out, int64_t* event_out, unsigned long long* counts,
+                            cudaStream_t s);
 // totals: [0] sum w, [1] sum w^2, [2 + j*nbins + b] histogram, [nacc] passing events, [nacc+1] Newton misses
 cudaError_t launch_reduce(const double* partials, const unsigned long long* counters, int nblocks, int ndim, int nbins,
                           double* totals, cudaStream_t s);

@@ -55,6 +55,81 @@ cudaError_t launch_uniforms(uint64_t seed, int iter, int64_t first_event, int64_
   return cudaGetLastError();
 }
 
+// Hit-or-miss unweighting of one chunk of evaluated events: event e (global
+// index first_event + e) with weight w[e] > 0 is kept if r w_max < w[e], r from
+// the unweighting stream; a kept event is written at the next free slot (warp-
+// aggregated atomics, so the order of the kept events is not fixed, their set
+// is): its global index, its weight max(1, w / w_max) and its momenta (beams
+// from sqrt(s_hat), final particles from the record), FP64 SoA [n_final + 2][4][cap].
+// counts[0] = events kept (may exceed cap: only the first cap are written),
+// counts[1] = overweight events kept.
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_unweight(RecordView<K> rec, const double* __restrict__ w, int64_t n,
+                                                       int n_final, uint64_t seed, int iter, int64_t first_event,
+                                                       double w_max, int64_t cap, double* __restrict__ mom_out,
+                                                       double* __restrict__ weight_out,
+                                                       int64_t* __restrict__ event_out,
+                                                       unsigned long long* __restrict__ counts) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < n; base += stride) {
+    const int64_t e = base + threadIdx.x;
+    double we = 0.0;
+    bool keep = false;
+    if (e < n) {
+      we = w[e];
+      if (we > 0.0) keep = __dmul_rn(unweight_uniform(seed, iter, uint64_t(first_event + e)), w_max) < we;
+    }
+    const unsigned bal = __ballot_sync(full, keep);
+    const unsigned over = __ballot_sync(full, keep && we > w_max);
+    unsigned long long slot0 = 0;
+    if (lane == 0 && bal) {
+      slot0 = atomicAdd(&counts[0], (unsigned long long)__popc(bal));
+      if (over) atomicAdd(&counts[1], (unsigned long long)__popc(over));
+    }
+    slot0 = __shfl_sync(full, slot0, 0);
+    const int64_t slot = int64_t(slot0) + __popc(bal & ((1u << lane) - 1u));
+    if (keep && slot < cap) {
+      event_out[slot] = first_event + e;
+      weight_out[slot] = we > w_max ? we / w_max : 1.0;
+      const double h = 0.5 * double(rec.rs[e]);
+      const double beams[2][4] = {{h, 0.0, 0.0, h}, {h, 0.0, 0.0, -h}};
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) mom_out[int64_t(i * 4 + c) * cap + slot] = beams[i][c];
+#pragma unroll
+      for (int i = 0; i < kMaxExt - 2; ++i)
+        if (i < n_final)
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            mom_out[int64_t((2 + i) * 4 + c) * cap + slot] = double(rec.mom[int64_t(i * 4 + c) * rec.C + e]);
+    }
+  }
+}
+
+cudaError_t launch_unweight(int precision, void* rec_base, int n_final, int ndim, int64_t C, const double* w,
+                            int64_t n, uint64_t seed, int iter, int64_t first_event, double w_max, int64_t cap,
+                            double* mom_out, double* weight_out, int64_t* event_out, unsigned long long* counts,
+                            cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t need = (n + kThreads - 1) / kThreads;
+  const int grid = int(need < int64_t(sms) * 16 ? need : int64_t(sms) * 16);
+  if (precision == 0)
+    k_unweight<double><<<grid, kThreads, 0, s>>>(RecordView<double>::carve(rec_base, n_final, ndim, C), w, n, n_final,
+                                                 seed, iter, first_event, w_max, cap, mom_out, weight_out, event_out,
+                                                 counts);
+  else
+    k_unweight<float><<<grid, kThreads, 0, s>>>(RecordView<float>::carve(rec_base, n_final, ndim, C), w, n, n_final,
+                                                seed, iter, first_event, w_max, cap, mom_out, weight_out, event_out,
+                                                counts);
+  return cudaGetLastError();
+}
+
 size_t record_bytes(int precision, int n_final, int ndim, int64_t C) {
   return precision == 0 ? RecordView<double>::bytes(n_final, ndim, C) : RecordView<float>::bytes(n_final, ndim, C);
 }

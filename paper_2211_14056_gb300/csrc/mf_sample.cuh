@@ -90,6 +90,15 @@ __device__ __forceinline__ void draw_uniforms(uint64_t seed, int iter, uint64_t 
   }
 }
 
+// The uniform of the stream for decisions taken after the weight (the
+// hit-or-miss unweighting): same key, counter (event_lo, event_hi, 0, 1),
+// words (0, 1); independent of the Vegas uniforms (counters ending in 0).
+__device__ __forceinline__ double unweight_uniform(uint64_t seed, int iter, uint64_t ev) {
+  const uint2 key = make_uint2(uint32_t(seed), uint32_t(seed >> 32) ^ uint32_t(iter));
+  const uint4 w = philox4x32_10(make_uint4(uint32_t(ev), uint32_t(ev >> 32), 0u, 1u), key);
+  return unit53(w.x, w.y);
+}
+
 // boost p given in the rest frame of Q (mass M) into the frame of Q
 template <typename K>
 __device__ __forceinline__ void boost_from_rest(const K* Q, K M, const K* p, K* out) {
