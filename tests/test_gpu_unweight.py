@@ -95,7 +95,7 @@ def test_capacity_and_fp32(mf):
     wt = torch.empty(n, dtype=torch.float64, device="cuda")
     r64 = p64.vegas_iterate(g64, seed, it, n, refine=False, weights=wt)
     w64 = wt.cpu().numpy()
-    w_max = 0.2 * w64.max()
+    w_max = 5.0 * w64[w64 > 0].mean()          # ~10% of the events kept, some overweight
     g64.reset()
     k64, o64, st, ev64, wt64, _ = _run(p64, g64, seed, it, 0, n, w_max, n)
     assert st == mf.MF_OK and k64 > 100
