@@ -38,11 +38,16 @@ __global__ void __launch_bounds__(256) k_pdf_eval(PdfView pv, int flavour, int64
     fl = reinterpret_cast<const K*>(smem_raw);
   }
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
-    // the logarithms in the arithmetic's own precision (an FP64 log would
-    // bound the FP32 kernel by GB300's FP64 rate)
-    const K lx = log(K(x[e])), lq = log(K(q2[e]));
-    const PdfCell<K> c = pdf_cell(pv, lx, lq);
-    out[e] = double(pdf_xfx_slice(pv, fl, c));
+    if constexpr (sizeof(K) == sizeof(float)) {
+      // FP32: the logarithms, the cell and the interpolation in FP32, and no
+      // FP64 instruction at all (conversions between FP64 and FP32 issue on
+      // the narrow FP64 pipe and would bound the kernel)
+      const PdfCell<float> c = pdf_cell(pv, log_f64_in_f32(x[e]), log_f64_in_f32(q2[e]));
+      out[e] = widen_f32(pdf_xfx_slice(pv, fl, c));
+    } else {
+      const PdfCell<double> c = pdf_cell(pv, log(x[e]), log(q2[e]));
+      out[e] = pdf_xfx_slice(pv, fl, c);
+    }
   }
 }
 
@@ -97,6 +102,11 @@ mf_status mf_pdf_create(int nflav, int nq, int nx, double x_min, double x_max, d
   v.hs = (std::log(q2_max) - v.s0) / (nq - 1);
   v.iht = 1.0 / v.ht;
   v.ihs = 1.0 / v.hs;
+  v.t0f = float(v.t0);
+  v.htf = float(v.ht);
+  v.s0f = float(v.s0);
+  v.ihtf = float(v.iht);
+  v.ihsf = float(v.ihs);
   // a flavour's slice of (value, slope) pairs, padded to 64 bytes in FP64 and FP32
   v.slice = (int64_t(nq) * nx * 2 + 7) / 8 * 8;
   std::vector<double> t64(size_t(nflav) * v.slice, 0.0);
