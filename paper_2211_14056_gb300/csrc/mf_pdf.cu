@@ -37,16 +37,34 @@ __global__ void __launch_bounds__(256) k_pdf_eval(PdfView pv, int flavour, int64
     __syncthreads();
     fl = reinterpret_cast<const K*>(smem_raw);
   }
-  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
-    if constexpr (sizeof(K) == sizeof(float)) {
-      // FP32: the logarithms, the cell and the interpolation in FP32, and no
-      // FP64 instruction at all (conversions between FP64 and FP32 issue on
-      // the narrow FP64 pipe and would bound the kernel)
-      const PdfCell<float> c = pdf_cell(pv, log_f64_in_f32(x[e]), log_f64_in_f32(q2[e]));
-      out[e] = widen_f32(pdf_xfx_slice(pv, fl, c));
-    } else {
-      const PdfCell<double> c = pdf_cell(pv, log(x[e]), log(q2[e]));
-      out[e] = pdf_xfx_slice(pv, fl, c);
+  // kPts points per thread per pass, their loads issued together (the
+  // points are read once: streaming loads and stores), so that each thread
+  // has several HBM requests in flight
+  constexpr int kPts = 4;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t e0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e0 < n; e0 += kPts * stride) {
+    double xv[kPts], qv[kPts];
+#pragma unroll
+    for (int u = 0; u < kPts; ++u) {
+      const int64_t e = e0 + u * stride;
+      xv[u] = e < n ? __ldcs(x + e) : 1.0;
+      qv[u] = e < n ? __ldcs(q2 + e) : 1.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kPts; ++u) {
+      const int64_t e = e0 + u * stride;
+      double r;
+      if constexpr (sizeof(K) == sizeof(float)) {
+        // FP32: the logarithms, the cell and the interpolation in FP32, and
+        // no FP64 instruction at all (conversions between FP64 and FP32 issue
+        // on the narrow FP64 pipe)
+        const PdfCell<float> c = pdf_cell(pv, log_f64_in_f32(xv[u]), log_f64_in_f32(qv[u]));
+        r = widen_f32(pdf_xfx_slice(pv, fl, c));
+      } else {
+        const PdfCell<double> c = pdf_cell(pv, log(xv[u]), log(qv[u]));
+        r = pdf_xfx_slice(pv, fl, c);
+      }
+      if (e < n) __stcs(out + e, r);
     }
   }
 }
@@ -71,7 +89,7 @@ cudaError_t pdf_launch(const mf_pdf* p, int flavour, int64_t n, const double* x,
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pdf_eval<K, SMEM>, 256, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
-  const int64_t need = (n + 255) / 256;
+  const int64_t need = (n + 4 * 256 - 1) / (4 * 256);   // four points per thread per pass
   const int64_t cap = int64_t(p->sms) * occ;
   k_pdf_eval<K, SMEM><<<int(need < cap ? need : cap), 256, smem, s>>>(p->view, flavour, n, x, q2, out);
   return cudaGetLastError();
