@@ -21,9 +21,9 @@ namespace mf {
 
 // Interpolation of one flavour at n points: x and Q^2 in, x f out (FP64 arrays,
 // arithmetic in K).  With SMEM the CTA first copies the flavour's node table
-// (a few tens of KB) into shared memory with 16-byte loads, so that the
-// sixteen node reads of a point hit shared memory; the points themselves are
-// read and written once, coalesced (24 bytes per point of HBM traffic).
+// (64 KB in FP32) into shared memory with 16-byte loads, so that the four
+// node reads of a point hit shared memory; the points themselves are read and
+// written once, coalesced (24 bytes per point of HBM traffic).
 template <typename K, bool SMEM>
 __global__ void __launch_bounds__(256) k_pdf_eval(PdfView pv, int flavour, int64_t n, const double* __restrict__ x,
                                                   const double* __restrict__ q2, double* __restrict__ out) {
@@ -77,7 +77,7 @@ int pdf_device(const mf_pdf* p) { return p->device; }
 }  // namespace mf
 
 namespace {
-constexpr size_t kPdfSmemMax = 100 * 1024;
+constexpr size_t kPdfSmemMax = 200 * 1024;
 
 template <typename K, bool SMEM>
 cudaError_t pdf_launch(const mf_pdf* p, int flavour, int64_t n, const double* x, const double* q2, double* out,
@@ -125,27 +125,33 @@ mf_status mf_pdf_create(int nflav, int nq, int nx, double x_min, double x_max, d
   v.s0f = float(v.s0);
   v.ihtf = float(v.iht);
   v.ihsf = float(v.ihs);
-  // a flavour's slice of (value, slope) pairs, padded to 64 bytes in FP64 and FP32
-  v.slice = (int64_t(nq) * nx * 2 + 7) / 8 * 8;
+  // a flavour's slice of (f, df, dq, dfq) 4-tuples per node, padded to 64
+  // bytes in FP64 and FP32; every slope is the finite difference per unit of
+  // the local coordinate: half the difference of the two neighbours inside,
+  // the one-sided difference at the first and last node
+  v.slice = (int64_t(nq) * nx * 4 + 7) / 8 * 8;
   std::vector<double> t64(size_t(nflav) * v.slice, 0.0);
   std::vector<float> t32(t64.size(), 0.0f);
-  for (int f = 0; f < nflav; ++f)
-    for (int l = 0; l < nq; ++l) {
-      const double* row = xf + (size_t(f) * nq + l) * nx;
+  auto fd = [](const double* g, int k, int n, int64_t stride) {
+    if (k == 0) return g[stride] - g[0];
+    if (k == n - 1) return g[(n - 1) * stride] - g[(n - 2) * stride];
+    return 0.5 * (g[(k + 1) * stride] - g[(k - 1) * stride]);
+  };
+  std::vector<double> dq(size_t(nq) * nx);
+  for (int f = 0; f < nflav; ++f) {
+    const double* tab = xf + size_t(f) * nq * nx;
+    for (int l = 0; l < nq; ++l)
+      for (int k = 0; k < nx; ++k) dq[size_t(l) * nx + k] = fd(tab + k, l, nq, nx);
+    for (int l = 0; l < nq; ++l)
       for (int k = 0; k < nx; ++k) {
-        // d(x f)/d ln x at the node: one-sided at the ends, else the mean of
-        // the two neighbouring difference quotients
-        double m;
-        if (k == 0) m = (row[1] - row[0]) / v.ht;
-        else if (k == nx - 1) m = (row[nx - 1] - row[nx - 2]) / v.ht;
-        else m = 0.5 * ((row[k + 1] - row[k]) / v.ht + (row[k] - row[k - 1]) / v.ht);
-        const size_t o = size_t(f) * v.slice + (size_t(l) * nx + k) * 2;
-        t64[o] = row[k];
-        t64[o + 1] = m;
-        t32[o] = float(row[k]);
-        t32[o + 1] = float(m);
+        const size_t o = size_t(f) * v.slice + (size_t(l) * nx + k) * 4;
+        t64[o] = tab[size_t(l) * nx + k];
+        t64[o + 1] = fd(tab + size_t(l) * nx, k, nx, 1);
+        t64[o + 2] = dq[size_t(l) * nx + k];
+        t64[o + 3] = fd(dq.data() + size_t(l) * nx, k, nx, 1);
+        for (int q = 0; q < 4; ++q) t32[o + q] = float(t64[o + q]);
       }
-    }
+  }
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
   if (e == cudaSuccess) e = cudaMalloc(&p->d64, sizeof(double) * t64.size());

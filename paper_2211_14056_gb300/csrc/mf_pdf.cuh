@@ -2,15 +2,21 @@
 // x f(x, Q^2) (arXiv:2211.14056 Sec. 1: the integrand's densities come from
 // PDFFlow, the GPU interpolation of tabulated LHAPDF sets).
 //
-// A set is stored per flavour as nq rows (ln Q^2 nodes) of nx nodes (ln x),
-// uniform in both logarithms; every node holds the pair (x f, d(x f)/d ln x),
-// the slope taken once when the table is loaded from the finite differences of
-// the node values (mean of the two neighbouring quotients, one-sided at the
-// first and last node).  A query (x, Q^2) is clamped to the table's range and
-// located in cell (i, j); each of the rows j-1 .. j+2 that exists is a cubic
-// Hermite polynomial in ln x on [t_i, t_i+1]; their values then give the ln Q^2
-// slopes at s_j and s_j+1 by the same finite differences, and a cubic Hermite
-// step in ln Q^2 finishes.
+// The scheme: on nodes uniform in ln x (step h_x) and ln Q^2 (step h_q), the
+// ln x slope of a row's node is the finite difference of the row's values
+// (mean of the two neighbouring quotients, one-sided at the first and last
+// node); a query (x, Q^2), clamped to the table's range and located in cell
+// (i, j) with local coordinates (u, v), is interpolated in ln x by a cubic
+// Hermite polynomial on each row around it, and in ln Q^2 by a cubic Hermite
+// step whose slopes at s_j and s_j+1 are the same finite differences of those
+// row values.
+//
+// Stored form: per flavour and node (l, k) four numbers, every slope per unit
+// of the local coordinate: f, df = FD_x(f), dq = FD_q(f) and dfq = FD_x(dq).
+// Because the x-interpolation and the finite differences are linear, the ln Q^2
+// slope at row l of the interpolated rows, FD_q(g)_l, equals the
+// x-interpolation of (dq, dfq) on row l: a query reads two rows of two nodes
+// (four 4-tuples), five Hermite steps, no branch at the table's edges.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -20,12 +26,13 @@ namespace mf {
 constexpr int kMaxPdfPairs = 8;
 
 // Device view of a loaded set: node tables in FP64 and FP32, flavour-major,
-// each flavour's slice padded to `slice` elements (pairs counted as two).
+// node (l, k) of a flavour at 4 (l nx + k) (f, df, dq, dfq), each flavour's
+// slice padded to `slice` elements.
 struct PdfView {
   const double* tab64;
   const float* tab32;
   int nflav, nq, nx;
-  int64_t slice;            // elements per flavour (>= nq * nx * 2)
+  int64_t slice;            // elements per flavour (>= nq * nx * 4)
   double t0, ht, s0, hs;    // ln x_min and the ln x step; ln Q2_min and the ln Q^2 step
   double iht, ihs;          // 1 / ht, 1 / hs
   float t0f, htf, s0f, ihtf, ihsf;   // the same in FP32 (no FP64 conversion per point in FP32)
@@ -51,10 +58,6 @@ __device__ __forceinline__ void pdf_locate(K z, K c0, K ih, int n, int& cell, K&
   loc = r - K(k);
 }
 
-template <typename K> __device__ __forceinline__ K pdf_ht(const PdfView& pv);
-template <> __device__ __forceinline__ double pdf_ht<double>(const PdfView& pv) { return pv.ht; }
-template <> __device__ __forceinline__ float pdf_ht<float>(const PdfView& pv) { return pv.htf; }
-
 __device__ __forceinline__ PdfCell<double> pdf_cell(const PdfView& pv, double lnx, double lnq2) {
   PdfCell<double> c;
   pdf_locate(lnx, pv.t0, pv.iht, pv.nx, c.i, c.u);
@@ -71,14 +74,14 @@ __device__ __forceinline__ PdfCell<float> pdf_cell(const PdfView& pv, float lnx,
 // ln x of an FP64 input in FP32 arithmetic without an FP64 instruction (an
 // FP64 -> FP32 conversion issues on GB300's narrow FP64 pipe): x = 2^e m,
 // m in [1, 2) rebuilt as an FP32 from the top 23 mantissa bits (relative
-// error below 2^-23), ln x = e ln 2 + ln m with ln 2 in two parts.  x <= 0
-// or subnormal gives a large negative value (the callers clamp to the table).
+// error below 2^-23), ln x = (e + log2 m) ln 2.  x <= 0 or subnormal gives a
+// large negative value (the callers clamp to the table).
 __device__ __forceinline__ float log_f64_in_f32(double x) {
   const long long b = __double_as_longlong(x);
   const int e = int((b >> 52) & 0x7ff) - 1023;
   const float m = __int_as_float(0x3f800000 | int((b >> 29) & 0x7fffff));
-  const float fe = float(e);
-  return fmaf(fe, 1.428606765330187e-06f, fmaf(fe, 0.693145751953125f, logf(m)));
+  // log2 m by the special-function unit (absolute error ~2^-22 on [1, 2))
+  return (float(e) + __log2f(m)) * 0.69314718055994531f;
 }
 
 // an FP32 value widened to FP64 with integer operations (zero for FP32
@@ -102,25 +105,32 @@ template <typename K> __device__ __forceinline__ K hermite01(K w, K f0, K f1, K 
   return fma(w, fma(w, fma(w, c3, c2), d0), f0);
 }
 
-// one row (ln Q^2 node l) of flavour slice `fl` at the cell's x
-template <typename K>
-__device__ __forceinline__ K pdf_row(const K* fl, int nx, int l, int i, K u, K ht) {
-  const K* r = fl + (int64_t(l) * nx + i) * 2;
-  return hermite01(u, r[0], r[2], ht * r[1], ht * r[3]);
-}
-
 // x f(x, Q^2) of the flavour whose slice starts at `fl`
 template <typename K>
 __device__ __forceinline__ K pdf_xfx_slice(const PdfView& pv, const K* fl, const PdfCell<K>& c) {
-  const int nq = pv.nq, j = c.j;
-  const K ht = pdf_ht<K>(pv);
-  const K g0 = pdf_row(fl, pv.nx, j, c.i, c.u, ht);
-  const K g1 = pdf_row(fl, pv.nx, j + 1, c.i, c.u, ht);
-  // slopes per ln Q^2 step at s_j and s_j+1 (times the step: per unit of v)
-  K d0 = g1 - g0, d1 = g1 - g0;
-  if (j > 0) d0 = K(0.5) * (g1 - pdf_row(fl, pv.nx, j - 1, c.i, c.u, ht));
-  if (j + 2 <= nq - 1) d1 = K(0.5) * (pdf_row(fl, pv.nx, j + 2, c.i, c.u, ht) - g0);
-  return hermite01(c.v, g0, g1, d0, d1);
+  const K* a = fl + (int64_t(c.j) * pv.nx + c.i) * 4;   // row j: nodes i, i + 1
+  const K* b = a + int64_t(pv.nx) * 4;                   // row j + 1
+  K na[8], nb[8];
+  if constexpr (sizeof(K) == sizeof(float)) {
+    const float4 a0 = *reinterpret_cast<const float4*>(a), a1 = *reinterpret_cast<const float4*>(a + 4);
+    const float4 b0 = *reinterpret_cast<const float4*>(b), b1 = *reinterpret_cast<const float4*>(b + 4);
+    na[0] = a0.x; na[1] = a0.y; na[2] = a0.z; na[3] = a0.w; na[4] = a1.x; na[5] = a1.y; na[6] = a1.z; na[7] = a1.w;
+    nb[0] = b0.x; nb[1] = b0.y; nb[2] = b0.z; nb[3] = b0.w; nb[4] = b1.x; nb[5] = b1.y; nb[6] = b1.z; nb[7] = b1.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double2 av = *reinterpret_cast<const double2*>(a + 2 * q);
+      const double2 bv = *reinterpret_cast<const double2*>(b + 2 * q);
+      na[2 * q] = av.x; na[2 * q + 1] = av.y;
+      nb[2 * q] = bv.x; nb[2 * q + 1] = bv.y;
+    }
+  }
+  // rows j and j + 1 at x: the values and their ln Q^2 slopes (per unit of v)
+  const K g0 = hermite01(c.u, na[0], na[4], na[1], na[5]);
+  const K q0 = hermite01(c.u, na[2], na[6], na[3], na[7]);
+  const K g1 = hermite01(c.u, nb[0], nb[4], nb[1], nb[5]);
+  const K q1 = hermite01(c.u, nb[2], nb[6], nb[3], nb[7]);
+  return hermite01(c.v, g0, g1, q0, q1);
 }
 
 template <typename K>
