@@ -25,6 +25,7 @@ processes       Process definitions (externals, masses, couplings, averages).
 pdf             Log-bicubic (Hermite) interpolation of tabulated parton densities.
 integrate       Event weights and Vegas iterations built from the above.
 unweight        Hit-or-miss unweighting of weighted events.
+helicity        |M|^2 of one helicity configuration; the helicity-sampled estimator.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test except the
 absolute cross sections of the 2->3 and 2->4 processes, which the paper never

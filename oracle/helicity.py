@@ -1,0 +1,102 @@
+"""Helicity sampling: the |M|^2 of one helicity configuration and the
+sampled estimator of the helicity sum.
+
+Test infrastructure (see ``oracle/__init__``).
+
+|M|^2 = (1/A) sum_h |M_h|^2 (``processes``).  Drawing one configuration of
+the gluons and the antitop uniformly from the 2^(n_g + 1), summing the top's
+two helicities, and weighting by 2^(n_g + 1) estimates that sum without bias
+(the practice of MadEvent and MadFlow of sampling helicities instead of
+summing them; arXiv:2211.14056 sums them, so the uniform draw is a reading).
+The draw comes from the third Philox stream (``philox.helicity_draws``).
+
+Helicity index h: bit g (g = 0 .. n_g - 1, the process's gluons in their
+order: the two incoming, then the final ones) set means helicity +1 of that
+gluon; bit n_g set means antitop helicity +1.  Processes: a top pair plus
+gluons only.
+"""
+import numpy as np
+
+from . import philox
+
+
+def _legs(proc):
+    parts = list(proc.particles)
+    gluons = [i for i, x in enumerate(parts) if x == "g"]
+    if len(gluons) + 2 != len(parts) or "t" not in parts or "t~" not in parts:
+        raise ValueError("helicity sampling covers a top pair plus gluons")
+    return gluons, parts.index("t"), parts.index("t~")
+
+
+def per_helicity(proc, p, algorithm="feynman", batch=256):
+    """Colour-summed |M_h|^2 of every helicity configuration, shape
+    (2,) * n_ext + (N,) (axis i: particle i's helicity, index 0 = -1, 1 = +1),
+    not averaged.  algorithm: "feynman" (every diagram with explicit colour)
+    or "bg" (colour-ordered recursion with the trace-basis colour matrix)."""
+    p = np.asarray(p, dtype=np.float64)
+    n, N = len(proc.particles), p.shape[0]
+    out = np.empty((2,) * n + (N,))
+    if algorithm == "bg":
+        from .berends_giele import QQbarGluons
+        bg = QQbarGluons(proc)
+    for s in range(0, N, batch):
+        q = p[s:s + batch]
+        if algorithm == "bg":
+            J = bg.partial_amplitudes(q)                 # [sigma, (2,)*n, N]
+            v = np.real(np.einsum("s...,st,t...->...", np.conj(J), bg.C, J))
+        else:
+            ext, k = proc.external(q)
+            K = proc.amp.amplitude_terms(ext, k)         # [term, (2,)*n, N]
+            Kf = K.reshape(K.shape[0], -1, K.shape[-1])
+            Y = np.einsum("st,thn->shn", proc.amp.colour_matrix(), Kf)
+            v = np.real(np.einsum("shn,shn->hn", np.conj(Kf), Y)).reshape((2,) * n + (q.shape[0],))
+        out[..., s:s + batch] = v
+    return out
+
+
+def config_index(proc, hel, top):
+    """Flat index (particle 0 most significant) into the (2,)*n_ext axes of
+    the configuration h (gluons and antitop) with top helicity index `top`."""
+    gluons, t, tb = _legs(proc)
+    hel = np.asarray(hel, dtype=np.int64)
+    n, ng = len(proc.particles), len(gluons)
+    idx = np.zeros_like(hel)
+    for g, leg in enumerate(gluons):
+        idx += ((hel >> g) & 1) << (n - 1 - leg)
+    idx += ((hel >> ng) & 1) << (n - 1 - tb)
+    return idx + (int(top) << (n - 1 - t))
+
+
+def me2_helicity(proc, p, hel, algorithm="feynman"):
+    """Per event e: (1/A) (|M_{h_e, t-}|^2 + |M_{h_e, t+}|^2), the configuration
+    h_e of the gluons and the antitop, the top's two helicities summed."""
+    per = per_helicity(proc, p, algorithm)
+    flat = per.reshape(-1, per.shape[-1])
+    e = np.arange(flat.shape[1])
+    s = flat[config_index(proc, hel, 0), e] + flat[config_index(proc, hel, 1), e]
+    return s / proc.average
+
+
+def n_configs(proc):
+    """2^(n_g + 1): the configurations the draw chooses from."""
+    return 2 ** (len(_legs(proc)[0]) + 1)
+
+
+def sampled_me2(proc, p, hel, algorithm="feynman"):
+    """The estimator 2^(n_g + 1) me2_helicity of each event."""
+    return n_configs(proc) * me2_helicity(proc, p, hel, algorithm)
+
+
+def sampled_weights(setup, y, edges, seed, iteration, events):
+    """Event weights of a Vegas iteration with sampled helicities: the steps of
+    ``integrate.Setup.weights`` with |M|^2 replaced by the estimator at the
+    configuration drawn for each event (drawn for every event, used where the
+    cuts pass).  Returns (w, bins, hel)."""
+    p, wk, bins, cut = setup.kinematics(y, edges)
+    bits = len(_legs(setup.proc)[0]) + 1
+    hel = philox.helicity_draws(seed, iteration, events, bits)
+    algorithm = "bg" if setup.bg is not None else "feynman"
+    w = np.zeros(y.shape[1])
+    if np.any(cut):
+        w[cut] = sampled_me2(setup.proc, p[cut], hel[cut], algorithm) * wk[cut]
+    return w, bins, hel

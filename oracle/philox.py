@@ -19,7 +19,9 @@ Stream layout (both sides implement this independently):
 A second stream, for decisions taken after the weight (the hit-or-miss
 unweighting), uses the same key and counter (event & 0xffffffff, event >> 32,
 0, 1): its words (w0, w1) give one uniform per event, independent of the
-Vegas uniforms (whose counters end in 0).
+Vegas uniforms (whose counters end in 0).  A third, for the helicity drawn
+per event when helicities are sampled, uses counter (event & 0xffffffff,
+event >> 32, 1, 1): the top `bits` bits of its word w0 are the helicity index.
 """
 import numpy as np
 
@@ -95,3 +97,15 @@ def unweight_uniforms(seed, iteration, events):
     w0, w1, _, _ = philox4x32_10(ev & np.uint64(MASK32), ev >> np.uint64(32), np.zeros_like(ev),
                                  np.ones_like(ev), k0, k1)
     return words_to_unit(w0, w1)
+
+
+def helicity_draws(seed, iteration, events, bits):
+    """h[len(events)]: the helicity index (the top `bits` bits of word w0 of
+    counter (event_lo, event_hi, 1, 1)) drawn for each listed event."""
+    ev = np.asarray(events, dtype=np.uint64)
+    seed = int(seed)
+    k0 = seed & MASK32
+    k1 = ((seed >> 32) ^ int(iteration)) & MASK32
+    w0, _, _, _ = philox4x32_10(ev & np.uint64(MASK32), ev >> np.uint64(32), np.ones_like(ev),
+                                np.ones_like(ev), k0, k1)
+    return (w0 >> np.uint64(32 - bits)).astype(np.int64)
