@@ -385,7 +385,7 @@ def main():
     peak_derived = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
 
     # 7. the derivative and mixed-launch workloads (N = 1 only)
-    grad = mixed = shapes = pp = pdfk = unw = None
+    grad = mixed = shapes = pp = pdfk = unw = hel = None
     if world == 1 and not args.no_extras:
         grad = _grad_leg(p32, p64, g32, g64, w, torch)
         mixed = _mixed_leg(mf, torch)
@@ -393,6 +393,7 @@ def main():
         pp = _pp_leg(mf, torch)
         pdfk = _pdf_leg(mf, torch)
         unw = _unweight_leg(p32, g32, w, torch, n, w_max_fp32)
+        hel = _helicity_leg(mf, torch, w, frozen, n)
 
     # 8. CPU baseline: the oracle on the host cores (rank 0 only, N = 1 only)
     cpu = None
@@ -454,6 +455,8 @@ def main():
             line["pdf_interpolation"] = pdfk
         if unw is not None:
             line["unweighting"] = unw
+        if hel is not None:
+            line["helicity_sampling"] = hel
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -643,6 +646,55 @@ def _unweight_leg(p, g, w, torch, n, w_max, reps=3):
     return {"events": n, "w_max": w_max, "ms": ms, "weighted_events_per_s": n / (ms * 1e-3),
             "kept_per_call": stats.mean(kept), "unweighted_events_per_s": stats.mean(kept) / (ms * 1e-3),
             "efficiency": stats.mean(kept) / n}
+
+
+def _helicity_leg(mf, torch, w, edges, n, reps=4):
+    """Helicity sampling against the helicity sum: FP32 g g -> t tbar g g on
+    the frozen grid `edges`, `reps` iterations of n events each way (distinct
+    iteration numbers, no refinement).  Per way: CUDA-event time per
+    iteration, its |M|^2 kernel's share, the variance per event n sigma_k^2
+    (mean over the iterations) and the estimate; the efficiency gain is
+    (time x variance) summed over (time x variance) sampled: how much less
+    device time the sampled form needs for the same statistical error."""
+    import statistics as stats
+    from paper_2211_14056_gb300 import flops as mflops
+    from paper_2211_14056_gb300.workloads import PROCESS_IDS, process_kwargs
+    out = {}
+    for label, on in (("summed", False), ("sampled", True)):
+        p = mf.Process(PROCESS_IDS[w["process"]], **process_kwargs(w, mf.MF_FP32))
+        p.set_helicity_sampling(on)
+        g = p.grid()
+        g.set(edges)
+        p.vegas_iterate(g, w["seed"], 7000, n, refine=False)
+        g.profile(True)
+        ts, me, var, Is, npass = [], [], [], [], []
+        for r in range(reps):
+            g.set(edges)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            res = p.vegas_iterate(g, w["seed"], 7001 + r, n, refine=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            me.append(g.profile_read()[1])
+            var.append(res["sigma_k"] ** 2 * n)
+            Is.append(res["I_k"])
+            npass.append(res["n_pass"])
+        g.profile(False)
+        fpe = mflops.me2_flops_per_event_hel(4) if on else mflops.me2_flops_per_event(4)
+        me_ms = stats.mean(me)
+        out[label] = {"ms_per_iteration": stats.mean(ts), "me_ms": me_ms, "events_per_s": n / (stats.mean(ts) * 1e-3),
+                      "var_per_event": stats.mean(var), "I_k": Is, "flops_per_event": fpe,
+                      "me_tflops": fpe * stats.mean(npass) / (me_ms * 1e-3) / 1e12}
+    s, u = out["sampled"], out["summed"]
+    out["kernel"] = "k_me_acc_hel<4,float> (sampled) vs k_me_acc<4,float> (summed)"
+    out["events"] = n
+    out["draw"] = "uniform over the 32 configurations of the gluons and the antitop, top summed"
+    out["variance_ratio"] = s["var_per_event"] / u["var_per_event"]
+    out["time_ratio"] = u["ms_per_iteration"] / s["ms_per_iteration"]
+    out["efficiency_gain"] = (u["ms_per_iteration"] * u["var_per_event"]) / (s["ms_per_iteration"] * s["var_per_event"])
+    return out
 
 
 def _launch_shape_leg(mf, torch, full=False, n=10 ** 6, reps=3):

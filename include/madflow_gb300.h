@@ -232,6 +232,34 @@ mf_status mf_sample(mf_process* proc, const mf_grid* grid, uint64_t seed, int it
  *   momenta [n_ext][4][n] FP64 device, me2 [n] FP64 device. */
 mf_status mf_matrix_element(mf_process* proc, int64_t n, const double* momenta, double* me2, void* stream);
 
+/* Helicity sampling (the paper sums the helicities inside its operator,
+ * Sec. 2; MadEvent and MadFlow can instead draw one configuration per event).
+ * A configuration h of g g -> t t~ + gluons fixes the helicities of the NG
+ * gluons and of the antitop: bit g (g < NG, the gluons in MadGraph order, the
+ * two incoming first) set means gluon g has helicity +1, bit NG set means the
+ * antitop has helicity +1; the top's two helicities are always summed.
+ *
+ * mf_matrix_element_hel: me2[e] = (1 / average) (|M(h_e, t-)|^2 + |M(h_e, t+)|^2)
+ * of event e at configuration hel[e] (int32 device array [n], only the low
+ * NG + 1 bits are read), momenta as mf_matrix_element; summed over the
+ * 2^(NG+1) configurations it is mf_matrix_element's value.  Covers the
+ * gluon-initiated processes in MF_FP64 and MF_FP32 (else MF_ERR_UNSUPPORTED).
+ *
+ * mf_set_helicity_sampling(proc, 1): from then on the process's iterations
+ * (mf_vegas_accumulate, mf_vegas_iterate, mf_unweight) estimate |M|^2 of each
+ * event by 2^(NG+1) mf_matrix_element_hel at a configuration drawn uniformly:
+ * the top NG + 1 bits of word 0 of Philox4x32-10 with the Vegas key
+ * (seed & 0xffffffff, (seed >> 32) ^ iter) and counter (event & 0xffffffff,
+ * event >> 32, 1, 1).  The estimate is unbiased; its variance is larger, its
+ * cost per event smaller.  0 restores the sum.  The launch shape
+ * (mf_set_launch_shape) applies to the summed kernel only.  Not covered while
+ * it is on: mf_vegas_accumulate_static, mf_grad, mixed plans
+ * (MF_ERR_UNSUPPORTED).  Errors: MF_ERR_ARG (on not 0 or 1), MF_ERR_UNSUPPORTED
+ * (not a gluon-initiated process, or MF_FP32_TC). */
+mf_status mf_matrix_element_hel(mf_process* proc, int64_t n, const double* momenta, const int32_t* hel, double* me2,
+                                void* stream);
+mf_status mf_set_helicity_sampling(mf_process* proc, int on);
+
 /* One Vegas iteration over global events 0..n-1 (chunks of 2^20 events: a
  * sampling kernel writes per-event records and the list of events passing the
  * cuts, the |M|^2 kernel reads them and accumulates), a deterministic reduction of the per-CTA

@@ -73,6 +73,8 @@ EXPORTS = {
     "mf_sample": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_int64, C.c_void_p, C.c_void_p,
                             C.c_void_p, C.c_void_p]),
     "mf_matrix_element": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mf_matrix_element_hel": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mf_set_helicity_sampling": (C.c_int, [C.c_void_p, C.c_int]),
     "mf_uniforms": (C.c_int, [C.c_uint64, C.c_int, C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
     "mf_vegas_iterate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_int64, C.c_int,
                                    C.POINTER(Result), C.c_void_p, C.c_void_p]),
@@ -312,6 +314,19 @@ class Process:
         _check(load_library().mf_matrix_element(
             self._h, n, _ptr(momenta, torch.float64, self.n_ext * 4 * n, "momenta"),
             _ptr(me2, torch.float64, n, "me2"), _stream(stream)))
+
+    def matrix_element_hel(self, n, momenta, hel, me2, stream=None):
+        """|M|^2 of one helicity configuration per event (hel: int32 [n], bit
+        g: gluon g helicity +1, bit NG: antitop helicity +1; the top summed)."""
+        import torch
+        _check(load_library().mf_matrix_element_hel(
+            self._h, n, _ptr(momenta, torch.float64, self.n_ext * 4 * n, "momenta"),
+            _ptr(hel, torch.int32, n, "hel"), _ptr(me2, torch.float64, n, "me2"), _stream(stream)))
+
+    def set_helicity_sampling(self, on):
+        """Iterations estimate |M|^2 from one drawn helicity configuration per
+        event (True) or sum the helicities (False, the default)."""
+        _check(load_library().mf_set_helicity_sampling(self._h, 1 if on else 0))
 
     def vegas_iterate(self, grid, seed, it, n, refine=True, weights=None, stream=None):
         import torch

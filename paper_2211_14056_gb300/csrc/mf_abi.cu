@@ -344,6 +344,21 @@ mf_status mf_set_launch_shape(mf_process* p, int warps_per_cta, int* max_ctas_pe
   return MF_OK;
 }
 
+mf_status mf_set_helicity_sampling(mf_process* p, int on) {
+  if (p == nullptr || (on != 0 && on != 1)) return fail(MF_ERR_ARG, "mf_set_helicity_sampling: need a process and on = 0 or 1");
+  if (on && (p->kind != 0 || p->precision == MF_FP32_TC))
+    return fail(MF_ERR_UNSUPPORTED, "mf_set_helicity_sampling: covers g g -> t t~ + gluons in MF_FP64 or MF_FP32");
+  if (on && p->hel_me_ctas == 0) {
+    size_t smem = 0;
+    int ctas = 0;
+    MF_CUDA(hel_me_config(p->ng, p->precision == MF_FP64 ? 0 : 1, &smem, &ctas), "mf_set_helicity_sampling");
+    if (ctas < 1) return fail(MF_ERR_UNSUPPORTED, "mf_set_helicity_sampling: the kernel does not fit on an SM");
+    p->hel_me_ctas = ctas;
+  }
+  p->hel = on;
+  return MF_OK;
+}
+
 mf_status mf_grid_create(const mf_process* p, int nbins, mf_grid** out) {
   if (p == nullptr || out == nullptr) return fail(MF_ERR_ARG, "mf_grid_create: null argument");
   if (nbins < 2 || nbins > 64) return fail(MF_ERR_ARG, "mf_grid_create: nbins must be in [2, 64]");
@@ -501,6 +516,44 @@ mf_status mf_matrix_element(mf_process* p, int64_t n, const double* momenta, dou
   return MF_OK;
 }
 
+mf_status mf_matrix_element_hel(mf_process* p, int64_t n, const double* momenta, const int32_t* hel, double* me2,
+                                void* stream) {
+  if (p == nullptr || n < 0) return fail(MF_ERR_ARG, "mf_matrix_element_hel: bad argument");
+  if (p->kind != 0 || p->precision == MF_FP32_TC)
+    return fail(MF_ERR_UNSUPPORTED, "mf_matrix_element_hel: covers g g -> t t~ + gluons in MF_FP64 or MF_FP32");
+  if (n == 0) return MF_OK;
+  if (momenta == nullptr || hel == nullptr || me2 == nullptr) return fail(MF_ERR_ARG, "mf_matrix_element_hel: null buffer");
+  const int prec = p->precision == MF_FP64 ? 0 : 1;
+  if (p->hel_me_ctas == 0) {
+    size_t smem = 0;
+    int ctas = 0;
+    MF_CUDA(hel_me_config(p->ng, prec, &smem, &ctas), "mf_matrix_element_hel");
+    if (ctas < 1) return fail(MF_ERR_UNSUPPORTED, "mf_matrix_element_hel: the kernel does not fit on an SM");
+    p->hel_me_ctas = ctas;
+  }
+  const int epb = kWarps * kHelEPW;   // events per CTA pass
+  const int64_t need = (n + epb - 1) / epb;
+  const int64_t cap = int64_t(p->sms) * effective_ctas(p, p->hel_me_ctas);
+  const int grid = int(need < cap ? need : cap);
+  MF_CUDA(launch_matrix_element_hel(p->ng, prec, p->mp, n, momenta, hel, me2, grid, (cudaStream_t)stream),
+          "mf_matrix_element_hel");
+  g_launches.fetch_add(1);
+  return MF_OK;
+}
+
+// CTAs per SM of the helicity-sampled |M|^2-and-accumulate kernel for a grid's
+// binning, queried once per grid
+static mf_status hel_grid_ctas(const mf_process* p, mf_grid* g) {
+  if (g->hel_ctas > 0) return MF_OK;
+  size_t smem = 0;
+  int ctas = 0;
+  MF_CUDA(hel_acc_config(p->ng, p->precision == MF_FP64 ? 0 : 1, g->ndim, g->nbins, &smem, &ctas),
+          "helicity-sampled kernel configuration");
+  if (ctas < 1) return fail(MF_ERR_UNSUPPORTED, "the helicity-sampled kernel does not fit on an SM");
+  g->hel_ctas = ctas;
+  return MF_OK;
+}
+
 mf_status mf_vegas_accumulate(mf_process* p, mf_grid* g, uint64_t seed, int iter, int64_t first_event, int64_t n,
                               double* weights, void* stream) {
   if (p == nullptr || g == nullptr) return fail(MF_ERR_ARG, "mf_vegas_accumulate: null argument");
@@ -523,6 +576,11 @@ mf_status mf_vegas_accumulate(mf_process* p, mf_grid* g, uint64_t seed, int iter
     }
     acc_ctas = g->shape_ctas;
   }
+  if (p->hel) {
+    const mf_status st = hel_grid_ctas(p, g);
+    if (st != MF_OK) return st;
+    acc_ctas = g->hel_ctas;
+  }
   const int64_t cap = std::min<int64_t>(int64_t(p->sms) * effective_ctas(p, acc_ctas), g->max_blocks);
   int grid = 0;
   if (g->profile) {
@@ -544,6 +602,13 @@ mf_status mf_vegas_accumulate(mf_process* p, mf_grid* g, uint64_t seed, int iter
     double* w = weights ? weights + done : nullptr;
     cudaEvent_t* evk = g->profile ? &g->ev[size_t(3) * k] : nullptr;
     cudaError_t e;
+    if (p->hel) {
+      e = launch_chunk_hel(p->ng, prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed,
+                           iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk);
+      if (e != cudaSuccess) return cuda_fail(e, "mf_vegas_accumulate (helicity-sampled chunk kernels)");
+      g_launches.fetch_add(2);
+      continue;
+    }
     switch (proc_key(p)) {
       case kUuxKey: e = launch_chunk_uux(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
       case kEeKey: e = launch_chunk_ee(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk); break;
@@ -627,7 +692,13 @@ mf_status mf_unweight(mf_process* p, mf_grid* g, uint64_t seed, int iter, int64_
   SampleParams sp = p->sp;
   sp.nbins = g->nbins;
   const int prec = p->precision == MF_FP64 ? 0 : 1;
-  const int64_t cap = int64_t(p->sms) * effective_ctas(p, g->acc_ctas);
+  int acc_ctas = g->acc_ctas;
+  if (p->hel) {
+    const mf_status st = hel_grid_ctas(p, g);
+    if (st != MF_OK) return st;
+    acc_ctas = g->hel_ctas;
+  }
+  const int64_t cap = int64_t(p->sms) * effective_ctas(p, acc_ctas);
   MF_CUDA(cudaMemsetAsync(g->d_ucount, 0, 2 * sizeof(unsigned long long), s), "mf_unweight (counts)");
   for (int64_t done = 0; done < n; done += g->chunk) {
     const int64_t m = std::min(g->chunk, n - done);
@@ -635,7 +706,10 @@ mf_status mf_unweight(mf_process* p, mf_grid* g, uint64_t seed, int iter, int64_
     const int grid = int(std::min(std::min(cap, std::max<int64_t>(ctas_needed, 1)), int64_t(g->max_blocks)));
     // the chunk's weights: the iteration's kernels (their Vegas sums are not recorded)
     cudaError_t e;
-    switch (proc_key(p)) {
+    if (p->hel) {
+      e = launch_chunk_hel(p->ng, prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed,
+                           iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s, nullptr);
+    } else switch (proc_key(p)) {
       case kUuxKey: e = launch_chunk_uux(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s, nullptr); break;
       case kEeKey: e = launch_chunk_ee(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s, nullptr); break;
       case 2: e = launch_chunk<2>(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s); break;
@@ -741,6 +815,8 @@ extern "C" mf_status mf_vegas_accumulate_static(mf_process* p, const double* edg
     return fail(MF_ERR_ARG, "mf_vegas_accumulate_static: null argument");
   if (p->kind != 0)
     return fail(MF_ERR_UNSUPPORTED, "mf_vegas_accumulate_static: covers the gluon-initiated processes");
+  if (p->hel)
+    return fail(MF_ERR_UNSUPPORTED, "mf_vegas_accumulate_static: sums the helicities (helicity sampling is on)");
   if (nbins < 2 || nbins > 64) return fail(MF_ERR_ARG, "mf_vegas_accumulate_static: nbins must be in [2, 64]");
   if (n < 1 || first_event < 0) return fail(MF_ERR_ARG, "mf_vegas_accumulate_static: need n >= 1 and first_event >= 0");
   size_t smem = 0;

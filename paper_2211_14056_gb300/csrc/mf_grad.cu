@@ -29,6 +29,7 @@ static mf_status grad_entry(bool reverse, mf_process* p, const mf_grid* g, uint6
     return fail(MF_ERR_ARG, "mf_grad: null argument");
   if (g->proc != p) return fail(MF_ERR_ARG, "mf_grad: grid belongs to another process");
   if (p->kind != 0) return fail(MF_ERR_UNSUPPORTED, "mf_grad: covers the gluon-initiated processes");
+  if (p->hel) return fail(MF_ERR_UNSUPPORTED, "mf_grad: differentiates the helicity sum (helicity sampling is on)");
   if (p->sp.lumi == 2) return fail(MF_ERR_UNSUPPORTED, "mf_grad: tabulated parton densities are not differentiated");
   if (n < 1) return fail(MF_ERR_ARG, "mf_grad: n must be >= 1");
   if (n > (int64_t(1) << 40)) return fail(MF_ERR_ARG, "mf_grad: n too large");

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "madflow_gb300.h"
+#include "mf_hel.cuh"
 #include "mf_kernels.cuh"
 
 namespace mf {
@@ -32,6 +33,8 @@ struct mf_process {
   size_t me_smem = 0;
   int ctas_override = 0;
   int me_warps = 0;                // warps per CTA of the |M|^2 kernel (0: the default 4; mf_set_launch_shape)
+  int hel = 0;                     // 1: one sampled helicity configuration per event (mf_set_helicity_sampling)
+  int hel_me_ctas = 0;             // CTAs per SM of k_matrix_element_hel (0: not queried yet)
   double g_s = 0.0, width = 0.0;   // strong coupling and top width of the descriptor
   int kind = 0;                    // 0: g g -> t t~ + gluons (ng = n_final), 1: u u~ -> t t~ g g,
                                    // 2: e+ e- -> mu+ mu- (ng = n_final = 2)
@@ -46,6 +49,7 @@ struct mf_grid {
   int acc_ctas = 1;            // CTAs per SM of the |M|^2-and-accumulate kernel
   int shape_warps = 0;         // launch shape whose occupancy shape_ctas holds (0: none yet)
   int shape_ctas = 0;
+  int hel_ctas = 0;            // CTAs per SM of the helicity-sampled |M|^2 kernel (0: not queried yet)
   size_t acc_smem = 0;
   int64_t chunk = 0;           // events per record chunk
   void* d_records = nullptr;   // per-event records of one chunk

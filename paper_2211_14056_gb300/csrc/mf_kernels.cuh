@@ -469,14 +469,49 @@ __device__ __forceinline__ void quark_walk_paired4(const S4<T>& v, const LaneCtx
   }
 }
 
-// Per event, helicity independent: the mask table (momentum sum K, -(q_tbar + K),
-// 1/K^2 and the top-propagator factor of every gluon subset, one subset per
-// lane) and the polarisation vectors (level-1 sub-currents).
+// One entry of the mask table of an event (helicity independent): for the
+// gluon subset `msk`, the momentum sum K (incoming gluons negated), -(q_tbar +
+// K), 1/K^2 (two or more gluons) and the top-propagator factor.  q: the
+// gluons' outgoing-convention momenta, qtb: the antitop's.
 template <int NG, typename T>
-__device__ __forceinline__ void event_tables(const T (&p)[NG + 2][4], const MaskTab<NG, T>& mtab, cplx<T>* Gs, int gl,
-                                             T mt, T mw) {
-  constexpr int L = Lanes<NG>::L;
-  R4<T> q[NG];
+__device__ __forceinline__ void mask_entry(const R4<T> (&q)[NG], const R4<T>& qtb, int msk, const MaskTab<NG, T>& mtab,
+                                           T mt, T mw) {
+  R4<T> K = {{T(0), T(0), T(0), T(0)}};
+#pragma unroll
+  for (int g = 0; g < NG; ++g)
+    if ((msk >> g) & 1) K = K + q[g];
+  const R4<T> P = qtb + K;
+  mtab.qsum[msk] = K;
+  mtab.ptab[msk] = -P;
+  const T k2 = mdot(K, K);
+  T den = mdot(P, P) - mt * mt;
+  if constexpr (sizeof(value_of(T(0))) == sizeof(float)) {
+    // FP32, subsets of outgoing gluons only (the top propagator that can come
+    // near its pole, t -> t + soft or collinear g): with massless gluons and
+    // an on-shell antitop, P^2 - m^2 = 2 q_tbar.K + sum_{i<j} 2 q_i.q_j, a sum
+    // of non-negative terms, free of the cancellation of P^2 against m^2
+    // that costs ~E^2/|P^2 - m^2| ulps.  With an incoming gluon the terms
+    // have both signs and the direct form is kept.
+    if ((msk & 3) == 0) {
+      T pairs = T(0);
+#pragma unroll
+      for (int i = 2; i < NG; ++i)
+#pragma unroll
+        for (int j = i + 1; j < NG; ++j)
+          if (((msk >> i) & 1) && ((msk >> j) & 1)) pairs += T(2) * mdot(q[i], q[j]);
+      den = fma(T(2), mdot(qtb, K), pairs);
+    }
+  }
+  mtab.ginv[msk] = __popc(unsigned(msk)) >= 2 ? T(1) / k2 : T(0);
+  const T inv = T(-1) / fma(den, den, mw * mw);
+  mtab.qf[msk] = {den * inv, -mw * inv};     // -1/den = -conj(den)/|den|^2
+}
+
+// The gluons' outgoing-convention momenta (incoming ones negated) of an event
+// given in MadGraph order (legs 0, 1 incoming gluons, 2 top, 3 antitop, then
+// the final gluons).
+template <int NG, typename T>
+__device__ __forceinline__ void gluon_momenta(const T (&p)[NG + 2][4], R4<T> (&q)[NG]) {
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
     const int leg = g < 2 ? g : g + 2;
@@ -484,41 +519,20 @@ __device__ __forceinline__ void event_tables(const T (&p)[NG + 2][4], const Mask
 #pragma unroll
     for (int c = 0; c < 4; ++c) q[g].v[c] = s * p[leg][c];
   }
+}
+
+// Per event, helicity independent: the mask table (one subset per lane, see
+// mask_entry) and the polarisation vectors (level-1 sub-currents).
+template <int NG, typename T>
+__device__ __forceinline__ void event_tables(const T (&p)[NG + 2][4], const MaskTab<NG, T>& mtab, cplx<T>* Gs, int gl,
+                                             T mt, T mw) {
+  constexpr int L = Lanes<NG>::L;
+  R4<T> q[NG];
+  gluon_momenta<NG, T>(p, q);
   R4<T> qtb;
 #pragma unroll
   for (int c = 0; c < 4; ++c) qtb.v[c] = p[3][c];
-  // the mask table (one mask per lane), and the polarisation vectors (level 1)
-  if (gl < (1 << NG)) {
-    R4<T> K = {{T(0), T(0), T(0), T(0)}};
-#pragma unroll
-    for (int g = 0; g < NG; ++g)
-      if ((gl >> g) & 1) K = K + q[g];
-    const R4<T> P = qtb + K;
-    mtab.qsum[gl] = K;
-    mtab.ptab[gl] = -P;
-    const T k2 = mdot(K, K);
-    T den = mdot(P, P) - mt * mt;
-    if constexpr (sizeof(value_of(T(0))) == sizeof(float)) {
-      // FP32, subsets of outgoing gluons only (the top propagator that can come
-      // near its pole, t -> t + soft or collinear g): with massless gluons and
-      // an on-shell antitop, P^2 - m^2 = 2 q_tbar.K + sum_{i<j} 2 q_i.q_j, a sum
-      // of non-negative terms, free of the cancellation of P^2 against m^2
-      // that costs ~E^2/|P^2 - m^2| ulps.  With an incoming gluon the terms
-      // have both signs and the direct form is kept.
-      if ((gl & 3) == 0) {
-        T pairs = T(0);
-#pragma unroll
-        for (int i = 2; i < NG; ++i)
-#pragma unroll
-          for (int j = i + 1; j < NG; ++j)
-            if (((gl >> i) & 1) && ((gl >> j) & 1)) pairs += T(2) * mdot(q[i], q[j]);
-        den = fma(T(2), mdot(qtb, K), pairs);
-      }
-    }
-    mtab.ginv[gl] = __popc(unsigned(gl)) >= 2 ? T(1) / k2 : T(0);
-    const T inv = T(-1) / fma(den, den, mw * mw);
-    mtab.qf[gl] = {den * inv, -mw * inv};     // -1/den = -conj(den)/|den|^2
-  }
+  if (gl < (1 << NG)) mask_entry<NG, T>(q, qtb, gl, mtab, mt, mw);
   for (int it = gl; it < 2 * NG; it += L) {
     const int g = it >> 1;
     const int leg = g < 2 ? g : g + 2;

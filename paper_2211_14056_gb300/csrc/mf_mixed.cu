@@ -386,6 +386,11 @@ mf_status mf_mixed_create(mf_process* const* procs, mf_grid* const* grids, const
       delete m;
       return fail(MF_ERR_ARG, "mf_mixed_create: process " + std::to_string(k) + ": bad process, grid or event count");
     }
+    if (procs[k]->hel) {
+      delete m;
+      return fail(MF_ERR_UNSUPPORTED, "mf_mixed_create: process " + std::to_string(k) +
+                                          " samples helicities; a mixed plan sums them");
+    }
     const int prec = procs[k]->precision == MF_FP64 ? 0 : 1;
     if (k > 0 && prec != m->precision) {
       delete m;

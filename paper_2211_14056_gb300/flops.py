@@ -101,6 +101,32 @@ def me2_flops_per_event(ng):
     return gluon_current_flops(ng) + shared_suffix_flops(ng) + lanes * (lane_flops(ng) + int(math.log2(lanes)))
 
 
+def me2_flops_per_event_hel(ng):
+    """Real FP operations of |M_h|^2 of one helicity configuration (both top
+    helicities), the helicity-sampled kernel's work per event: the mask table,
+    one polarisation vector per gluon, one sub-current per block, every suffix
+    current and ordered amplitude once, the colour form for each top helicity,
+    and the antitop and top spinors."""
+    bl, ids, off, nstore, first, o3, o4 = tables(ng)
+    total = ng * EXT + mask_table_flops(ng) + 3 * EXT
+    for k in range(2, ng + 1):
+        nblk = first[k + 1] - first[k]
+        n3, n4 = k - 1, (k - 1) * (k - 2) // 2
+        total += nblk * (n3 * O3 + n4 * O4 + 8)
+    for l in range(1, ng):
+        count = math.factorial(ng) // math.factorial(ng - l)
+        total += count * (APPLY + (l - 1) * APPLY_ACC + l * SLASH + 4 * l + QPROP)
+    total += math.factorial(ng) * (APPLY + (ng - 1) * APPLY_ACC + ng * SLASH + 2 * ROWDOT)
+    orders, M, D = colour_matrix_exact(ng)
+    P = len(orders)
+    per_h = 0
+    for a in range(P):
+        terms = [b for b in range(a, P) if M[a][b] != 0]
+        if terms:
+            per_h += 2 + 4 * (len(terms) - 1) + 4
+    return total + 2 * (per_h + 2) + 2
+
+
 def sampler_bytes_per_event(n_final, ndim, pass_fraction, kin_bytes):
     """Algorithmic HBM bytes the sampling kernel (k_sample_rec) writes per
     event: the record (final-state momenta and sqrt(s_hat) in the kinematics
@@ -112,4 +138,4 @@ def sampler_bytes_per_event(n_final, ndim, pass_fraction, kin_bytes):
 
 if __name__ == "__main__":
     for ng in (2, 3, 4):
-        print(ng, gluon_current_flops(ng), lane_flops(ng), me2_flops_per_event(ng))
+        print(ng, gluon_current_flops(ng), lane_flops(ng), me2_flops_per_event(ng), me2_flops_per_event_hel(ng))

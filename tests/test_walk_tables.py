@@ -67,3 +67,37 @@ def test_depth_first_layout():
                 assert T[1:] == levels[l - 1][p][0]
         # the completions are the n! orderings, each once
         assert sorted(o for (o, _) in final) == list(range(len(list(itertools.permutations(range(n))))))
+
+
+def _first(src, ng):
+    m = re.search(r"struct TTNG<%d> \{.*?FIRST\[\d+\] = \{([^}]*)\}" % ng, src, re.S)
+    return [int(x) for x in m.group(1).split(",")]
+
+
+def _hel_blk(ref, first, ng):
+    """The helicity-sampled kernels' block index of a reference (mf_hel.cuh,
+    hel_blk): stored offsets advance by 2^len per block of length len."""
+    off, mask = ref & 511, (ref >> 9) & 15
+    length = bin(mask).count("1")
+    o0 = sum((first[k + 1] - first[k]) << k for k in range(1, length))
+    return first[length] + ((off - o0) >> length)
+
+
+def test_compact_block_index_inverts_the_stored_offsets():
+    """Every reference in the generated tables names, through hel_blk, the
+    block whose stored offset and gluon mask it carries."""
+    src = gen_tables.render()
+    for ng in (2, 3, 4):
+        first = _first(src, ng)
+        off, msk = _array(src, f"kBlkOff{ng}"), _array(src, f"kBlkMask{ng}")
+        assert len(off) == first[ng + 1]
+        for b in range(len(off)):
+            assert _hel_blk(off[b] | (msk[b] << 9), first, ng) == b
+        refs = []
+        names = set(re.findall(r"(kO[34]_%d_\d+|kPathBlk%d_\d+|kFinalBlk%d)\[" % (ng, ng, ng), src))
+        assert f"kFinalBlk{ng}" in names and f"kO3_{ng}_2" in names and (ng < 3 or f"kO4_{ng}_3" in names)
+        for name in names:
+            refs += _array(src, name)
+        for r in refs:
+            b = _hel_blk(r, first, ng)
+            assert 0 <= b < len(off) and off[b] == (r & 511) and msk[b] == ((r >> 9) & 15)
