@@ -21,6 +21,7 @@
 #include <type_traits>
 
 #include "mf_device.cuh"
+#include "mf_f32x2.cuh"
 #include "mf_gen_ttng.cuh"
 #include "mf_sample.cuh"
 
@@ -36,6 +37,10 @@ struct MeParams {
 // MeParams::chan of the two-quark-line amplitude (mf_kernels_uux.cu): u u~, u~ u,
 // u g, g u, u~ g, g u~ initial states
 constexpr int kChanQQB = 0, kChanQBQ = 1, kChanQG = 2, kChanGQ = 3, kChanQBG = 4, kChanGQB = 5;
+
+// The FP32 four-gluon quark line walks both antitop helicities of a lane as
+// packed pairs (quark_walk_paired4_x2); false restores the scalar walk.
+constexpr bool kPackedWalk = true;
 
 template <int NG> struct Lanes {
   static constexpr int L = 2 << NG;        // lanes per event
@@ -521,6 +526,98 @@ __device__ __forceinline__ void gluon_momenta(const T (&p)[NG + 2][4], R4<T> (&q
   }
 }
 
+// The four-gluon quark line in FP32 with both antitop helicities of a gluon
+// helicity pattern H in one lane, as packed pairs (f2: half 0 = antitop
+// helicity -1, half 1 = +1), each lane taking the last gluons c of its half of
+// the warp (lanes 0-15: c = 0, 1; lanes 16-31: c = 2, 3).  The suffix
+// currents depend on the antitop helicity through v(tbar) only, so the two
+// halves run the same walk on different data and every FP32 operation of
+// the walk issues once for both.  Lane H + 16 h computes what lane H + 16 h
+// of quark_walk_paired4 would for its c (the same three-gluon pairing
+// between lanes l and l ^ 2^g, now within a half), and the amplitudes land
+// in the same columns of the J planes (column H + 16 (antitop bit)), so
+// the colour sums that follow are unchanged.  Results equal the scalar
+// walk's: each half of a paired instruction rounds as the scalar one.
+__device__ __forceinline__ void final_amplitudes_x2(int path, const S4<f2> (&R)[4], const LaneCtx<float>& cx,
+                                                    float* J0, float* J1) {
+  using PT = Paths<4>;
+  // two independent partial sums (the paired instructions' latency is longer
+  // than the scalar ones', so shorter dependency chains keep them issuing)
+  S4<f2> W = apply(dup(make_slash(lane_block<4, float>(cx, PT::final_blk(path, 0)))), R[3]);
+  S4<f2> V = apply(dup(make_slash(lane_block<4, float>(cx, PT::final_blk(path, 2)))), R[1]);
+  apply_acc(dup(make_slash(lane_block<4, float>(cx, PT::final_blk(path, 1)))), R[2], W);
+  apply_acc(dup(make_slash(lane_block<4, float>(cx, PT::final_blk(path, 3)))), R[0], V);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) W.c[k] = W.c[k] + V.c[k];
+  const int sig = PT::final_sigma(path);
+  const cplx<f2> j0 = rowdot(cx.ub0, W), j1 = rowdot(cx.ub1, W);
+  constexpr int S = kJStride<float>, P = kJPlane<4, float>;
+  J0[(sig * 2 + 0) * S] = j0.r.v.x;
+  J0[(sig * 2 + 0) * S + P] = j0.i.v.x;
+  J0[(sig * 2 + 1) * S] = j1.r.v.x;
+  J0[(sig * 2 + 1) * S + P] = j1.i.v.x;
+  J1[(sig * 2 + 0) * S] = j0.r.v.y;
+  J1[(sig * 2 + 0) * S + P] = j0.i.v.y;
+  J1[(sig * 2 + 1) * S] = j1.r.v.y;
+  J1[(sig * 2 + 1) * S + P] = j1.i.v.y;
+}
+
+__device__ __forceinline__ void quark_walk_paired4_x2(const S4<f2>& v, const LaneCtx<float>& cx, unsigned H,
+                                                      int half, float* J0, float* J1) {
+  using PT = Paths<4>;
+  constexpr int NR2 = WarpMem<4, float>::NR2;
+  auto load_r2 = [&](int p2) {
+    const uint8_t m2 = PT::template mask<2>(p2);
+    const int idx = p2 * 8 + int(unsigned(cx.pk >> (4 * m2)) & 15u);
+    S4<f2> r;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.c[k] = pack(cx.R2[k * NR2 + idx], cx.R2[k * NR2 + idx + 4]);
+    return r;
+  };
+#pragma unroll 1
+  for (int ci = 0; ci < 2; ++ci) {
+    const int c = 2 * half + ci;
+    S4<f2> R[4];
+    R[0] = v;
+    const uint8_t m1 = PT::template mask<1>(c);
+    R[1] = quark_prop_f(dup(cx.Ptab[m1]), f2(cx.m), dup(cx.qf[m1]),
+                        apply(dup(make_slash(lane_block<4, float>(cx, PT::template blk<1>(c, 0)))), v));
+#pragma unroll 1
+    for (int gi = 0; gi < 3; ++gi) {
+      const int g = kL3Miss4[c * 3 + gi];
+      const unsigned bit = (H >> g) & 1u;
+      const int mine = kL3Pair4[(c * 3 + gi) * 2 + bit], other = kL3Pair4[(c * 3 + gi) * 2 + (bit ^ 1u)];
+      R[2] = load_r2(mine >> 1);
+      S4<f2> X = apply(dup(make_slash(lane_block<4, float>(cx, PT::template blk<3>(mine, 0)))), R[2]);
+      apply_acc(dup(make_slash(lane_block<4, float>(cx, PT::template blk<3>(mine, 1)))), R[1], X);
+      apply_acc(dup(make_slash(lane_block<4, float>(cx, PT::template blk<3>(mine, 2)))), v, X);
+      const uint8_t m3 = PT::template mask<3>(mine);
+      R[3] = quark_prop_f(dup(cx.Ptab[m3]), f2(cx.m), dup(cx.qf[m3]), X);
+      S4<f2> Ro;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        Ro.c[k].r.v.x = __shfl_xor_sync(0xffffffffu, R[3].c[k].r.v.x, 1 << g);
+        Ro.c[k].r.v.y = __shfl_xor_sync(0xffffffffu, R[3].c[k].r.v.y, 1 << g);
+        Ro.c[k].i.v.x = __shfl_xor_sync(0xffffffffu, R[3].c[k].i.v.x, 1 << g);
+        Ro.c[k].i.v.y = __shfl_xor_sync(0xffffffffu, R[3].c[k].i.v.y, 1 << g);
+      }
+      // the two completions in one loop body: the packed code is about twice
+      // the scalar walk's per instruction issued, and two inlined copies of
+      // the last level overflow the instruction cache
+      int path = mine;
+#pragma unroll 1
+      for (int w = 0; w < 2; ++w) {
+        final_amplitudes_x2(path, R, cx, J0, J1);
+        if (w == 0) {
+          R[2] = load_r2(other >> 1);
+          R[3] = Ro;
+          path = other;
+        }
+      }
+    }
+  }
+}
+
 // Per event, helicity independent: the mask table (one subset per lane, see
 // mask_entry) and the polarisation vectors (level-1 sub-currents).
 template <int NG, typename T>
@@ -591,7 +688,11 @@ __device__ __forceinline__ T group_me2(const T (&p)[NG + 2][4], unsigned char* w
   cx.ltb = unsigned((gl >> NG) & 1);
   S4<T> R[NG];
   R[0] = v_out(qtb, mt, ltb);
-  if constexpr (NG == 4 && kShareSuffixes<T>) {
+  if constexpr (NG == 4 && std::is_same<T, float>::value && kPackedWalk) {
+    // both antitop helicities of pattern H in this lane, packed; c by warp half
+    quark_walk_paired4_x2(pack(v_out(qtb, mt, -1), v_out(qtb, mt, 1)), cx, H, gl >> 4, Jw + H, Jw + H + 16);
+    __syncwarp();   // every column of this lane's colour sum was written by the lanes of both halves
+  } else if constexpr (NG == 4 && kShareSuffixes<T>) {
     quark_walk_paired4<T>(R[0], cx, H);
   } else {
     quark_walk<NG, 1, T>(0, R, cx);
