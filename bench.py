@@ -207,9 +207,10 @@ def main():
     ap.add_argument("--launch-shapes", action="store_true",
                     help="only run the full launch-shape sweep of the |M|^2 kernel (10^6 g g -> t tbar g g events "
                          "per shape) and print it as one JSON line")
-    ap.add_argument("--profile-kernel", default="iterate", choices=["iterate", "me", "grad", "pdf"],
-                    help="--profile-case target: whole iterations, sampling + the |M|^2 kernel alone, or "
-                         "two reverse-mode derivative calls (mf_grad with every per-event output)")
+    ap.add_argument("--profile-kernel", default="iterate", choices=["iterate", "me", "grad", "pdf", "hel"],
+                    help="--profile-case target: whole iterations, sampling + the |M|^2 kernel alone, "
+                         "two reverse-mode derivative calls (mf_grad with every per-event output), the "
+                         "parton-density kernel, or iterations with helicity sampling (hel)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -258,6 +259,8 @@ def main():
             print(json.dumps({"profile_case": args.workload, "kernel": "grad", "events": ne,
                               "precision": args.precision, "sigma": sigma, "dsigma": ds}))
             return 0
+        if args.profile_kernel == "hel":
+            p.set_helicity_sampling(True)     # iterations with one drawn helicity configuration per event
         for it in range(3):
             r = p.vegas_iterate(g, w["seed"], it, args.profile_case, refine=True)
         print(json.dumps({"profile_case": args.workload, "events": args.profile_case, "precision": args.precision,
