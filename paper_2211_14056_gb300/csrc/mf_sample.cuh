@@ -111,20 +111,16 @@ __device__ __forceinline__ void boost_from_rest(const K* Q, K M, const K* p, K* 
   out[3] = fma(c, Q[3], p[3]);
 }
 
-// root v in [0,1] of (k+1) v^k - k v^(k+1) = r, for k = 1 (closed form) and
-// k = 2 (trigonometric cubic solution), each followed by Newton polish
+// root v in [0,1] of 3 v^2 - 2 v^3 = r: the trigonometric cubic solution,
+// then Newton polish, which restores relative accuracy for small v, where the
+// closed form cancels
 template <typename K>
-__device__ __forceinline__ K mass_ratio(K r, int k) {
-  if (k == 1) {
-    // 2v - v^2 = r  ->  v = 1 - sqrt(1 - r) = r / (1 + sqrt(1 - r))
-    return r / (K(1) + sqrt(K(1) - r));
-  }
-  // 3 v^2 - 2 v^3 = r: v = 1/2 + cos(acos(1 - 2r)/3 - 2 pi/3)
+__device__ __forceinline__ K cubic_root01(K r) {
+  // v = 1/2 + cos(acos(1 - 2r)/3 - 2 pi/3)
   K v = K(0.5) + cos(acos(K(1) - K(2) * r) * K(1.0 / 3.0) - K(2.0943951023931954923));
   if (v < K(0)) v = K(0);
   if (v > K(1)) v = K(1);
-  // Newton polish on f(v) = 3 v^2 - 2 v^3 - r, f' = 6 v (1 - v); restores
-  // relative accuracy for small v, where the closed form cancels
+  // Newton on f(v) = 3 v^2 - 2 v^3 - r, f' = 6 v (1 - v)
   if (v <= K(0)) v = sqrt(r / K(3));
 #pragma unroll
   for (int it = 0; it < 3; ++it) {
@@ -132,6 +128,29 @@ __device__ __forceinline__ K mass_ratio(K r, int k) {
     if (fp > K(0)) v -= (v * v * (K(3) - K(2) * v) - r) / fp;
   }
   return v;
+}
+
+// Root v in [0,1] of (k+1) v^k - k v^(k+1) = r and its complement w = 1 - v,
+// from r and s = 1 - r, each given to full relative accuracy (s is formed
+// before r is rounded to the kinematics type: for r within a few ulps of 1,
+// 1 - r formed afterwards has no correct digit, and the two-body momentum of
+// the step, M w / 2, inherits that).  k = 1: v = 1 - sqrt(s) = r / (1 +
+// sqrt(s)), w = sqrt(s).  k = 2: w solves the same cubic with s in place of
+// r (3 w^2 - 2 w^3 = s), so the smaller of v, w comes from its own argument.
+template <typename K>
+__device__ __forceinline__ void mass_ratio(K r, K s, int k, K& v, K& w) {
+  if (k == 1) {
+    w = sqrt(s);
+    v = r / (K(1) + w);
+    return;
+  }
+  if (r <= s) {
+    v = cubic_root01(r);
+    w = K(1) - v;
+  } else {
+    w = cubic_root01(s);
+    v = K(1) - w;
+  }
 }
 
 __device__ __forceinline__ void sincos_turns(double t, double* s, double* c) { sincospi(2.0 * t, s, c); }
@@ -233,14 +252,24 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
   const D rs = sqrt(shat);
   const K rsk = K(rs);
   const int n = sp.n_final;
-  // RAMBO on diet: intermediate masses M[i - 1] of Q_i (M[0] = sqrt(s_hat), M[n - 1] = 0)
-  K M[kMaxExt];
+  // RAMBO on diet: intermediate masses M[i - 1] of Q_i (M[0] = sqrt(s_hat),
+  // M[n - 1] = 0) and the complements W[i - 1] = 1 - M[i]^2 / M[i - 1]^2 of
+  // their squared ratios (W = 1 at the last step)
+  K M[kMaxExt], W[kMaxExt];
   M[0] = rsk;
 #pragma unroll
   for (int i = 2; i <= kMaxExt; ++i) {
-    if (i <= n - 1) M[i - 1] = M[i - 2] * sqrt(mass_ratio(K(xr[i - 2]), n - i));
-    else M[i - 1] = K(0);
+    W[i - 2] = K(1);
+    if (i <= n - 1) {
+      K v, wc;
+      mass_ratio(K(xr[i - 2]), K(D(1.0) - xr[i - 2]), n - i, v, wc);
+      M[i - 1] = M[i - 2] * sqrt(v);
+      W[i - 2] = wc;
+    } else {
+      M[i - 1] = K(0);
+    }
   }
+  W[kMaxExt - 1] = K(1);
   // the angle uniforms xa: the phase-space uniforms after the n - 2 mass
   // ones, shifted one place per mass uniform (a runtime offset into xr would
   // be a runtime index)
@@ -259,11 +288,14 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
   for (int i = 1; i <= kMaxExt - 1; ++i) {
     if (i <= n - 1) {
       const K Mi = M[i - 1], Mn = M[i];
-      const K q = (Mi - Mn) * (Mi + Mn) / (K(2) * Mi);
-      // (cos theta, phi) uniforms of this step: after the n - 2 mass uniforms
-      const K rc = K(xa[2 * (i - 1)]), rp = K(xa[2 * (i - 1) + 1]);
-      const K cth = K(2) * rc - K(1);
-      const K sth = K(2) * sqrt(rc * (K(1) - rc));
+      // massless momentum of the two-body step, (Mi^2 - Mn^2) / (2 Mi), as
+      // Mi (1 - Mn^2/Mi^2) / 2 with the accurate complement
+      const K q = K(0.5) * Mi * W[i - 1];
+      // (cos theta, phi) uniforms of this step: after the n - 2 mass uniforms;
+      // sin theta from rc (1 - rc) with 1 - rc formed before rounding
+      const K rc = K(xa[2 * (i - 1)]), rcm = K(D(1.0) - xa[2 * (i - 1)]), rp = K(xa[2 * (i - 1) + 1]);
+      const K cth = rc - rcm;
+      const K sth = K(2) * sqrt(rc * rcm);
       K sph, cph;
       sincos_turns(rp, &sph, &cph);
       const K pr[4] = {q, q * sth * cph, q * sth * sph, q * cth};
