@@ -14,6 +14,22 @@ Helicity index h: bit g (g = 0 .. n_g - 1, the process's gluons in their
 order: the two incoming, then the final ones) set means helicity +1 of that
 gluon; bit n_g set means antitop helicity +1.  Processes: a top pair plus
 gluons only.
+
+Adapted draw (a reading: MadEvent's choice of helicities by their weight,
+written as a discrete Vegas dimension).  The configuration of an event is
+drawn from integer thresholds 0 = T_0 <= T_1 <= ... <= T_H = 2^32 by the 32-bit
+word w0 of the helicity stream: h = max{h : T_h <= w0}, with probability
+p_h = (T_{h+1} - T_h) / 2^32, and the event weighs f_h / p_h.  Uniform
+thresholds T_h = h 2^(32 - n_g - 1) give the uniform draw above.  After an
+iteration, with S_h the sum of the squared weights of the events drawn in
+configuration h, sqrt(p_h S_h) estimates sqrt(N E[f_h^2]) (each event draws
+h with probability p_h, and its weight squared is f_h^2 / p_h^2), the choice
+of p that minimises the variance; the refined probabilities mix it with the
+uniform ones, p'_h = (1 - a) q_h / sum(q) + a / H with q_h = sqrt(p_h S_h),
+so that no configuration is left out (unbiasedness needs p_h > 0 wherever f_h
+is not zero), and T'_h = floor(2^32 sum_{k<h} p'_k).  Every sum runs in
+configuration order, one addition at a time, so that the device, which
+rounds each operation separately, computes the same numbers.
 """
 import numpy as np
 
@@ -100,3 +116,73 @@ def sampled_weights(setup, y, edges, seed, iteration, events):
     if np.any(cut):
         w[cut] = sampled_me2(setup.proc, p[cut], hel[cut], algorithm) * wk[cut]
     return w, bins, hel
+
+
+# ---------------------------------------------------------------------------
+# adapted draw
+
+REFINE_FLOOR = 0.1      # the share a of the uniform probabilities kept in a refined table
+
+
+def uniform_thresholds(n_configs):
+    """T_h = h 2^32 / H (H a power of two)."""
+    return np.arange(n_configs + 1, dtype=np.int64) * (2 ** 32 // n_configs)
+
+
+def thresholds(p):
+    """T_0..T_H for probabilities p (summing to 1): T_h = floor(2^32 c_h) with
+    c_h = p_0 + ... + p_{h-1} added in order, T_0 = 0, T_H = 2^32."""
+    p = np.asarray(p, dtype=np.float64)
+    c = np.zeros(p.size + 1)
+    for h in range(p.size):
+        c[h + 1] = c[h] + p[h]
+    T = np.floor(c * 2.0 ** 32).astype(np.int64)
+    T[0], T[-1] = 0, 2 ** 32
+    return np.maximum.accumulate(T)
+
+
+def probabilities(T):
+    """p_h = (T_{h+1} - T_h) / 2^32, the probabilities the thresholds realise."""
+    T = np.asarray(T, dtype=np.int64)
+    return np.diff(T).astype(np.float64) * 2.0 ** -32
+
+
+def draw(words, T):
+    """h = max{h : T_h <= w0} for each 32-bit word."""
+    return np.searchsorted(np.asarray(T, dtype=np.int64), np.asarray(words, dtype=np.int64), side="right") - 1
+
+
+def refine(T, S, a=REFINE_FLOOR):
+    """Refined thresholds from the current ones and the per-configuration sums
+    of squared weights S_h; unchanged if every S_h is zero."""
+    p = probabilities(T)
+    S = np.asarray(S, dtype=np.float64)
+    q = np.sqrt(p * S)
+    tot = 0.0
+    for h in range(q.size):
+        tot = tot + q[h]
+    if not tot > 0:
+        return np.asarray(T, dtype=np.int64).copy()
+    H = q.size
+    pn = np.empty(H)
+    for h in range(H):
+        pn[h] = (1.0 - a) * (q[h] / tot) + a / H
+    return thresholds(pn)
+
+
+def adapted_weights(setup, y, edges, seed, iteration, events, T):
+    """Event weights of an iteration whose configurations are drawn with the
+    thresholds T: f_h / p_h at the drawn h, with f_h = me2_helicity times the
+    weight factor.  Returns (w, bins, hel, S) with S_h the sum of the squared
+    weights of the events drawn in configuration h."""
+    p, wk, bins, cut = setup.kinematics(y, edges)
+    T = np.asarray(T, dtype=np.int64)
+    hel = draw(philox.helicity_words(seed, iteration, events), T)
+    ph = probabilities(T)
+    algorithm = "bg" if setup.bg is not None else "feynman"
+    w = np.zeros(y.shape[1])
+    if np.any(cut):
+        w[cut] = me2_helicity(setup.proc, p[cut], hel[cut], algorithm) / ph[hel[cut]] * wk[cut]
+    S = np.zeros(T.size - 1)
+    np.add.at(S, hel, w * w)
+    return w, bins, hel, S

@@ -99,6 +99,18 @@ def unweight_uniforms(seed, iteration, events):
     return words_to_unit(w0, w1)
 
 
+def helicity_words(seed, iteration, events):
+    """w0[len(events)] (uint64 holding 32 bits): word w0 of counter
+    (event_lo, event_hi, 1, 1), the helicity stream's word of each event."""
+    ev = np.asarray(events, dtype=np.uint64)
+    seed = int(seed)
+    k0 = seed & MASK32
+    k1 = ((seed >> 32) ^ int(iteration)) & MASK32
+    w0, _, _, _ = philox4x32_10(ev & np.uint64(MASK32), ev >> np.uint64(32), np.ones_like(ev),
+                                np.ones_like(ev), k0, k1)
+    return np.asarray(w0, dtype=np.uint64)
+
+
 def helicity_draws(seed, iteration, events, bits):
     """h[len(events)]: the helicity index (the top `bits` bits of word w0 of
     counter (event_lo, event_hi, 1, 1)) drawn for each listed event."""

@@ -13,7 +13,13 @@ the third Philox stream that draws it.
 * the draw: counter layout of the stream, values in [0, 2^bits), uniform
   (chi^2), independent of the Vegas and the unweighting streams;
 * unbiasedness: the estimator's mean over draws is |M|^2 (within 5 sigma),
-  and the sampled weights of an iteration integrate to the summed ones.
+  and the sampled weights of an iteration integrate to the summed ones;
+* the adapted draw: uniform thresholds reproduce the uniform draw exactly;
+  the draw's frequencies follow the thresholds' probabilities (chi^2); with
+  an adapted table the estimator stays unbiased; the refinement's fixed
+  point is the closed-form optimum mixed with the uniform floor, it lowers
+  the exact per-event variance on real configurations, keeps every
+  probability at or above the floor, and leaves the table alone without data.
 """
 import numpy as np
 import pytest
@@ -158,3 +164,94 @@ def test_sampled_weights_integrate_to_the_summed_ones():
     d = w_s - w_sum                                  # zero mean: E_h[w_s | y] = w_sum
     assert abs(d.mean()) < 5 * d.std() / np.sqrt(n)
     assert np.mean(np.abs(d[w_sum > 0]) > 1e-3 * w_sum[w_sum > 0]) > 0.9   # the draw does move the weights
+
+
+def test_uniform_thresholds_reproduce_the_uniform_draw():
+    ev = np.arange(50_000, dtype=np.uint64)
+    for bits in (3, 4, 5):
+        T = oh.uniform_thresholds(2 ** bits)
+        np.testing.assert_array_equal(oh.draw(philox.helicity_words(9, 4, ev), T), philox.helicity_draws(9, 4, ev, bits))
+        assert np.all(oh.probabilities(T) == 2.0 ** -bits)
+
+
+def test_draw_follows_the_thresholds():
+    rng = np.random.default_rng(5)
+    p = rng.uniform(0.2, 3.0, 32)
+    p /= p.sum()
+    T = oh.thresholds(p)
+    assert T[0] == 0 and T[-1] == 2 ** 32 and np.all(np.diff(T) > 0)
+    assert np.max(np.abs(oh.probabilities(T) - p)) < 2.0 ** -31
+    n = 400_000
+    h = oh.draw(philox.helicity_words(2, 0, np.arange(n, dtype=np.uint64)), T)
+    counts = np.bincount(h, minlength=32)
+    assert stats.chisquare(counts, n * oh.probabilities(T)).pvalue > 1e-4
+
+
+def test_adapted_estimator_is_unbiased():
+    proc = Process("gg_ttxg", wt=1.5)
+    p = points(3, 1, seed=16)
+    per = oh.per_helicity(proc, p, "bg").reshape(-1)
+    f = np.array([per[oh.config_index(proc, [h], 0)[0]] + per[oh.config_index(proc, [h], 1)[0]]
+                  for h in range(16)]) / proc.average
+    T = oh.refine(oh.uniform_thresholds(16), f ** 2 * 16)      # a table adapted to this event
+    n = 40_000
+    h = oh.draw(philox.helicity_words(4, 0, np.arange(n, dtype=np.uint64)), T)
+    v = f[h] / oh.probabilities(T)[h]
+    me2 = proc.me2(p)[0]
+    assert abs(v.mean() - me2) < 5 * v.std() / np.sqrt(n)
+    # adapted to the event itself, the estimator's spread is far below the uniform one's
+    vu = 16 * f[philox.helicity_draws(4, 0, np.arange(n, dtype=np.uint64), 4)]
+    assert v.std() < 0.5 * vu.std()
+
+
+def test_refinement_fixed_point_floor_and_no_data():
+    rng = np.random.default_rng(7)
+    f = rng.uniform(0.0, 1.0, 32) ** 3
+    T0 = oh.uniform_thresholds(32)
+    p0 = oh.probabilities(T0)
+    # expected S for N events: N E[f_h^2 / p_h^2 ; h drawn] = N f_h^2 / p_h
+    T1 = oh.refine(T0, 1000.0 * f ** 2 / p0)
+    a = oh.REFINE_FLOOR
+    want = (1 - a) * f / f.sum() + a / 32
+    assert np.max(np.abs(oh.probabilities(T1) - want)) < 2.0 ** -31
+    assert np.all(oh.probabilities(T1) >= a / 32 - 2.0 ** -32)
+    # the same expectation under the refined table is its own fixed point
+    T2 = oh.refine(T1, 1000.0 * f ** 2 / oh.probabilities(T1))
+    assert np.max(np.abs(oh.probabilities(T2) - want)) < 2.0 ** -30
+    np.testing.assert_array_equal(oh.refine(T1, np.zeros(32)), T1)
+    # a configuration never drawn keeps the floor
+    S = 1000.0 * f ** 2 / p0
+    S[3] = 0.0
+    assert abs(oh.probabilities(oh.refine(T0, S))[3] - a / 32) < 2.0 ** -31
+
+
+def test_refinement_lowers_the_exact_variance():
+    """Per-configuration values of 200 gg -> t tbar g events: the exact
+    variance of the estimator, sum_h f_h^2 / p_h - (sum_h f_h)^2 averaged
+    over the events, drops once the table is refined on the expected sums."""
+    proc = Process("gg_ttxg", wt=1.5)
+    p = points(3, 200, seed=17)
+    f = np.stack([oh.me2_helicity(proc, p, np.full(200, h), "bg") for h in range(16)], axis=1)   # [N, 16]
+    T0 = oh.uniform_thresholds(16)
+
+    def var(T):
+        ph = oh.probabilities(T)
+        return np.mean(np.sum(f ** 2 / ph, axis=1) - f.sum(axis=1) ** 2)
+
+    T1 = oh.refine(T0, np.sum(f ** 2, axis=0) / oh.probabilities(T0))
+    print(f"exact variance ratio refined / uniform: {var(T1) / var(T0):.3f}")
+    assert var(T1) < var(T0)
+
+
+def test_adapted_weights_with_uniform_thresholds_equal_the_sampled_weights():
+    cfg = dict(process="gg_ttxg", sqrt_s=1000.0, mt=173.0, wt=1.5, pt_cut=20.0, dr_cut=0.4, lumi=False)
+    st = oi.Setup(cfg, amplitude="bg")
+    n = 600
+    ev = np.arange(n, dtype=np.uint64)
+    edges = np.tile(np.linspace(0, 1, 11), (st.ndim, 1))
+    y = philox.uniforms(22, 1, ev, st.ndim)
+    w_s, _, hel_s = oh.sampled_weights(st, y, edges, 22, 1, ev)
+    w_a, _, hel_a, S = oh.adapted_weights(st, y, edges, 22, 1, ev, oh.uniform_thresholds(16))
+    np.testing.assert_array_equal(hel_a, hel_s)
+    np.testing.assert_allclose(w_a, w_s, rtol=1e-15)
+    assert abs(S.sum() / np.sum(w_a ** 2) - 1) < 1e-13
