@@ -245,13 +245,22 @@ mf_status mf_matrix_element(mf_process* proc, int64_t n, const double* momenta, 
  * 2^(NG+1) configurations it is mf_matrix_element's value.  Covers the
  * gluon-initiated processes in MF_FP64 and MF_FP32 (else MF_ERR_UNSUPPORTED).
  *
- * mf_set_helicity_sampling(proc, 1): from then on the process's iterations
- * (mf_vegas_accumulate, mf_vegas_iterate, mf_unweight) estimate |M|^2 of each
- * event by 2^(NG+1) mf_matrix_element_hel at a configuration drawn uniformly:
- * the top NG + 1 bits of word 0 of Philox4x32-10 with the Vegas key
- * (seed & 0xffffffff, (seed >> 32) ^ iter) and counter (event & 0xffffffff,
- * event >> 32, 1, 1).  The estimate is unbiased; its variance is larger, its
- * cost per event smaller.  0 restores the sum.  The launch shape
+ * mf_set_helicity_sampling(proc, on), on = 1: from then on the process's
+ * iterations (mf_vegas_accumulate, mf_vegas_iterate, mf_unweight) estimate
+ * |M|^2 of each event by mf_matrix_element_hel / p_h at a configuration h
+ * drawn from the grid's helicity table: with w0 word 0 of Philox4x32-10 under
+ * the Vegas key (seed & 0xffffffff, (seed >> 32) ^ iter) and counter
+ * (event & 0xffffffff, event >> 32, 1, 1), h = max{h : T_h <= w0} for the
+ * table's thresholds 0 = T_0 <= ... <= T_H = 2^32 (H = 2^(NG+1)), and p_h =
+ * (T_{h+1} - T_h) / 2^32.  A new grid's table is uniform (T_h = h 2^32 / H:
+ * h is the top NG + 1 bits of w0, the weight 2^(NG+1) |M_h|^2).  on = 2 also
+ * sums, per configuration, the squared weights of the events that drew it
+ * (appended to the totals of mf_grid_totals) so that mf_vegas_finish with
+ * refine bit 2 refines the table: q_h = sqrt(p_h S_h), p'_h = 0.9 q_h / sum(q)
+ * + 0.1 / H (every sum in configuration order), T'_h = floor(2^32 (p'_0 + ...
+ * + p'_{h-1})); a table whose S are all zero stays.  The estimate is unbiased
+ * for any table with every p_h > 0; its variance is larger than the sum's,
+ * its cost per event smaller.  0 restores the sum.  The launch shape
  * (mf_set_launch_shape) applies to the summed kernel only.  Not covered while
  * it is on: mf_vegas_accumulate_static, mf_grad, mixed plans
  * (MF_ERR_UNSUPPORTED).  Errors: MF_ERR_ARG (on not 0 or 1), MF_ERR_UNSUPPORTED
@@ -260,10 +269,23 @@ mf_status mf_matrix_element_hel(mf_process* proc, int64_t n, const double* momen
                                 void* stream);
 mf_status mf_set_helicity_sampling(mf_process* proc, int on);
 
+/* The grid's helicity table as probabilities p[0..n-1] (host, n = 2^(NG+1)):
+ * mf_grid_helicity reads them (p_h = (T_{h+1} - T_h) / 2^32, exact);
+ * mf_grid_set_helicity sets the thresholds T_h = floor(2^32 (p_0 + ... +
+ * p_{h-1})) (partial sums added in order), which mf_grid_helicity then
+ * returns exactly.  Synchronous.  Errors: MF_ERR_ARG (wrong n, a p_h that is
+ * not finite and > 0 or that leaves its configuration no threshold step,
+ * sum not 1 within 1e-9), MF_ERR_UNSUPPORTED (the process has no helicity
+ * table: only the gluon-initiated processes do). */
+mf_status mf_grid_helicity(const mf_grid* grid, double* prob, int n);
+mf_status mf_grid_set_helicity(mf_grid* grid, const double* prob, int n);
+
 /* One Vegas iteration over global events 0..n-1 (chunks of 2^20 events: a
  * sampling kernel writes per-event records and the list of events passing the
  * cuts, the |M|^2 kernel reads them and accumulates), a deterministic reduction of the per-CTA
- * sums, and, if refine != 0, the grid refinement.  The iteration is recorded
+ * sums, and the refinements that refine asks for: bit 1 the Vegas edges,
+ * bit 2 the helicity table (processes with mf_set_helicity_sampling(proc, 2);
+ * other values are MF_ERR_ARG).  The iteration is recorded
  * on the grid and *out (host) receives it and the running combination.
  * weights (device [n] FP64, may be NULL) receives every event weight.
  * Synchronises the stream.  Returns MF_WARN_NEWTON if any event missed the
@@ -278,10 +300,11 @@ mf_status mf_vegas_iterate(mf_process* proc, mf_grid* grid, uint64_t seed, int i
  *     per-CTA partial sums into the grid's totals buffer (asynchronous);
  *   mf_grid_totals exposes that device buffer, double[count] laid out as
  *     [0] sum w, [1] sum w^2, [2 + j*nbins + b] sum w^2 in bin b of dim j,
- *     then events passing cuts and Newton misses, so that the caller can
- *     all-reduce it (sum) over shards; the library owns it;
+ *     then events passing cuts and Newton misses, then (adaptive helicity
+ *     sampling) the sums of squared weights of the 2^(NG+1) configurations,
+ *     so that the caller can all-reduce it (sum) over shards; the library owns it;
  *   mf_vegas_finish turns the (summed) totals of n_total events into the
- *     estimate, refines the grid if asked, records the iteration and fills
+ *     estimate, refines as refine asks, records the iteration and fills
  *     *out like mf_vegas_iterate (synchronises the stream). */
 mf_status mf_vegas_accumulate(mf_process* proc, mf_grid* grid, uint64_t seed, int iter, int64_t first_event,
                               int64_t n, double* weights, void* stream);

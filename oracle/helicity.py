@@ -44,11 +44,13 @@ def _legs(proc):
     return gluons, parts.index("t"), parts.index("t~")
 
 
-def per_helicity(proc, p, algorithm="feynman", batch=256):
+def per_helicity(proc, p, algorithm="feynman", batch=256, amp=None):
     """Colour-summed |M_h|^2 of every helicity configuration, shape
     (2,) * n_ext + (N,) (axis i: particle i's helicity, index 0 = -1, 1 = +1),
-    not averaged.  algorithm: "feynman" (every diagram with explicit colour)
-    or "bg" (colour-ordered recursion with the trace-basis colour matrix)."""
+    not averaged.  algorithm: "feynman" (every diagram with explicit colour;
+    amp: another ``feynman.Amplitude`` of the process, e.g. with its diagrams
+    rooted at another leg, else the process's own) or "bg" (colour-ordered
+    recursion with the trace-basis colour matrix)."""
     p = np.asarray(p, dtype=np.float64)
     n, N = len(proc.particles), p.shape[0]
     out = np.empty((2,) * n + (N,))
@@ -61,10 +63,11 @@ def per_helicity(proc, p, algorithm="feynman", batch=256):
             J = bg.partial_amplitudes(q)                 # [sigma, (2,)*n, N]
             v = np.real(np.einsum("s...,st,t...->...", np.conj(J), bg.C, J))
         else:
+            a = proc.amp if amp is None else amp
             ext, k = proc.external(q)
-            K = proc.amp.amplitude_terms(ext, k)         # [term, (2,)*n, N]
+            K = a.amplitude_terms(ext, k)                # [term, (2,)*n, N]
             Kf = K.reshape(K.shape[0], -1, K.shape[-1])
-            Y = np.einsum("st,thn->shn", proc.amp.colour_matrix(), Kf)
+            Y = np.einsum("st,thn->shn", a.colour_matrix(), Kf)
             v = np.real(np.einsum("shn,shn->hn", np.conj(Kf), Y)).reshape((2,) * n + (q.shape[0],))
         out[..., s:s + batch] = v
     return out
@@ -83,10 +86,10 @@ def config_index(proc, hel, top):
     return idx + (int(top) << (n - 1 - t))
 
 
-def me2_helicity(proc, p, hel, algorithm="feynman"):
+def me2_helicity(proc, p, hel, algorithm="feynman", amp=None):
     """Per event e: (1/A) (|M_{h_e, t-}|^2 + |M_{h_e, t+}|^2), the configuration
     h_e of the gluons and the antitop, the top's two helicities summed."""
-    per = per_helicity(proc, p, algorithm)
+    per = per_helicity(proc, p, algorithm, amp=amp)
     flat = per.reshape(-1, per.shape[-1])
     e = np.arange(flat.shape[1])
     s = flat[config_index(proc, hel, 0), e] + flat[config_index(proc, hel, 1), e]

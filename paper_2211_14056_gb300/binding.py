@@ -75,6 +75,8 @@ EXPORTS = {
     "mf_matrix_element": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mf_matrix_element_hel": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mf_set_helicity_sampling": (C.c_int, [C.c_void_p, C.c_int]),
+    "mf_grid_helicity": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int]),
+    "mf_grid_set_helicity": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int]),
     "mf_uniforms": (C.c_int, [C.c_uint64, C.c_int, C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
     "mf_vegas_iterate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_int64, C.c_int,
                                    C.POINTER(Result), C.c_void_p, C.c_void_p]),
@@ -184,6 +186,20 @@ def _ptr(t, dtype, numel, name):
     return t.data_ptr()
 
 
+def _refine_bits(refine):
+    """refine as the C mask: True -> edges and helicity table (1 | 2), False ->
+    nothing, "edges" -> 1, "helicities" -> 2, or the mask itself."""
+    if refine is True:
+        return 3
+    if refine is False or refine is None:
+        return 0
+    if refine == "edges":
+        return 1
+    if refine == "helicities":
+        return 2
+    return int(refine)
+
+
 def _stream(stream):
     import torch
     if stream is None:
@@ -243,6 +259,7 @@ class Process:
         if ng is None:
             raise MFError(MF_ERR_UNSUPPORTED, "unknown process id")
         self.ngluons, self.n_ext = ng, ng + 2
+        self.process_id = process_id
         if masses is None:
             masses = [0.0] * 4 if process_id == MF_PROC_EE_MUMU else [0.0, 0.0, mt, mt] + [0.0] * (ng - 2)
         masses = (C.c_double * self.n_ext)(*masses)
@@ -324,15 +341,17 @@ class Process:
             _ptr(hel, torch.int32, n, "hel"), _ptr(me2, torch.float64, n, "me2"), _stream(stream)))
 
     def set_helicity_sampling(self, on):
-        """Iterations estimate |M|^2 from one drawn helicity configuration per
-        event (True) or sum the helicities (False, the default)."""
-        _check(load_library().mf_set_helicity_sampling(self._h, 1 if on else 0))
+        """Iterations estimate |M|^2 from one helicity configuration per event
+        drawn from the grid's table (True), also adapting that table as the
+        grid refines ("adaptive"), or sum the helicities (False, the default)."""
+        mode = 2 if on == "adaptive" else (1 if on else 0)
+        _check(load_library().mf_set_helicity_sampling(self._h, mode))
 
     def vegas_iterate(self, grid, seed, it, n, refine=True, weights=None, stream=None):
         import torch
         r = Result()
         st = _check(load_library().mf_vegas_iterate(
-            self._h, grid._h, seed, it, n, 1 if refine else 0, C.byref(r),
+            self._h, grid._h, seed, it, n, _refine_bits(refine), C.byref(r),
             _ptr(weights, torch.float64, n, "weights"), _stream(stream)))
         out = r.as_dict()
         out["status"] = st
@@ -384,7 +403,7 @@ class Process:
 
     def vegas_finish(self, grid, n_total, refine=True, stream=None):
         r = Result()
-        st = _check(load_library().mf_vegas_finish(self._h, grid._h, n_total, 1 if refine else 0, C.byref(r),
+        st = _check(load_library().mf_vegas_finish(self._h, grid._h, n_total, _refine_bits(refine), C.byref(r),
                                                    _stream(stream)))
         out = r.as_dict()
         out["status"] = st
@@ -396,6 +415,9 @@ class Grid:
 
     def __init__(self, proc, nbins=50):
         self.proc, self.nbins, self.ndim = proc, nbins, proc.ndim
+        # helicity configurations of the table (gluon-initiated processes: 2^(NG+1))
+        self.n_configs = (1 << (proc.n_ext - 1)) if proc.process_id in (MF_PROC_GG_TTX, MF_PROC_GG_TTXG,
+                                                                         MF_PROC_GG_TTXGG) else 0
         h = C.c_void_p()
         _check(load_library().mf_grid_create(proc._h, nbins, C.byref(h)))
         self._h = h
@@ -437,14 +459,32 @@ class Grid:
         _check(load_library().mf_grid_history(self._h, C.byref(n), I.ctypes.data, v.ctypes.data))
         return I[:n.value], v[:n.value]
 
+    def helicity(self):
+        """Probabilities of the helicity table (2^(NG+1) configurations), or
+        None for a process without one."""
+        import numpy as np
+        if self.n_configs == 0:
+            return None
+        out = np.empty(self.n_configs)
+        _check(load_library().mf_grid_helicity(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), self.n_configs))
+        return out
+
+    def set_helicity(self, prob):
+        import numpy as np
+        p = np.ascontiguousarray(prob, dtype=np.float64)
+        _check(load_library().mf_grid_set_helicity(self._h, p.ctypes.data_as(C.POINTER(C.c_double)), p.size))
+
     def checkpoint(self):
-        """The grid's whole state: edges and the recorded iterations."""
+        """The grid's whole state: edges, the helicity table and the recorded
+        iterations."""
         I, v = self.history()
-        return {"edges": self.get(), "I_k": I, "var_k": v}
+        return {"edges": self.get(), "I_k": I, "var_k": v, "helicity": self.helicity()}
 
     def restore(self, state):
         import numpy as np
         self.set(state["edges"])
+        if state.get("helicity") is not None:
+            self.set_helicity(state["helicity"])
         I = np.ascontiguousarray(state["I_k"], dtype=np.float64)
         v = np.ascontiguousarray(state["var_k"], dtype=np.float64)
         if I.shape != v.shape or I.ndim != 1:

@@ -345,7 +345,7 @@ mf_status mf_set_launch_shape(mf_process* p, int warps_per_cta, int* max_ctas_pe
 }
 
 mf_status mf_set_helicity_sampling(mf_process* p, int on) {
-  if (p == nullptr || (on != 0 && on != 1)) return fail(MF_ERR_ARG, "mf_set_helicity_sampling: need a process and on = 0 or 1");
+  if (p == nullptr || on < 0 || on > 2) return fail(MF_ERR_ARG, "mf_set_helicity_sampling: need a process and on = 0, 1 or 2");
   if (on && (p->kind != 0 || p->precision == MF_FP32_TC))
     return fail(MF_ERR_UNSUPPORTED, "mf_set_helicity_sampling: covers g g -> t t~ + gluons in MF_FP64 or MF_FP32");
   if (on && p->hel_me_ctas == 0) {
@@ -389,12 +389,24 @@ mf_status mf_grid_create(const mf_process* p, int nbins, mf_grid** out) {
   if (e == cudaSuccess) e = cudaMalloc(&g->d_edges, sizeof(double) * edges.size());
   if (e == cudaSuccess) e = cudaMalloc(&g->d_partials, sizeof(double) * nacc * g->max_blocks);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_counters, sizeof(unsigned long long) * 2 * g->max_blocks);
-  if (e == cudaSuccess) e = cudaMalloc(&g->d_totals, sizeof(double) * (nacc + 2));
+  // totals: the Vegas sums, the counters, then (adaptive helicity sampling)
+  // the configurations' sums of squared weights
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_totals, sizeof(double) * (nacc + 2 + kHelMaxConfigs));
   if (e == cudaSuccess)
     e = cudaMalloc(&g->d_records, record_bytes(p->precision == MF_FP64 ? 0 : 1, p->sp.n_final, g->ndim, g->chunk));
   if (e == cudaSuccess) e = cudaMalloc(&g->d_result, sizeof(double) * 8);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_wchunk, sizeof(double) * g->chunk);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_ucount, sizeof(unsigned long long) * 2);
+  if (e == cudaSuccess && p->kind == 0) {
+    // the helicity table: uniform thresholds over the 2^(NG+1) configurations
+    g->hel_n = 2 << p->ng;
+    std::vector<unsigned long long> T(g->hel_n + 1);
+    for (int h = 0; h <= g->hel_n; ++h) T[h] = (unsigned long long)h * (4294967296ull / g->hel_n);
+    e = cudaMalloc(&g->d_hel_T, sizeof(unsigned long long) * (g->hel_n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_hel_part, sizeof(double) * kHelMaxConfigs * g->max_blocks);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(g->d_hel_T, T.data(), sizeof(unsigned long long) * T.size(), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMallocHost(&g->h_result, sizeof(double) * 8);
   if (e == cudaSuccess) e = cudaMemcpy(g->d_edges, edges.data(), sizeof(double) * edges.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
@@ -416,6 +428,8 @@ mf_status mf_grid_destroy(mf_grid* g) {
   cudaFree(g->d_result);
   cudaFree(g->d_wchunk);
   cudaFree(g->d_ucount);
+  cudaFree(g->d_hel_T);
+  cudaFree(g->d_hel_part);
   cudaFreeHost(g->h_result);
   delete g;
   return MF_OK;
@@ -604,7 +618,8 @@ mf_status mf_vegas_accumulate(mf_process* p, mf_grid* g, uint64_t seed, int iter
     cudaError_t e;
     if (p->hel) {
       e = launch_chunk_hel(p->ng, prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed,
-                           iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk);
+                           iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk, g->d_hel_T,
+                           p->hel == 2 ? g->d_hel_part : nullptr);
       if (e != cudaSuccess) return cuda_fail(e, "mf_vegas_accumulate (helicity-sampled chunk kernels)");
       g_launches.fetch_add(2);
       continue;
@@ -622,6 +637,11 @@ mf_status mf_vegas_accumulate(mf_process* p, mf_grid* g, uint64_t seed, int iter
   MF_CUDA(launch_reduce(g->d_partials, g->d_counters, grid, g->ndim, g->nbins, g->d_totals, s),
           "mf_vegas_accumulate (reduce)");
   g_launches.fetch_add(1);
+  if (p->hel == 2) {
+    MF_CUDA(launch_hel_reduce(g->d_hel_part, grid, g->hel_n, g->d_totals + 2 + g->ndim * g->nbins + 2, s),
+            "mf_vegas_accumulate (helicity sums)");
+    g_launches.fetch_add(1);
+  }
   return MF_OK;
 }
 
@@ -652,7 +672,39 @@ mf_status mf_grid_profile_read(mf_grid* g, double* sample_ms, double* me_ms, int
 mf_status mf_grid_totals(mf_grid* g, double** totals, int* count) {
   if (g == nullptr || totals == nullptr || count == nullptr) return fail(MF_ERR_ARG, "mf_grid_totals: null argument");
   *totals = g->d_totals;
-  *count = 2 + g->ndim * g->nbins + 2;
+  *count = 2 + g->ndim * g->nbins + 2 + (g->proc->hel == 2 ? g->hel_n : 0);
+  return MF_OK;
+}
+
+mf_status mf_grid_helicity(const mf_grid* g, double* prob, int n) {
+  if (g == nullptr || prob == nullptr) return fail(MF_ERR_ARG, "mf_grid_helicity: null argument");
+  if (g->hel_n == 0) return fail(MF_ERR_UNSUPPORTED, "mf_grid_helicity: the process has no helicity table");
+  if (n != g->hel_n) return fail(MF_ERR_ARG, "mf_grid_helicity: n must be " + std::to_string(g->hel_n));
+  std::vector<unsigned long long> T(n + 1);
+  MF_CUDA(cudaMemcpy(T.data(), g->d_hel_T, sizeof(unsigned long long) * T.size(), cudaMemcpyDeviceToHost),
+          "mf_grid_helicity");
+  for (int h = 0; h < n; ++h) prob[h] = double(T[h + 1] - T[h]) * 2.3283064365386963e-10;   // 2^-32
+  return MF_OK;
+}
+
+mf_status mf_grid_set_helicity(mf_grid* g, const double* prob, int n) {
+  if (g == nullptr || prob == nullptr) return fail(MF_ERR_ARG, "mf_grid_set_helicity: null argument");
+  if (g->hel_n == 0) return fail(MF_ERR_UNSUPPORTED, "mf_grid_set_helicity: the process has no helicity table");
+  if (n != g->hel_n) return fail(MF_ERR_ARG, "mf_grid_set_helicity: n must be " + std::to_string(g->hel_n));
+  double sum = 0.0;
+  for (int h = 0; h < n; ++h) {
+    if (!(prob[h] > 0.0) || !std::isfinite(prob[h]))
+      return fail(MF_ERR_ARG, "mf_grid_set_helicity: every probability must be finite and > 0");
+    sum += prob[h];
+  }
+  if (std::fabs(sum - 1.0) > 1e-9) return fail(MF_ERR_ARG, "mf_grid_set_helicity: the probabilities must sum to 1");
+  std::vector<unsigned long long> T(n + 1);
+  hel_thresholds(prob, n, T.data());
+  for (int h = 0; h < n; ++h)
+    if (T[h + 1] <= T[h])
+      return fail(MF_ERR_ARG, "mf_grid_set_helicity: a probability below 2^-32 leaves its configuration undrawn");
+  MF_CUDA(cudaMemcpy(g->d_hel_T, T.data(), sizeof(unsigned long long) * T.size(), cudaMemcpyHostToDevice),
+          "mf_grid_set_helicity");
   return MF_OK;
 }
 
@@ -660,10 +712,16 @@ mf_status mf_vegas_finish(mf_process* p, mf_grid* g, int64_t n_total, int refine
   if (p == nullptr || g == nullptr || out == nullptr) return fail(MF_ERR_ARG, "mf_vegas_finish: null argument");
   if (g->proc != p) return fail(MF_ERR_ARG, "mf_vegas_finish: grid belongs to another process");
   if (n_total < 2) return fail(MF_ERR_ARG, "mf_vegas_finish: need at least 2 events");
+  if (refine < 0 || refine > 3) return fail(MF_ERR_ARG, "mf_vegas_finish: refine is a mask of 1 (edges) and 2 (helicity table)");
   cudaStream_t s = (cudaStream_t)stream;
-  MF_CUDA(launch_finish(g->d_totals, g->ndim, g->nbins, n_total, refine, g->d_edges, g->d_result, s),
+  MF_CUDA(launch_finish(g->d_totals, g->ndim, g->nbins, n_total, refine & 1, g->d_edges, g->d_result, s),
           "mf_vegas_finish (estimate)");
   g_launches.fetch_add(1);
+  if ((refine & 2) && p->hel == 2) {
+    MF_CUDA(launch_hel_refine(g->d_totals + 2 + g->ndim * g->nbins + 2, g->hel_n, g->d_hel_T, s),
+            "mf_vegas_finish (helicity table)");
+    g_launches.fetch_add(1);
+  }
   MF_CUDA(cudaMemcpyAsync(g->h_result, g->d_result, sizeof(double) * 6, cudaMemcpyDeviceToHost, s), "mf_vegas_finish (copy)");
   MF_CUDA(cudaStreamSynchronize(s), "mf_vegas_finish (sync)");
   return record_iteration(g, g->h_result, n_total, out);
@@ -708,7 +766,7 @@ mf_status mf_unweight(mf_process* p, mf_grid* g, uint64_t seed, int iter, int64_
     cudaError_t e;
     if (p->hel) {
       e = launch_chunk_hel(p->ng, prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed,
-                           iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s, nullptr);
+                           iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s, nullptr, g->d_hel_T, nullptr);
     } else switch (proc_key(p)) {
       case kUuxKey: e = launch_chunk_uux(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s, nullptr); break;
       case kEeKey: e = launch_chunk_ee(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s, nullptr); break;

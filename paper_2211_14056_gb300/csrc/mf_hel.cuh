@@ -212,13 +212,23 @@ __device__ __forceinline__ T hel_me2(const T (&p)[NG + 2][4], unsigned hel, unsi
   return part;
 }
 
-// The helicity configuration drawn for global event ev: the top NG + 1 bits
-// of word 0 of the third Philox stream (key as the Vegas uniforms', counter
-// (ev & 0xffffffff, ev >> 32, 1, 1)).
-template <int NG> __device__ __forceinline__ unsigned helicity_draw(uint64_t seed, int iter, uint64_t ev) {
+// The helicity stream's word of global event ev: word 0 of the third Philox
+// stream (key as the Vegas uniforms', counter (ev & 0xffffffff, ev >> 32, 1, 1)).
+__device__ __forceinline__ uint32_t helicity_word(uint64_t seed, int iter, uint64_t ev) {
   const uint2 key = make_uint2(uint32_t(seed), uint32_t(seed >> 32) ^ uint32_t(iter));
-  const uint4 w = philox4x32_10(make_uint4(uint32_t(ev), uint32_t(ev >> 32), 1u, 1u), key);
-  return w.x >> (31 - NG);
+  return philox4x32_10(make_uint4(uint32_t(ev), uint32_t(ev >> 32), 1u, 1u), key).x;
+}
+
+// The configuration drawn by word w0 from the thresholds T[0..H] (T[0] = 0,
+// T[H] = 2^32, non-decreasing): h = max{h : T[h] <= w0}, by bisection.  With
+// uniform thresholds this is the top NG + 1 bits of w0.
+template <int NG> __device__ __forceinline__ unsigned helicity_draw(uint32_t w0, const unsigned long long* T) {
+  constexpr int H = 2 << NG;
+  unsigned lo = 0;
+#pragma unroll
+  for (int step = H / 2; step > 0; step >>= 1)
+    if (T[lo + step] <= (unsigned long long)w0) lo += step;
+  return lo;
 }
 
 // ----------------------------------------------------------------------------
@@ -249,24 +259,33 @@ __global__ void __launch_bounds__(kThreads) k_matrix_element_hel(MeParams mp, in
   }
 }
 
-// Shared memory of k_me_acc_hel: the CTA's Vegas histogram and sums, then the
-// warps' events.
+// Shared memory of k_me_acc_hel: the CTA's Vegas histogram and sums, the
+// draw's thresholds and the per-configuration sums of squared weights, then
+// the warps' events.
+constexpr int kHelMaxConfigs = 32;
 template <int NG, typename T> struct HelAccLayout {
   __host__ __device__ static size_t al(size_t x) { return (x + 15) & ~size_t(15); }
   __host__ __device__ static size_t sums(int nacc) { return al(sizeof(double) * (nacc - 2)); }
-  __host__ __device__ static size_t warps(int nacc) { return al(sums(nacc) + sizeof(double) * 2); }
+  __host__ __device__ static size_t thr(int nacc) { return al(sums(nacc) + sizeof(double) * 2); }
+  __host__ __device__ static size_t hsq(int nacc) { return al(thr(nacc) + sizeof(unsigned long long) * (kHelMaxConfigs + 1)); }
+  __host__ __device__ static size_t warps(int nacc) { return al(hsq(nacc) + sizeof(double) * kHelMaxConfigs); }
   __host__ __device__ static size_t total(int nacc) { return warps(nacc) + HelMem<NG, T>::warp_bytes * kWarps; }
 };
 
 // |M|^2 estimates of the listed events of one record chunk with one sampled
-// helicity configuration each, weights w = 2^(NG+1) |M_h|^2 norm * prefactor,
-// Vegas sums (as k_me_acc).  The configuration of the chunk's event e is drawn
-// for global event first_event + e.
+// helicity configuration each, weights w = |M_h|^2 norm * prefactor / p_h,
+// p_h = (T[h+1] - T[h]) / 2^32 (2^(NG+1) |M_h|^2 ... with uniform
+// thresholds), and the Vegas sums (as k_me_acc).  The configuration of the
+// chunk's event e is drawn for global event first_event + e from the
+// thresholds hel_T[0..2^(NG+1)].  With hel_sq given, hel_sq[blockIdx.x * 32 + h]
+// receives (accumulate = 0) or adds (1) the CTA's sum of w^2 over the events
+// drawn in configuration h (the refinement's input).
 template <int NG, typename T>
 __global__ void __launch_bounds__(kThreads, 3)
     k_me_acc_hel(MeParams mp, int ndim, int nbins, RecordView<T> rec, int accumulate, double* __restrict__ partials,
                  unsigned long long* __restrict__ counters, double* __restrict__ w_out, uint64_t seed, int iter,
-                 int64_t first_event) {
+                 int64_t first_event, const unsigned long long* __restrict__ hel_T, double* __restrict__ hel_sq) {
+  constexpr int H = 2 << NG;
   using LY = HelAccLayout<NG, T>;
   constexpr int NEXT = NG + 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -275,11 +294,14 @@ __global__ void __launch_bounds__(kThreads, 3)
   double* sums = reinterpret_cast<double*>(smem_raw + LY::sums(nacc));
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int group = lane / kHelGroup, gl = lane % kHelGroup;
+  unsigned long long* thr = reinterpret_cast<unsigned long long*>(smem_raw + LY::thr(nacc));
+  double* hsq = reinterpret_cast<double*>(smem_raw + LY::hsq(nacc));
   unsigned char* em = smem_raw + LY::warps(nacc) + size_t(warp * kHelEPW + group) * HelMem<NG, T>::event_bytes;
   for (int i = t; i < ndim * nbins; i += kThreads) hist[i] = 0.0;
   if (t < 2) sums[t] = 0.0;
+  if (t <= H) thr[t] = hel_T[t];
+  if (t < H) hsq[t] = 0.0;
   const T mt = T(mp.mt), mw = T(mp.mw);
-  const double scale = mp.norm * double(2 << NG);
   const unsigned full = 0xffffffffu;
   const int64_t npass = rec.count[0];
   double s1 = 0.0, s2 = 0.0;
@@ -298,14 +320,16 @@ __global__ void __launch_bounds__(kThreads, 3)
     for (int i = 0; i < NG; ++i)
 #pragma unroll
       for (int c = 0; c < 4; ++c) p[2 + i][c] = rec.mom[int64_t(i * 4 + c) * rec.C + e];
-    const unsigned h = helicity_draw<NG>(seed, iter, uint64_t(first_event + e));
+    const unsigned h = helicity_draw<NG>(helicity_word(seed, iter, uint64_t(first_event + e)), thr);
     const T v = hel_me2<NG, T>(p, h, em, gl, mt, mw);
     if (ok) {
-      const double w = double(v) * scale * rec.pref[e];
+      // 1 / p_h = 2^32 / (T[h+1] - T[h]), exact for the uniform thresholds
+      const double w = double(v) * mp.norm * rec.pref[e] * (4294967296.0 / double(thr[h + 1] - thr[h]));
       if (gl == 0) {
         s1 += w;
         s2 += w * w;
         if (w_out != nullptr) w_out[e] = w;
+        if (hel_sq != nullptr) atomicAdd(&hsq[h], w * w);
       }
       for (int j = gl; j < ndim; j += kHelGroup)
         atomicAdd(&hist[j * nbins + rec.flag[int64_t(j) * rec.C + e]], w * w);
@@ -327,6 +351,10 @@ __global__ void __launch_bounds__(kThreads, 3)
     const unsigned long long c = blockIdx.x == 0 ? (unsigned long long)rec.count[t] : 0ull;
     counters[blockIdx.x * 2 + t] = (accumulate ? counters[blockIdx.x * 2 + t] : 0ull) + c;
   }
+  if (hel_sq != nullptr && t < H) {
+    double* d = hel_sq + int64_t(blockIdx.x) * kHelMaxConfigs + t;
+    *d = (accumulate ? *d : 0.0) + hsq[t];
+  }
 }
 
 // host-side helpers (mf_hel.cu), NG = 2, 3, 4; precision 0: FP64, 1: FP32
@@ -334,10 +362,20 @@ cudaError_t hel_me_config(int ng, int precision, size_t* smem, int* ctas_per_sm)
 cudaError_t launch_matrix_element_hel(int ng, int precision, const MeParams& mp, int64_t n, const double* mom,
                                       const int* hel, double* out, int grid, cudaStream_t s);
 cudaError_t hel_acc_config(int ng, int precision, int ndim, int nbins, size_t* smem, int* ctas_per_sm);
-// one record chunk: k_sample_rec, then k_me_acc_hel (ev: 3 events as launch_chunk)
+// one record chunk: k_sample_rec, then k_me_acc_hel (ev: 3 events as launch_chunk);
+// hel_T: the draw's thresholds (device), hel_sq: per-CTA sums of squared
+// weights by configuration, [grid][32] (device, may be null)
 cudaError_t launch_chunk_hel(int ng, int precision, const SampleParams& sp, const MeParams& mp, const double* edges,
                              int64_t first_event, int64_t n, int64_t C, void* rec_base, uint64_t seed, int iter,
                              int accumulate, double* partials, unsigned long long* counters, double* w_out, int grid,
-                             cudaStream_t s, cudaEvent_t* ev);
+                             cudaStream_t s, cudaEvent_t* ev, const unsigned long long* hel_T, double* hel_sq);
+// the configurations' sums of squared weights over the CTAs (fixed order) into
+// S[0..H-1], then (refine) the refined thresholds T[0..H]
+cudaError_t launch_hel_reduce(const double* hel_sq, int nblocks, int n_configs, double* S, cudaStream_t s);
+cudaError_t launch_hel_refine(const double* S, int n_configs, unsigned long long* T, cudaStream_t s);
+// thresholds of probabilities p[0..H-1] (host): T_h = floor(2^32 (p_0 + ... + p_{h-1})),
+// the partial sums added in order; T_0 = 0, T_H = 2^32
+void hel_thresholds(const double* p, int n_configs, unsigned long long* T);
+constexpr double kHelRefineFloor = 0.1;   // the share of the uniform probabilities kept by a refinement
 
 }  // namespace mf

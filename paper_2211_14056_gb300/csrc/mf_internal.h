@@ -33,7 +33,8 @@ struct mf_process {
   size_t me_smem = 0;
   int ctas_override = 0;
   int me_warps = 0;                // warps per CTA of the |M|^2 kernel (0: the default 4; mf_set_launch_shape)
-  int hel = 0;                     // 1: one sampled helicity configuration per event (mf_set_helicity_sampling)
+  int hel = 0;                     // helicity sampling (mf_set_helicity_sampling): 0 sum, 1 draw from the
+                                   // grid's table, 2 also accumulate the table's refinement input
   int hel_me_ctas = 0;             // CTAs per SM of k_matrix_element_hel (0: not queried yet)
   double g_s = 0.0, width = 0.0;   // strong coupling and top width of the descriptor
   int kind = 0;                    // 0: g g -> t t~ + gluons (ng = n_final), 1: u u~ -> t t~ g g,
@@ -50,6 +51,9 @@ struct mf_grid {
   int shape_warps = 0;         // launch shape whose occupancy shape_ctas holds (0: none yet)
   int shape_ctas = 0;
   int hel_ctas = 0;            // CTAs per SM of the helicity-sampled |M|^2 kernel (0: not queried yet)
+  int hel_n = 0;               // helicity configurations drawn from (2^(NG+1); 0: no helicity table)
+  unsigned long long* d_hel_T = nullptr;   // [hel_n + 1] the draw's thresholds (uniform at creation)
+  double* d_hel_part = nullptr;            // [max_blocks][32] per-CTA sums of squared weights by configuration
   size_t acc_smem = 0;
   int64_t chunk = 0;           // events per record chunk
   void* d_records = nullptr;   // per-event records of one chunk
