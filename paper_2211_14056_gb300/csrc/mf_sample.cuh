@@ -73,9 +73,17 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
+// m 2^-53 for the 53 bits m = (a << 21) | (b >> 11), assembled with integer
+// instructions (the conversion and multiply would issue on the FP64 pipe,
+// which bounds the sampler): with the leading one of m at bit p = 63 - clz(m),
+// the value is 1.f 2^(p - 53), i.e. exponent field 1033 - clz(m) and the bits
+// below the leading one as the fraction.  Exact, as the FP64 product is.
 __device__ __forceinline__ double unit53(uint32_t a, uint32_t b) {
-  const uint64_t bits = (uint64_t(a) << 21) | uint64_t(b >> 11);
-  return double(bits) * 0x1.0p-53;
+  const uint64_t m = (uint64_t(a) << 21) | uint64_t(b >> 11);
+  if (m == 0) return 0.0;
+  const int lz = __clzll((long long)m);   // 11 .. 63
+  const uint64_t frac = (m << (lz - 11)) & 0x000FFFFFFFFFFFFFull;
+  return __longlong_as_double((long long)((uint64_t(1033 - lz) << 52) | frac));
 }
 
 __device__ __forceinline__ void draw_uniforms(uint64_t seed, int iter, uint64_t ev, int ndim, double* y) {
@@ -319,9 +327,11 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
   // f(xi) = sum_{i=0,1} (sqrt(m^2 + xi^2 E_i^2) - m) + xi E_rest - (sqrt(s) - 2m), with
   // sqrt(m^2 + u^2) - m = u^2 / (sqrt(m^2 + u^2) + m): no cancellation near
   // threshold, so Newton reaches full relative precision in xi there too.
-  // Stop at |dxi| <= 1e-15 xi, or when the steps no longer shrink (the
-  // rounding floor, once below 1e-12 xi); 50 steps at most.  With dual
-  // numbers the converged xi is refined by one more step, which carries the
+  // Stop after a step |dxi| <= 1e-8 xi: f is convex with xi f''/f' =
+  // sum m^2 E^2 xi / r^3 / (sum xi E^2 / r + E_rest) <= 1 (m <= r), so a
+  // Newton step of relative size d from that close leaves a relative error
+  // below d^2 / 2 <= 5e-17; 50 steps at most.  With dual numbers the
+  // converged xi is refined by one more step, which carries the
   // implicit-function derivative d xi = -(df/dtheta) / f'.
   const D m2 = mtd * mtd;
   D E[kMaxExt];
@@ -336,7 +346,8 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
     }
   }
   excess = (shat - thr * thr) / (rs + thr);     // sqrt(s) - 2m
-  double xi0 = sqrt(fmax(value_of(excess) * value_of(rs + thr), 0.0)) / value_of(rs);
+  const D irs = D(1.0) / rs;                     // one FP64 division for the three uses below
+  double xi0 = sqrt(fmax(value_of(excess) * value_of(rs + thr), 0.0)) * value_of(irs);
   if constexpr (sizeof(value_of(K(0))) < sizeof(double)) {
     using KB = decltype(value_of(K(0)));
     const KB m2k = KB(value_of(m2)), mk = KB(value_of(mtd)), e0 = value_of(pm[0][0]), e1 = value_of(pm[1][0]),
@@ -358,7 +369,7 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
   {
     const double mv = value_of(mtd), m2v = value_of(m2), e0 = value_of(E[0]), e1 = value_of(E[1]);
     const double er = value_of(Erest), exv = value_of(excess);
-    double xi = xi0, prev = 0.0;
+    double xi = xi0;
 #pragma unroll 1
     for (int it = 0; it < 50; ++it) {
       const double u0 = xi * e0, u1 = xi * e1;
@@ -371,9 +382,7 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
       const double fp = fma(xi * fma(e0 * e0, r1, e1 * e1 * r0), ab * iden, er);
       const double dxi = f / fp;
       xi -= dxi;
-      const double ad = fabs(dxi);
-      if (ad <= 1e-15 * xi || (it > 0 && ad <= 1e-12 * xi && ad >= 0.5 * prev)) { converged = 1; break; }
-      prev = ad;
+      if (fabs(dxi) <= 1e-8 * xi) { converged = 1; break; }
     }
     xi0 = xi;
   }
@@ -404,14 +413,24 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
         ksum = ksum + ka;
         k2sum = k2sum + ka;
       }
-      out.p[2 + i][1] = K(xi * D(pm[i][1]));
-      out.p[2 + i][2] = K(xi * D(pm[i][2]));
-      out.p[2 + i][3] = K(xi * D(pm[i][3]));
+      if constexpr (std::is_same<K, float>::value && std::is_same<D, double>::value) {
+        // FP32 kinematics: the massless components are FP32; scaling them in
+        // FP32 (one more rounding, 1.2e-7 at most) saves two FP64-pipe
+        // conversions and a multiply per component
+        const float xf = float(xi);
+        out.p[2 + i][1] = xf * pm[i][1];
+        out.p[2 + i][2] = xf * pm[i][2];
+        out.p[2 + i][3] = xf * pm[i][3];
+      } else {
+        out.p[2 + i][1] = K(xi * D(pm[i][1]));
+        out.p[2 + i][2] = K(xi * D(pm[i][2]));
+        out.p[2 + i][3] = K(xi * D(pm[i][3]));
+      }
     }
   }
   D wm = D(1.0);
   {
-    const D r = ksum / rs;
+    const D r = ksum * irs;
     for (int i = 0; i < 2 * n - 3; ++i) wm = wm * r;
     wm = wm * (kprod * rs / k2sum);
   }
@@ -449,7 +468,7 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
   }
   out.pass = pass;
   out.newton_fail = converged ? 0 : 1;
-  out.prefactor = pass ? phi * wm * lum / (D(2.0) * shat) * (jac * kGeV2pb) : D(0.0);
+  out.prefactor = pass ? phi * wm * lum * (D(0.5) * irs * irs) * (jac * kGeV2pb) : D(0.0);
 }
 
 }  // namespace mf
