@@ -10,10 +10,19 @@ two helicities, and weighting by 2^(n_g + 1) estimates that sum without bias
 summing them; arXiv:2211.14056 sums them, so the uniform draw is a reading).
 The draw comes from the third Philox stream (``philox.helicity_draws``).
 
-Helicity index h: bit g (g = 0 .. n_g - 1, the process's gluons in their
-order: the two incoming, then the final ones) set means helicity +1 of that
-gluon; bit n_g set means antitop helicity +1.  Processes: a top pair plus
-gluons only.
+Helicity index h, for a top pair plus gluons: bit g (g = 0 .. n_g - 1, the
+process's gluons in their order: the two incoming, then the final ones) set
+means helicity +1 of that gluon; bit n_g set means antitop helicity +1; the
+top is summed.  For the two-quark-line subprocesses of p p -> t t~ g g (a
+reading: the bits follow the slots of the u u~ -> t t~ g g amplitude that
+the crossed channels fill, and each bit is the helicity of the physical
+particle in that slot): bit 0 the incoming quark of the amplitude's light
+line (the u, or for u~ g and g u~, whose amplitude is the charge conjugate,
+the incoming u~), bit 1 the other light fermion (the incoming u~, or the
+outgoing quark of the q g channels), bit 2 the heavy fermion in the antitop
+slot (the antitop, or the top for the charge-conjugate channels, where the
+antitop is the summed one), bits 3 and 4 the two gluons (for q g the
+incoming gluon first).
 
 Adapted draw (a reading: MadEvent's choice of helicities by their weight,
 written as a discrete Vegas dimension).  The configuration of an event is
@@ -36,12 +45,27 @@ import numpy as np
 from . import philox
 
 
-def _legs(proc):
+# the legs of bits 0..4 and the summed heavy fermion, per two-quark-line process
+_TWO_LINE_LEGS = {
+    "uux_ttxgg":  ([0, 1, 3, 4, 5], 2),
+    "uxu_ttxgg":  ([1, 0, 3, 4, 5], 2),
+    "ug_ttxgu":   ([0, 5, 3, 1, 4], 2),
+    "gu_ttxgu":   ([1, 5, 3, 0, 4], 2),
+    "uxg_ttxgux": ([0, 5, 2, 1, 4], 3),
+    "gux_ttxgux": ([1, 5, 2, 0, 4], 3),
+}
+
+
+def sampled_legs(proc):
+    """(legs of bits 0, 1, ..., the summed leg) of a process."""
+    if proc.name in _TWO_LINE_LEGS:
+        legs, summed = _TWO_LINE_LEGS[proc.name]
+        return list(legs), summed
     parts = list(proc.particles)
     gluons = [i for i, x in enumerate(parts) if x == "g"]
     if len(gluons) + 2 != len(parts) or "t" not in parts or "t~" not in parts:
-        raise ValueError("helicity sampling covers a top pair plus gluons")
-    return gluons, parts.index("t"), parts.index("t~")
+        raise ValueError("helicity sampling covers a top pair plus gluons and the p p -> t t~ g g channels")
+    return gluons + [parts.index("t~")], parts.index("t")
 
 
 def per_helicity(proc, p, algorithm="feynman", batch=256, amp=None):
@@ -75,20 +99,19 @@ def per_helicity(proc, p, algorithm="feynman", batch=256, amp=None):
 
 def config_index(proc, hel, top):
     """Flat index (particle 0 most significant) into the (2,)*n_ext axes of
-    the configuration h (gluons and antitop) with top helicity index `top`."""
-    gluons, t, tb = _legs(proc)
+    the configuration h with the summed heavy fermion's helicity index `top`."""
+    legs, summed = sampled_legs(proc)
     hel = np.asarray(hel, dtype=np.int64)
-    n, ng = len(proc.particles), len(gluons)
+    n = len(proc.particles)
     idx = np.zeros_like(hel)
-    for g, leg in enumerate(gluons):
-        idx += ((hel >> g) & 1) << (n - 1 - leg)
-    idx += ((hel >> ng) & 1) << (n - 1 - tb)
-    return idx + (int(top) << (n - 1 - t))
+    for b, leg in enumerate(legs):
+        idx += ((hel >> b) & 1) << (n - 1 - leg)
+    return idx + (int(top) << (n - 1 - summed))
 
 
 def me2_helicity(proc, p, hel, algorithm="feynman", amp=None):
-    """Per event e: (1/A) (|M_{h_e, t-}|^2 + |M_{h_e, t+}|^2), the configuration
-    h_e of the gluons and the antitop, the top's two helicities summed."""
+    """Per event e: (1/A) (|M_{h_e, -}|^2 + |M_{h_e, +}|^2), the configuration
+    h_e, the summed heavy fermion's two helicities added."""
     per = per_helicity(proc, p, algorithm, amp=amp)
     flat = per.reshape(-1, per.shape[-1])
     e = np.arange(flat.shape[1])
@@ -97,12 +120,12 @@ def me2_helicity(proc, p, hel, algorithm="feynman", amp=None):
 
 
 def n_configs(proc):
-    """2^(n_g + 1): the configurations the draw chooses from."""
-    return 2 ** (len(_legs(proc)[0]) + 1)
+    """2^(number of sampled legs): the configurations the draw chooses from."""
+    return 2 ** len(sampled_legs(proc)[0])
 
 
 def sampled_me2(proc, p, hel, algorithm="feynman"):
-    """The estimator 2^(n_g + 1) me2_helicity of each event."""
+    """The estimator n_configs me2_helicity of each event."""
     return n_configs(proc) * me2_helicity(proc, p, hel, algorithm)
 
 
@@ -112,7 +135,7 @@ def sampled_weights(setup, y, edges, seed, iteration, events):
     configuration drawn for each event (drawn for every event, used where the
     cuts pass).  Returns (w, bins, hel)."""
     p, wk, bins, cut = setup.kinematics(y, edges)
-    bits = len(_legs(setup.proc)[0]) + 1
+    bits = len(sampled_legs(setup.proc)[0])
     hel = philox.helicity_draws(seed, iteration, events, bits)
     algorithm = "bg" if setup.bg is not None else "feynman"
     w = np.zeros(y.shape[1])

@@ -255,3 +255,53 @@ def test_adapted_weights_with_uniform_thresholds_equal_the_sampled_weights():
     np.testing.assert_array_equal(hel_a, hel_s)
     np.testing.assert_allclose(w_a, w_s, rtol=1e-15)
     assert abs(S.sum() / np.sum(w_a ** 2) - 1) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# the two-quark-line subprocesses of p p -> t t~ g g
+
+TWO_LINE = ["uux_ttxgg", "uxu_ttxgg", "ug_ttxgu", "gu_ttxgu", "uxg_ttxgux", "gux_ttxgux"]
+
+
+def _two_line_points(N, seed):
+    return points(4, N, masses=[173.0, 173.0, 0.0, 0.0], seed=seed)
+
+
+@pytest.mark.parametrize("name", TWO_LINE)
+def test_two_line_configurations_sum_and_chirality(name):
+    """The 32 configurations sum to the helicity-summed |M|^2, and the massless
+    light line conserves chirality: an incoming quark and antiquark that
+    annihilate have opposite helicities (u u~, u~ u), a quark or antiquark
+    that passes through keeps its helicity (q g -> ... q), so half of the
+    configurations vanish exactly: bits 0 and 1 are the light line's two
+    fermions."""
+    proc = Process(name, wt=1.5)
+    assert oh.n_configs(proc) == 32
+    N = 2
+    p = _two_line_points(N, seed=18)
+    v = oh.me2_helicity(proc, np.repeat(p, 32, axis=0), np.tile(np.arange(32), N)).reshape(N, 32)
+    assert np.max(np.abs(v.sum(axis=1) / proc.me2(p) - 1)) < 1e-12
+    h = np.arange(32)
+    annihilate = name in ("uux_ttxgg", "uxu_ttxgg")
+    zero = ((h & 1) == ((h >> 1) & 1)) if annihilate else ((h & 1) != ((h >> 1) & 1))
+    assert np.all(v[:, zero] <= 1e-25 * v.sum(axis=1, keepdims=True))
+    assert np.all(v[:, ~zero].sum(axis=1) > 0)
+
+
+@pytest.mark.parametrize("a,b,swap", [("uxu_ttxgg", "uux_ttxgg", (0, 1)), ("gu_ttxgu", "ug_ttxgu", (0, 1)),
+                                      ("gux_ttxgux", "uxg_ttxgux", (0, 1)), ("uxg_ttxgux", "ug_ttxgu", (2, 3)),
+                                      ("gux_ttxgux", "gu_ttxgu", (2, 3))])
+def test_two_line_configurations_related_by_beams_and_charge_conjugation(a, b, swap):
+    """Per configuration, with the same bits: exchanging the beams relates the
+    channels whose quark comes from the other beam; exchanging the top and
+    antitop momenta relates a channel to its charge conjugate (the summed and
+    the sampled heavy fermion trade places, as the bits say)."""
+    pa, pb = Process(a, wt=1.5), Process(b, wt=1.5)
+    N = 4
+    p = _two_line_points(N, seed=19)
+    q = p.copy()
+    q[:, [swap[0], swap[1]]] = p[:, [swap[1], swap[0]]]
+    h = (np.arange(N) * 9 + 5) % 32
+    va, vb = oh.me2_helicity(pa, p, h), oh.me2_helicity(pb, q, h)
+    scale = np.maximum(va, vb) + 1e-30
+    assert np.max(np.abs(va - vb) / scale) < 1e-10
