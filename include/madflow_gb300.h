@@ -237,13 +237,24 @@ mf_status mf_matrix_element(mf_process* proc, int64_t n, const double* momenta, 
  * A configuration h of g g -> t t~ + gluons fixes the helicities of the NG
  * gluons and of the antitop: bit g (g < NG, the gluons in MadGraph order, the
  * two incoming first) set means gluon g has helicity +1, bit NG set means the
- * antitop has helicity +1; the top's two helicities are always summed.
+ * antitop has helicity +1; the top's two helicities are always summed.  For
+ * the two-quark-line processes (MF_PROC_UUX_TTXGG and MF_PROC_UXU_TTXGG ..
+ * MF_PROC_GUX_TTXGUX) h has 5 bits, those of the u u~ -> t t~ g g
+ * amplitude's slots that the channel fills, each the helicity of the
+ * physical particle there: bit 0 the incoming quark of the light line (the
+ * incoming antiquark for u~ g and g u~, whose amplitude is the charge
+ * conjugate), bit 1 the other light fermion (the incoming antiquark, or the
+ * outgoing (anti)quark of the q g channels), bit 2 the heavy fermion in the
+ * antitop slot (the antitop; the top for u~ g and g u~), bits 3 and 4 the
+ * gluons (the incoming one first in the q g channels); the other heavy
+ * fermion's two helicities are summed.
  *
  * mf_matrix_element_hel: me2[e] = (1 / average) (|M(h_e, t-)|^2 + |M(h_e, t+)|^2)
  * of event e at configuration hel[e] (int32 device array [n], only the low
  * NG + 1 bits are read), momenta as mf_matrix_element; summed over the
- * 2^(NG+1) configurations it is mf_matrix_element's value.  Covers the
- * gluon-initiated processes in MF_FP64 and MF_FP32 (else MF_ERR_UNSUPPORTED).
+ * 2^(NG+1) (32) configurations it is mf_matrix_element's value.  Covers the
+ * gluon-initiated and the two-quark-line processes in MF_FP64 and MF_FP32
+ * (else MF_ERR_UNSUPPORTED).
  *
  * mf_set_helicity_sampling(proc, on), on = 1: from then on the process's
  * iterations (mf_vegas_accumulate, mf_vegas_iterate, mf_unweight) estimate
@@ -253,7 +264,8 @@ mf_status mf_matrix_element(mf_process* proc, int64_t n, const double* momenta, 
  * (event & 0xffffffff, event >> 32, 1, 1), h = max{h : T_h <= w0} for the
  * table's thresholds 0 = T_0 <= ... <= T_H = 2^32 (H = 2^(NG+1)), and p_h =
  * (T_{h+1} - T_h) / 2^32.  A new grid's table is uniform (T_h = h 2^32 / H:
- * h is the top NG + 1 bits of w0, the weight 2^(NG+1) |M_h|^2).  on = 2 also
+ * h is the top log2(H) bits of w0, the weight H |M_h|^2; H = 2^(NG+1), or 32
+ * for the two-quark-line processes).  on = 2 also
  * sums, per configuration, the squared weights of the events that drew it
  * (appended to the totals of mf_grid_totals) so that mf_vegas_finish with
  * refine bit 2 refines the table: q_h = sqrt(p_h S_h), p'_h = 0.9 q_h / sum(q)
@@ -263,8 +275,8 @@ mf_status mf_matrix_element(mf_process* proc, int64_t n, const double* momenta, 
  * its cost per event smaller.  0 restores the sum.  The launch shape
  * (mf_set_launch_shape) applies to the summed kernel only.  Not covered while
  * it is on: mf_vegas_accumulate_static, mf_grad, mixed plans
- * (MF_ERR_UNSUPPORTED).  Errors: MF_ERR_ARG (on not 0 or 1), MF_ERR_UNSUPPORTED
- * (not a gluon-initiated process, or MF_FP32_TC). */
+ * (MF_ERR_UNSUPPORTED).  Errors: MF_ERR_ARG (on not 0, 1 or 2),
+ * MF_ERR_UNSUPPORTED (e+ e- -> mu+ mu-, or MF_FP32_TC). */
 mf_status mf_matrix_element_hel(mf_process* proc, int64_t n, const double* momenta, const int32_t* hel, double* me2,
                                 void* stream);
 mf_status mf_set_helicity_sampling(mf_process* proc, int on);
@@ -276,7 +288,7 @@ mf_status mf_set_helicity_sampling(mf_process* proc, int on);
  * returns exactly.  Synchronous.  Errors: MF_ERR_ARG (wrong n, a p_h that is
  * not finite and > 0 or that leaves its configuration no threshold step,
  * sum not 1 within 1e-9), MF_ERR_UNSUPPORTED (the process has no helicity
- * table: only the gluon-initiated processes do). */
+ * table: e+ e- -> mu+ mu- has none). */
 mf_status mf_grid_helicity(const mf_grid* grid, double* prob, int n);
 mf_status mf_grid_set_helicity(mf_grid* grid, const double* prob, int n);
 

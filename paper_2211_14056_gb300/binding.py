@@ -415,9 +415,14 @@ class Grid:
 
     def __init__(self, proc, nbins=50):
         self.proc, self.nbins, self.ndim = proc, nbins, proc.ndim
-        # helicity configurations of the table (gluon-initiated processes: 2^(NG+1))
-        self.n_configs = (1 << (proc.n_ext - 1)) if proc.process_id in (MF_PROC_GG_TTX, MF_PROC_GG_TTXG,
-                                                                         MF_PROC_GG_TTXGG) else 0
+        # helicity configurations of the table (gluon-initiated processes:
+        # 2^(NG+1); two-quark-line ones: 32; e+ e- -> mu+ mu-: none)
+        if proc.process_id in (MF_PROC_GG_TTX, MF_PROC_GG_TTXG, MF_PROC_GG_TTXGG):
+            self.n_configs = 1 << (proc.n_ext - 1)
+        elif proc.process_id == MF_PROC_EE_MUMU:
+            self.n_configs = 0
+        else:
+            self.n_configs = 32
         h = C.c_void_p()
         _check(load_library().mf_grid_create(proc._h, nbins, C.byref(h)))
         self._h = h

@@ -346,12 +346,15 @@ mf_status mf_set_launch_shape(mf_process* p, int warps_per_cta, int* max_ctas_pe
 
 mf_status mf_set_helicity_sampling(mf_process* p, int on) {
   if (p == nullptr || on < 0 || on > 2) return fail(MF_ERR_ARG, "mf_set_helicity_sampling: need a process and on = 0, 1 or 2");
-  if (on && (p->kind != 0 || p->precision == MF_FP32_TC))
-    return fail(MF_ERR_UNSUPPORTED, "mf_set_helicity_sampling: covers g g -> t t~ + gluons in MF_FP64 or MF_FP32");
+  if (on && (p->kind == 2 || p->precision == MF_FP32_TC))
+    return fail(MF_ERR_UNSUPPORTED, "mf_set_helicity_sampling: covers the g g and p p -> t t~ + jets processes "
+                                    "in MF_FP64 or MF_FP32");
   if (on && p->hel_me_ctas == 0) {
     size_t smem = 0;
     int ctas = 0;
-    MF_CUDA(hel_me_config(p->ng, p->precision == MF_FP64 ? 0 : 1, &smem, &ctas), "mf_set_helicity_sampling");
+    MF_CUDA(p->kind == 1 ? uux_hel_me_config(p->precision == MF_FP64 ? 0 : 1, &ctas)
+                         : hel_me_config(p->ng, p->precision == MF_FP64 ? 0 : 1, &smem, &ctas),
+            "mf_set_helicity_sampling");
     if (ctas < 1) return fail(MF_ERR_UNSUPPORTED, "mf_set_helicity_sampling: the kernel does not fit on an SM");
     p->hel_me_ctas = ctas;
   }
@@ -397,9 +400,10 @@ mf_status mf_grid_create(const mf_process* p, int nbins, mf_grid** out) {
   if (e == cudaSuccess) e = cudaMalloc(&g->d_result, sizeof(double) * 8);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_wchunk, sizeof(double) * g->chunk);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_ucount, sizeof(unsigned long long) * 2);
-  if (e == cudaSuccess && p->kind == 0) {
+  if (e == cudaSuccess && (p->kind == 0 || p->kind == 1)) {
     // the helicity table: uniform thresholds over the 2^(NG+1) configurations
-    g->hel_n = 2 << p->ng;
+    // of the gluon-initiated processes, the 32 of the two-quark-line ones
+    g->hel_n = p->kind == 0 ? 2 << p->ng : 32;
     std::vector<unsigned long long> T(g->hel_n + 1);
     for (int h = 0; h <= g->hel_n; ++h) T[h] = (unsigned long long)h * (4294967296ull / g->hel_n);
     e = cudaMalloc(&g->d_hel_T, sizeof(unsigned long long) * (g->hel_n + 1));
@@ -533,24 +537,30 @@ mf_status mf_matrix_element(mf_process* p, int64_t n, const double* momenta, dou
 mf_status mf_matrix_element_hel(mf_process* p, int64_t n, const double* momenta, const int32_t* hel, double* me2,
                                 void* stream) {
   if (p == nullptr || n < 0) return fail(MF_ERR_ARG, "mf_matrix_element_hel: bad argument");
-  if (p->kind != 0 || p->precision == MF_FP32_TC)
-    return fail(MF_ERR_UNSUPPORTED, "mf_matrix_element_hel: covers g g -> t t~ + gluons in MF_FP64 or MF_FP32");
+  if (p->kind == 2 || p->precision == MF_FP32_TC)
+    return fail(MF_ERR_UNSUPPORTED, "mf_matrix_element_hel: covers the g g and p p -> t t~ + jets processes "
+                                    "in MF_FP64 or MF_FP32");
   if (n == 0) return MF_OK;
   if (momenta == nullptr || hel == nullptr || me2 == nullptr) return fail(MF_ERR_ARG, "mf_matrix_element_hel: null buffer");
   const int prec = p->precision == MF_FP64 ? 0 : 1;
   if (p->hel_me_ctas == 0) {
     size_t smem = 0;
     int ctas = 0;
-    MF_CUDA(hel_me_config(p->ng, prec, &smem, &ctas), "mf_matrix_element_hel");
+    MF_CUDA(p->kind == 1 ? uux_hel_me_config(prec, &ctas) : hel_me_config(p->ng, prec, &smem, &ctas),
+            "mf_matrix_element_hel");
     if (ctas < 1) return fail(MF_ERR_UNSUPPORTED, "mf_matrix_element_hel: the kernel does not fit on an SM");
     p->hel_me_ctas = ctas;
   }
-  const int epb = kWarps * kHelEPW;   // events per CTA pass
+  const int epb = p->kind == 1 ? kThreads : kWarps * kHelEPW;   // events per CTA pass
   const int64_t need = (n + epb - 1) / epb;
   const int64_t cap = int64_t(p->sms) * effective_ctas(p, p->hel_me_ctas);
   const int grid = int(need < cap ? need : cap);
-  MF_CUDA(launch_matrix_element_hel(p->ng, prec, p->mp, n, momenta, hel, me2, grid, (cudaStream_t)stream),
-          "mf_matrix_element_hel");
+  if (p->kind == 1)
+    MF_CUDA(launch_matrix_element_uux_hel(prec, p->mp, n, momenta, hel, me2, grid, (cudaStream_t)stream),
+            "mf_matrix_element_hel");
+  else
+    MF_CUDA(launch_matrix_element_hel(p->ng, prec, p->mp, n, momenta, hel, me2, grid, (cudaStream_t)stream),
+            "mf_matrix_element_hel");
   g_launches.fetch_add(1);
   return MF_OK;
 }
@@ -561,7 +571,8 @@ static mf_status hel_grid_ctas(const mf_process* p, mf_grid* g) {
   if (g->hel_ctas > 0) return MF_OK;
   size_t smem = 0;
   int ctas = 0;
-  MF_CUDA(hel_acc_config(p->ng, p->precision == MF_FP64 ? 0 : 1, g->ndim, g->nbins, &smem, &ctas),
+  MF_CUDA(p->kind == 1 ? uux_hel_acc_config(p->precision == MF_FP64 ? 0 : 1, g->ndim, g->nbins, &ctas)
+                       : hel_acc_config(p->ng, p->precision == MF_FP64 ? 0 : 1, g->ndim, g->nbins, &smem, &ctas),
           "helicity-sampled kernel configuration");
   if (ctas < 1) return fail(MF_ERR_UNSUPPORTED, "the helicity-sampled kernel does not fit on an SM");
   g->hel_ctas = ctas;
@@ -617,9 +628,12 @@ mf_status mf_vegas_accumulate(mf_process* p, mf_grid* g, uint64_t seed, int iter
     cudaEvent_t* evk = g->profile ? &g->ev[size_t(3) * k] : nullptr;
     cudaError_t e;
     if (p->hel) {
-      e = launch_chunk_hel(p->ng, prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed,
-                           iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk, g->d_hel_T,
-                           p->hel == 2 ? g->d_hel_part : nullptr);
+      double* hsq = p->hel == 2 ? g->d_hel_part : nullptr;
+      e = p->kind == 1
+              ? launch_chunk_uux_hel(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed,
+                                     iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk, g->d_hel_T, hsq)
+              : launch_chunk_hel(p->ng, prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records,
+                                 seed, iter, k > 0, g->d_partials, g->d_counters, w, grid, s, evk, g->d_hel_T, hsq);
       if (e != cudaSuccess) return cuda_fail(e, "mf_vegas_accumulate (helicity-sampled chunk kernels)");
       g_launches.fetch_add(2);
       continue;
@@ -765,8 +779,13 @@ mf_status mf_unweight(mf_process* p, mf_grid* g, uint64_t seed, int iter, int64_
     // the chunk's weights: the iteration's kernels (their Vegas sums are not recorded)
     cudaError_t e;
     if (p->hel) {
-      e = launch_chunk_hel(p->ng, prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed,
-                           iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s, nullptr, g->d_hel_T, nullptr);
+      e = p->kind == 1
+              ? launch_chunk_uux_hel(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed,
+                                     iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s, nullptr, g->d_hel_T,
+                                     nullptr)
+              : launch_chunk_hel(p->ng, prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records,
+                                 seed, iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s, nullptr,
+                                 g->d_hel_T, nullptr);
     } else switch (proc_key(p)) {
       case kUuxKey: e = launch_chunk_uux(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s, nullptr); break;
       case kEeKey: e = launch_chunk_ee(prec, sp, p->mp, g->d_edges, first_event + done, m, g->chunk, g->d_records, seed, iter, 0, g->d_partials, g->d_counters, g->d_wchunk, grid, s, nullptr); break;

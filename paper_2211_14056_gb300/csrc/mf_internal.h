@@ -84,6 +84,16 @@ cudaError_t launch_chunk_uux(int precision, const SampleParams& sp, const MePara
                              int64_t first_event, int64_t n, int64_t C, void* rec_base, uint64_t seed, int iter,
                              int accumulate, double* partials, unsigned long long* counters, double* w_out, int grid,
                              cudaStream_t s, cudaEvent_t* ev);
+// helicity sampling for the two-quark-line channels (mf_kernels_uux.cu)
+cudaError_t uux_hel_me_config(int precision, int* ctas);
+cudaError_t uux_hel_acc_config(int precision, int ndim, int nbins, int* ctas);
+cudaError_t launch_matrix_element_uux_hel(int precision, const MeParams& mp, int64_t n, const double* mom,
+                                          const int* hel, double* out, int grid, cudaStream_t s);
+cudaError_t launch_chunk_uux_hel(int precision, const SampleParams& sp, const MeParams& mp, const double* edges,
+                                 int64_t first_event, int64_t n, int64_t C, void* rec_base, uint64_t seed, int iter,
+                                 int accumulate, double* partials, unsigned long long* counters, double* w_out,
+                                 int grid, cudaStream_t s, cudaEvent_t* ev, const unsigned long long* hel_T,
+                                 double* hel_sq);
 // e+ e- -> mu+ mu- (mf_kernels_ee.cu)
 cudaError_t ee_me_config(int precision, size_t* smem, int* ctas);
 cudaError_t ee_acc_config(int precision, int ndim, int nbins, size_t* smem, int* ctas);

@@ -16,7 +16,11 @@
   events' |M_h|^2 amplifies ~10^4-fold), and I_k, sigma_k follow from them;
 * unbiasedness: sampled and summed iterations agree within their errors;
 * edge cases: n = 0, one event, bits above NG + 1 ignored; the combinations
-  that are not covered raise.
+  that are not covered raise;
+* the two-quark-line channels of p p -> t t~ g g (one event per thread):
+  per configuration in FP64 against the oracle's Feynman diagrams, the 32
+  configurations summing to the summed kernel, a sampled iteration of
+  u u~ -> t t~ g g against the oracle, and sampled against summed estimates.
 """
 import numpy as np
 import pytest
@@ -51,9 +55,11 @@ def hel_spread(proc, p, h):
     from oracle.processes import outgoing_flavours
     ds = DiagramSet(outgoing_flavours(proc.name), root=list(proc.particles).index("t~"))
     rerooted = Amplitude(ds, proc.mass, proc.amp.widths, {"gs": proc.gs, "e": proc.ee})
-    v = np.stack([oh.me2_helicity(proc, p, h, "bg"), oh.me2_helicity(proc, _rotated(p), h, "bg"),
+    alg = "bg" if all(x in ("g", "t", "t~") for x in proc.particles) else "feynman"
+    v = np.stack([oh.me2_helicity(proc, p, h, alg), oh.me2_helicity(proc, _rotated(p), h, alg),
                   oh.me2_helicity(proc, p, h, "feynman"), oh.me2_helicity(proc, p, h, "feynman", amp=rerooted)])
-    return (v.max(axis=0) - v.min(axis=0)) / np.abs(v[0])
+    scale = np.maximum(np.abs(v[0]), 1e-300)
+    return (v.max(axis=0) - v.min(axis=0)) / scale
 
 
 def kin_spread(st, y, edges, p, h):
@@ -89,11 +95,12 @@ def kin_spread(st, y, edges, p, h):
                                np.longdouble(tau0), np.longdouble(S), *args)[3]
         dwk = dwk + np.asarray(np.abs(L64 / Lx - 1), dtype=np.float64)
     rng = np.random.default_rng(35)
-    m0 = oh.me2_helicity(st.proc, p, h, "bg")
+    alg = "bg" if st.bg is not None else "feynman"
+    m0 = oh.me2_helicity(st.proc, p, h, alg)
     dme = np.zeros(p.shape[0])
     for _ in range(2):
         pp = p * (1 + 2.0 ** -51 * rng.uniform(-1, 1, p.shape))
-        dme = np.maximum(dme, np.abs(oh.me2_helicity(st.proc, pp, h, "bg") / m0 - 1))
+        dme = np.maximum(dme, np.abs(oh.me2_helicity(st.proc, pp, h, alg) / m0 - 1))
     return dwk + dme
 
 
@@ -244,9 +251,9 @@ def test_edge_cases_and_errors(mf):
     ptc, _ = _proc(mf, "gg_ttxg_13tev", mf.MF_FP32_TC)
     with pytest.raises(mf.MFError):
         ptc.set_helicity_sampling(True)
-    puu, _ = _proc(mf, "uux_ttxgg_13tev", mf.MF_FP64)
+    pee, _ = _proc(mf, "epem_mupmum_100gev", mf.MF_FP64)
     with pytest.raises(mf.MFError):
-        puu.set_helicity_sampling(True)
+        pee.set_helicity_sampling(True)
     p.set_helicity_sampling(True)
     g = p.grid()
     with pytest.raises(mf.MFError):
@@ -369,8 +376,111 @@ def test_helicity_table_arguments_and_checkpoint(mf):
     g2 = p.grid()
     g2.restore(state)
     np.testing.assert_array_equal(g2.helicity(), g.helicity())
+    pe, _ = _proc(mf, "epem_mupmum_100gev", mf.MF_FP64)
+    ge = pe.grid()
+    assert ge.n_configs == 0 and ge.helicity() is None
     pu, _ = _proc(mf, "uux_ttxgg_13tev", mf.MF_FP64)
-    gu = pu.grid()
-    assert gu.n_configs == 0 and gu.helicity() is None
+    assert pu.grid().n_configs == 32
     with pytest.raises(mf.MFError):
         p.vegas_finish(g, 100, refine=4)
+
+
+
+# ---------------------------------------------------------------------------
+# the two-quark-line channels
+
+TWO_LINE = ["uux_ttxgg_13tev", "pp_ttxgg_qxq", "pp_ttxgg_qg", "pp_ttxgg_gq", "pp_ttxgg_qxg", "pp_ttxgg_gqx"]
+
+
+@pytest.mark.parametrize("name", TWO_LINE)
+def test_two_line_configuration_fp64_matches_oracle(mf, name):
+    """|M_h|^2 of given configurations (the synthetic luminosity's events; the
+    amplitude does not depend on it) against the oracle's Feynman diagrams,
+    and every configuration summed against the summed kernel (FP64, FP32)."""
+    p, w = _proc(mf, name, mf.MF_FP64, lumi=True)
+    st = _oracle_setup(w)
+    po = _cut_events(st, 12, 40)
+    hel = (np.arange(len(po)) * 11 + 7) % 32
+    ref = oh.me2_helicity(st.proc, po, hel)
+    got = _hel_me(p, po, hel)
+    nz = ref > 1e-20 * ref.max()
+    assert np.all(np.abs(got[~nz]) <= 1e-20 * ref.max())     # the light line's chirality zeros
+    assert_hel_parity(got[nz], ref[nz], st.proc, po[nz], hel[nz])
+    m = 6
+    rep = np.repeat(po[:m], 32, axis=0)
+    for prec, bar in ((mf.MF_FP64, 1e-12), (mf.MF_FP32, 1e-5)):
+        q, _ = _proc(mf, name, prec, lumi=True)
+        v = _hel_me(q, rep, np.tile(np.arange(32), m)).reshape(m, 32).sum(axis=1)
+        tot = torch.empty(m, dtype=torch.float64, device="cuda")
+        q.matrix_element(m, _aos_to_soa(po[:m]), tot)
+        torch.cuda.synchronize()
+        rel = np.abs(v / tot.cpu().numpy() - 1)
+        assert np.median(rel) < bar and rel.max() < 100 * bar
+
+
+def test_two_line_sampled_iteration_matches_oracle(mf):
+    name, n = "uux_ttxgg_13tev", 1201
+    p, w = _proc(mf, name, mf.MF_FP64)
+    p.set_helicity_sampling(True)
+    g = p.grid()
+    edges = random_grid(p.ndim, seed=36)
+    g.set(edges)
+    seed, it = 44, 3
+    wt = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    r = p.vegas_iterate(g, seed, it, n, refine=False, weights=wt)
+    st = _oracle_setup(w)
+    ev = np.arange(n, dtype=np.uint64)
+    y = oph.uniforms(seed, it, ev, st.ndim)
+    wo, bins, hel = oh.sampled_weights(st, y, edges, seed, it, ev)
+    wg = wt.cpu().numpy()
+    tiny = 1e-20 * np.abs(wo).max()
+    nz = np.flatnonzero(np.abs(wo) > tiny)
+    zero = np.flatnonzero(np.abs(wo) <= tiny)
+    assert np.all(np.abs(wg[zero]) <= tiny)                 # cuts and the chirality zeros
+    po = st.kinematics(y[:, nz], edges)[0]
+    allowed = np.zeros(n)
+    allowed[nz] = assert_hel_parity(wg[nz], wo[nz], st.proc, po, hel[nz], kin=(st, y[:, nz], edges))
+    sw, sw2, _ = ov.accumulate(wo, bins, edges.shape[1] - 1)
+    I, var = ov.estimate(sw, sw2, n)
+    dI = np.sum(allowed * np.abs(wo)) / n + 1e-12 * abs(I)
+    assert abs(r["I_k"] - I) <= dI
+
+
+@pytest.mark.parametrize("name", ["uux_ttxgg_13tev", "pp_ttxgg_qg"])
+def test_two_line_sampling_is_unbiased(mf, name):
+    """FP32, 2^18 events per iteration on a grid adapted by three summed
+    iterations, then frozen: four uniform-draw and four summed iterations
+    agree within their combined errors; the adapted draw likewise."""
+    from paper_2211_14056_gb300.workloads import PROCESS_IDS, WORKLOADS, process_kwargs
+    w = WORKLOADS[name]
+    pdf = mf.PDFSet.from_dict(__import__("paper_2211_14056_gb300.pdfgrid", fromlist=["x"]).synthetic_set()) \
+        if w["lumi"] == "pdf" else None
+    mk = lambda: mf.Process(PROCESS_IDS[w["process"]], **process_kwargs(w, mf.MF_FP32, pdf=pdf))
+    n = 1 << 18
+    pu = mk()
+    gu = pu.grid()
+    for it in range(3):
+        pu.vegas_iterate(gu, 70, it, n, refine=True)
+    edges = gu.get()
+    ps, pa = mk(), mk()
+    ps.set_helicity_sampling(True)
+    pa.set_helicity_sampling("adaptive")
+    gs, ga = ps.grid(), pa.grid()
+    ga.set(edges)
+    for it in range(3):
+        pa.vegas_iterate(ga, 71, it, n, refine="helicities")
+    est = {}
+    for label, p, g in (("sampled", ps, gs), ("adapted", pa, ga), ("summed", pu, gu)):
+        Is, Vs = [], []
+        for it in range(4):
+            g.set(edges)
+            r = p.vegas_iterate(g, 72, 10 + it, n, refine=False)
+            Is.append(r["I_k"])
+            Vs.append(r["sigma_k"] ** 2)
+        Is, Vs = np.array(Is), np.array(Vs)
+        est[label] = (np.sum(Is / Vs) / np.sum(1 / Vs), 1 / np.sqrt(np.sum(1 / Vs)), Vs.mean())
+    (I_s, s_s, v_s), (I_a, s_a, v_a), (I_u, s_u, v_u) = est["sampled"], est["adapted"], est["summed"]
+    print(f"{name}: sampled {I_s:.6g} +- {s_s:.2g}, adapted {I_a:.6g} +- {s_a:.2g}, summed {I_u:.6g} +- {s_u:.2g}; "
+          f"variance / summed: sampled {v_s / v_u:.2f}, adapted {v_a / v_u:.2f}")
+    assert abs(I_s - I_u) < 5 * np.hypot(s_s, s_u)
+    assert abs(I_a - I_u) < 5 * np.hypot(s_a, s_u)
