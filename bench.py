@@ -582,12 +582,52 @@ def _pp_leg(mf, torch, iters=5):
     total = sum(n)
     sig = sum(r["I_k"] for r in res)
     err = sum(r["sigma_k"] ** 2 for r in res) ** 0.5
+    hel = _pp_helicity(mf, torch, names, n, [g.get() for g in grids], pdf)
     return {"channels": names, "events": n, "ms_per_iteration": ms, "events_per_s": total / (ms * 1e-3),
+            "helicity_sampling": hel,
             "sigma_pb": sig, "sigma_err_pb": err,
             "channel_sigma_pb": {k: r["I_k"] for k, r in zip(names, res)},
             "autotune": {"candidates": cands, "ms": times, "best": cands[best]}, "precision": "FP32",
             "pdf": "synthetic tabulated set (9 flavours, 97 x 41 nodes), log-bicubic interpolation, "
                    "Q = sqrt(s_hat)/2"}
+
+
+def _pp_helicity(mf, torch, names, n, edges, pdf, rounds=3):
+    """The seven channels on their grids frozen after the mixed run, summed
+    against the adapted helicity draw (three table-refining iterations per
+    channel first): each round iterates every channel once (one channel
+    after another, CUDA events around the round); sigma is the sum of the
+    channels' estimates, its error their errors in quadrature, and the
+    efficiency gain (time x error^2) summed over the same for the draw."""
+    import statistics as stats
+    from paper_2211_14056_gb300.workloads import PP_CHANNELS, PROCESS_IDS, process_kwargs
+    out = {}
+    for label in ("summed", "adapted"):
+        procs = [mf.Process(PROCESS_IDS[PP_CHANNELS[k]["process"]], **process_kwargs(PP_CHANNELS[k], mf.MF_FP32, pdf=pdf))
+                 for k in names]
+        grids = [p.grid() for p in procs]
+        for p, g, e, k in zip(procs, grids, edges, names):
+            g.set(e)
+            if label == "adapted":
+                p.set_helicity_sampling("adaptive")
+                for it in range(3):
+                    p.vegas_iterate(g, 21, 100 + it, PP_CHANNELS[k]["events"], refine="helicities")
+        ts, sig, err = [], [], []
+        for r in range(rounds):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            res = [p.vegas_iterate(g, 22, 200 + r, m, refine=False) for p, g, m in zip(procs, grids, n)]
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            sig.append(sum(x["I_k"] for x in res))
+            err.append(sum(x["sigma_k"] ** 2 for x in res) ** 0.5)
+        out[label] = {"ms_per_round": stats.mean(ts), "events_per_s": sum(n) / (stats.mean(ts) * 1e-3),
+                      "sigma_pb": stats.mean(sig), "sigma_err_pb": stats.mean(err)}
+    u, a = out["summed"], out["adapted"]
+    out["efficiency_gain"] = (u["ms_per_round"] * u["sigma_err_pb"] ** 2) / (a["ms_per_round"] * a["sigma_err_pb"] ** 2)
+    return out
 
 
 def _pdf_leg(mf, torch, n=2 ** 26, reps=5):
