@@ -67,3 +67,42 @@ def test_shards_equal_one_iteration(mf, name, precision, sizes):
     assert r["sigma_k"] == pytest.approx(ref["sigma_k"], rel=1e-12)
     assert r["n_pass"] == ref["n_pass"] and r["n_newton_fail"] == ref["n_newton_fail"]
     np.testing.assert_allclose(grids[0].get(), ref_grid.get(), rtol=0, atol=1e-12)
+
+
+def test_adaptive_helicity_shards_equal_one_iteration(mf):
+    """With the adapted helicity draw the totals carry the per-configuration
+    sums of squared weights; summed over two shards they refine the table as
+    one iteration over all events does (thresholds equal, or a step of 2^-32
+    apart where the sums' rounding order differs)."""
+    from paper_2211_14056_gb300.sharding import totals_tensor
+    from paper_2211_14056_gb300.workloads import PROCESS_IDS, WORKLOADS, process_kwargs
+    w = WORKLOADS["gg_ttxgg_13tev"]
+    p = mf.Process(PROCESS_IDS[w["process"]], **process_kwargs(w, 1))
+    p.set_helicity_sampling("adaptive")
+    edges = random_grid(p.ndim, seed=24)
+    sizes = (30000, 20001)
+    n = sum(sizes)
+    ref_grid = p.grid()
+    ref_grid.set(edges)
+    w_ref = torch.empty(n, dtype=torch.float64, device="cuda")
+    ref = p.vegas_iterate(ref_grid, 14, 1, n, refine=True, weights=w_ref)
+    ref_tot = totals_tensor(ref_grid).clone()
+    grids, first = [], 0
+    w_sh = torch.empty(n, dtype=torch.float64, device="cuda")
+    for m in sizes:
+        g = p.grid()
+        g.set(edges)
+        p.vegas_accumulate(g, 14, 1, first, m, weights=w_sh[first:first + m])
+        grids.append(g)
+        first += m
+    summed = totals_tensor(grids[0])
+    assert summed.numel() == 2 + p.ndim * grids[0].nbins + 2 + 32
+    for g in grids[1:]:
+        summed += totals_tensor(g)
+    r = p.vegas_finish(grids[0], n, refine=True)
+    torch.cuda.synchronize()
+    assert torch.equal(w_sh, w_ref)
+    np.testing.assert_allclose(summed.cpu().numpy()[-32:], ref_tot.cpu().numpy()[-32:], rtol=1e-12)
+    assert r["I_k"] == pytest.approx(ref["I_k"], rel=1e-12)
+    assert np.max(np.abs(grids[0].helicity() - ref_grid.helicity())) <= 2.0 ** -32
+    assert ref_grid.helicity().max() > 1.5 / 32               # the table did adapt

@@ -12,7 +12,9 @@ weights, its uniforms of that stream and oracle.unweight:
     written events a subset of the kept ones;
   * FP32 weights give the FP64 decisions except where the FP32 weight lies on
     the other side of the threshold; the estimate w_max * sum(weights) / n
-    agrees with the iteration's I_k within its statistical error.
+    agrees with the iteration's I_k within its statistical error;
+  * with helicity sampling on, the weights unweighted are the sampled ones:
+    the kept set is the oracle's for its sampled weights.
 """
 import numpy as np
 import pytest
@@ -130,3 +132,28 @@ def test_arguments(mf):
         p.unweight(g, 1, 0, 0, 0, 1.0, 0)
     k, o, st = p.unweight(g, 1, 0, 0, 1000, 1e-30, 0)          # nothing written, all counted
     assert st == mf.MF_WARN_CAPACITY and k > 0
+
+
+def test_unweighting_with_helicity_sampling(mf):
+    from paper_2211_14056_gb300.workloads import oracle_cfg
+    from oracle import helicity as oh
+    p, w = _proc(mf, "gg_ttxg_13tev", mf.MF_FP64)
+    p.set_helicity_sampling(True)
+    g = p.grid()
+    edges = random_grid(p.ndim, seed=37)
+    g.set(edges)
+    seed, it, first, n = 38, 2, 500, 8000
+    st = oi.Setup(oracle_cfg(w), amplitude="bg")
+    events = np.arange(first, first + n, dtype=np.uint64)
+    y = oph.uniforms(seed, it, events, st.ndim)
+    wo, _, _ = oh.sampled_weights(st, y, edges, seed, it, events)
+    r = oph.unweight_uniforms(seed, it, events)
+    w_max = 0.4 * wo.max()
+    kept_o, weight_o = ou.unweight(wo, r, w_max)
+    ambiguous = np.abs(r * w_max - wo) <= 1e-10 * np.abs(wo)
+    assert not np.any(ambiguous & (wo > 0))
+    kept, over, status, ev, wt, mom = _run(p, g, seed, it, first, n, w_max, n)
+    assert status == mf.MF_OK and kept == int(kept_o.sum()) > 0
+    order = np.argsort(ev)
+    np.testing.assert_array_equal(ev[order], events[np.flatnonzero(kept_o)].astype(np.int64))
+    np.testing.assert_allclose(wt[order], weight_o[kept_o], rtol=1e-10)
