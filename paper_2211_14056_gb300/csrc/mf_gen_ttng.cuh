@@ -12,6 +12,7 @@ template <int NG> __device__ __forceinline__ const uint8_t* blk_mask();
 template <int NG> __device__ __forceinline__ const uint16_t* blk_off();
 template <int NG> struct Paths;
 template <int NG> struct ColourTC;
+template <int NG> struct ColourPerm;
 template <int NG> __device__ __forceinline__ const float* colour_frag_a();
 template <int NG> __device__ __forceinline__ const int* colour_num_dev();
 template <typename T> __device__ __forceinline__ V4<T> neg(const V4<T>& a) {
@@ -76,6 +77,21 @@ template <typename T> __device__ __forceinline__ T colour_form(const cplx<T> (&J
 template <> struct ColourTC<2> { static constexpr int MT = 1, KS = 1; };
 static __device__ const float kColourFragA2[128] = {16.f, -2.f, 0.f, 0.f, -2.f, 16.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 template <> __device__ __forceinline__ const float* colour_frag_a<2>() { return kColourFragA2; }
+// Half of J^dagger (D C) J / 2 for 2 orderings by the gluon relabelling
+// symmetry (gen_tables.colour_orbit_terms): F(J) + F(J o perm) = J^dagger (D C) J / 2.
+static __constant__ uint8_t kColourPerm2[2] = {1, 0};
+template <typename T>
+__device__ __forceinline__ T colour_form_orbit_2(const cplx<T> (&J)[2]) {
+  T s = T(0);
+  { cplx<T> y = T(8.0) * J[0];
+    y = rfma(T(-1.0), J[1], y);
+    s = fma(J[0].r, y.r, fma(J[0].i, y.i, s)); }
+  return s;
+}
+template <typename T> __device__ __forceinline__ T colour_form_orbit(const cplx<T> (&J)[2]) { return colour_form_orbit_2<T>(J); }
+template <> struct ColourPerm<2> {
+  static __device__ __forceinline__ int at(int a) { return kColourPerm2[a]; }
+};
 // colour matrix, 3 gluons: C = M / 9; orderings lexicographic
 static constexpr int kColourDen3 = 9;
 static const int kColourNum3[36] = {64, -8, -8, 1, 1, 10, -8, 64, 1, 10, -8, 1, -8, 1, 64, -8, 10, 1, 1, 10, -8, 64, 1, -8, 1, -8, 10, 1, 64, -8, 10, 1, 1, -8, -8, 64};
@@ -165,6 +181,33 @@ template <typename T> __device__ __forceinline__ T colour_form(const cplx<T> (&J
 template <> struct ColourTC<3> { static constexpr int MT = 1, KS = 1; };
 static __device__ const float kColourFragA3[128] = {64.f, -8.f, -8.f, 1.f, -8.f, 64.f, 1.f, 10.f, -8.f, 1.f, 64.f, -8.f, 1.f, 10.f, -8.f, 64.f, 1.f, -8.f, 10.f, 1.f, 10.f, 1.f, 1.f, -8.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f, 10.f, 0.f, 0.f, -8.f, 1.f, 0.f, 0.f, 10.f, 1.f, 0.f, 0.f, 1.f, -8.f, 0.f, 0.f, 64.f, -8.f, 0.f, 0.f, -8.f, 64.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 template <> __device__ __forceinline__ const float* colour_frag_a<3>() { return kColourFragA3; }
+// Half of J^dagger (D C) J / 2 for 6 orderings by the gluon relabelling
+// symmetry (gen_tables.colour_orbit_terms): F(J) + F(J o perm) = J^dagger (D C) J / 2.
+static __constant__ uint8_t kColourPerm3[6] = {2, 3, 0, 1, 5, 4};
+template <typename T>
+__device__ __forceinline__ T colour_form_orbit_3(const cplx<T> (&J)[6]) {
+  T s = T(0);
+  { cplx<T> y = T(32.0) * J[0];
+    y = rfma(T(-8.0), J[1], y);
+    y = rfma(T(-4.0), J[2], y);
+    y = rfma(T(1.0), J[3], y);
+    y = rfma(T(1.0), J[4], y);
+    y = rfma(T(10.0), J[5], y);
+    s = fma(J[0].r, y.r, fma(J[0].i, y.i, s)); }
+  { cplx<T> y = T(32.0) * J[1];
+    y = rfma(T(5.0), J[3], y);
+    y = rfma(T(-8.0), J[4], y);
+    y = rfma(T(1.0), J[5], y);
+    s = fma(J[1].r, y.r, fma(J[1].i, y.i, s)); }
+  { cplx<T> y = T(32.0) * J[4];
+    y = rfma(T(-4.0), J[5], y);
+    s = fma(J[4].r, y.r, fma(J[4].i, y.i, s)); }
+  return s;
+}
+template <typename T> __device__ __forceinline__ T colour_form_orbit(const cplx<T> (&J)[6]) { return colour_form_orbit_3<T>(J); }
+template <> struct ColourPerm<3> {
+  static __device__ __forceinline__ int at(int a) { return kColourPerm3[a]; }
+};
 // colour matrix, 4 gluons: C = M / 54; orderings lexicographic
 static constexpr int kColourDen4 = 54;
 static const int kColourNum4[576] = {512, -64, -64, 8, 8, 80, -64, 8, 8, -1, -1, -10, 8, -1, 80, -10, 71, 62, -1, -10, -10, 62, 62, -28, -64, 512, 8, 80, -64, 8, 8, -64, -1, -10, 8, -1, -1, -10, -10, 62, 62, -28, 8, -1, 80, -10, 71, 62, -64, 8, 512, -64, 80, 8, 8, -1, 80, -10, 71, 62, -64, 8, 8, -1, -1, -10, -10, -1, 62, -28, -10, 62, 8, 80, -64, 512, 8, -64, -1, -10, -10, 62, 62, -28, 8, -64, -1, -10, 8, -1, -1, 8, 71, 62, 80, -10, 8, -64, 80, 8, 512, -64, -1, 8, 71, 62, 80, -10, -10, -1, 62, -28, -10, 62, -64, 8, 8, -1, -1, -10, 80, 8, 8, -64, -64, 512, -10, -1, 62, -28, -10, 62, -1, 8, 71, 62, 80, -10, 8, -64, -1, -10, 8, -1, -64, 8, 8, -1, -1, -10, 512, -64, -64, 8, 8, 80, 80, -10, 8, -1, 62, 71, -10, 62, -1, -10, -28, 62, 8, -64, -1, -10, 8, -1, -64, 512, 8, 80, -64, 8, -10, 62, -1, -10, -28, 62, 80, -10, 8, -1, 62, 71, 8, -1, 80, -10, 71, 62, -64, 8, 512, -64, 80, 8, 8, -1, -64, 8, -10, -1, 62, -28, -10, -1, 62, -10, -1, -10, -10, 62, 62, -28, 8, 80, -64, 512, 8, -64, -1, -10, 8, -64, -1, 8, 71, 62, -1, 8, -10, 80, -1, 8, 71, 62, 80, -10, 8, -64, 80, 8, 512, -64, 62, -28, -10, -1, 62, -10, 8, -1, -64, 8, -10, -1, -10, -1, 62, -28, -10, 62, 80, 8, 8, -64, -64, 512, 71, 62, -1, 8, -10, 80, -1, -10, 8, -64, -1, 8, 8, -1, -64, 8, -10, -1, 80, -10, 8, -1, 62, 71, 512, -64, -64, 8, 8, 80, 62, -10, -28, 62, -1, -10, -1, -10, 8, -64, -1, 8, -10, 62, -1, -10, -28, 62, -64, 512, 8, 80, -64, 8, -10, 80, 62, 71, 8, -1, 80, -10, 8, -1, 62, 71, 8, -1, -64, 8, -10, -1, -64, 8, 512, -64, 80, 8, -28, 62, 62, -10, -10, -1, -10, 62, -1, -10, -28, 62, -1, -10, 8, -64, -1, 8, 8, 80, -64, 512, 8, -64, 62, 71, -10, 80, -1, 8, 71, 62, -1, 8, -10, 80, 62, -28, -10, -1, 62, -10, 8, -64, 80, 8, 512, -64, -1, 8, -10, -1, -64, 8, 62, -28, -10, -1, 62, -10, 71, 62, -1, 8, -10, 80, 80, 8, 8, -64, -64, 512, -10, -1, -1, 8, 8, -64, -1, 8, -10, -1, -64, 8, -10, 80, 62, 71, 8, -1, 62, -10, -28, 62, -1, -10, 512, -64, -64, 8, 8, 80, -10, -1, -1, 8, 8, -64, 62, -10, -28, 62, -1, -10, -10, 80, 62, 71, 8, -1, -64, 512, 8, 80, -64, 8, -10, 80, 62, 71, 8, -1, -1, 8, -10, -1, -64, 8, -28, 62, 62, -10, -10, -1, -64, 8, 512, -64, 80, 8, 62, -10, -28, 62, -1, -10, -10, -1, -1, 8, 8, -64, 62, 71, -10, 80, -1, 8, 8, 80, -64, 512, 8, -64, 62, 71, -10, 80, -1, 8, -28, 62, 62, -10, -10, -1, -1, 8, -10, -1, -64, 8, 8, -64, 80, 8, 512, -64, -28, 62, 62, -10, -10, -1, 62, 71, -10, 80, -1, 8, -10, -1, -1, 8, 8, -64, 80, 8, 8, -64, -64, 512};
@@ -564,4 +607,184 @@ template <typename T> __device__ __forceinline__ T colour_form(const cplx<T> (&J
 template <> struct ColourTC<4> { static constexpr int MT = 2, KS = 3; };
 static __device__ const float kColourFragA4[768] = {512.f, -64.f, -64.f, 8.f, -64.f, 512.f, 8.f, 80.f, -64.f, 8.f, 512.f, -64.f, 8.f, 80.f, -64.f, 512.f, 8.f, -64.f, 80.f, 8.f, 80.f, 8.f, 8.f, -64.f, -64.f, 8.f, 8.f, -1.f, 8.f, -64.f, -1.f, -10.f, 8.f, -1.f, 80.f, -10.f, -1.f, -10.f, -10.f, 62.f, -1.f, 8.f, 71.f, 62.f, -10.f, -1.f, 62.f, -28.f, 8.f, -1.f, -64.f, 8.f, -1.f, -10.f, 8.f, -64.f, 80.f, -10.f, 8.f, -1.f, -10.f, 62.f, -1.f, -10.f, 8.f, 80.f, -64.f, 8.f, -64.f, 8.f, 8.f, -64.f, 80.f, 8.f, 8.f, -1.f, 8.f, -64.f, -1.f, -10.f, 512.f, -64.f, -1.f, 8.f, -64.f, 512.f, -10.f, -1.f, -1.f, -10.f, 512.f, -64.f, 8.f, -1.f, -64.f, 512.f, 71.f, 62.f, -64.f, 8.f, 62.f, -28.f, 8.f, 80.f, 80.f, -10.f, 8.f, -64.f, -10.f, 62.f, 80.f, 8.f, -10.f, -1.f, 80.f, -10.f, -1.f, 8.f, -10.f, 62.f, 62.f, 71.f, 8.f, -1.f, -28.f, 62.f, -1.f, -10.f, 8.f, -1.f, -1.f, -10.f, -1.f, -10.f, 8.f, -1.f, 80.f, -10.f, 71.f, 62.f, -10.f, 62.f, 62.f, -28.f, 71.f, 62.f, 80.f, -10.f, 62.f, -28.f, -10.f, 62.f, -64.f, 8.f, 8.f, 80.f, 8.f, 80.f, -64.f, 8.f, 512.f, -64.f, 80.f, 8.f, -64.f, 512.f, 8.f, -64.f, 80.f, 8.f, 512.f, -64.f, 8.f, -64.f, -64.f, 512.f, 8.f, -1.f, 62.f, 71.f, -1.f, -10.f, -28.f, 62.f, -64.f, 8.f, -10.f, -1.f, 8.f, -64.f, -1.f, 8.f, 8.f, -1.f, 80.f, -10.f, -1.f, -10.f, -10.f, 62.f, -64.f, 8.f, 8.f, -1.f, 8.f, -64.f, -1.f, -10.f, -10.f, -1.f, 62.f, -28.f, -1.f, 8.f, 71.f, 62.f, 80.f, -10.f, 8.f, -1.f, -10.f, 62.f, -1.f, -10.f, 8.f, -1.f, -64.f, 8.f, -1.f, -10.f, 8.f, -64.f, 62.f, -28.f, -10.f, -1.f, 71.f, 62.f, -1.f, 8.f, 512.f, -64.f, -64.f, 8.f, -64.f, 512.f, 8.f, 80.f, -64.f, 8.f, 512.f, -64.f, 8.f, 80.f, -64.f, 512.f, 71.f, 62.f, -1.f, -10.f, 62.f, -28.f, 8.f, -1.f, -1.f, -10.f, -10.f, -1.f, 8.f, -1.f, -1.f, 8.f, -10.f, 62.f, -64.f, 8.f, 80.f, -10.f, 8.f, -64.f, 62.f, 71.f, -10.f, 62.f, -28.f, 62.f, 80.f, -10.f, -10.f, -1.f, 62.f, -28.f, -1.f, 8.f, 71.f, 62.f, 62.f, -10.f, 8.f, -1.f, -10.f, 80.f, -1.f, -10.f, 8.f, 80.f, 62.f, -10.f, -64.f, 8.f, -10.f, 80.f, 80.f, 8.f, -28.f, 62.f, 8.f, -64.f, 62.f, 71.f, -10.f, 62.f, 62.f, -28.f, 80.f, -10.f, 71.f, 62.f, 62.f, -28.f, -10.f, 62.f, 71.f, 62.f, 80.f, -10.f, 8.f, -1.f, -1.f, -10.f, -1.f, -10.f, 8.f, -1.f, -1.f, -10.f, -28.f, 62.f, 8.f, -1.f, 62.f, 71.f, -10.f, -1.f, 62.f, -10.f, -1.f, 8.f, -10.f, 80.f, -64.f, 8.f, -10.f, -1.f, 8.f, -64.f, -1.f, 8.f, -28.f, 62.f, -1.f, -10.f, 62.f, 71.f, 8.f, -1.f, 62.f, -10.f, -10.f, -1.f, -10.f, 80.f, -1.f, 8.f, 71.f, 62.f, -1.f, 8.f, 62.f, -28.f, -10.f, -1.f, -1.f, 8.f, -10.f, -1.f, -10.f, -1.f, -1.f, 8.f, -10.f, 80.f, 62.f, 71.f, 62.f, -10.f, -28.f, 62.f, 62.f, 71.f, -10.f, 80.f, -28.f, 62.f, 62.f, -10.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -10.f, 80.f, 62.f, -28.f, 62.f, -10.f, 71.f, 62.f, -64.f, 8.f, -10.f, 80.f, 8.f, -64.f, 62.f, -10.f, 8.f, -1.f, -1.f, 8.f, -1.f, -10.f, -10.f, -1.f, -1.f, 8.f, -28.f, 62.f, -10.f, -1.f, 62.f, 71.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -10.f, -1.f, 62.f, -10.f, -1.f, 8.f, -10.f, 80.f, 62.f, 71.f, 8.f, -1.f, -28.f, 62.f, -1.f, -10.f, -10.f, -1.f, -64.f, 8.f, -1.f, 8.f, 8.f, -64.f, 62.f, -10.f, -10.f, -1.f, -10.f, 80.f, -1.f, 8.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 8.f, -64.f, 80.f, 8.f, 80.f, 8.f, 8.f, -64.f, 62.f, -10.f, -28.f, 62.f, -10.f, 80.f, 62.f, 71.f, -28.f, 62.f, 62.f, -10.f, 62.f, 71.f, -10.f, 80.f, -1.f, 8.f, -10.f, -1.f, -10.f, -1.f, -1.f, 8.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 512.f, -64.f, -1.f, 8.f, -64.f, 512.f, -10.f, -1.f, -1.f, -10.f, 512.f, -64.f, 8.f, -1.f, -64.f, 512.f, -10.f, -1.f, -64.f, 8.f, -1.f, 8.f, 8.f, 80.f, -64.f, 8.f, 8.f, -64.f, 8.f, -64.f, 80.f, 8.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -10.f, -1.f, -64.f, 8.f, -1.f, 8.f, 8.f, -64.f, -64.f, 8.f, 8.f, 80.f, 8.f, 80.f, -64.f, 8.f, 512.f, -64.f, 80.f, 8.f, -64.f, 512.f, 8.f, -64.f, 80.f, 8.f, 512.f, -64.f, 8.f, -64.f, -64.f, 512.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 template <> __device__ __forceinline__ const float* colour_frag_a<4>() { return kColourFragA4; }
+// Half of J^dagger (D C) J / 2 for 24 orderings by the gluon relabelling
+// symmetry (gen_tables.colour_orbit_terms): F(J) + F(J o perm) = J^dagger (D C) J / 2.
+static __constant__ uint8_t kColourPerm4[24] = {7, 6, 10, 11, 8, 9, 1, 0, 4, 5, 2, 3, 20, 21, 18, 19, 23, 22, 14, 15, 12, 13, 17, 16};
+template <typename T>
+__device__ __forceinline__ T colour_form_orbit_4(const cplx<T> (&J)[24]) {
+  T s = T(0);
+  { cplx<T> y = T(256.0) * J[0];
+    y = rfma(T(-64.0), J[1], y);
+    y = rfma(T(-64.0), J[2], y);
+    y = rfma(T(8.0), J[3], y);
+    y = rfma(T(8.0), J[4], y);
+    y = rfma(T(80.0), J[5], y);
+    y = rfma(T(-64.0), J[6], y);
+    y = rfma(T(4.0), J[7], y);
+    y = rfma(T(8.0), J[8], y);
+    y = rfma(T(-1.0), J[9], y);
+    y = rfma(T(-1.0), J[10], y);
+    y = rfma(T(-10.0), J[11], y);
+    y = rfma(T(8.0), J[12], y);
+    y = rfma(T(-1.0), J[13], y);
+    y = rfma(T(80.0), J[14], y);
+    y = rfma(T(-10.0), J[15], y);
+    y = rfma(T(71.0), J[16], y);
+    y = rfma(T(62.0), J[17], y);
+    y = rfma(T(-1.0), J[18], y);
+    y = rfma(T(-10.0), J[19], y);
+    y = rfma(T(-10.0), J[20], y);
+    y = rfma(T(62.0), J[21], y);
+    y = rfma(T(62.0), J[22], y);
+    y = rfma(T(-28.0), J[23], y);
+    s = fma(J[0].r, y.r, fma(J[0].i, y.i, s)); }
+  { cplx<T> y = T(256.0) * J[1];
+    y = rfma(T(8.0), J[2], y);
+    y = rfma(T(80.0), J[3], y);
+    y = rfma(T(-64.0), J[4], y);
+    y = rfma(T(8.0), J[5], y);
+    y = rfma(T(4.0), J[6], y);
+    y = rfma(T(-1.0), J[8], y);
+    y = rfma(T(-10.0), J[9], y);
+    y = rfma(T(8.0), J[10], y);
+    y = rfma(T(-1.0), J[11], y);
+    y = rfma(T(-1.0), J[12], y);
+    y = rfma(T(-10.0), J[13], y);
+    y = rfma(T(-10.0), J[14], y);
+    y = rfma(T(62.0), J[15], y);
+    y = rfma(T(62.0), J[16], y);
+    y = rfma(T(-28.0), J[17], y);
+    y = rfma(T(8.0), J[18], y);
+    y = rfma(T(-1.0), J[19], y);
+    y = rfma(T(80.0), J[20], y);
+    y = rfma(T(-10.0), J[21], y);
+    y = rfma(T(71.0), J[22], y);
+    y = rfma(T(62.0), J[23], y);
+    s = fma(J[1].r, y.r, fma(J[1].i, y.i, s)); }
+  { cplx<T> y = T(256.0) * J[2];
+    y = rfma(T(-64.0), J[3], y);
+    y = rfma(T(80.0), J[4], y);
+    y = rfma(T(8.0), J[5], y);
+    y = rfma(T(80.0), J[8], y);
+    y = rfma(T(-10.0), J[9], y);
+    y = rfma(T(35.5), J[10], y);
+    y = rfma(T(62.0), J[11], y);
+    y = rfma(T(-64.0), J[12], y);
+    y = rfma(T(8.0), J[13], y);
+    y = rfma(T(8.0), J[14], y);
+    y = rfma(T(-1.0), J[15], y);
+    y = rfma(T(-1.0), J[16], y);
+    y = rfma(T(-10.0), J[17], y);
+    y = rfma(T(-10.0), J[18], y);
+    y = rfma(T(-1.0), J[19], y);
+    y = rfma(T(62.0), J[20], y);
+    y = rfma(T(-28.0), J[21], y);
+    y = rfma(T(-10.0), J[22], y);
+    y = rfma(T(62.0), J[23], y);
+    s = fma(J[2].r, y.r, fma(J[2].i, y.i, s)); }
+  { cplx<T> y = T(256.0) * J[3];
+    y = rfma(T(8.0), J[4], y);
+    y = rfma(T(-64.0), J[5], y);
+    y = rfma(T(-10.0), J[8], y);
+    y = rfma(T(62.0), J[9], y);
+    y = rfma(T(-14.0), J[11], y);
+    y = rfma(T(8.0), J[12], y);
+    y = rfma(T(-64.0), J[13], y);
+    y = rfma(T(-1.0), J[14], y);
+    y = rfma(T(-10.0), J[15], y);
+    y = rfma(T(8.0), J[16], y);
+    y = rfma(T(-1.0), J[17], y);
+    y = rfma(T(-1.0), J[18], y);
+    y = rfma(T(8.0), J[19], y);
+    y = rfma(T(71.0), J[20], y);
+    y = rfma(T(62.0), J[21], y);
+    y = rfma(T(80.0), J[22], y);
+    y = rfma(T(-10.0), J[23], y);
+    s = fma(J[3].r, y.r, fma(J[3].i, y.i, s)); }
+  { cplx<T> y = T(256.0) * J[4];
+    y = rfma(T(-64.0), J[5], y);
+    y = rfma(T(35.5), J[8], y);
+    y = rfma(T(62.0), J[9], y);
+    y = rfma(T(-10.0), J[12], y);
+    y = rfma(T(-1.0), J[13], y);
+    y = rfma(T(62.0), J[14], y);
+    y = rfma(T(-28.0), J[15], y);
+    y = rfma(T(-10.0), J[16], y);
+    y = rfma(T(62.0), J[17], y);
+    y = rfma(T(-64.0), J[18], y);
+    y = rfma(T(8.0), J[19], y);
+    y = rfma(T(8.0), J[20], y);
+    y = rfma(T(-1.0), J[21], y);
+    y = rfma(T(-1.0), J[22], y);
+    y = rfma(T(-10.0), J[23], y);
+    s = fma(J[4].r, y.r, fma(J[4].i, y.i, s)); }
+  { cplx<T> y = T(256.0) * J[5];
+    y = rfma(T(-14.0), J[9], y);
+    y = rfma(T(-1.0), J[12], y);
+    y = rfma(T(8.0), J[13], y);
+    y = rfma(T(71.0), J[14], y);
+    y = rfma(T(62.0), J[15], y);
+    y = rfma(T(80.0), J[16], y);
+    y = rfma(T(-10.0), J[17], y);
+    y = rfma(T(8.0), J[18], y);
+    y = rfma(T(-64.0), J[19], y);
+    y = rfma(T(-1.0), J[20], y);
+    y = rfma(T(-10.0), J[21], y);
+    y = rfma(T(8.0), J[22], y);
+    y = rfma(T(-1.0), J[23], y);
+    s = fma(J[5].r, y.r, fma(J[5].i, y.i, s)); }
+  { cplx<T> y = T(256.0) * J[12];
+    y = rfma(T(-64.0), J[13], y);
+    y = rfma(T(-64.0), J[14], y);
+    y = rfma(T(8.0), J[15], y);
+    y = rfma(T(8.0), J[16], y);
+    y = rfma(T(80.0), J[17], y);
+    y = rfma(T(62.0), J[18], y);
+    y = rfma(T(-10.0), J[19], y);
+    y = rfma(T(-14.0), J[20], y);
+    y = rfma(T(62.0), J[21], y);
+    y = rfma(T(-1.0), J[22], y);
+    y = rfma(T(-10.0), J[23], y);
+    s = fma(J[12].r, y.r, fma(J[12].i, y.i, s)); }
+  { cplx<T> y = T(256.0) * J[13];
+    y = rfma(T(8.0), J[14], y);
+    y = rfma(T(80.0), J[15], y);
+    y = rfma(T(-64.0), J[16], y);
+    y = rfma(T(8.0), J[17], y);
+    y = rfma(T(-10.0), J[18], y);
+    y = rfma(T(80.0), J[19], y);
+    y = rfma(T(35.5), J[21], y);
+    y = rfma(T(8.0), J[22], y);
+    y = rfma(T(-1.0), J[23], y);
+    s = fma(J[13].r, y.r, fma(J[13].i, y.i, s)); }
+  { cplx<T> y = T(256.0) * J[14];
+    y = rfma(T(-64.0), J[15], y);
+    y = rfma(T(80.0), J[16], y);
+    y = rfma(T(8.0), J[17], y);
+    y = rfma(T(-14.0), J[18], y);
+    y = rfma(T(62.0), J[19], y);
+    y = rfma(T(-10.0), J[22], y);
+    y = rfma(T(-1.0), J[23], y);
+    s = fma(J[14].r, y.r, fma(J[14].i, y.i, s)); }
+  { cplx<T> y = T(256.0) * J[15];
+    y = rfma(T(8.0), J[16], y);
+    y = rfma(T(-64.0), J[17], y);
+    y = rfma(T(35.5), J[19], y);
+    y = rfma(T(-1.0), J[22], y);
+    y = rfma(T(8.0), J[23], y);
+    s = fma(J[15].r, y.r, fma(J[15].i, y.i, s)); }
+  { cplx<T> y = T(256.0) * J[16];
+    y = rfma(T(-64.0), J[17], y);
+    y = rfma(T(-64.0), J[22], y);
+    y = rfma(T(4.0), J[23], y);
+    s = fma(J[16].r, y.r, fma(J[16].i, y.i, s)); }
+  { cplx<T> y = T(256.0) * J[17];
+    y = rfma(T(4.0), J[22], y);
+    s = fma(J[17].r, y.r, fma(J[17].i, y.i, s)); }
+  return s;
+}
+template <typename T> __device__ __forceinline__ T colour_form_orbit(const cplx<T> (&J)[24]) { return colour_form_orbit_4<T>(J); }
+template <> struct ColourPerm<4> {
+  static __device__ __forceinline__ int at(int a) { return kColourPerm4[a]; }
+};
 }  // namespace mf

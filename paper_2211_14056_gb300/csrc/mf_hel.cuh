@@ -10,8 +10,10 @@
 // pattern only, so each block B holds a single current (34 for NG = 4, about
 // 1 KB in FP32), built level by level by the group; lane c < NG then walks the
 // quark-line subtree whose last gluon is c (the level-1 suffix (c)), which
-// gives the colour orderings ending in c; lanes 0 and 1 take the colour form
-// J^dagger (D C) J of top helicity -1 and +1.  The summed kernels' tables
+// gives the colour orderings ending in c; the four lanes share the colour
+// forms J^dagger (D C) J of the two top helicities, each lane half of one
+// form (a gluon relabelling that leaves D C invariant maps one half onto the
+// other: colour_form_orbit in mf_gen_ttng.cuh).  The summed kernels' tables
 // (mf_gen_ttng.cuh) serve unchanged: a block reference's stored offset is
 // mapped to the block's index (hel_blk).
 #pragma once
@@ -199,13 +201,15 @@ __device__ __forceinline__ T hel_me2(const T (&p)[NG + 2][4], unsigned hel, unsi
     hel_path<NG, 1, T>(gl, R, cx);
   }
   __syncwarp();   // every ordering's amplitudes are in shared memory
-  T part = T(0);
-  if (gl < 2) {
-    cplx<T> Jl[NP];
+  // colour forms: lane gl takes top helicity gl & 1 and, for gl >> 1 = 1, the
+  // orderings relabelled by the gluon symmetry that leaves D C invariant;
+  // the same half of the quadratic form (colour_form_orbit) on the two data
+  // sets adds up to the helicity's form, so the four lanes share the work
+  const int th = gl & 1, rel = gl >> 1;
+  cplx<T> Jl[NP];
 #pragma unroll
-    for (int sg = 0; sg < NP; ++sg) Jl[sg] = J[sg * 2 + gl];
-    part = colour_form<T>(Jl);
-  }
+  for (int sg = 0; sg < NP; ++sg) Jl[sg] = J[(rel ? ColourPerm<NG>::at(sg) : sg) * 2 + th];
+  T part = T(2) * colour_form_orbit<T>(Jl);
   part += __shfl_xor_sync(0xffffffffu, part, 1);
   part += __shfl_xor_sync(0xffffffffu, part, 2);
   __syncwarp();   // the event's shared memory may be overwritten after this

@@ -277,6 +277,68 @@ def emit_lane(n, lines, colour):
     lines += L
 
 
+def colour_orbit_terms(n, colour):
+    """The colour form split in two halves of equal code by a symmetry.  The
+    relabelling pi of the gluons (0 1)(2 3)... (an involution) maps ordering
+    sigma to pi(sigma) and leaves D C invariant (relabelling summed colour
+    indices), so the terms c_ab Re(J_a^* J_b) of the form (a <= b) fall into
+    orbits {(a, b), (pi a, pi b)}.  Returns (perm, terms): perm[a] = the index
+    of pi(sigma_a); terms = [(a, b, c)] with one representative of every orbit
+    of two terms at its coefficient and every term its own image (an orbit of
+    one) at half its coefficient, so that with J'_a = J_perm[a]
+        F(J) + F(J') = J^dagger (D C) J / 2,  F(J) = sum_terms c Re(J_a^* J_b),
+    the same straight-line F serving both halves on different data."""
+    orders, M, D = colour
+    P = len(orders)
+    pi = list(range(n))
+    for g in range(0, n - 1, 2):
+        pi[g], pi[g + 1] = g + 1, g
+    perm = [orders.index(tuple(pi[g] for g in o)) for o in orders]
+    for a in range(P):
+        for b in range(P):
+            assert M[perm[a]][perm[b]] == M[a][b]
+    seen = set()
+    terms = []
+    for a in range(P):
+        for b in range(a, P):
+            if M[a][b] == 0 or (a, b) in seen:
+                continue
+            c = Fraction(M[a][b], 2) if a == b else Fraction(M[a][b])
+            img = tuple(sorted((perm[a], perm[b])))
+            seen.add((a, b))
+            seen.add(img)
+            terms.append((a, b, c if img != (a, b) else c / 2))
+    return perm, terms
+
+
+def emit_colour_orbit(n, lines, colour):
+    perm, terms = colour_orbit_terms(n, colour)
+    P = len(perm)
+    lines.append(f"// Half of J^dagger (D C) J / 2 for {P} orderings by the gluon relabelling")
+    lines.append(f"// symmetry (gen_tables.colour_orbit_terms): F(J) + F(J o perm) = J^dagger (D C) J / 2.")
+    lines.append(f"static __constant__ uint8_t kColourPerm{n}[{P}] = {{{', '.join(map(str, perm))}}};")
+    lines.append("template <typename T>")
+    lines.append(f"__device__ __forceinline__ T colour_form_orbit_{n}(const cplx<T> (&J)[{P}]) {{")
+    lines.append("  T s = T(0);")
+    by_a = {}
+    for a, b, c in terms:
+        by_a.setdefault(a, []).append((b, c))
+    for a in sorted(by_a):
+        row = by_a[a]
+        b0, c0 = row[0]
+        lines.append(f"  {{ cplx<T> y = T({float(c0)!r}) * J[{b0}];")
+        for b, c in row[1:]:
+            lines.append(f"    y = rfma(T({float(c)!r}), J[{b}], y);")
+        lines.append(f"    s = fma(J[{a}].r, y.r, fma(J[{a}].i, y.i, s)); }}")
+    lines.append("  return s;")
+    lines.append("}")
+    lines.append(f"template <typename T> __device__ __forceinline__ T colour_form_orbit(const cplx<T> (&J)[{P}]) "
+                 f"{{ return colour_form_orbit_{n}<T>(J); }}")
+    lines.append(f"template <> struct ColourPerm<{n}> {{")
+    lines.append(f"  static __device__ __forceinline__ int at(int a) {{ return kColourPerm{n}[a]; }}")
+    lines.append("};")
+
+
 def colour_tc_fragments(n, colour):
     """(m-tiles, k-steps, values) of D C as the A operand of mma.m16n8k8 (TF32,
     row-major 16 x 8 tiles), laid out [m-tile][k-step][register][lane]:
@@ -324,6 +386,7 @@ def render():
         "template <int NG> __device__ __forceinline__ const uint16_t* blk_off();",
         "template <int NG> struct Paths;",
         "template <int NG> struct ColourTC;",
+        "template <int NG> struct ColourPerm;",
         "template <int NG> __device__ __forceinline__ const float* colour_frag_a();",
         "template <int NG> __device__ __forceinline__ const int* colour_num_dev();",
         "template <typename T> __device__ __forceinline__ V4<T> neg(const V4<T>& a) {",
@@ -347,6 +410,7 @@ def render():
         emit_tables(n, lines)
         emit_lane(n, lines, colours[n])
         emit_colour_tc(n, lines, colours[n])
+        emit_colour_orbit(n, lines, colours[n])
     lines.append("}  // namespace mf")
     return "\n".join(lines) + "\n"
 

@@ -105,3 +105,32 @@ def test_emulated_tensor_core_sum_is_the_quadratic_form(ng):
             q = np.einsum("sn,st,tn->n", B, C, B)
             want += q.reshape(32 // L, L).sum(axis=1)
     np.testing.assert_allclose(got, want, rtol=1e-12)
+
+
+def test_orbit_halves_sum_to_the_colour_form():
+    """The two halves of the colour form that the helicity-sampled kernel's
+    lanes evaluate (the same straight-line terms on J and on J relabelled by
+    the gluon symmetry) add up to J^dagger (D C) J / 2, for random complex J."""
+    import numpy as np
+    from paper_2211_14056_gb300 import gen_tables
+    rng = np.random.default_rng(3)
+    for n in (2, 3, 4):
+        colour = gen_tables.colour_matrix_exact(n)
+        orders, M, D = colour
+        perm, terms = gen_tables.colour_orbit_terms(n, colour)
+        assert sorted(perm) == list(range(len(orders))) and all(perm[perm[a]] == a for a in range(len(perm)))
+        Mf = np.array(M, dtype=float)
+        full = 0
+        for a in range(len(orders)):
+            for b in range(a, len(orders)):
+                full += (M[a][b] != 0)
+        assert len(terms) <= full // 2 + n * len(orders)      # about half the form's terms per half
+        for _ in range(5):
+            J = rng.normal(size=len(orders)) + 1j * rng.normal(size=len(orders))
+
+            def F(v):
+                return sum(float(c) * np.real(np.conj(v[a]) * v[b]) for a, b, c in terms)
+
+            want = np.real(np.conj(J) @ Mf @ J) / 2
+            got = F(J) + F(J[perm])
+            assert abs(got - want) <= 1e-12 * np.abs(J).max() ** 2 * np.abs(Mf).sum()
