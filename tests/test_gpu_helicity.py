@@ -484,3 +484,27 @@ def test_two_line_sampling_is_unbiased(mf, name):
           f"variance / summed: sampled {v_s / v_u:.2f}, adapted {v_a / v_u:.2f}")
     assert abs(I_s - I_u) < 5 * np.hypot(s_s, s_u)
     assert abs(I_a - I_u) < 5 * np.hypot(s_a, s_u)
+
+
+def test_adapted_sums_over_several_chunks(mf):
+    """2^21 + 3 FP32 events (three record chunks): the per-configuration sums
+    of squared weights in the totals equal the sums of the returned weights
+    squared over the events that drew each configuration (draws from the
+    oracle's Philox and thresholds), so the chunks' partial sums add up."""
+    from paper_2211_14056_gb300.sharding import totals_tensor
+    p, _ = _proc(mf, "gg_ttxgg_13tev", mf.MF_FP32)
+    p.set_helicity_sampling("adaptive")
+    g = p.grid()
+    rng = np.random.default_rng(39)
+    prob = rng.uniform(0.5, 2.0, 32)
+    prob /= prob.sum()
+    g.set_helicity(prob)
+    n = (1 << 21) + 3
+    wt = torch.empty(n, dtype=torch.float64, device="cuda")
+    p.vegas_accumulate(g, 45, 1, 7, n, weights=wt)
+    S = totals_tensor(g).cpu().numpy()[-32:]
+    torch.cuda.synchronize()
+    w = wt.cpu().numpy()
+    h = oh.draw(oph.helicity_words(45, 1, np.arange(7, 7 + n, dtype=np.uint64)), oh.thresholds(prob))
+    want = np.bincount(h, weights=w * w, minlength=32)
+    np.testing.assert_allclose(S, want, rtol=1e-10)
