@@ -244,29 +244,73 @@ template <typename T> struct AdjCtx {
 
 // Add a lane's adjoint of a sub-current it used.  The stored position depends
 // only on the helicities of the block's own gluons, so the lanes that differ
-// in the other gluons' or the antitop's helicity add to the same entry: they
-// are summed by xor shuffles first and one lane per entry adds the sum.
+// in the other gluons' or the antitop's helicity (the R = popcount(other) bits
+// of `other`) add to the same entry.  Their sum is formed by a reduce-scatter
+// over those lane bits: over each of the first min(R, 3) bits a lane keeps
+// half of its remaining components and exchanges the other half (4 + 2 + 1
+// shuffles instead of 8 per bit), over any further bit it exchanges its last
+// component; then every lane whose further bits are zero holds the complete
+// sums of 8 >> min(R, 3) components and adds them (the entry's eight
+// additions spread over 2^min(R, 3) lanes).
+template <int S, typename T>
+__device__ __forceinline__ void gb_split(T (&v)[8], unsigned b, unsigned gl, int& coff) {
+  const bool up = (gl >> b) & 1u;
+#pragma unroll
+  for (int i = 0; i < S / 2; ++i) {
+    const T send = up ? v[i] : v[i + S / 2];
+    const T keep = up ? v[i + S / 2] : v[i];
+    v[i] = keep + shfl_xor_any(0xffffffffu, send, 1 << b);
+  }
+  if (up) coff += S / 2;
+}
+
+template <int NG, int R, typename T>
+__device__ __forceinline__ void gb_scatter_add(T (&v)[8], unsigned other, unsigned gl, cplx<T>* Gb, int pos, T sg) {
+  constexpr int M = R < 3 ? R : 3;
+  constexpr int S = 8 >> M;
+  unsigned rem = other;
+  int coff = 0;
+  if constexpr (M >= 1) { gb_split<8, T>(v, unsigned(__ffs(rem) - 1), gl, coff); rem &= rem - 1u; }
+  if constexpr (M >= 2) { gb_split<4, T>(v, unsigned(__ffs(rem) - 1), gl, coff); rem &= rem - 1u; }
+  if constexpr (M >= 3) { gb_split<2, T>(v, unsigned(__ffs(rem) - 1), gl, coff); rem &= rem - 1u; }
+  const unsigned extra = rem;
+#pragma unroll
+  for (int e = 0; e < R - M; ++e) {
+    const unsigned b = unsigned(__ffs(rem) - 1);
+    rem &= rem - 1u;
+#pragma unroll
+    for (int i = 0; i < S; ++i) v[i] += shfl_xor_any(0xffffffffu, v[i], 1 << b);
+  }
+  if ((gl & extra) != 0u) return;
+  T* base = reinterpret_cast<T*>(Gb);
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    const int c = coff + i;   // component c: k = c / 2, real (c even) or imaginary part
+    atomicAdd(base + 2 * ((c >> 1) * TTNG<NG>::NSTORE + pos) + (c & 1), sg * v[i]);
+  }
+}
+
 template <int NG, typename T>
 __device__ __forceinline__ void gb_add(const AdjCtx<T>& cx, uint16_t ref, V4<T> g) {
   const unsigned mb = ref_mask(ref);
   const unsigned other = ((2u << NG) - 1u) & ~mb;
-#pragma unroll
-  for (int b = 0; b <= NG; ++b)
-    if ((other >> b) & 1u) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        g.c[k].r += shfl_xor_any(0xffffffffu, g.c[k].r, 1 << b);
-        g.c[k].i += shfl_xor_any(0xffffffffu, g.c[k].i, 1 << b);
-      }
-    }
-  if ((cx.gl & other) != 0u) return;
   const unsigned idx = unsigned(cx.pk >> (4 * mb)) & 15u;
   const int pos = ref_off(ref) + int(idx);
-  const T s = ref_neg(ref) ? T(-1) : T(1);
+  const T sg = ref_neg(ref) ? T(-1) : T(1);
+  T v[8];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    atomicAdd(&cx.Gb[k * TTNG<NG>::NSTORE + pos].r, s * g.c[k].r);
-    atomicAdd(&cx.Gb[k * TTNG<NG>::NSTORE + pos].i, s * g.c[k].i);
+    v[2 * k] = g.c[k].r;
+    v[2 * k + 1] = g.c[k].i;
+  }
+  // R = NG + 1 - |B| ranges over 1 .. NG (a block holds 1 .. NG gluons); the
+  // branch is uniform over the warp (every lane walks the same path)
+  switch (__popc(other)) {
+    case 1: gb_scatter_add<NG, 1, T>(v, other, cx.gl, cx.Gb, pos, sg); break;
+    case 2: gb_scatter_add<NG, 2, T>(v, other, cx.gl, cx.Gb, pos, sg); break;
+    case 3: gb_scatter_add<NG, 3, T>(v, other, cx.gl, cx.Gb, pos, sg); break;
+    case 4: if constexpr (NG >= 3) gb_scatter_add<NG, 4, T>(v, other, cx.gl, cx.Gb, pos, sg); break;
+    default: if constexpr (NG >= 4) gb_scatter_add<NG, 5, T>(v, other, cx.gl, cx.Gb, pos, sg); break;
   }
 }
 
@@ -373,6 +417,8 @@ template <int NG, int K, typename T>
 __device__ __forceinline__ void gb_item_add(cplx<T>* Gb, int pos, V4<T> g, unsigned red, unsigned c, bool act) {
 #pragma unroll
   for (int j = 0; j < K; ++j) {
+    // a bit no item of the warp reduces over needs no exchange
+    if (!__any_sync(0xffffffffu, (red >> j) & 1u)) continue;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const T r = shfl_xor_any(0xffffffffu, g.c[k].r, 1 << j);
