@@ -242,6 +242,21 @@ template <typename T> struct AdjCtx {
   unsigned gl;   // lane within the event's group
 };
 
+// The sub-current adjoints Gb are stored component-major like Gs, but with a
+// component stride of NSTORE + 1: where NSTORE is a multiple of 16 complex
+// numbers (320 for four gluons) the four components of one entry would share
+// a bank, and the lanes that add different components of one entry at once
+// would conflict.
+template <int NG> constexpr int kGbStride = TTNG<NG>::NSTORE + 1;
+
+template <int NG, typename T>
+__device__ __forceinline__ V4<T> gb_load(const cplx<T>* Gb, int pos) {
+  V4<T> g;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) g.c[k] = Gb[k * kGbStride<NG> + pos];
+  return g;
+}
+
 // Add a lane's adjoint of a sub-current it used.  The stored position depends
 // only on the helicities of the block's own gluons, so the lanes that differ
 // in the other gluons' or the antitop's helicity (the R = popcount(other) bits
@@ -286,7 +301,7 @@ __device__ __forceinline__ void gb_scatter_add(T (&v)[8], unsigned other, unsign
 #pragma unroll
   for (int i = 0; i < S; ++i) {
     const int c = coff + i;   // component c: k = c / 2, real (c even) or imaginary part
-    atomicAdd(base + 2 * ((c >> 1) * TTNG<NG>::NSTORE + pos) + (c & 1), sg * v[i]);
+    atomicAdd(base + 2 * ((c >> 1) * kGbStride<NG> + pos) + (c & 1), sg * v[i]);
   }
 }
 
@@ -432,8 +447,8 @@ __device__ __forceinline__ void gb_item_add(cplx<T>* Gb, int pos, V4<T> g, unsig
   if (!act || (c & red) != 0u) return;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    atomicAdd(&Gb[k * TTNG<NG>::NSTORE + pos].r, g.c[k].r);
-    atomicAdd(&Gb[k * TTNG<NG>::NSTORE + pos].i, g.c[k].i);
+    atomicAdd(&Gb[k * kGbStride<NG> + pos].r, g.c[k].r);
+    atomicAdd(&Gb[k * kGbStride<NG> + pos].i, g.c[k].i);
   }
 }
 
@@ -460,7 +475,7 @@ __device__ __forceinline__ void adj_gluon_level(const MaskTab<NG, T>& mt, const 
     const unsigned H = pdep_mask<NG>(c, mb);
     const int pos = blk_off<NG>()[b] + int(c);
     const V4<T> G = gs_load<NG, T>(Gs, pos);
-    V4<T> Gbar = gs_load<NG, T>(Gb, pos);
+    V4<T> Gbar = gb_load<NG, T>(Gb, pos);
     if (!act) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) Gbar.c[k] = {T(0), T(0)};
@@ -525,8 +540,9 @@ __device__ __forceinline__ void adj_gluon_level(const MaskTab<NG, T>& mt, const 
 template <int NG, typename T> struct AdjMem {
   static constexpr int EPW = Lanes<NG>::EPW;
   static constexpr size_t gs_bytes = sizeof(cplx<T>) * 4 * TTNG<NG>::NSTORE * EPW;
+  static constexpr size_t gb_bytes = sizeof(cplx<T>) * 4 * kGbStride<NG> * EPW;
   static constexpr size_t gb_off = gs_bytes;
-  static constexpr size_t pt_off = gb_off + gs_bytes;
+  static constexpr size_t pt_off = gb_off + gb_bytes;
   static constexpr size_t j_off = (pt_off + MaskTab<NG, T>::bytes * EPW + 15) & ~size_t(15);
   static constexpr size_t bytes = (j_off + sizeof(T) * 2 * kAdjPlane<NG> + 15) & ~size_t(15);
 };
@@ -541,10 +557,10 @@ __device__ __forceinline__ T adj_group_me2(const T (&p)[NG + 2][4], unsigned cha
   constexpr int L = Lanes<NG>::L, NP = TTNG<NG>::NPERM, NS = TTNG<NG>::NSTORE, NR = AdjRows<NG>::N;
   const int lane = threadIdx.x & 31;
   cplx<T>* Gs = reinterpret_cast<cplx<T>*>(wm) + group * 4 * NS;
-  cplx<T>* Gb = reinterpret_cast<cplx<T>*>(wm + AM::gb_off) + group * 4 * NS;
+  cplx<T>* Gb = reinterpret_cast<cplx<T>*>(wm + AM::gb_off) + group * 4 * kGbStride<NG>;
   const MaskTab<NG, T> mtab(wm + AM::pt_off + group * MaskTab<NG, T>::bytes);
   T* Jw = reinterpret_cast<T*>(wm + AM::j_off) + lane;
-  for (int i = gl; i < 4 * NS; i += L) Gb[i] = {T(0), T(0)};
+  for (int i = gl; i < 4 * kGbStride<NG>; i += L) Gb[i] = {T(0), T(0)};
   AdjAcc<NG, T> pb;
 #pragma unroll
   for (int r = 0; r < NR; ++r) pb.r[r] = T(0);
@@ -625,7 +641,7 @@ __device__ __forceinline__ T adj_group_me2(const T (&p)[NG + 2][4], unsigned cha
 #pragma unroll
     for (int bit = 0; bit < 2; ++bit) {
       if (gl != (2 * g + bit) % L) continue;
-      const V4<T> eb = gs_load<NG, T>(Gb, 2 * g + bit);
+      const V4<T> eb = gb_load<NG, T>(Gb, 2 * g + bit);
       using D = Dual<T, 3>;
       R4<D> kd;
       kd.v[0] = D(p[g + 2][0]);
