@@ -23,6 +23,16 @@
 
 namespace mf {
 
+// f(std::integral_constant<int, i>) for i = 0 .. N-1, each call inlined with
+// its index a compile-time constant
+template <int I, int N, typename F> __device__ __forceinline__ void static_for_from(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for_from<I + 1, N>(f);
+  }
+}
+template <int N, typename F> __device__ __forceinline__ void static_for(F&& f) { static_for_from<0, N>(f); }
+
 // conj(a) * b and acc + conj(a) * b
 template <typename T> __device__ __forceinline__ cplx<T> cmulc(cplx<T> a, cplx<T> b) {
   return {fma(a.r, b.r, a.i * b.i), fma(a.r, b.i, -(a.i * b.r))};
@@ -305,10 +315,14 @@ __device__ __forceinline__ void gb_scatter_add(T (&v)[8], unsigned other, unsign
   }
 }
 
-template <int NG, typename T>
+// BL = the block's gluon count, a compile-time constant at every call site:
+// the walk's m-th block of a path (m = 0, 1, ...) holds m + 1 gluons (the
+// path tables are built that way), so each site inlines one reduction form.
+template <int NG, int BL, typename T>
 __device__ __forceinline__ void gb_add(const AdjCtx<T>& cx, uint16_t ref, V4<T> g) {
+  static_assert(BL >= 1 && BL <= NG, "a block holds 1 .. NG gluons");
   const unsigned mb = ref_mask(ref);
-  const unsigned other = ((2u << NG) - 1u) & ~mb;
+  const unsigned other = ((2u << NG) - 1u) & ~mb;   // NG + 1 - BL lane bits
   const unsigned idx = unsigned(cx.pk >> (4 * mb)) & 15u;
   const int pos = ref_off(ref) + int(idx);
   const T sg = ref_neg(ref) ? T(-1) : T(1);
@@ -318,15 +332,7 @@ __device__ __forceinline__ void gb_add(const AdjCtx<T>& cx, uint16_t ref, V4<T> 
     v[2 * k] = g.c[k].r;
     v[2 * k + 1] = g.c[k].i;
   }
-  // R = NG + 1 - |B| ranges over 1 .. NG (a block holds 1 .. NG gluons); the
-  // branch is uniform over the warp (every lane walks the same path)
-  switch (__popc(other)) {
-    case 1: gb_scatter_add<NG, 1, T>(v, other, cx.gl, cx.Gb, pos, sg); break;
-    case 2: gb_scatter_add<NG, 2, T>(v, other, cx.gl, cx.Gb, pos, sg); break;
-    case 3: gb_scatter_add<NG, 3, T>(v, other, cx.gl, cx.Gb, pos, sg); break;
-    case 4: if constexpr (NG >= 3) gb_scatter_add<NG, 4, T>(v, other, cx.gl, cx.Gb, pos, sg); break;
-    default: if constexpr (NG >= 4) gb_scatter_add<NG, 5, T>(v, other, cx.gl, cx.Gb, pos, sg); break;
-  }
+  gb_scatter_add<NG, NG + 1 - BL, T>(v, other, cx.gl, cx.Gb, pos, sg);
 }
 
 template <int NG, typename T>
@@ -382,15 +388,15 @@ __device__ __forceinline__ void adj_walk(int parent, S4<T> (&R)[NG], S4<T> (&Rb)
             cx.ubb0.c[c] = cfmac(W.c[c], jb0, cx.ubb0.c[c]);
             cx.ubb1.c[c] = cfmac(W.c[c], jb1, cx.ubb1.c[c]);
           }
-#pragma unroll
-          for (int m = 0; m < NG; ++m) {
+          static_for<NG>([&](auto mc) {
+            constexpr int m = decltype(mc)::value;
             const uint16_t ref = PT::final_blk(path, m);
             V4<T> gb;
 #pragma unroll
             for (int c = 0; c < 4; ++c) gb.c[c] = {T(0), T(0)};
             adj_apply(adj_block<NG, T>(cx, ref), R[NG - 1 - m], Wb, gb, Rb[NG - 1 - m]);
-            gb_add<NG, T>(cx, ref, gb);
-          }
+            gb_add<NG, m + 1, T>(cx, ref, gb);
+          });
         }
       }
     }
@@ -409,15 +415,15 @@ __device__ __forceinline__ void adj_walk(int parent, S4<T> (&R)[NG], S4<T> (&Rb)
       adj_prop(Pt, cx.m, f, X, Rb[LV], Xb, Ptb, mb, fb);
       acc_row<NG, T>(pb, AdjRows<NG>::MB, mb);
       chain_prop<NG, T>(pb, msk, Pt, f, fb, Ptb, cx.m);
-#pragma unroll
-      for (int m = 0; m < LV; ++m) {
+      static_for<LV>([&](auto mc) {
+        constexpr int m = decltype(mc)::value;
         const uint16_t ref = PT::template blk<LV>(path, m);
         V4<T> gb;
 #pragma unroll
         for (int c = 0; c < 4; ++c) gb.c[c] = {T(0), T(0)};
         adj_apply(adj_block<NG, T>(cx, ref), R[LV - 1 - m], Xb, gb, Rb[LV - 1 - m]);
-        gb_add<NG, T>(cx, ref, gb);
-      }
+        gb_add<NG, m + 1, T>(cx, ref, gb);
+      });
     }
   }
 }

@@ -101,3 +101,23 @@ def test_compact_block_index_inverts_the_stored_offsets():
         for r in refs:
             b = _hel_blk(r, first, ng)
             assert 0 <= b < len(off) and off[b] == (r & 511) and msk[b] == ((r >> 9) & 15)
+
+
+def test_walk_block_lengths_follow_their_position():
+    """The m-th block reference of a walk path (m = 0, 1, ...) holds m + 1
+    gluons, in the node tables (kPathBlk, LV per path) and in the completions
+    (kFinalBlk, NG per path): the adjoint kernel takes the block length at
+    each of these positions as a compile-time constant (its lane reduction
+    over the gluons outside the block is specialised on it)."""
+    src = gen_tables.render()
+    for ng in (2, 3, 4):
+        for lv in range(1, ng):
+            refs = _array(src, f"kPathBlk{ng}_{lv}")
+            assert len(refs) % lv == 0
+            for k, r in enumerate(refs):
+                assert bin((r >> 9) & 15).count("1") == k % lv + 1
+        refs = _array(src, f"kFinalBlk{ng}")
+        assert len(refs) == ng * len(list(itertools.permutations(range(ng))))
+        for k, r in enumerate(refs):
+            assert bin((r >> 9) & 15).count("1") == k % ng + 1
+
