@@ -19,6 +19,7 @@
 // zb = df/dx + i df/dy; then z = a w gives wb += conj(a) zb, and a real
 // parameter t with dz/dt = z' gets tb += Re(conj(z') zb).
 #pragma once
+#include "mf_gen_adj.cuh"
 #include "mf_kernels.cuh"
 
 namespace mf {
@@ -253,11 +254,23 @@ template <typename T> struct AdjCtx {
 };
 
 // The sub-current adjoints Gb are stored component-major like Gs, but with a
-// component stride of NSTORE + 1: where NSTORE is a multiple of 16 complex
-// numbers (320 for four gluons) the four components of one entry would share
-// a bank, and the lanes that add different components of one entry at once
-// would conflict.
-template <int NG> constexpr int kGbStride = TTNG<NG>::NSTORE + 1;
+// component stride of one entry more than they hold: where the entry count is
+// a multiple of 16 complex numbers (128 or 320 for four gluons) the four
+// components of one entry would share a bank, and the lanes that add
+// different components of one entry at once would conflict.
+//
+// With four gluons the adjoints of the four-gluon blocks (192 of the 320
+// entries) are not in Gb: each such block is used only by the completions of
+// its two colour orderings, and its adjoint is kept in the amplitude rows of
+// the ordering the walk completes first (rows that are dead once that
+// completion has read its Jb); see g4_leaf_add.  The shared footprint of a
+// warp drops from 33.5 to 26.7 KB, which lets eight one-warp CTAs share an SM
+// instead of six.
+template <int NG> constexpr bool kG4InJ = NG == 4;
+template <int NG>
+constexpr int kGbEntries = kG4InJ<NG> ? TTNG<NG>::NSTORE - ((TTNG<NG>::FIRST[NG + 1] - TTNG<NG>::FIRST[NG]) << NG)
+                                      : TTNG<NG>::NSTORE;
+template <int NG> constexpr int kGbStride = kGbEntries<NG> + 1;
 
 template <int NG, typename T>
 __device__ __forceinline__ V4<T> gb_load(const cplx<T>* Gb, int pos) {
@@ -335,6 +348,49 @@ __device__ __forceinline__ void gb_add(const AdjCtx<T>& cx, uint16_t ref, V4<T> 
   gb_scatter_add<NG, NG + 1 - BL, T>(v, other, cx.gl, cx.Gb, pos, sg);
 }
 
+// Position, in the warp's amplitude planes, of value c (component c / 2, real
+// or imaginary part by c & 1) of helicity entry idx of a four-gluon block
+// kept in the rows of colour ordering `slot`: the rows (slot, top helicity
+// 0/1) of both planes, 32 words each, in half rows of 16 entries; half
+// (c / 4) ^ parity of the block, so that the two antitop lanes' stores of
+// one entry, and the two blocks of a round of the reversed gluon level,
+// fall in different banks.
+__device__ __forceinline__ int g4_off(int slot, int c, unsigned par, unsigned idx) {
+  const int row = c & 3, half = (c >> 2) ^ int(par);
+  return (row >> 1) * kAdjPlane<4> + (slot * 2 + (row & 1)) * 32 + half * 16 + int(idx);
+}
+
+// A completion's adjoint of its four-gluon block: summed over the antitop
+// lane bit (each lane keeps four of the eight values), then stored, at the
+// block's first completion, or added, at its second, by the lane that owns
+// each value (the same lane both times, so no atomics).  The first
+// completion writes over the rows it has just read, hence the warp barrier.
+template <typename T>
+__device__ __forceinline__ void g4_leaf_add(const AdjCtx<T>& cx, int path, uint16_t ref, const V4<T>& g) {
+  const unsigned e = kG4Leaf4[path];
+  const int slot = int(e & 31u);
+  const unsigned par = (e >> 5) & 1u;
+  const T sg = ref_neg(ref) ? T(-1) : T(1);
+  const unsigned idx = unsigned(cx.pk >> (4 * ref_mask(ref))) & 15u;
+  T v[8];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[2 * k] = g.c[k].r;
+    v[2 * k + 1] = g.c[k].i;
+  }
+  int coff = 0;
+  gb_split<8, T>(v, 4u, cx.gl, coff);
+  T* base = cx.J - (threadIdx.x & 31);
+  __syncwarp();
+  if (e & 0x80u) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) base[g4_off(slot, coff + i, par, idx)] = sg * v[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) base[g4_off(slot, coff + i, par, idx)] += sg * v[i];
+  }
+}
+
 template <int NG, typename T>
 __device__ __forceinline__ V4<T> adj_block(const AdjCtx<T>& cx, uint16_t ref) {
   const unsigned idx = unsigned(cx.pk >> (4 * ref_mask(ref))) & 15u;
@@ -395,7 +451,10 @@ __device__ __forceinline__ void adj_walk(int parent, S4<T> (&R)[NG], S4<T> (&Rb)
 #pragma unroll
             for (int c = 0; c < 4; ++c) gb.c[c] = {T(0), T(0)};
             adj_apply(adj_block<NG, T>(cx, ref), R[NG - 1 - m], Wb, gb, Rb[NG - 1 - m]);
-            gb_add<NG, m + 1, T>(cx, ref, gb);
+            if constexpr (m == NG - 1 && kG4InJ<NG>)
+              g4_leaf_add<T>(cx, path, ref, gb);
+            else
+              gb_add<NG, m + 1, T>(cx, ref, gb);
           });
         }
       }
@@ -463,8 +522,8 @@ __device__ __forceinline__ void gb_item_add(cplx<T>* Gb, int pos, V4<T> g, unsig
 // sub-blocks' adjoints, the momentum sums and 1/K^2.  Rounds of L items run
 // on all lanes (idle lanes carry zero adjoints through the shuffles).
 template <int NG, int K, typename T>
-__device__ __forceinline__ void adj_gluon_level(const MaskTab<NG, T>& mt, const cplx<T>* Gs, cplx<T>* Gb, int gl,
-                                                AdjAcc<NG, T>& pb) {
+__device__ __forceinline__ void adj_gluon_level(const MaskTab<NG, T>& mt, const cplx<T>* Gs, cplx<T>* Gb, const T* Jw,
+                                                int gl, AdjAcc<NG, T>& pb) {
   constexpr int L = Lanes<NG>::L;
   constexpr int nblk = TTNG<NG>::FIRST[K + 1] - TTNG<NG>::FIRST[K];
   constexpr int items = nblk << K;
@@ -481,7 +540,17 @@ __device__ __forceinline__ void adj_gluon_level(const MaskTab<NG, T>& mt, const 
     const unsigned H = pdep_mask<NG>(c, mb);
     const int pos = blk_off<NG>()[b] + int(c);
     const V4<T> G = gs_load<NG, T>(Gs, pos);
-    V4<T> Gbar = gb_load<NG, T>(Gb, pos);
+    V4<T> Gbar;
+    if constexpr (K == NG && kG4InJ<NG>) {
+      // kept in the amplitude rows (g4_leaf_add)
+      const int slot = kG4Slot4[bl];
+      const unsigned par = unsigned(bl) & 1u;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        Gbar.c[k] = {Jw[g4_off(slot, 2 * k, par, c)], Jw[g4_off(slot, 2 * k + 1, par, c)]};
+    } else {
+      Gbar = gb_load<NG, T>(Gb, pos);
+    }
     if (!act) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) Gbar.c[k] = {T(0), T(0)};
@@ -636,9 +705,9 @@ __device__ __forceinline__ T adj_group_me2(const T (&p)[NG + 2][4], unsigned cha
   chain_spinor<NG, T>(pb, 2, p[2], mt, cx.ubb1, [&](const R4<Dual<T, 5>>& q, Dual<T, 5> m) { return ubar_out(q, m, 1); });
   __syncwarp();
   // gluon levels in reverse
-  if constexpr (NG >= 4) { adj_gluon_level<NG, 4, T>(mtab, Gs, Gb, gl, pb); __syncwarp(); }
-  if constexpr (NG >= 3) { adj_gluon_level<NG, 3, T>(mtab, Gs, Gb, gl, pb); __syncwarp(); }
-  adj_gluon_level<NG, 2, T>(mtab, Gs, Gb, gl, pb);
+  if constexpr (NG >= 4) { adj_gluon_level<NG, 4, T>(mtab, Gs, Gb, Jw - lane, gl, pb); __syncwarp(); }
+  if constexpr (NG >= 3) { adj_gluon_level<NG, 3, T>(mtab, Gs, Gb, Jw - lane, gl, pb); __syncwarp(); }
+  adj_gluon_level<NG, 2, T>(mtab, Gs, Gb, Jw - lane, gl, pb);
   __syncwarp();
   // polarisation vectors of the outgoing gluons (the incoming ones lie on the
   // beam axis, where eps does not depend on the momentum)

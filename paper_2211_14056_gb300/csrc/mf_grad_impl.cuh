@@ -151,7 +151,7 @@ constexpr int kAdjStride = 1 + 16 + 1;
 // Adjoint |M|^2 of the listed events (one lane group per event), contracted
 // with the records' two tangents; per-CTA sums of w, dw/dm_t, dw/dGamma_t.
 template <int NG, typename B>
-__global__ void __launch_bounds__(32, 6) k_adj_me(GradArgs a, GradRec<B> rec, int64_t out_off) {
+__global__ void __launch_bounds__(32, 8) k_adj_me(GradArgs a, GradRec<B> rec, int64_t out_off) {
   using TD = Dual<B, kGradTangents>;
   using DD = Dual<double, kGradTangents>;
   constexpr int EPW = Lanes<NG>::EPW, L = Lanes<NG>::L, NEXT = Lanes<NG>::NEXT;

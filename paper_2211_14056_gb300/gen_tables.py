@@ -37,6 +37,7 @@ import numpy as np
 NC = 3
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "csrc", "mf_gen_ttng.cuh")
+OUT_ADJ = os.path.join(HERE, "csrc", "mf_gen_adj.cuh")
 
 
 # ---------------------------------------------------------------------------
@@ -415,11 +416,58 @@ def render():
     return "\n".join(lines) + "\n"
 
 
+def full_block_slots(n):
+    """Where the adjoint kernel keeps the adjoints of the n-gluon blocks.
+
+    Each n-gluon block (all gluons, one ordering up to reversal) is used by
+    exactly two completions of the quark-line walk, sigma and its reversal.
+    Its adjoint is kept in the amplitude rows of the ordering whose completion
+    the walk reaches first (those rows are read just before and are dead
+    afterwards).  Returns, per completion path p in walk order,
+    slot | (block parity << 5) | (first << 7), and per n-gluon block (in
+    generator order) its slot."""
+    levels, final = lane_paths(n)
+    bl, ids, off, nstore, first, o3, o4 = tables(n)
+    nfull = first[n + 1] - first[n]
+    slot, per_path, uses = {}, [], {}
+    for (sig, refs) in final:
+        i, _ = refs[n - 1]
+        b = i - first[n]
+        assert 0 <= b < nfull and len(bl[i]) == n
+        uses[b] = uses.get(b, 0) + 1
+        is_first = b not in slot
+        if is_first:
+            slot[b] = sig
+        assert slot[b] < 32
+        per_path.append(slot[b] | ((b & 1) << 5) | (0x80 if is_first else 0))
+    assert sorted(uses) == list(range(nfull)) and set(uses.values()) == {2}
+    return per_path, [slot[b] for b in range(nfull)]
+
+
+def render_adj():
+    lines = [
+        "// GENERATED by paper_2211_14056_gb300/gen_tables.py -- do not edit.",
+        "// Adjoint kernel, four gluons: where the adjoints of the four-gluon",
+        "// blocks are kept (the amplitude rows of one of the two colour orderings",
+        "// whose completions use the block; see full_block_slots).",
+        "#pragma once",
+        "#include <cstdint>",
+        "namespace mf {",
+    ]
+    per_path, per_block = full_block_slots(4)
+    lines.append("// per completion path (walk order): slot | (block parity << 5) | (first use << 7)")
+    lines.append(f"static __constant__ uint8_t kG4Leaf4[{len(per_path)}] = {{{', '.join(map(str, per_path))}}};")
+    lines.append("// per four-gluon block (generator order): its slot")
+    lines.append(f"static __constant__ uint8_t kG4Slot4[{len(per_block)}] = {{{', '.join(map(str, per_block))}}};")
+    lines.append("}  // namespace mf")
+    return "\n".join(lines) + "\n"
+
+
 def main():
-    src = render()
-    with open(OUT, "w") as f:
-        f.write(src)
-    print(f"wrote {OUT} ({len(src.splitlines())} lines)")
+    for out, src in ((OUT, render()), (OUT_ADJ, render_adj())):
+        with open(out, "w") as f:
+            f.write(src)
+        print(f"wrote {out} ({len(src.splitlines())} lines)")
 
 
 if __name__ == "__main__":

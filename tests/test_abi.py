@@ -75,6 +75,7 @@ def test_rejects_bad_descriptions_without_device(lib):
 def test_generated_header_is_current(tmp_path):
     from paper_2211_14056_gb300 import gen_tables
     assert open(gen_tables.OUT).read() == gen_tables.render()
+    assert open(gen_tables.OUT_ADJ).read() == gen_tables.render_adj()
 
 
 def test_product_colour_matrix_matches_oracle_brute_force():

@@ -121,3 +121,34 @@ def test_walk_block_lengths_follow_their_position():
         for k, r in enumerate(refs):
             assert bin((r >> 9) & 15).count("1") == k % ng + 1
 
+
+
+def test_full_block_adjoint_slots():
+    """The adjoint kernel keeps the adjoint of each four-gluon block in the
+    amplitude rows of a colour ordering (kG4Leaf4, kG4Slot4): the ordering is
+    that of the block's first completion in walk order, both completions of
+    the block (sigma and its reversal, the only ones that use it) name it,
+    exactly the first is flagged to store, and no two blocks share rows."""
+    src = gen_tables.render()
+    adj = gen_tables.render_adj()
+    leaf, slot = _array(adj, "kG4Leaf4"), _array(adj, "kG4Slot4")
+    fsig, fblk = _array(src, "kFinalSigma4"), _array(src, "kFinalBlk4")
+    first = _first(src, 4)
+    off = _array(src, "kBlkOff4")
+    assert len(leaf) == 24 and len(slot) == first[5] - first[4] == 12
+    assert len(set(slot)) == 12
+    seen = {}
+    perms = list(itertools.permutations(range(4)))
+    for p in range(24):
+        ref = fblk[p * 4 + 3]
+        b = next(i for i in range(first[4], first[5]) if off[i] == (ref & 511)) - first[4]
+        s, par, is_first = leaf[p] & 31, (leaf[p] >> 5) & 1, bool(leaf[p] & 0x80)
+        assert s == slot[b] and par == b & 1
+        assert is_first == (b not in seen)
+        if is_first:
+            assert s == fsig[p]
+            seen[b] = p
+        else:
+            # the second completion is the reversal of the first
+            assert perms[fsig[p]] == tuple(reversed(perms[fsig[seen[b]]]))
+    assert len(seen) == 12
