@@ -303,7 +303,8 @@ __device__ __forceinline__ void gb_split(T (&v)[8], unsigned b, unsigned gl, int
 }
 
 template <int NG, int R, typename T>
-__device__ __forceinline__ void gb_scatter_add(T (&v)[8], unsigned other, unsigned gl, cplx<T>* Gb, int pos, T sg) {
+__device__ __forceinline__ void gb_scatter_add(T (&v)[8], unsigned other, unsigned gl, cplx<T>* Gb, int pos, T sg,
+                                               bool act = true) {
   constexpr int M = R < 3 ? R : 3;
   constexpr int S = 8 >> M;
   unsigned rem = other;
@@ -319,7 +320,7 @@ __device__ __forceinline__ void gb_scatter_add(T (&v)[8], unsigned other, unsign
 #pragma unroll
     for (int i = 0; i < S; ++i) v[i] += shfl_xor_any(0xffffffffu, v[i], 1 << b);
   }
-  if ((gl & extra) != 0u) return;
+  if (!act || (gl & extra) != 0u) return;
   T* base = reinterpret_cast<T*>(Gb);
 #pragma unroll
   for (int i = 0; i < S; ++i) {
@@ -488,33 +489,36 @@ __device__ __forceinline__ void adj_walk(int parent, S4<T> (&R)[NG], S4<T> (&Rb)
 }
 
 
-// Add an item's adjoint of one of its sub-blocks.  The items of a round sit on
-// consecutive lanes with the helicity index c in the low K lane bits; the
-// items of one block whose helicities differ only in gluons outside the
-// sub-block (bits red of c) hit the same entry, so they are summed by xor
-// shuffles first and one of them adds.  Every lane of the group calls this.
-template <int NG, int K, typename T>
-__device__ __forceinline__ void gb_item_add(cplx<T>* Gb, int pos, V4<T> g, unsigned red, unsigned c, bool act) {
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
-    // a bit no item of the warp reduces over needs no exchange
-    if (!__any_sync(0xffffffffu, (red >> j) & 1u)) continue;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const T r = shfl_xor_any(0xffffffffu, g.c[k].r, 1 << j);
-      const T i = shfl_xor_any(0xffffffffu, g.c[k].i, 1 << j);
-      if ((red >> j) & 1u) {
-        g.c[k].r += r;
-        g.c[k].i += i;
-      }
-    }
-  }
-  if (!act || (c & red) != 0u) return;
+// Add an item's adjoint of one of its sub-blocks (R = the number of the
+// block's gluons outside the sub-block, a compile-time constant at every
+// split).  The items of a round sit on consecutive lanes with the helicity
+// index c in the low K lane bits; the items of one block whose helicities
+// differ only in gluons outside the sub-block (lane bits `red`) hit the same
+// entry, so they are summed by the reduce-scatter of gb_scatter_add and the
+// sums added by 2^min(R, 3) of them.  Inactive lanes (past the last item;
+// whole blocks of them) carry zeros through the shuffles and add nothing.
+// Every lane of the group calls this.
+template <int NG, int R, typename T>
+__device__ __forceinline__ void gb_item_add(cplx<T>* Gb, int pos, const V4<T>& g, unsigned red, unsigned gl, bool act) {
+  T v[8];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    atomicAdd(&Gb[k * kGbStride<NG> + pos].r, g.c[k].r);
-    atomicAdd(&Gb[k * kGbStride<NG> + pos].i, g.c[k].i);
+    v[2 * k] = g.c[k].r;
+    v[2 * k + 1] = g.c[k].i;
   }
+  gb_scatter_add<NG, R, T>(v, red, gl, Gb, pos, T(1), act);
+}
+
+// The s-th four-vertex split of a K-gluon block t: blocks t[:a], t[a:b],
+// t[b:] in generator order (a < b); which = 0 gives a, 1 gives b.
+template <int K> constexpr int o4_cut(int s, int which) {
+  int i = 0;
+  for (int a = 1; a < K - 1; ++a)
+    for (int b = a + 1; b < K; ++b) {
+      if (i == s) return which == 0 ? a : b;
+      ++i;
+    }
+  return 0;
 }
 
 // Reverse of gluon_level<NG, K>: every item's adjoint Gb is complete (all its
@@ -569,10 +573,12 @@ __device__ __forceinline__ void adj_gluon_level(const MaskTab<NG, T>& mt, const 
     V4<T> accb;
 #pragma unroll
     for (int k = 0; k < 4; ++k) accb.c[k] = ginv * Gbar.c[k];
+    // one inlined body per split: each sub-block's length, hence the number of
+    // lane bits its adjoint is summed over, is a compile-time constant
     const uint16_t* t3 = o3_table<NG, K>() + bl * n3 * 2;
-#pragma unroll 1
-    for (int s = 0; s < n3; ++s) {
-      const uint16_t rl = t3[2 * s], rr = t3[2 * s + 1];
+    static_for<n3>([&](auto sc) {
+      constexpr int sp = decltype(sc)::value;   // blocks t[:sp+1], t[sp+1:]
+      const uint16_t rl = t3[2 * sp], rr = t3[2 * sp + 1];
       const V4<T> GL = load_block<NG, T>(Gs, rl, H), GR = load_block<NG, T>(Gs, rr, H);
       const R4<T> PL = mt.qsum[ref_mask(rl)], PR = mt.qsum[ref_mask(rr)];
       V4<T> GLb, GRb;
@@ -580,31 +586,32 @@ __device__ __forceinline__ void adj_gluon_level(const MaskTab<NG, T>& mt, const 
       for (int k = 0; k < 4; ++k) GLb.c[k] = GRb.c[k] = {T(0), T(0)};
       R4<T> PLb = {{T(0), T(0), T(0), T(0)}}, PRb = {{T(0), T(0), T(0), T(0)}};
       adj_o3(GL, GR, PL, PR, (ref_neg(rl) != ref_neg(rr)) ? T(-1) : T(1), accb, GLb, GRb, PLb, PRb);
-      gb_item_add<NG, K, T>(Gb, ref_off(rl) + int(pext_mask<NG>(H, ref_mask(rl))), GLb,
-                            pext_mask<NG>(mb & ~ref_mask(rl), mb), c, act);
-      gb_item_add<NG, K, T>(Gb, ref_off(rr) + int(pext_mask<NG>(H, ref_mask(rr))), GRb,
-                            pext_mask<NG>(mb & ~ref_mask(rr), mb), c, act);
+      gb_item_add<NG, K - sp - 1, T>(Gb, ref_off(rl) + int(pext_mask<NG>(H, ref_mask(rl))), GLb,
+                                     pext_mask<NG>(mb & ~ref_mask(rl), mb), unsigned(gl), act);
+      gb_item_add<NG, sp + 1, T>(Gb, ref_off(rr) + int(pext_mask<NG>(H, ref_mask(rr))), GRb,
+                                 pext_mask<NG>(mb & ~ref_mask(rr), mb), unsigned(gl), act);
       add_mask<NG, T>(pb, ref_mask(rl), PLb);
       add_mask<NG, T>(pb, ref_mask(rr), PRb);
-    }
+    });
     if constexpr (K >= 3) {
       const uint16_t* t4 = o4_table<NG, K>() + bl * n4 * 3;
-#pragma unroll 1
-      for (int s = 0; s < n4; ++s) {
-        const uint16_t r0 = t4[3 * s], r1 = t4[3 * s + 1], r2 = t4[3 * s + 2];
+      static_for<n4>([&](auto sc) {
+        constexpr int sp = decltype(sc)::value;
+        constexpr int a = o4_cut<K>(sp, 0), b = o4_cut<K>(sp, 1);   // blocks t[:a], t[a:b], t[b:]
+        const uint16_t r0 = t4[3 * sp], r1 = t4[3 * sp + 1], r2 = t4[3 * sp + 2];
         const V4<T> GL = load_block<NG, T>(Gs, r0, H), GM = load_block<NG, T>(Gs, r1, H),
                     GR = load_block<NG, T>(Gs, r2, H);
         V4<T> GLb, GMb, GRb;
 #pragma unroll
         for (int k = 0; k < 4; ++k) GLb.c[k] = GMb.c[k] = GRb.c[k] = {T(0), T(0)};
         adj_o4(GL, GM, GR, (ref_neg(r0) ^ ref_neg(r1) ^ ref_neg(r2)) ? T(-1) : T(1), accb, GLb, GMb, GRb);
-        gb_item_add<NG, K, T>(Gb, ref_off(r0) + int(pext_mask<NG>(H, ref_mask(r0))), GLb,
-                              pext_mask<NG>(mb & ~ref_mask(r0), mb), c, act);
-        gb_item_add<NG, K, T>(Gb, ref_off(r1) + int(pext_mask<NG>(H, ref_mask(r1))), GMb,
-                              pext_mask<NG>(mb & ~ref_mask(r1), mb), c, act);
-        gb_item_add<NG, K, T>(Gb, ref_off(r2) + int(pext_mask<NG>(H, ref_mask(r2))), GRb,
-                              pext_mask<NG>(mb & ~ref_mask(r2), mb), c, act);
-      }
+        gb_item_add<NG, K - a, T>(Gb, ref_off(r0) + int(pext_mask<NG>(H, ref_mask(r0))), GLb,
+                                  pext_mask<NG>(mb & ~ref_mask(r0), mb), unsigned(gl), act);
+        gb_item_add<NG, K - (b - a), T>(Gb, ref_off(r1) + int(pext_mask<NG>(H, ref_mask(r1))), GMb,
+                                        pext_mask<NG>(mb & ~ref_mask(r1), mb), unsigned(gl), act);
+        gb_item_add<NG, b, T>(Gb, ref_off(r2) + int(pext_mask<NG>(H, ref_mask(r2))), GRb,
+                              pext_mask<NG>(mb & ~ref_mask(r2), mb), unsigned(gl), act);
+      });
     }
   }
 }

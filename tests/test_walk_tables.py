@@ -152,3 +152,32 @@ def test_full_block_adjoint_slots():
             # the second completion is the reversal of the first
             assert perms[fsig[p]] == tuple(reversed(perms[fsig[seen[b]]]))
     assert len(seen) == 12
+
+
+def test_vertex_split_lengths_follow_their_position():
+    """The reversed gluon levels of the adjoint kernel take the length of
+    every sub-block of a split as a compile-time constant: the s-th
+    three-vertex split of a K-gluon block holds blocks of s + 1 and K - s - 1
+    gluons (kO3), the s-th four-vertex split blocks of a, b - a and K - b
+    gluons for the s-th pair a < b in generator order (kO4)."""
+    src = gen_tables.render()
+    pop = lambda r: bin((r >> 9) & 15).count("1")
+    for ng in (2, 3, 4):
+        for K in range(2, ng + 1):
+            o3 = _array(src, f"kO3_{ng}_{K}")
+            n3 = K - 1
+            assert len(o3) % (2 * n3) == 0
+            for blk in range(len(o3) // (2 * n3)):
+                for s in range(n3):
+                    rl, rr = o3[blk * 2 * n3 + 2 * s], o3[blk * 2 * n3 + 2 * s + 1]
+                    assert (pop(rl), pop(rr)) == (s + 1, K - s - 1)
+            if K < 3:
+                continue
+            cuts = [(a, b) for a in range(1, K - 1) for b in range(a + 1, K)]
+            o4 = _array(src, f"kO4_{ng}_{K}")
+            n4 = len(cuts)
+            assert n4 == (K - 1) * (K - 2) // 2 and len(o4) % (3 * n4) == 0
+            for blk in range(len(o4) // (3 * n4)):
+                for s, (a, b) in enumerate(cuts):
+                    r = o4[blk * 3 * n4 + 3 * s:blk * 3 * n4 + 3 * s + 3]
+                    assert [pop(x) for x in r] == [a, b - a, K - b]
