@@ -409,13 +409,11 @@ __device__ __forceinline__ void adj_walk(int parent, S4<T> (&R)[NG], S4<T> (&Rb)
   for (int k = 0; k <= NG - LV; ++k) {
     const int path = first + k;
     const uint8_t msk = PT::template mask<LV>(path);
-    {
-      S4<T> X = apply(make_slash(adj_block<NG, T>(cx, PT::template blk<LV>(path, 0))), R[LV - 1]);
+    S4<T> Xd = apply(make_slash(adj_block<NG, T>(cx, PT::template blk<LV>(path, 0))), R[LV - 1]);
 #pragma unroll
-      for (int m = 1; m < LV; ++m)
-        apply_acc(make_slash(adj_block<NG, T>(cx, PT::template blk<LV>(path, m))), R[LV - 1 - m], X);
-      R[LV] = quark_prop_f(cx.Ptab[msk], cx.m, cx.qf[msk], X);
-    }
+    for (int m = 1; m < LV; ++m)
+      apply_acc(make_slash(adj_block<NG, T>(cx, PT::template blk<LV>(path, m))), R[LV - 1 - m], Xd);
+    R[LV] = quark_prop_f(cx.Ptab[msk], cx.m, cx.qf[msk], Xd);
     if constexpr (ADJ) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) Rb[LV].c[c] = {T(0), T(0)};
@@ -461,11 +459,19 @@ __device__ __forceinline__ void adj_walk(int parent, S4<T> (&R)[NG], S4<T> (&Rb)
       }
     }
     if constexpr (ADJ) {
-      // node adjoint: R[LV] = f (P-slash + m) X, X = sum_m G_m-slash R[LV-1-m]
-      S4<T> X = apply(make_slash(adj_block<NG, T>(cx, PT::template blk<LV>(path, 0))), R[LV - 1]);
+      // node adjoint: R[LV] = f (P-slash + m) X, X = sum_m G_m-slash R[LV-1-m];
+      // in FP32 the node above the completions keeps its X over its one
+      // completion; the higher nodes and FP64 recompute it (more live values:
+      // spills)
+      S4<T> X;
+      if constexpr (LV == NG - 1 && std::is_same<T, float>::value) {
+        X = Xd;
+      } else {
+        X = apply(make_slash(adj_block<NG, T>(cx, PT::template blk<LV>(path, 0))), R[LV - 1]);
 #pragma unroll
-      for (int m = 1; m < LV; ++m)
-        apply_acc(make_slash(adj_block<NG, T>(cx, PT::template blk<LV>(path, m))), R[LV - 1 - m], X);
+        for (int m = 1; m < LV; ++m)
+          apply_acc(make_slash(adj_block<NG, T>(cx, PT::template blk<LV>(path, m))), R[LV - 1 - m], X);
+      }
       S4<T> Xb;
       R4<T> Ptb = {{T(0), T(0), T(0), T(0)}};
       T mb = T(0);
