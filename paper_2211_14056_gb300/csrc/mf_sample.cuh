@@ -327,10 +327,13 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
   // f(xi) = sum_{i=0,1} (sqrt(m^2 + xi^2 E_i^2) - m) + xi E_rest - (sqrt(s) - 2m), with
   // sqrt(m^2 + u^2) - m = u^2 / (sqrt(m^2 + u^2) + m): no cancellation near
   // threshold, so Newton reaches full relative precision in xi there too.
-  // Stop after a step |dxi| <= 1e-8 xi: f is convex with xi f''/f' =
+  // Stop after a step |dxi| <= tol xi: f is convex with xi f''/f' =
   // sum m^2 E^2 xi / r^3 / (sum xi E^2 / r + E_rest) <= 1 (m <= r), so a
   // Newton step of relative size d from that close leaves a relative error
-  // below d^2 / 2 <= 5e-17; 50 steps at most.  With dual numbers the
+  // below d^2 / 2: tol = 1e-8 (5e-17) for FP64 kinematics; 1e-6 (5e-13,
+  // far below the FP32 momenta's rounding) for FP32 kinematics, where the
+  // first FP64 step from the converged FP32 start (relative size ~1e-7)
+  // already meets it; 50 steps at most.  With dual numbers the
   // converged xi is refined by one more step, which carries the
   // implicit-function derivative d xi = -(df/dtheta) / f'.
   const D m2 = mtd * mtd;
@@ -369,6 +372,7 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
   {
     const double mv = value_of(mtd), m2v = value_of(m2), e0 = value_of(E[0]), e1 = value_of(E[1]);
     const double er = value_of(Erest), exv = value_of(excess);
+    constexpr double tol = sizeof(value_of(K(0))) < sizeof(double) ? 1e-6 : 1e-8;
     double xi = xi0;
 #pragma unroll 1
     for (int it = 0; it < 50; ++it) {
@@ -382,7 +386,7 @@ __device__ __forceinline__ void sample_event(const SampleParams& sp, const doubl
       const double fp = fma(xi * fma(e0 * e0, r1, e1 * e1 * r0), ab * iden, er);
       const double dxi = f / fp;
       xi -= dxi;
-      if (fabs(dxi) <= 1e-8 * xi) { converged = 1; break; }
+      if (fabs(dxi) <= tol * xi) { converged = 1; break; }
     }
     xi0 = xi;
   }
