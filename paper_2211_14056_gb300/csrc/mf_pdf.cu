@@ -38,18 +38,26 @@ __global__ void __launch_bounds__(256) k_pdf_eval(PdfView pv, int flavour, int64
     fl = reinterpret_cast<const K*>(smem_raw);
   }
   // kPts points per thread per pass, their loads issued together (the
-  // points are read once: streaming loads and stores), so that each thread
-  // has several HBM requests in flight
+  // points are read once: streaming loads and stores), and the next pass's
+  // loads issued before this pass's arithmetic, so that each thread keeps
+  // HBM requests in flight while it computes
   constexpr int kPts = 4;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t e0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e0 < n; e0 += kPts * stride) {
-    double xv[kPts], qv[kPts];
+  const int64_t step = kPts * stride;
+  double xv[kPts], qv[kPts];
+  auto load = [&](int64_t b, double (&xs)[kPts], double (&qs)[kPts]) {
 #pragma unroll
     for (int u = 0; u < kPts; ++u) {
-      const int64_t e = e0 + u * stride;
-      xv[u] = e < n ? __ldcs(x + e) : 1.0;
-      qv[u] = e < n ? __ldcs(q2 + e) : 1.0;
+      const int64_t e = b + u * stride;
+      xs[u] = e < n ? __ldcs(x + e) : 1.0;
+      qs[u] = e < n ? __ldcs(q2 + e) : 1.0;
     }
+  };
+  int64_t e0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  load(e0, xv, qv);
+  for (; e0 < n; e0 += step) {
+    double xn[kPts], qn[kPts];
+    load(e0 + step, xn, qn);
 #pragma unroll
     for (int u = 0; u < kPts; ++u) {
       const int64_t e = e0 + u * stride;
@@ -65,6 +73,11 @@ __global__ void __launch_bounds__(256) k_pdf_eval(PdfView pv, int flavour, int64
         r = pdf_xfx_slice(pv, fl, c);
       }
       if (e < n) __stcs(out + e, r);
+    }
+#pragma unroll
+    for (int u = 0; u < kPts; ++u) {
+      xv[u] = xn[u];
+      qv[u] = qn[u];
     }
   }
 }
