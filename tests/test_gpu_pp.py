@@ -131,6 +131,31 @@ def test_pdf_eval_matches_oracle(mf, pdf, n):
             assert np.median(err) < (1e-14 if prec == mf.MF_FP64 else 1e-6)
 
 
+def test_pdf_eval_over_several_passes_matches_oracle(mf, pdf):
+    """A launch whose threads take several passes over the points (the
+    persistent grid holds about half a million points per pass) with a ragged
+    last pass: every point against the oracle, in FP64 and FP32, for the
+    gluon and a quark flavour."""
+    from paper_2211_14056_gb300 import pdfgrid
+    og, d = _oracle_pdf()
+    n = 1_500_007
+    x, q2 = _points(n, seed=11)
+    xt = torch.tensor(x, dtype=torch.float64, device="cuda")
+    qt = torch.tensor(q2, dtype=torch.float64, device="cuda")
+    for f in (pdfgrid.GLUON, 1):
+        ref = og.xfx(f, x, q2)
+        for prec, bar in ((mf.MF_FP64, 1e-12), (mf.MF_FP32, 5e-5)):
+            out = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+            pdf.eval(f, n, xt, qt, out, precision=prec)
+            torch.cuda.synchronize()
+            got = out.cpu().numpy()
+            assert np.all(np.isfinite(got))
+            floor = 1e-6 if prec == mf.MF_FP64 else 1e-3
+            scale = np.maximum(np.abs(ref), floor * np.max(np.abs(d["xf"][f])))
+            err = np.abs(got - ref) / scale
+            assert err.max() < bar, (f, prec, err.max())
+
+
 def test_pdf_eval_arguments(mf, pdf):
     x = torch.ones(4, dtype=torch.float64, device="cuda")
     with pytest.raises(mf.MFError):
