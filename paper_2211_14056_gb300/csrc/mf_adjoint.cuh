@@ -495,6 +495,72 @@ __device__ __forceinline__ void adj_walk(int parent, S4<T> (&R)[NG], S4<T> (&Rb)
 }
 
 
+// The forward pass (amplitudes J only) for four gluons as the |M|^2 kernel
+// computes it: the two-gluon suffix currents once per event by the group
+// (shared_suffixes, into R2), the three-gluon currents shared by the lane
+// pairs that differ in the missing gluon's helicity (as quark_walk_paired4),
+// both completions of a pair in one loop body.  J in the adjoint's layout.
+template <typename T>
+__device__ __forceinline__ void adj_forward_paired4(const S4<T>& v, const AdjCtx<T>& cx, const cplx<T>* R2,
+                                                    unsigned H, unsigned ltb) {
+  using PT = Paths<4>;
+  constexpr int NR2 = WarpMem<4, T>::NR2;
+  auto load_r2 = [&](int p2) {
+    const uint8_t m2 = PT::template mask<2>(p2);
+    const int idx = p2 * 8 + int((unsigned(cx.pk >> (4 * m2)) & 15u) | (ltb << 2));
+    S4<T> r;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.c[k] = R2[k * NR2 + idx];
+    return r;
+  };
+#pragma unroll 1
+  for (int c = 0; c < 4; ++c) {
+    S4<T> R[4];
+    R[0] = v;
+    const uint8_t m1 = PT::template mask<1>(c);
+    R[1] = quark_prop_f(cx.Ptab[m1], cx.m, cx.qf[m1],
+                        apply(make_slash(adj_block<4, T>(cx, PT::template blk<1>(c, 0))), v));
+#pragma unroll 1
+    for (int gi = 0; gi < 3; ++gi) {
+      const int g = kL3Miss4[c * 3 + gi];
+      const unsigned bit = (H >> g) & 1u;
+      const int mine = kL3Pair4[(c * 3 + gi) * 2 + bit], other = kL3Pair4[(c * 3 + gi) * 2 + (bit ^ 1u)];
+      R[2] = load_r2(mine >> 1);
+      S4<T> X = apply(make_slash(adj_block<4, T>(cx, PT::template blk<3>(mine, 0))), R[2]);
+      apply_acc(make_slash(adj_block<4, T>(cx, PT::template blk<3>(mine, 1))), R[1], X);
+      apply_acc(make_slash(adj_block<4, T>(cx, PT::template blk<3>(mine, 2))), v, X);
+      const uint8_t m3 = PT::template mask<3>(mine);
+      R[3] = quark_prop_f(cx.Ptab[m3], cx.m, cx.qf[m3], X);
+      S4<T> Ro;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        Ro.c[k].r = shfl_xor_any(0xffffffffu, R[3].c[k].r, 1 << g);
+        Ro.c[k].i = shfl_xor_any(0xffffffffu, R[3].c[k].i, 1 << g);
+      }
+      int path = mine;
+#pragma unroll 1
+      for (int w = 0; w < 2; ++w) {
+        S4<T> W = apply(make_slash(adj_block<4, T>(cx, PT::final_blk(path, 0))), R[3]);
+#pragma unroll
+        for (int m = 1; m < 4; ++m)
+          apply_acc(make_slash(adj_block<4, T>(cx, PT::final_blk(path, m))), R[3 - m], W);
+        const int sig = PT::final_sigma(path);
+        T* j = cx.J + (sig * 2) * 32;
+        const cplx<T> j0 = rowdot(cx.ub0, W), j1 = rowdot(cx.ub1, W);
+        j[0] = j0.r;
+        j[kAdjPlane<4>] = j0.i;
+        j[32] = j1.r;
+        j[32 + kAdjPlane<4>] = j1.i;
+        if (w == 0) {
+          R[2] = load_r2(other >> 1);
+          R[3] = Ro;
+          path = other;
+        }
+      }
+    }
+  }
+}
+
 // Add an item's adjoint of one of its sub-blocks (R = the number of the
 // block's gluons outside the sub-block, a compile-time constant at every
 // split).  The items of a round sit on consecutive lanes with the helicity
@@ -648,7 +714,12 @@ __device__ __forceinline__ T adj_group_me2(const T (&p)[NG + 2][4], unsigned cha
   cplx<T>* Gb = reinterpret_cast<cplx<T>*>(wm + AM::gb_off) + group * 4 * kGbStride<NG>;
   const MaskTab<NG, T> mtab(wm + AM::pt_off + group * MaskTab<NG, T>::bytes);
   T* Jw = reinterpret_cast<T*>(wm + AM::j_off) + lane;
-  for (int i = gl; i < 4 * kGbStride<NG>; i += L) Gb[i] = {T(0), T(0)};
+  // four gluons: the sub-current adjoint store holds the two-gluon suffix
+  // currents during the forward pass and is cleared after it
+  constexpr bool kFwdPaired = NG == 4 && kShareSuffixes<T>;
+  static_assert(!kFwdPaired || WarpMem<NG, T>::NR2 <= kGbStride<NG>, "R2 fits the adjoint store");
+  if constexpr (!kFwdPaired)
+    for (int i = gl; i < 4 * kGbStride<NG>; i += L) Gb[i] = {T(0), T(0)};
   AdjAcc<NG, T> pb;
 #pragma unroll
   for (int r = 0; r < NR; ++r) pb.r[r] = T(0);
@@ -684,7 +755,15 @@ __device__ __forceinline__ T adj_group_me2(const T (&p)[NG + 2][4], unsigned cha
   cx.gl = unsigned(gl);
   S4<T> R[NG], Rb[NG];
   R[0] = v_out(qtb, mt, ltb);
-  adj_walk<NG, 1, false, T>(0, R, Rb, cx, pb);
+  if constexpr (kFwdPaired) {
+    shared_suffixes<NG, T>(Gs, mtab, qtb, mt, Gb, gl);
+    __syncwarp();
+    adj_forward_paired4<T>(R[0], cx, Gb, H, unsigned((gl >> NG) & 1));
+    __syncwarp();   // every lane has read the suffix currents
+    for (int i = gl; i < 4 * kGbStride<NG>; i += L) Gb[i] = {T(0), T(0)};
+  } else {
+    adj_walk<NG, 1, false, T>(0, R, Rb, cx, pb);
+  }
   // colour form and its adjoint Jb = 2 norm C J (in place), per top helicity
   const int* num = colour_num_dev<NG>();
   const T js = T(2) * norm;     // norm carries the colour matrix's 1/D
