@@ -181,3 +181,23 @@ def test_vertex_split_lengths_follow_their_position():
                 for s, (a, b) in enumerate(cuts):
                     r = o4[blk * 3 * n4 + 3 * s:blk * 3 * n4 + 3 * s + 3]
                     assert [pop(x) for x in r] == [a, b - a, K - b]
+
+
+def test_full_blocks_are_stored_last():
+    """The adjoint kernel's sub-current adjoint store holds only the blocks of
+    fewer than four gluons (their adjoints land at the blocks' own offsets),
+    sized as NSTORE minus the four-gluon blocks' entries: that needs every
+    shorter block to lie below the first four-gluon block's offset."""
+    src = gen_tables.render()
+    first = _first(src, 4)
+    off, msk = _array(src, "kBlkOff4"), _array(src, "kBlkMask4")
+    nstore = int(re.search(r"struct TTNG<4> \{.*?NSTORE = (\d+);", src, re.S).group(1))
+    nfull = first[5] - first[4]
+    limit = nstore - (nfull << 4)
+    for b in range(len(off)):
+        length = bin(msk[b]).count("1")
+        if length < 4:
+            assert off[b] + (1 << length) <= limit, b
+        else:
+            assert off[b] >= limit, b
+    assert limit == 128
